@@ -302,6 +302,7 @@ static double link_q(const lattice *L, double alpha_s, double c1x,
   if (gn < 1e-12) return 0.5;
   double cl = sqrt((double)(L->c[i][0] * L->c[i][0] + L->c[i][1] * L->c[i][1] +
                             L->c[i][2] * L->c[i][2]));
+  if (cl == 0.0) return 0.5; /* the rest population has no link */
   double nd = (gc1[0] * L->c[i][0] + gc1[1] * L->c[i][1] + gc1[2] * L->c[i][2]) /
               (gn * cl);
   if (nd <= 1e-6) return 0.5;

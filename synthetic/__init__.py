@@ -156,6 +156,17 @@ def drop_c2(shape, centre, radius, alpha=1.0, solid_sd=None, solid_width=1.0):
     return c2
 
 
+def cap_c2(shape, wall: float, radius: float, theta_deg: float, alpha=1.0,
+           solid_sd=None, solid_width=1.0, centre_x=None):
+    """Initial liquid field: a circular cap (2D) or spherical cap (3D) of the given
+    radius meeting the plane `wall` (along the last axis) at theta_deg."""
+    centre = [(s - 1) / 2.0 for s in shape]
+    if centre_x is not None:
+        centre[0] = centre_x
+    centre[-1] = wall - radius * math.cos(math.radians(theta_deg))
+    return drop_c2(shape, centre, radius, alpha, solid_sd, solid_width)
+
+
 def layer_c2(shape, axis, lo, hi, alpha=1.0, solid_sd=None, solid_width=1.0):
     """Initial liquid field: a layer lo <= coordinate < hi along `axis`."""
     X = _coords(shape)
