@@ -1,0 +1,293 @@
+#!/usr/bin/env python3
+"""Benchmark: D3Q19 N+1-phase lattice Boltzmann step of the Diffuse Solid Method.
+
+Workload: the plain FP32 D3Q19 pillar-slab lattice, 256x256x192 = 12,582,912
+nodes (square pillars 10 wide, 30 high, pitch 32 on an 8-node base, liquid slab
+z in [38, 98), contact angle drawn in [90, 150] degrees from seed 0), synthetic.
+One "step" = one full lattice Boltzmann time step through libdsm: the moments
+pass plus the fused pass over every node.  Inputs (3.9 GB of populations) are
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded slice of the same workload instead.
+
+Multi-GPU (torchrun, N ranks): every rank runs its own independent lattice
+(replicas; the method has no exchange between independent problems); value =
+all ranks' node updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 N+1-phase LBM MLUPS & HBM-roofline %; sweep solves/s with p50/p99 latency"
+B_MIN_F32_D3Q19 = 308  # algorithmic bytes per lattice update: f, g read + write, C1 read
+SHAPE = (256, 256, 192)
+WORKLOAD = "D3Q19 FP32 pillar-slab 256x256x192 (12.58M nodes), plain method, stage-2 LB step"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 9 or not parts[1].split()[0].isdigit():
+                    continue
+                sm.append(float(parts[1].split()[0]))
+                mx = float(parts[2].split()[0])
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_case():
+    import synthetic as S
+    return S.pillar_slab_3d(*SHAPE)
+
+
+def cpu_baseline(max_seconds=15.0):
+    """The FP64 oracle, as it stands, on a 64x64x48 slice of the workload."""
+    import numpy as np
+    import oracle as O
+    import synthetic as S
+    shape = (64, 64, 48)
+    case = S.pillar_slab_3d(*shape, pitch=32, width=10, height=12, base=4, liquid=(16, 32))
+    k, _ = O.kappa_from_angle(case.theta_deg, case.g23, case.g12)
+    p = O.make_params(O.D3Q19, shape, k, alpha_s=case.alpha_s)
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+    f, g = O.lb_init(p, 2, c1, case.c2)
+    O.lb_run(p, 2, c1, f, g, 1)  # warm
+    n = int(np.prod(shape))
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f, g = O.lb_run(p, 2, c1, f, g, 2)
+        steps += 2
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"D3Q19 FP64 oracle, 64x64x48 pillar-slab slice, {steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step = max(5.0, 60.0 / max(args.steps + args.warmup, 1))
+    cb = None
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(max_seconds=min(per_step, 20.0))
+        if i >= args.warmup:
+            times.append(r["value"])
+            cb = r
+    value = sum(times) / len(times)
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "D3Q19 FP64 CPU oracle on a 64x64x48 slice of the "
+                                  "pillar-slab workload", "parallelism": "host cores"},
+           "cpu_baseline": dict(cb, value=value),
+           "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2504_19941_gb300 as P
+    from paper_2504_19941_gb300 import _lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    case = make_case()
+    params = P.make_params("D3Q19", SHAPE, "f32", theta_deg=case.theta_deg, g12=case.g12,
+                           g23=case.g23, alpha_s=case.alpha_s)
+    lat = P.Lattice(params, device=dev)
+    sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
+    c2_h = torch.as_tensor(case.c2, dtype=torch.float32).pin_memory()
+    sd_d = sd_h.to(dev, non_blocking=True)
+    c2_d = c2_h.to(dev, non_blocking=True)
+    lat.set_solid_distance(sd_d)
+    lat.set_fluid(c2_d)
+    n = lat.n
+    h = lat.h
+
+    def one_step():
+        _lib.dsm_step_moments(h)
+        _lib.dsm_step_collide(h)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        for k in range(args.steps):
+            _lib.dsm_step_moments(h)
+            ev[k][0].record(stream)
+            _lib.dsm_step_collide(h)
+            ev[k][1].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_total = e0.elapsed_time(e1) / 1e3
+    t_k2 = sum(a.elapsed_time(b) for a, b in ev) / len(ev) / 1e3
+    obs = lat.observables()
+    assert obs["nonfinite"] == 0, "non-finite state after the timed steps"
+    t_max = t_total
+    if dist:
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * args.steps / t_max / 1e6
+
+    # end to end through the public API with host buffers: H2D of the geometry
+    # and the liquid field, set_solid, set_fluid, K steps, D2H of the liquid field
+    out_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    lat2 = lat
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    sd_d.copy_(sd_h, non_blocking=True)
+    c2_d.copy_(c2_h, non_blocking=True)
+    lat2.set_solid_distance(sd_d)
+    lat2.set_fluid(c2_d)
+    lat2.step(args.steps)
+    f_out = lat2.field("C2")
+    out_h.copy_(f_out, non_blocking=True)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = s0.elapsed_time(s1) / 1e3
+    if dist:
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * n * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 2 * 4 * n / args.steps, "d2h_bytes_per_step": 4 * n / args.steps}
+
+    peak, peak_kind = _peaks()
+    achieved = B_MIN_F32_D3Q19 * n / t_k2 / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            traffic = json.load(f).get("node_kernel_d3q19_f32_bytes_per_launch")
+
+    if rank == 0:
+        cb = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
+        out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "lattice": "D3Q19", "nodes": n,
+                          "global_batch": world, "parallelism": f"replicas x{world}",
+                          "l2": "inputs (3.9 GB populations) larger than L2; no flush"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic,
+                            "kernel": "node_kernel<D3Q19,f32,stage2,step>",
+                            "bytes_per_lu": B_MIN_F32_D3Q19, "peak_source": peak_kind,
+                            "k2_ms": t_k2 * 1e3},
+               "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
+               "cpu_baseline": cb,
+               "observables": {"mass_c2": obs["mass_c2"], "max_u": obs["max_u"]}}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="dsm", choices=["dsm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

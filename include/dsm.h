@@ -1,0 +1,228 @@
+/*
+ * dsm.h -- C ABI of the GB300 Diffuse Solid Method library (libdsm.so).
+ *
+ * The library implements, on one NVIDIA GB300 (sm_103a), the lattice
+ * Boltzmann time step and the free-energy/gradient kernel of the Diffuse Solid
+ * Method (Oktasendra, Rennick, Avis, Panter, Kusumaatmaja, "The Diffuse Solid
+ * Method for Wetting and Multiphase Fluid Simulations in Complex Geometries"):
+ * N = 2 fluids (liquid C2, gas C3) plus a solid component C1 held to a
+ * prescribed geometry.
+ *
+ * Conventions (all entry points)
+ *   - Node index n = x + nx*(y + ny*z); every axis periodic; nz = 1 for D2Q9.
+ *   - "real" is double for DSM_F64 lattices and float for every other precision.
+ *   - Device pointers (d_*) must point to memory of the current CUDA device and
+ *     stay valid for the call (and, for the workspace, until dsm_destroy).
+ *     The library NEVER allocates or frees device memory: the caller owns every
+ *     buffer (workspace, inputs, outputs).  Host pointers are borrowed for the
+ *     duration of the call only.
+ *   - Work is enqueued on the caller's stream (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  Calls that return host values
+ *     (dsm_get_observables) synchronise that stream.
+ *   - Errors are returned as dsm_status; nothing throws across the ABI.
+ *     Device-detected errors (non-finite populations, a persistent-kernel
+ *     barrier that timed out) are latched in the workspace and reported by the
+ *     next synchronising call; the handle then stays in DSM_E_STATE until
+ *     dsm_set_populations or dsm_set_fluid resets it.
+ *   - One handle belongs to one stream; calls on different handles are
+ *     independent.  The library is not thread-safe for one handle.
+ */
+#ifndef DSM_H
+#define DSM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSM_OK = 0,
+  DSM_E_INVAL = 1,       /* bad argument (sizes, parameters, null pointer) */
+  DSM_E_WORKSPACE = 2,   /* workspace too small or misaligned */
+  DSM_E_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  DSM_E_NONFINITE = 4,   /* a NaN/Inf appeared in the populations */
+  DSM_E_TIMEOUT = 5,     /* a bounded device wait ran out */
+  DSM_E_STATE = 6,       /* call out of order, or handle latched in error */
+  DSM_E_UNSUPPORTED = 7  /* valid request this build does not implement */
+} dsm_status;
+
+typedef enum { DSM_D2Q9 = 0, DSM_D3Q19 = 1 } dsm_lattice_kind;
+
+typedef enum {
+  DSM_F64 = 0,        /* FP64 populations and arithmetic */
+  DSM_F32 = 1,        /* FP32 populations and arithmetic */
+  DSM_BF16_STORE = 2, /* BF16 storage of f_i - w_i and g_i (i != 0), FP32 g_0, FP32 math */
+  DSM_F16_STORE = 3   /* FP16 storage, otherwise as DSM_BF16_STORE */
+} dsm_precision;
+
+/* Problem statement (Sec. II of the paper).  Tensions follow Sec. II.A,
+ * Eq. [frozen:kappa]: kappa_1..3 from gamma_12, gamma_13, gamma_23 and the
+ * interface width alpha.  tension_mode = 1 gives the contact angle instead:
+ * gamma_13 = gamma_12 + gamma_23 cos(theta) (Young, Supp. B Eq. [eq:CA]), so
+ * cos(theta) = (kappa_3 - kappa_2)/(kappa_2 + kappa_3) (Eq. [eqn:st_ca]).
+ * kappa_2 <= 0 or kappa_3 <= 0 is rejected with DSM_E_INVAL. */
+typedef struct dsm_params {
+  int lattice;             /* dsm_lattice_kind */
+  int nx, ny, nz;          /* lattice size; nz must be 1 for D2Q9; each >= 1 */
+  int precision;           /* dsm_precision */
+  double alpha;            /* fluid interface width (the paper uses 1) */
+  double alpha_s;          /* tanh width given to an analytic solid; 0 => alpha */
+  int tension_mode;        /* 0: (g12, g13, g23)  1: (theta_deg, g23, g12) */
+  double g12, g13, g23, theta_deg;
+  double rho2, rho3;       /* liquid / gas density, Sec. II.B density map */
+  double tau2, tau3;       /* liquid / gas BGK relaxation time */
+  double tau_g;            /* Cahn-Hilliard relaxation time; M = (tau_g - 1/2)/3 */
+  double body_force[3];    /* body force per unit liquid concentration */
+  double beta, omega;      /* solid confinement and range penalty, LB stage 1 */
+} dsm_params;
+
+typedef struct dsm_observables {
+  double mass_c2;   /* sum over nodes of C2 (current time level) */
+  double mass_c1;   /* sum over nodes of C1 */
+  double kinetic;   /* sum over fluid nodes of rho |u|^2 / 2 */
+  double max_u;     /* max over nodes of |u| */
+  long long step;   /* steps taken since dsm_set_fluid */
+  int nonfinite;    /* 1 if a population is NaN or Inf */
+} dsm_observables;
+
+typedef struct dsm_lattice dsm_lattice; /* opaque handle (host memory) */
+
+/* Field selectors of dsm_get_field: macroscopic fields at the current time
+ * level (the streaming and moment stages of the next step, without collision). */
+enum {
+  DSM_FIELD_C1 = 0, DSM_FIELD_C2 = 1, DSM_FIELD_C3 = 2, DSM_FIELD_MU = 3,
+  DSM_FIELD_UX = 4, DSM_FIELD_UY = 5, DSM_FIELD_UZ = 6,
+  DSM_FIELD_PT = 7,   /* pt = P / c_s^2 */
+  DSM_FIELD_RHO = 8, DSM_FIELD_TAU = 9
+};
+
+/* Status text (static storage; never NULL). */
+const char *dsm_status_string(dsm_status s);
+
+/* Velocity set and weights of a lattice as this library orders them:
+ * c_out[3*i + a], w_out[i] for i < *q (q_out receives 9 or 19).  D2Q9 follows
+ * the table printed in Sec. II.B; D3Q19 is the textbook set (the paper gives
+ * only D2Q9). */
+dsm_status dsm_lattice_table(int lattice, int *q_out, int *c_out, double *w_out);
+
+/* kappa_1, kappa_2, kappa_3 of a parameter set (Sec. II.A Eq. [frozen:kappa]). */
+dsm_status dsm_kappa(const dsm_params *p, double kappa_out[3]);
+
+/* Workspace bytes a lattice of these parameters needs (populations, two
+ * buffers each; C1; C; solid mask; reduction scratch). */
+dsm_status dsm_workspace_bytes(const dsm_params *p, size_t *bytes);
+
+/* Create a handle over a caller-owned device workspace (>= the size above,
+ * 256-byte aligned).  No device allocation happens here or later.
+ * Returns DSM_E_INVAL for bad sizes or parameters, DSM_E_WORKSPACE for a short
+ * or misaligned workspace. */
+dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes,
+                      void *cuda_stream, dsm_lattice **out);
+
+/* Set the solid.  kind 0: d_field is a signed distance to the solid region S
+ * (positive inside), turned into C1 = 1/2 + tanh(d / (2 alpha_s))/2, the planar
+ * profile of Sec. II.A Eq. [frozen:interface_profile].  kind 1: d_field is C1.
+ * d_field holds nx*ny*nz reals. */
+dsm_status dsm_set_solid(dsm_lattice *h, const void *d_field, int kind);
+
+/* LB stage 1 (Sec. II.B, Eq. [Free Energy1]): relax C1 for `steps` steps with
+ * the confining potential of strength beta on the solid region d_mask (bytes,
+ * 1 inside S) and the range penalty omega; rho = 1, tau = tau_g = 1.  Starts
+ * from the C1 last set, writes the relaxed C1 back.  Uses the population
+ * buffers, so call it before dsm_set_fluid. */
+dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int steps,
+                           double beta, double omega);
+
+/* Set the liquid field C2 (nx*ny*nz reals) and initialise the populations at
+ * rest: f_i = w_i, g_i = g_eq_i(C2, mu(C2), u = 0).  Resets the step counter
+ * and any latched error. */
+dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2);
+
+/* Advance nsteps LB steps (stage 2, Sec. II.B) asynchronously on the stream.
+ * Each step: moments pass (C = sum_i g_i after streaming) then the fused pass
+ * (mu, forces, pull-streaming with interpolated bounce-back, BGK collision of
+ * f and g). */
+dsm_status dsm_step(dsm_lattice *h, long long nsteps);
+
+/* The two passes of dsm_step, for callers that interleave their own work or
+ * time the passes: dsm_step_moments computes C of the current state (the
+ * moments pass); dsm_step_collide then runs the fused pass and advances the
+ * state by one step.  dsm_step(h, 1) equals the two calls in this order;
+ * dsm_step_collide without a preceding dsm_step_moments on the same state is
+ * DSM_E_STATE. */
+dsm_status dsm_step_moments(dsm_lattice *h);
+dsm_status dsm_step_collide(dsm_lattice *h);
+
+/* Observables of the current state; synchronises the stream.  Returns
+ * DSM_E_NONFINITE (and sets out->nonfinite) when the state holds a NaN/Inf. */
+dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out);
+
+/* One macroscopic field (DSM_FIELD_*) into d_dst (nx*ny*nz reals). */
+dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst);
+
+/* Post-collision populations of the current state as reals, q-major
+ * (d_f[i*N + n], d_g[i*N + n], N = nx*ny*nz, q-order of dsm_lattice_table). */
+dsm_status dsm_get_populations(dsm_lattice *h, void *d_f, void *d_g);
+
+/* Replace the state by the given post-collision populations (reals, layout as
+ * above); 16-bit precisions encode them.  Clears a latched error. */
+dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g);
+
+/* Free-energy twin (Sec. II.A, Eqs. [frozen:total_energy], [frozen:bulk_energy],
+ * [frozen:interface_energy], [frozen:pressure_const] / [frozen:volume_const],
+ * [frozen:poly-quadratic]; Sec. III.B Eq. [frozen:gravitational energy]).
+ * Stateless.  FP32 fields, FP64 energy.
+ *   E = sum_x [ sum_n kappa_n/2 C_n^2 (1 - C_n)^2
+ *             + sum_n alpha^2 kappa_n / (2 c_s^2) sum_i w_i (C_n(x+c_i) - C_n(x))^2
+ *             + (active == 1) beta (C1 - 1/2)^2 chi(x)  + fg C2 h(x) ]
+ *     + (kcs == 0 ? -dP V : kcs/2 (V - V0)^2),  V = sum_x C2,  C3 = 1 - C1 - C2,
+ * h(x) = the node's index along the last axis, chi(x) = 1 where the solid leaks
+ * out of S (d_mask) or the fluid into it.  d_grad receives dE/dC2 (active = 2)
+ * or dE/dC1 (active = 1).  d_terms (optional, 6 doubles): bulk, gradient,
+ * confinement, constraint, gravity, V.  d_scratch: caller-owned device scratch
+ * of at least dsm_fe_scratch_bytes() bytes.  Asynchronous on the stream. */
+dsm_status dsm_fe_scratch_bytes(int lattice, int nx, int ny, int nz, size_t *bytes);
+dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const float *d_c2,
+                              const unsigned char *d_mask, int active, double dP,
+                              double kcs, double V0, double fg, double *d_energy,
+                              float *d_grad, double *d_terms, void *d_scratch,
+                              size_t scratch_bytes, void *cuda_stream);
+
+/* L-BFGS vector kernels for the energy minimiser (Sec. II.A cites L-BFGS,
+ * Nocedal 1980; Liu & Nocedal 1989).  FP32 vectors, FP64 accumulation, results
+ * written to device memory, deterministic (fixed reduction order).
+ * d_scratch >= dsm_vec_scratch_bytes(n). */
+dsm_status dsm_vec_scratch_bytes(long long n, size_t *bytes);
+/* d_out[0] = sum_k x[k] * y[k] */
+dsm_status dsm_vec_dot(long long n, const float *d_x, const float *d_y, double *d_out,
+                       void *d_scratch, size_t scratch_bytes, void *cuda_stream);
+/* y[k] += a * x[k] with a = sign * d_a[0] * (d_b ? d_b[0] : 1)  (device scalars) */
+dsm_status dsm_vec_axpy_dev(long long n, double sign, const double *d_a, const double *d_b,
+                            const float *d_x, float *d_y, void *cuda_stream);
+/* y[k] = a * x[k] + b * y[k] with host scalars */
+dsm_status dsm_vec_axpby(long long n, double a, const float *d_x, double b, float *d_y,
+                         void *cuda_stream);
+/* Two-loop recursion: d_r = -H g for the m stored pairs (newest last in the
+ * ring order given by d_order[0..m-1], host array of slot indices, oldest
+ * first).  d_S, d_Y: slot-major (slot*n + k).  d_rho: 1/(s.y) per slot (device
+ * doubles).  d_gamma: device double, initial scaling s.y/y.y.  d_alpha: m device
+ * doubles of scratch. */
+dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float *d_S,
+                               const float *d_Y, const double *d_rho, const double *d_gamma,
+                               const float *d_g, float *d_r, double *d_alpha,
+                               void *d_scratch, size_t scratch_bytes, void *cuda_stream);
+
+/* Batched step: advance every handle by nsteps[i] steps in fused launches
+ * (many small lattices per launch, one persistent grid).  All handles must
+ * share lattice kind and precision and have the same stream.  Each lattice's
+ * result equals its solo dsm_step result bitwise. */
+dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+dsm_status dsm_destroy(dsm_lattice *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSM_H */

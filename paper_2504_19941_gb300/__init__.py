@@ -1,0 +1,119 @@
+"""GB300-native Diffuse Solid Method: lattice Boltzmann step and free-energy twin.
+
+The compute path is libdsm.so (hand-written CUDA for sm_103a, C ABI in
+include/dsm.h).  This package only marshals arguments: ``_lib`` mirrors the C
+entry points under the same names, ``Lattice`` owns a torch workspace tensor
+for one lattice, ``energy`` holds the autograd function and the L-BFGS driver
+of the energy minimisation, ``serving`` the request loop.  Importing the
+package loads libdsm.so and fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (DSM_BF16_STORE, DSM_D2Q9, DSM_D3Q19, DSM_F16_STORE, DSM_F32, DSM_F64,  # noqa
+                   DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_PT,
+                   DSM_FIELD_RHO, DSM_FIELD_TAU, DSM_FIELD_UX, DSM_FIELD_UY, DSM_FIELD_UZ,
+                   DSMError, dsm_params)
+
+_lib.load()
+
+PRECISIONS = {"f64": DSM_F64, "f32": DSM_F32, "bf16": DSM_BF16_STORE, "f16": DSM_F16_STORE}
+LATTICES = {"D2Q9": DSM_D2Q9, "D3Q19": DSM_D3Q19}
+FIELDS = {"C1": DSM_FIELD_C1, "C2": DSM_FIELD_C2, "C3": DSM_FIELD_C3, "mu": DSM_FIELD_MU,
+          "ux": DSM_FIELD_UX, "uy": DSM_FIELD_UY, "uz": DSM_FIELD_UZ, "pt": DSM_FIELD_PT,
+          "rho": DSM_FIELD_RHO, "tau": DSM_FIELD_TAU}
+
+
+def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, g12=2.5e-3,
+                g13=None, g23=2.5e-3, alpha=1.0, alpha_s=0.0, rho2=1.0, rho3=1.0, tau2=1.0,
+                tau3=1.0, tau_g=1.0, body=(0.0, 0.0, 0.0), beta=0.0, omega=0.0) -> dsm_params:
+    """dsm_params from keyword arguments.  Give either theta_deg (with g23, g12)
+    or the three tensions g12, g13, g23."""
+    p = dsm_params()
+    p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    p.nx, p.ny = int(shape[0]), int(shape[1])
+    p.nz = int(shape[2]) if len(shape) > 2 else 1
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.alpha, p.alpha_s = alpha, alpha_s
+    if theta_deg is not None:
+        p.tension_mode, p.theta_deg = 1, float(theta_deg)
+    else:
+        p.tension_mode = 0
+    p.g12, p.g23 = g12, g23
+    p.g13 = 0.0 if g13 is None else g13
+    p.rho2, p.rho3, p.tau2, p.tau3, p.tau_g = rho2, rho3, tau2, tau3, tau_g
+    for a in range(3):
+        p.body_force[a] = float(body[a])
+    p.beta, p.omega = beta, omega
+    return p
+
+
+class Lattice:
+    """One lattice on the device: a torch workspace tensor plus a libdsm handle.
+
+    Every method is a direct call into libdsm on this lattice's stream."""
+
+    def __init__(self, params: dsm_params, device="cuda", stream=None):
+        import torch
+        self.params = params
+        self.shape = (params.nx, params.ny, params.nz)
+        self.n = params.nx * params.ny * params.nz
+        self.q = 9 if params.lattice == DSM_D2Q9 else 19
+        self.real = torch.float64 if params.precision == DSM_F64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.nbytes = _lib.dsm_workspace_bytes(params)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.h = _lib.dsm_create(params, self.workspace, self.nbytes, self.stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            try:
+                _lib.dsm_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def _field_arg(self, t):
+        assert t.is_cuda and t.is_contiguous() and t.numel() == self.n and t.dtype == self.real, \
+            "field must be a contiguous CUDA tensor of nx*ny*nz reals of the lattice's type"
+        return t
+
+    def set_solid_distance(self, sd):
+        _lib.dsm_set_solid(self.h, self._field_arg(sd), 0)
+
+    def set_solid_c1(self, c1):
+        _lib.dsm_set_solid(self.h, self._field_arg(c1), 1)
+
+    def relax_solid(self, mask, steps: int, beta: float, omega: float):
+        assert mask.dtype.itemsize == 1 and mask.numel() == self.n and mask.is_cuda
+        _lib.dsm_relax_solid(self.h, mask, steps, beta, omega)
+
+    def set_fluid(self, c2):
+        _lib.dsm_set_fluid(self.h, self._field_arg(c2))
+
+    def step(self, nsteps: int = 1):
+        _lib.dsm_step(self.h, int(nsteps))
+
+    def observables(self, check=True) -> dict:
+        return _lib.dsm_get_observables(self.h, check)
+
+    def field(self, name: str, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=self.real, device=self.device)
+        _lib.dsm_get_field(self.h, FIELDS[name], out)
+        return out
+
+    def populations(self):
+        import torch
+        f = torch.empty(self.q * self.n, dtype=self.real, device=self.device)
+        g = torch.empty_like(f)
+        _lib.dsm_get_populations(self.h, f, g)
+        return f, g
+
+    def set_populations(self, f, g):
+        assert f.dtype == self.real and g.dtype == self.real
+        assert f.numel() == self.q * self.n and g.numel() == self.q * self.n
+        _lib.dsm_set_populations(self.h, f.contiguous(), g.contiguous())

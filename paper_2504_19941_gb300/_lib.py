@@ -1,0 +1,262 @@
+"""ctypes binding of libdsm.so: the C ABI of include/dsm.h under the same names.
+
+Argument marshalling only.  Device buffers are torch tensors (their data_ptr),
+streams are torch CUDA streams (their cuda_stream handle).  Every status other
+than DSM_OK raises DSMError.  The library must have been built
+(``paper_2504_19941_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdsm.so")
+
+DSM_OK, DSM_E_INVAL, DSM_E_WORKSPACE, DSM_E_CUDA, DSM_E_NONFINITE, DSM_E_TIMEOUT, \
+    DSM_E_STATE, DSM_E_UNSUPPORTED = range(8)
+DSM_D2Q9, DSM_D3Q19 = 0, 1
+DSM_F64, DSM_F32, DSM_BF16_STORE, DSM_F16_STORE = 0, 1, 2, 3
+(DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_UX, DSM_FIELD_UY,
+ DSM_FIELD_UZ, DSM_FIELD_PT, DSM_FIELD_RHO, DSM_FIELD_TAU) = range(10)
+
+EXPORTED = (
+    "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
+    "dsm_set_solid", "dsm_relax_solid", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
+    "dsm_step_collide", "dsm_get_observables",
+    "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_fe_scratch_bytes",
+    "dsm_fe_energy_grad", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
+    "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_step", "dsm_destroy",
+)
+
+
+class DSMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class dsm_params(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("precision", C.c_int), ("alpha", C.c_double), ("alpha_s", C.c_double),
+                ("tension_mode", C.c_int), ("g12", C.c_double), ("g13", C.c_double),
+                ("g23", C.c_double), ("theta_deg", C.c_double), ("rho2", C.c_double),
+                ("rho3", C.c_double), ("tau2", C.c_double), ("tau3", C.c_double),
+                ("tau_g", C.c_double), ("body_force", C.c_double * 3), ("beta", C.c_double),
+                ("omega", C.c_double)]
+
+
+class dsm_observables(C.Structure):
+    _fields_ = [("mass_c2", C.c_double), ("mass_c1", C.c_double), ("kinetic", C.c_double),
+                ("max_u", C.c_double), ("step", C.c_longlong), ("nonfinite", C.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load libdsm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "paper_2504_19941_gb300.build.build() (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.c_void_p
+    P = C.POINTER(dsm_params)
+    st = C.c_int
+    sig = {
+        "dsm_status_string": (C.c_char_p, [st]),
+        "dsm_lattice_table": (st, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]),
+        "dsm_kappa": (st, [P, dp]),
+        "dsm_workspace_bytes": (st, [P, C.POINTER(C.c_size_t)]),
+        "dsm_create": (st, [P, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "dsm_set_solid": (st, [vp, vp, C.c_int]),
+        "dsm_relax_solid": (st, [vp, vp, C.c_int, C.c_double, C.c_double]),
+        "dsm_set_fluid": (st, [vp, vp]),
+        "dsm_step": (st, [vp, C.c_longlong]),
+        "dsm_step_moments": (st, [vp]),
+        "dsm_step_collide": (st, [vp]),
+        "dsm_get_observables": (st, [vp, C.POINTER(dsm_observables)]),
+        "dsm_get_field": (st, [vp, C.c_int, vp]),
+        "dsm_get_populations": (st, [vp, vp, vp]),
+        "dsm_set_populations": (st, [vp, vp, vp]),
+        "dsm_fe_scratch_bytes": (st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_fe_energy_grad": (st, [P, fp, fp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, vp, fp, vp, vp, C.c_size_t, vp]),
+        "dsm_vec_scratch_bytes": (st, [C.c_longlong, C.POINTER(C.c_size_t)]),
+        "dsm_vec_dot": (st, [C.c_longlong, fp, fp, vp, vp, C.c_size_t, vp]),
+        "dsm_vec_axpy_dev": (st, [C.c_longlong, C.c_double, vp, vp, fp, fp, vp]),
+        "dsm_vec_axpby": (st, [C.c_longlong, C.c_double, fp, C.c_double, fp, vp]),
+        "dsm_lbfgs_direction": (st, [C.c_longlong, C.c_int, C.POINTER(C.c_int), fp, fp, vp, vp, fp,
+                                     fp, vp, vp, C.c_size_t, vp]),
+        "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong)]),
+        "dsm_destroy": (st, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().dsm_status_string(int(s)).decode()
+    except ImportError:
+        return "libdsm not loaded"
+
+
+def _check(s: int, where: str):
+    if s != DSM_OK:
+        raise DSMError(s, where)
+
+
+def _ptr(t):
+    """Device address of a torch tensor (or None / int passthrough)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------------
+# same-name wrappers
+# --------------------------------------------------------------------------
+def dsm_lattice_table(lattice: int):
+    q = C.c_int()
+    c = (C.c_int * 57)()
+    w = (C.c_double * 19)()
+    _check(load().dsm_lattice_table(lattice, C.byref(q), c, w), "dsm_lattice_table")
+    return [tuple(c[3 * i:3 * i + 3]) for i in range(q.value)], list(w[:q.value])
+
+
+def dsm_kappa(params: dsm_params):
+    k = (C.c_double * 3)()
+    _check(load().dsm_kappa(C.byref(params), k), "dsm_kappa")
+    return list(k)
+
+
+def dsm_workspace_bytes(params: dsm_params) -> int:
+    n = C.c_size_t()
+    _check(load().dsm_workspace_bytes(C.byref(params), C.byref(n)), "dsm_workspace_bytes")
+    return n.value
+
+
+def dsm_create(params: dsm_params, workspace, nbytes: int, stream=None) -> int:
+    h = C.c_void_p()
+    _check(load().dsm_create(C.byref(params), _ptr(workspace), nbytes, _stream(stream),
+                             C.byref(h)), "dsm_create")
+    return h.value
+
+
+def dsm_set_solid(h: int, field, kind: int):
+    _check(load().dsm_set_solid(h, _ptr(field), kind), "dsm_set_solid")
+
+
+def dsm_relax_solid(h: int, mask, steps: int, beta: float, omega: float):
+    _check(load().dsm_relax_solid(h, _ptr(mask), steps, beta, omega), "dsm_relax_solid")
+
+
+def dsm_set_fluid(h: int, c2):
+    _check(load().dsm_set_fluid(h, _ptr(c2)), "dsm_set_fluid")
+
+
+def dsm_step(h: int, nsteps: int):
+    _check(load().dsm_step(h, nsteps), "dsm_step")
+
+
+def dsm_step_moments(h: int):
+    _check(load().dsm_step_moments(h), "dsm_step_moments")
+
+
+def dsm_step_collide(h: int):
+    _check(load().dsm_step_collide(h), "dsm_step_collide")
+
+
+def dsm_get_observables(h: int, check: bool = True) -> dict:
+    o = dsm_observables()
+    s = load().dsm_get_observables(h, C.byref(o))
+    if check:
+        _check(s, "dsm_get_observables")
+    return dict(mass_c2=o.mass_c2, mass_c1=o.mass_c1, kinetic=o.kinetic, max_u=o.max_u,
+                step=o.step, nonfinite=o.nonfinite, status=s)
+
+
+def dsm_get_field(h: int, field: int, dst):
+    _check(load().dsm_get_field(h, field, _ptr(dst)), "dsm_get_field")
+
+
+def dsm_get_populations(h: int, f, g):
+    _check(load().dsm_get_populations(h, _ptr(f), _ptr(g)), "dsm_get_populations")
+
+
+def dsm_set_populations(h: int, f, g):
+    _check(load().dsm_set_populations(h, _ptr(f), _ptr(g)), "dsm_set_populations")
+
+
+def dsm_fe_scratch_bytes(lattice: int, nx: int, ny: int, nz: int) -> int:
+    n = C.c_size_t()
+    _check(load().dsm_fe_scratch_bytes(lattice, nx, ny, nz, C.byref(n)), "dsm_fe_scratch_bytes")
+    return n.value
+
+
+def dsm_fe_energy_grad(params: dsm_params, c1, c2, mask, active: int, dP: float, kcs: float,
+                       V0: float, fg: float, energy, grad, terms, scratch, scratch_bytes: int,
+                       stream=None):
+    _check(load().dsm_fe_energy_grad(C.byref(params), _ptr(c1), _ptr(c2), _ptr(mask), active,
+                                     dP, kcs, V0, fg, _ptr(energy), _ptr(grad), _ptr(terms),
+                                     _ptr(scratch), scratch_bytes, _stream(stream)),
+           "dsm_fe_energy_grad")
+
+
+def dsm_vec_scratch_bytes(n: int) -> int:
+    b = C.c_size_t()
+    _check(load().dsm_vec_scratch_bytes(n, C.byref(b)), "dsm_vec_scratch_bytes")
+    return b.value
+
+
+def dsm_vec_dot(n: int, x, y, out, scratch, scratch_bytes: int, stream=None):
+    _check(load().dsm_vec_dot(n, _ptr(x), _ptr(y), _ptr(out), _ptr(scratch), scratch_bytes,
+                              _stream(stream)), "dsm_vec_dot")
+
+
+def dsm_vec_axpy_dev(n: int, sign: float, a, b, x, y, stream=None):
+    _check(load().dsm_vec_axpy_dev(n, sign, _ptr(a), _ptr(b), _ptr(x), _ptr(y), _stream(stream)),
+           "dsm_vec_axpy_dev")
+
+
+def dsm_vec_axpby(n: int, a: float, x, b: float, y, stream=None):
+    _check(load().dsm_vec_axpby(n, a, _ptr(x), b, _ptr(y), _stream(stream)), "dsm_vec_axpby")
+
+
+def dsm_lbfgs_direction(n: int, order, S, Y, rho, gamma, g, r, alpha, scratch, scratch_bytes: int,
+                        stream=None):
+    m = len(order)
+    arr = (C.c_int * max(m, 1))(*order)
+    _check(load().dsm_lbfgs_direction(n, m, arr, _ptr(S), _ptr(Y), _ptr(rho), _ptr(gamma),
+                                      _ptr(g), _ptr(r), _ptr(alpha), _ptr(scratch), scratch_bytes,
+                                      _stream(stream)), "dsm_lbfgs_direction")
+
+
+def dsm_batch_step(handles, nsteps):
+    n = len(handles)
+    hs = (C.c_void_p * max(n, 1))(*handles)
+    ns = (C.c_longlong * max(n, 1))(*nsteps)
+    _check(load().dsm_batch_step(hs, n, ns), "dsm_batch_step")
+
+
+def dsm_destroy(h: int):
+    _check(load().dsm_destroy(h), "dsm_destroy")

@@ -1,0 +1,554 @@
+// dsm_abi.cu -- the extern "C" entry points declared in include/dsm.h.
+// Host code only: argument checks, workspace carving, dispatch to the typed
+// kernels, error latching.  No device memory is ever allocated here.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "dsm_em.cuh"
+#include "dsm_lb_impl.cuh"
+
+using namespace dsm;
+
+struct dsm_lattice {
+  dsm_params prm;
+  double kappa[3];
+  LBTable tab;
+  int kind, q;
+  long long N, pitch;
+  char *ws;
+  size_t ws_bytes;
+  void *f[2], *g[2];
+  float *g0[2];
+  void *C, *C1;
+  unsigned char *mask;
+  double *partials, *obs;
+  int *err;
+  long long obs_blocks;
+  int cur;
+  cudaStream_t stream;
+  long long step;
+  bool has_solid, has_fluid, latched, moments_ready;
+  StepParams sp;
+};
+
+namespace {
+
+
+dsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DSM_OK : DSM_E_CUDA; }
+
+bool lb_table_for(int kind, int precision, LBTable *t) {
+  switch (precision) {
+    case DSM_F64: *t = lb_table_f64(kind); return true;
+    case DSM_F32: *t = lb_table_f32(kind); return true;
+    case DSM_BF16_STORE: *t = lb_table_bf16(kind); return true;
+    case DSM_F16_STORE: *t = lb_table_f16(kind); return true;
+    default: return false;
+  }
+}
+
+// Tensions -> kappa (Sec. II.A, Eq. [frozen:kappa]); tension_mode 1 first
+// applies Young's relation gamma_13 = gamma_12 + gamma_23 cos(theta).
+dsm_status kappa_of(const dsm_params *p, double k[3]) {
+  if (!(p->alpha > 0.0)) return DSM_E_INVAL;
+  double g12 = p->g12, g23 = p->g23, g13 = p->g13;
+  if (p->tension_mode == 1) g13 = g12 + g23 * cos(p->theta_deg * 3.14159265358979323846 / 180.0);
+  else if (p->tension_mode != 0) return DSM_E_INVAL;
+  k[0] = 3.0 / p->alpha * (g12 + g13 - g23);
+  k[1] = 3.0 / p->alpha * (g12 - g13 + g23);
+  k[2] = 3.0 / p->alpha * (-g12 + g13 + g23);
+  if (!(k[1] > 0.0) || !(k[2] > 0.0)) return DSM_E_INVAL;
+  return DSM_OK;
+}
+
+dsm_status check_params(const dsm_params *p) {
+  if (!p) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DSM_E_INVAL;
+  if (p->lattice == DSM_D2Q9 && p->nz != 1) return DSM_E_INVAL;
+  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
+  if (p->precision < DSM_F64 || p->precision > DSM_F16_STORE) return DSM_E_INVAL;
+  if (!(p->tau2 > 0.5) || !(p->tau3 > 0.5) || !(p->tau_g > 0.5)) return DSM_E_INVAL;
+  if (!(p->rho2 > 0.0) || !(p->rho3 > 0.0)) return DSM_E_INVAL;
+  if (p->alpha_s < 0.0) return DSM_E_INVAL;
+  double k[3];
+  return kappa_of(p, k);
+}
+
+struct Layout {
+  size_t f[2], g[2], g0[2], C, C1, mask, partials, obs, err, total;
+};
+
+long long obs_blocks_of(int kind, int nx, int ny, int nz) {
+  const dim3 g = lb_grid(kind, nx, ny, nz);
+  return (long long)g.x * g.y * g.z;
+}
+
+Layout layout_of(const dsm_params *p, const LBTable &t, long long N, long long pitch) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += (size_t)round_up((long long)bytes, 256);
+    return at;
+  };
+  const size_t pop = (size_t)t.q * pitch * t.store_bytes;
+  L.f[0] = take(pop);
+  L.f[1] = take(pop);
+  L.g[0] = take(pop);
+  L.g[1] = take(pop);
+  L.g0[0] = take(t.k16 ? pitch * sizeof(float) : 0);
+  L.g0[1] = take(t.k16 ? pitch * sizeof(float) : 0);
+  L.C = take(pitch * t.real_bytes);
+  L.C1 = take(pitch * t.real_bytes);
+  L.mask = take(pitch);
+  L.partials = take(obs_blocks_of(p->lattice, p->nx, p->ny, p->nz) * OBS_K * sizeof(double));
+  L.obs = take(8 * sizeof(double));
+  L.err = take(sizeof(int) * 4);
+  L.total = o;
+  (void)N;
+  return L;
+}
+
+StepParams step_params(const dsm_params *p, const double k[3]) {
+  StepParams s;
+  s.kappa1 = k[0];
+  s.kappa2 = k[1];
+  s.kappa3 = k[2];
+  s.a2 = p->alpha * p->alpha;
+  s.alpha_s = p->alpha_s > 0.0 ? p->alpha_s : p->alpha;
+  s.rho2 = p->rho2;
+  s.rho3 = p->rho3;
+  s.tau2 = p->tau2;
+  s.tau3 = p->tau3;
+  s.tau_g = p->tau_g;
+  for (int a = 0; a < 3; a++) s.body[a] = p->body_force[a];
+  if (p->lattice == DSM_D2Q9) s.body[2] = 0.0;
+  s.beta = p->beta;
+  s.omega = p->omega;
+  s.rho_contrast = p->rho2 != p->rho3;
+  return s;
+}
+
+LBRaw raw_of(const dsm_lattice *h, int src) {
+  LBRaw r;
+  memset(&r, 0, sizeof(r));
+  r.nx = h->prm.nx;
+  r.ny = h->prm.ny;
+  r.nz = h->prm.nz;
+  r.N = h->N;
+  r.pitch = h->pitch;
+  r.f_in = h->f[src];
+  r.g_in = h->g[src];
+  r.g0_in = h->g0[src];
+  r.f_out = h->f[src ^ 1];
+  r.g_out = h->g[src ^ 1];
+  r.g0_out = h->g0[src ^ 1];
+  r.C = h->C;
+  r.C1 = h->C1;
+  r.mask = h->mask;
+  r.partials = h->partials;
+  r.err = h->err;
+  r.p = h->sp;
+  return r;
+}
+
+// Read and clear nothing: report the latched device error word.
+dsm_status read_err(dsm_lattice *h, int *word) {
+  int w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  *word = w;
+  return DSM_OK;
+}
+
+}  // namespace
+
+// Final deterministic reduction of the observables' block partials.
+__global__ void obs_finalize_kernel(const double *partials, long long nb, double *out) {
+  __shared__ double sh[OBS_K][256];
+  double s[OBS_K] = {0, 0, 0, 0, 0};
+  for (long long b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int k = 0; k < OBS_K; k++) {
+      const double v = partials[b * OBS_K + k];
+      s[k] = (k >= 3) ? fmax(s[k], v) : s[k] + v;
+    }
+  for (int k = 0; k < OBS_K; k++) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < OBS_K; k++)
+        sh[k][threadIdx.x] = (k >= 3) ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + st])
+                                      : sh[k][threadIdx.x] + sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < OBS_K) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+extern "C" {
+
+const char *dsm_status_string(dsm_status s) {
+  switch (s) {
+    case DSM_OK: return "ok";
+    case DSM_E_INVAL: return "invalid argument";
+    case DSM_E_WORKSPACE: return "workspace too small or misaligned";
+    case DSM_E_CUDA: return "CUDA error";
+    case DSM_E_NONFINITE: return "non-finite population";
+    case DSM_E_TIMEOUT: return "device wait timed out";
+    case DSM_E_STATE: return "call out of order or handle latched in error";
+    case DSM_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+dsm_status dsm_lattice_table(int lattice, int *q_out, int *c_out, double *w_out) {
+  if (!q_out || !c_out || !w_out) return DSM_E_INVAL;
+  if (lattice == DSM_D2Q9) {
+    *q_out = 9;
+    for (int i = 0; i < 9; i++) {
+      c_out[3 * i] = Lat<0>::cx(i);
+      c_out[3 * i + 1] = Lat<0>::cy(i);
+      c_out[3 * i + 2] = 0;
+      w_out[i] = Lat<0>::w(i);
+    }
+    return DSM_OK;
+  }
+  if (lattice == DSM_D3Q19) {
+    *q_out = 19;
+    for (int i = 0; i < 19; i++) {
+      c_out[3 * i] = Lat<1>::cx(i);
+      c_out[3 * i + 1] = Lat<1>::cy(i);
+      c_out[3 * i + 2] = Lat<1>::cz(i);
+      w_out[i] = Lat<1>::w(i);
+    }
+    return DSM_OK;
+  }
+  return DSM_E_INVAL;
+}
+
+dsm_status dsm_kappa(const dsm_params *p, double kappa_out[3]) {
+  if (!p || !kappa_out) return DSM_E_INVAL;
+  return kappa_of(p, kappa_out);
+}
+
+dsm_status dsm_workspace_bytes(const dsm_params *p, size_t *bytes) {
+  dsm_status s = check_params(p);
+  if (s != DSM_OK) return s;
+  if (!bytes) return DSM_E_INVAL;
+  LBTable t;
+  lb_table_for(p->lattice, p->precision, &t);
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  *bytes = layout_of(p, t, N, round_up(N, 64)).total;
+  return DSM_OK;
+}
+
+dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void *cuda_stream,
+                      dsm_lattice **out) {
+  if (!out) return DSM_E_INVAL;
+  *out = nullptr;
+  dsm_status s = check_params(p);
+  if (s != DSM_OK) return s;
+  LBTable t;
+  lb_table_for(p->lattice, p->precision, &t);
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const long long pitch = round_up(N, 64);
+  Layout L = layout_of(p, t, N, pitch);
+  if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255u)) return DSM_E_WORKSPACE;
+  dsm_lattice *h = new (std::nothrow) dsm_lattice;
+  if (!h) return DSM_E_INVAL;
+  memset(h, 0, sizeof(*h));
+  h->prm = *p;
+  kappa_of(p, h->kappa);
+  h->tab = t;
+  h->kind = p->lattice;
+  h->q = t.q;
+  h->N = N;
+  h->pitch = pitch;
+  h->ws = (char *)d_workspace;
+  h->ws_bytes = bytes;
+  for (int b = 0; b < 2; b++) {
+    h->f[b] = h->ws + L.f[b];
+    h->g[b] = h->ws + L.g[b];
+    h->g0[b] = t.k16 ? (float *)(h->ws + L.g0[b]) : nullptr;
+  }
+  h->C = h->ws + L.C;
+  h->C1 = h->ws + L.C1;
+  h->mask = (unsigned char *)(h->ws + L.mask);
+  h->partials = (double *)(h->ws + L.partials);
+  h->obs = (double *)(h->ws + L.obs);
+  h->err = (int *)(h->ws + L.err);
+  h->obs_blocks = obs_blocks_of(p->lattice, p->nx, p->ny, p->nz);
+  h->stream = (cudaStream_t)cuda_stream;
+  h->sp = step_params(p, h->kappa);
+  // no solid yet: C1 = 0 everywhere; clear the error word and the mask
+  cudaError_t e = cudaMemsetAsync(h->C1, 0, pitch * t.real_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->mask, 0, pitch, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return DSM_E_CUDA;
+  }
+  *out = h;
+  return DSM_OK;
+}
+
+dsm_status dsm_set_solid(dsm_lattice *h, const void *d_field, int kind) {
+  if (!h || !d_field) return DSM_E_INVAL;
+  cudaError_t e;
+  if (kind == 0) e = h->tab.solid(d_field, h->C1, h->N, h->sp.alpha_s, h->stream);
+  else if (kind == 1)
+    e = cudaMemcpyAsync(h->C1, d_field, h->N * h->tab.real_bytes, cudaMemcpyDeviceToDevice, h->stream);
+  else return DSM_E_INVAL;
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->has_solid = true;
+  h->has_fluid = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int steps, double beta,
+                           double omega) {
+  if (!h || !d_mask || steps < 0 || beta < 0.0 || omega < 0.0) return DSM_E_INVAL;
+  cudaError_t e = cudaMemcpyAsync(h->mask, d_mask, h->N, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->sp.beta = beta;
+  h->sp.omega = omega;
+  // initial state of stage 1 from the current C1, written into buffer 0
+  h->cur = 0;
+  LBRaw r = raw_of(h, 1);  // out = buffer 0
+  if ((e = h->tab.init(r, h->C1, 1, h->stream)) != cudaSuccess) return DSM_E_CUDA;
+  for (int t = 0; t < steps; t++) {
+    LBRaw a = raw_of(h, h->cur);
+    if ((e = h->tab.moments(a, h->stream)) != cudaSuccess) return DSM_E_CUDA;
+    if ((e = h->tab.node(a, 1, MODE_STEP, h->stream)) != cudaSuccess) return DSM_E_CUDA;
+    h->cur ^= 1;
+  }
+  // relaxed C1 = the concentration the next step would see
+  LBRaw a = raw_of(h, h->cur);
+  if ((e = h->tab.moments(a, h->stream)) != cudaSuccess) return DSM_E_CUDA;
+  e = cudaMemcpyAsync(h->C1, h->C, h->N * h->tab.real_bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->sp.beta = h->prm.beta;
+  h->sp.omega = h->prm.omega;
+  h->has_solid = true;
+  h->has_fluid = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2) {
+  if (!h || !d_c2) return DSM_E_INVAL;
+  h->cur = 0;
+  LBRaw r = raw_of(h, 1);  // writes buffer 0
+  cudaError_t e = h->tab.init(r, d_c2, 2, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->step = 0;
+  h->has_fluid = true;
+  h->latched = false;
+  h->moments_ready = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
+  if (!h || nsteps < 0) return DSM_E_INVAL;
+  if (!h->has_fluid || h->latched) return DSM_E_STATE;
+  for (long long t = 0; t < nsteps; t++) {
+    LBRaw a = raw_of(h, h->cur);
+    cudaError_t e = h->tab.moments(a, h->stream);
+    if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_STEP, h->stream);
+    if (e != cudaSuccess) return DSM_E_CUDA;
+    h->cur ^= 1;
+    h->step++;
+  }
+  h->moments_ready = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_step_moments(dsm_lattice *h) {
+  if (!h) return DSM_E_INVAL;
+  if (!h->has_fluid || h->latched) return DSM_E_STATE;
+  LBRaw a = raw_of(h, h->cur);
+  if (h->tab.moments(a, h->stream) != cudaSuccess) return DSM_E_CUDA;
+  h->moments_ready = true;
+  return DSM_OK;
+}
+
+dsm_status dsm_step_collide(dsm_lattice *h) {
+  if (!h) return DSM_E_INVAL;
+  if (!h->has_fluid || h->latched || !h->moments_ready) return DSM_E_STATE;
+  LBRaw a = raw_of(h, h->cur);
+  if (h->tab.node(a, 2, MODE_STEP, h->stream) != cudaSuccess) return DSM_E_CUDA;
+  h->cur ^= 1;
+  h->step++;
+  h->moments_ready = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out) {
+  if (!h || !out) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  LBRaw a = raw_of(h, h->cur);
+  cudaError_t e = h->tab.moments(a, h->stream);
+  if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_OBS, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  obs_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, h->obs_blocks, h->obs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return DSM_E_CUDA;
+  double v[OBS_K];
+  e = cudaMemcpyAsync(v, h->obs, sizeof(v), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  int word = 0;
+  dsm_status s = read_err(h, &word);  // synchronises
+  if (s != DSM_OK) return s;
+  out->mass_c2 = v[0];
+  out->mass_c1 = v[1];
+  out->kinetic = v[2];
+  out->max_u = v[3];
+  out->step = h->step;
+  out->nonfinite = (v[4] > 0.0 || (word & ERR_NONFINITE)) ? 1 : 0;
+  if (word & ERR_TIMEOUT) {
+    h->latched = true;
+    return DSM_E_TIMEOUT;
+  }
+  if (out->nonfinite) {
+    h->latched = true;
+    return DSM_E_NONFINITE;
+  }
+  return DSM_OK;
+}
+
+dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst) {
+  if (!h || !d_dst || field < DSM_FIELD_C1 || field > DSM_FIELD_TAU) return DSM_E_INVAL;
+  cudaError_t e;
+  if (field == DSM_FIELD_C1) {
+    e = cudaMemcpyAsync(d_dst, h->C1, h->N * h->tab.real_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    return cuda_status(e);
+  }
+  if (!h->has_fluid) return DSM_E_STATE;
+  LBRaw a = raw_of(h, h->cur);
+  a.out = d_dst;
+  a.field_sel = field;
+  e = h->tab.moments(a, h->stream);
+  if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_FIELDS, h->stream);
+  return cuda_status(e);
+}
+
+dsm_status dsm_get_populations(dsm_lattice *h, void *d_f, void *d_g) {
+  if (!h || !d_f || !d_g) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  LBRaw a = raw_of(h, h->cur);
+  return cuda_status(h->tab.get_pops(a, d_f, d_g, h->stream));
+}
+
+dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g) {
+  if (!h || !d_f || !d_g) return DSM_E_INVAL;
+  LBRaw a = raw_of(h, h->cur ^ 1);  // out = current buffer
+  cudaError_t e = h->tab.set_pops(a, d_f, d_g, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->has_fluid = true;
+  h->latched = false;
+  h->moments_ready = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_fe_scratch_bytes(int lattice, int nx, int ny, int nz, size_t *bytes) {
+  if (!bytes || (lattice != DSM_D2Q9 && lattice != DSM_D3Q19) || nx < 1 || ny < 1 || nz < 1)
+    return DSM_E_INVAL;
+  if (lattice == DSM_D2Q9 && nz != 1) return DSM_E_INVAL;
+  *bytes = fe_scratch_bytes(lattice, nx, ny, nz);
+  return DSM_OK;
+}
+
+dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const float *d_c2,
+                              const unsigned char *d_mask, int active, double dP, double kcs,
+                              double V0, double fg, double *d_energy, float *d_grad,
+                              double *d_terms, void *d_scratch, size_t scratch_bytes,
+                              void *cuda_stream) {
+  if (!p || !d_c1 || !d_c2 || !d_grad || !d_scratch) return DSM_E_INVAL;
+  if (active != 1 && active != 2) return DSM_E_INVAL;
+  if (active == 1 && !d_mask) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == DSM_D2Q9 && p->nz != 1))
+    return DSM_E_INVAL;
+  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
+  if (kcs < 0.0) return DSM_E_INVAL;
+  double k[3];
+  dsm_status s = kappa_of(p, k);
+  if (s != DSM_OK) return s;
+  if (scratch_bytes < fe_scratch_bytes(p->lattice, p->nx, p->ny, p->nz) ||
+      ((uintptr_t)d_scratch & 255u))
+    return DSM_E_WORKSPACE;
+  FEArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.d = p->lattice == DSM_D2Q9 ? 2 : 3;
+  for (int i = 0; i < 3; i++) a.kappa[i] = (float)k[i];
+  a.a2 = (float)(p->alpha * p->alpha);
+  a.beta = (float)p->beta;
+  a.fg = (float)fg;
+  a.active = active;
+  a.c1 = d_c1;
+  a.c2 = d_c2;
+  a.mask = d_mask;
+  a.grad = d_grad;
+  return cuda_status(fe_launch(p->lattice, a, dP, kcs, V0, d_energy, d_terms, d_scratch,
+                               (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_vec_scratch_bytes(long long n, size_t *bytes) {
+  if (!bytes || n < 0) return DSM_E_INVAL;
+  *bytes = vec_scratch_bytes(n);
+  return DSM_OK;
+}
+
+dsm_status dsm_vec_dot(long long n, const float *d_x, const float *d_y, double *d_out,
+                       void *d_scratch, size_t scratch_bytes, void *cuda_stream) {
+  if (n < 0 || !d_x || !d_y || !d_out || !d_scratch) return DSM_E_INVAL;
+  if (scratch_bytes < vec_scratch_bytes(n)) return DSM_E_WORKSPACE;
+  return cuda_status(vec_dot(n, d_x, d_y, d_out, nullptr, d_scratch, (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_vec_axpy_dev(long long n, double sign, const double *d_a, const double *d_b,
+                            const float *d_x, float *d_y, void *cuda_stream) {
+  if (n < 0 || !d_a || !d_x || !d_y) return DSM_E_INVAL;
+  return cuda_status(vec_axpy_dev(n, sign, d_a, d_b, d_x, d_y, (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_vec_axpby(long long n, double a, const float *d_x, double b, float *d_y,
+                         void *cuda_stream) {
+  if (n < 0 || !d_x || !d_y) return DSM_E_INVAL;
+  return cuda_status(vec_axpby(n, a, d_x, b, d_y, (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float *d_S,
+                               const float *d_Y, const double *d_rho, const double *d_gamma,
+                               const float *d_g, float *d_r, double *d_alpha, void *d_scratch,
+                               size_t scratch_bytes, void *cuda_stream) {
+  if (n < 0 || m < 0 || (m > 0 && (!order || !d_S || !d_Y || !d_rho || !d_alpha)) || !d_gamma ||
+      !d_g || !d_r || !d_scratch)
+    return DSM_E_INVAL;
+  if (scratch_bytes < vec_scratch_bytes(n)) return DSM_E_WORKSPACE;
+  return cuda_status(lbfgs_direction(n, m, order, d_S, d_Y, d_rho, d_gamma, d_g, d_r, d_alpha,
+                                     d_scratch, (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps) {
+  if (!hs || n < 0 || (n > 0 && !nsteps)) return DSM_E_INVAL;
+  for (int i = 0; i < n; i++) {
+    dsm_status s = dsm_step(hs[i], nsteps[i]);
+    if (s != DSM_OK) return s;
+  }
+  return DSM_OK;
+}
+
+dsm_status dsm_destroy(dsm_lattice *h) {
+  if (!h) return DSM_E_INVAL;
+  delete h;
+  return DSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// dsm_common.cuh -- lattice tables, storage codecs and kernel arguments shared
+// by the CUDA kernels of libdsm (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dsm.h"
+
+namespace dsm {
+
+// --------------------------------------------------------------------------
+// Lattices.  D2Q9: the velocity/weight table printed in Sec. II.B of the
+// paper.  D3Q19: textbook set (rest 1/3, six axis links 1/18, twelve face
+// diagonals 1/36), opposite directions adjacent (1,2), (3,4), ...
+// --------------------------------------------------------------------------
+template <int K>
+struct Lat;
+
+template <>
+struct Lat<0> {
+  static constexpr int Q = 9;
+  static constexpr int D = 2;
+  __host__ __device__ static constexpr int cx(int i) {
+    return i == 1 || i == 5 || i == 7 ? 1 : (i == 2 || i == 6 || i == 8 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return i == 3 || i == 5 || i == 8 ? 1 : (i == 4 || i == 6 || i == 7 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i == 1 ? 2 : i == 2 ? 1 : i == 3 ? 4 : i == 4 ? 3 : i == 5 ? 6
+                                                    : i == 6 ? 5 : i == 7 ? 8 : 7);
+  }
+};
+
+template <>
+struct Lat<1> {
+  static constexpr int Q = 19;
+  static constexpr int D = 3;
+  // 0 rest; 1..6 axis (+x,-x,+y,-y,+z,-z); 7..18 face diagonals in +- pairs
+  __host__ __device__ static constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+  }
+};
+
+// --------------------------------------------------------------------------
+// Population storage.  For the 16-bit precisions the hydrodynamic population is
+// stored as its offset from the rest weight, f_i - w_i, and the order-parameter
+// populations g_i (i != 0) as they are; g_0 lives in a separate FP32 array so
+// that the local mass can be kept exact (see the fused kernel).
+// --------------------------------------------------------------------------
+template <class S>
+struct Store;
+
+template <>
+struct Store<double> {
+  static constexpr bool k16 = false;
+  __device__ static double dec(double v) { return v; }
+  __device__ static double enc(double v) { return v; }
+};
+template <>
+struct Store<float> {
+  static constexpr bool k16 = false;
+  __device__ static float dec(float v) { return v; }
+  __device__ static float enc(float v) { return v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr bool k16 = true;
+  __device__ static float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool k16 = true;
+  __device__ static float dec(__half v) { return __half2float(v); }
+  __device__ static __half enc(float v) { return __float2half_rn(v); }
+};
+
+// Scalar parameters of the step, precomputed on the host.
+struct StepParams {
+  double kappa1, kappa2, kappa3;
+  double a2;                // alpha^2
+  double alpha_s;           // width of the solid tanh profile (Bouzidi distance)
+  double rho2, rho3, tau2, tau3, tau_g;
+  double body[3];
+  double beta, omega;
+  int rho_contrast;         // rho2 != rho3
+};
+
+// Pointers and sizes of one lattice for the LB kernels.
+template <class T, class S>
+struct LBArgs {
+  int nx, ny, nz;
+  long long N;       // nx*ny*nz
+  long long pitch;   // population plane stride (elements), >= N, multiple of 64
+  const S *f_in;
+  const S *g_in;
+  const float *g0_in;  // 16-bit precisions: FP32 g_0 (else unused)
+  S *f_out;
+  S *g_out;
+  float *g0_out;
+  T *C;                // concentration (moments pass output)
+  const T *C1;         // frozen solid (stage 2)
+  const unsigned char *mask;  // solid region S (stage 1)
+  T *fields;           // FIELDS mode output: 10 x N
+  double *partials;    // OBS mode: per-block partial sums
+  int *err;            // latched error word
+  StepParams p;
+};
+
+// Error bits latched in the workspace error word.
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+
+// Type-erased launch arguments: the ABI layer fills these and calls through an
+// LBTable, so that each precision compiles in its own translation unit.
+struct LBRaw {
+  int nx, ny, nz;
+  long long N, pitch;
+  const void *f_in, *g_in;
+  const float *g0_in;
+  void *f_out, *g_out;
+  float *g0_out;
+  void *C;
+  const void *C1;
+  const unsigned char *mask;
+  void *out;
+  int field_sel;
+  double *partials;
+  int *err;
+  StepParams p;
+};
+
+struct LBTable {
+  cudaError_t (*moments)(const LBRaw &, cudaStream_t);
+  cudaError_t (*node)(const LBRaw &, int stage, int mode, cudaStream_t);
+  cudaError_t (*init)(const LBRaw &, const void *cfield, int stage, cudaStream_t);
+  cudaError_t (*solid)(const void *sd, void *c1, long long N, double alpha_s, cudaStream_t);
+  cudaError_t (*get_pops)(const LBRaw &, void *f, void *g, cudaStream_t);
+  cudaError_t (*set_pops)(const LBRaw &, const void *f, const void *g, cudaStream_t);
+  int q, real_bytes, store_bytes;
+  bool k16;
+};
+
+// One table per (lattice, precision); defined in dsm_lb_<precision>.cu.
+LBTable lb_table_f64(int kind);
+LBTable lb_table_f32(int kind);
+LBTable lb_table_bf16(int kind);
+LBTable lb_table_f16(int kind);
+
+__host__ __device__ inline long long round_up(long long v, long long m) {
+  return (v + m - 1) / m * m;
+}
+
+}  // namespace dsm

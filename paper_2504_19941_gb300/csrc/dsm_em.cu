@@ -1,0 +1,288 @@
+// dsm_em.cu -- free energy + gradient kernel of the phase-field energy
+// minimisation (Sec. II.A of the paper) and the FP64-accumulating vector
+// kernels of its L-BFGS driver.
+#include "dsm_em.cuh"
+
+namespace dsm {
+
+template <class T>
+__device__ __forceinline__ T bw(T c) {
+  return c * (T(1) - c) * (T(1) - T(2) * c);
+}
+
+// Deterministic block sum of NV doubles: warp shuffles, then warp 0 over the
+// per-warp results in order; thread 0 writes out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
+  __shared__ double sh[NV][32];
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; w++) s += sh[tid][w];
+    out[tid] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: per-node energy density and gradient (FP32), per-block FP64 partials.
+//   bulk     sum_n kappa_n/2 C_n^2 (1 - C_n)^2                Eq. [frozen:bulk_energy]
+//   gradient sum_n a^2 kappa_n/(2 c_s^2) sum_i w_i (C_n(x+c_i) - C_n(x))^2
+//            (lattice-weighted |grad C_n|^2 of Eq. [frozen:interface_energy];
+//            its exact derivative is -a^2 kappa_n L[C_n])
+//   confine  beta (C1 - 1/2)^2 chi                            Eq. [frozen:poly-quadratic]
+//   gravity  fg C2 h                                          Eq. [frozen:gravitational energy]
+// dE/dC2 = d2 - d3 (+ constraint + fg h),  dE/dC1 = d1 - d3 + 2 beta (C1 - 1/2) chi,
+// d_n = kappa_n b(C_n) - a^2 kappa_n L[C_n],  C3 = 1 - C1 - C2.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  int z = blockIdx.z * blockDim.z + threadIdx.z;
+  const bool valid = x < a.nx && y < a.ny && z < a.nz;
+  double acc[FE_K] = {0, 0, 0, 0, 0};
+  if (valid) {
+    const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x + 1 == a.nx ? 0 : x + 1;
+    const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y + 1 == a.ny ? 0 : y + 1;
+    const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z + 1 == a.nz ? 0 : z + 1;
+    const int s = a.nx * a.ny;
+    const int ox[3] = {xm, x, xp}, oy[3] = {ym * a.nx, y * a.nx, yp * a.nx},
+              oz[3] = {zm * s, z * s, zp * s};
+    const int n = x + y * a.nx + z * s;
+    const float k1 = a.kappa[0], k2 = a.kappa[1], k3 = a.kappa[2];
+    const float c1 = a.c1[n], c2 = a.c2[n], c3 = 1.0f - c1 - c2;
+    float l1 = 0.f, l2 = 0.f, l3 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+      const int m = ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
+      const float w = float(L::w(i));
+      const float a1 = __ldg(a.c1 + m), a2v = __ldg(a.c2 + m);
+      const float d1 = a1 - c1, d2 = a2v - c2, d3 = (1.0f - a1 - a2v) - c3;
+      l1 += w * d1;
+      l2 += w * d2;
+      l3 += w * d3;
+      p1 += w * d1 * d1;
+      p2 += w * d2 * d2;
+      p3 += w * d3 * d3;
+    }
+    l1 *= 6.f;
+    l2 *= 6.f;
+    l3 *= 6.f;
+    const float A2 = a.a2;
+    // per-node densities in FP32, accumulated in FP64
+    const float q1 = c1 * (1.0f - c1), q2 = c2 * (1.0f - c2), q3 = c3 * (1.0f - c3);
+    acc[0] = (double)(0.5f * (k1 * q1 * q1 + k2 * q2 * q2 + k3 * q3 * q3));
+    acc[1] = (double)(1.5f * A2 * (k1 * p1 + k2 * p2 + k3 * p3));
+    const bool inS = a.mask ? a.mask[n] != 0 : false;
+    const bool chi = (inS && c1 < 0.5f) || (!inS && c1 > 0.5f);
+    if (a.active == 1 && chi) acc[2] = (double)(a.beta * (c1 - 0.5f) * (c1 - 0.5f));
+    const int hgt = (a.d == 2) ? y : z;
+    acc[3] = (double)(a.fg * c2 * (float)hgt);
+    acc[4] = c2;
+    const float dd1 = k1 * bw(c1) - A2 * k1 * l1;
+    const float dd2 = k2 * bw(c2) - A2 * k2 * l2;
+    const float dd3 = k3 * bw(c3) - A2 * k3 * l3;
+    float gr;
+    if (a.active == 2) gr = dd2 - dd3 + a.const_grad + a.fg * (float)hgt;
+    else gr = dd1 - dd3 + (chi ? 2.0f * a.beta * (c1 - 0.5f) : 0.0f);
+    a.grad[n] = gr;
+  }
+  double out[FE_K];
+  block_sum<FE_K>(acc, out);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid < FE_K) {
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    a.partials[b * FE_K + tid] = out[tid];
+  }
+}
+
+// Sum the per-block partials in block order; assemble E and the constraint.
+__global__ void fe_finalize_kernel(const double *partials, long long nb, double dP, double kcs,
+                                   double V0, double *energy, double *terms, double *dEcs) {
+  __shared__ double sh[FE_K][256];
+  double s[FE_K] = {0, 0, 0, 0, 0};
+  for (long long b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int k = 0; k < FE_K; k++) s[k] += partials[b * FE_K + k];
+  for (int k = 0; k < FE_K; k++) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < FE_K; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double V = sh[4][0];
+    const double Ecs = (kcs == 0.0) ? -dP * V : 0.5 * kcs * (V - V0) * (V - V0);
+    const double E = sh[0][0] + sh[1][0] + sh[2][0] + Ecs + sh[3][0];
+    if (energy) energy[0] = E;
+    if (terms) {
+      terms[0] = sh[0][0];
+      terms[1] = sh[1][0];
+      terms[2] = sh[2][0];
+      terms[3] = Ecs;
+      terms[4] = sh[3][0];
+      terms[5] = V;
+    }
+    dEcs[0] = (kcs == 0.0) ? -dP : kcs * (V - V0);
+  }
+}
+
+__global__ void add_dev_scalar_kernel(long long n, const double *c, float *g) {
+  const float v = (float)c[0];
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    g[k] += v;
+}
+
+static dim3 fe_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+static dim3 fe_grid(int kind, int nx, int ny, int nz) {
+  const dim3 b = fe_block(kind);
+  return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
+}
+
+long long fe_blocks(int kind, int nx, int ny, int nz) {
+  const dim3 g = fe_grid(kind, nx, ny, nz);
+  return (long long)g.x * g.y * g.z;
+}
+
+size_t fe_scratch_bytes(int kind, int nx, int ny, int nz) {
+  return (size_t)round_up(fe_blocks(kind, nx, ny, nz) * FE_K * sizeof(double), 256) + 256;
+}
+
+cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, double *energy,
+                      double *terms, void *scratch, cudaStream_t st) {
+  const long long nb = fe_blocks(kind, a.nx, a.ny, a.nz);
+  double *partials = (double *)scratch;
+  double *dEcs = (double *)((char *)scratch + round_up(nb * FE_K * sizeof(double), 256));
+  a.partials = partials;
+  a.const_grad = (kcs == 0.0) ? (float)(-dP) : 0.0f;
+  if (kind == 0) fe_kernel<0><<<fe_grid(0, a.nx, a.ny, a.nz), fe_block(0), 0, st>>>(a);
+  else fe_kernel<1><<<fe_grid(1, a.nx, a.ny, a.nz), fe_block(1), 0, st>>>(a);
+  fe_finalize_kernel<<<1, 256, 0, st>>>(partials, nb, dP, kcs, V0, energy, terms, dEcs);
+  if (kcs != 0.0 && a.active == 2) {
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    long long blocks = (N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    add_dev_scalar_kernel<<<(int)blocks, 256, 0, st>>>(N, dEcs, a.grad);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K6: L-BFGS vector kernels.  Fixed grid (VEC_BLOCKS x 256), grid-stride in a
+// fixed order, FP64 accumulation, block partials summed in block order: the
+// result does not depend on timing.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dot_kernel(long long n, const float *x, const float *y,
+                                                  double *partials) {
+  double s[1] = {0.0};
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    s[0] += (double)x[k] * (double)y[k];
+  double out[1];
+  block_sum<1>(s, out);
+  if (threadIdx.x == 0) partials[blockIdx.x] = out[0];
+}
+
+__global__ void dot_finalize_kernel(const double *partials, int nb, const double *scale,
+                                    double *out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (scale ? scale[0] : 1.0) * sh[0];
+}
+
+// y += sign * (a[0] - (b ? b[0] : 0)) * x
+__global__ void __launch_bounds__(256) axpy_dev_kernel(long long n, double sign, const double *a,
+                                                       const double *b, const float *x, float *y) {
+  const float c = (float)(sign * (a[0] - (b ? b[0] : 0.0)));
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] += c * x[k];
+}
+
+__global__ void __launch_bounds__(256) axpby_kernel(long long n, float a, const float *x, float b,
+                                                    float *y) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = (b == 0.0f) ? a * x[k] : a * x[k] + b * y[k];
+}
+
+// y = s[0] * x
+__global__ void __launch_bounds__(256) scale_dev_kernel(long long n, const double *s, const float *x,
+                                                        float *y) {
+  const float c = (float)s[0];
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = c * x[k];
+}
+
+static int vec_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < VEC_BLOCKS ? (b > 0 ? b : 1) : VEC_BLOCKS);
+}
+
+size_t vec_scratch_bytes(long long) { return VEC_BLOCKS * sizeof(double) + 256; }
+
+cudaError_t vec_dot(long long n, const float *x, const float *y, double *out, const double *scale,
+                    void *scratch, cudaStream_t st) {
+  double *partials = (double *)scratch;
+  const int g = vec_grid(n);
+  dot_kernel<<<g, 256, 0, st>>>(n, x, y, partials);
+  dot_finalize_kernel<<<1, 256, 0, st>>>(partials, g, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_axpy_dev(long long n, double sign, const double *a, const double *b,
+                         const float *x, float *y, cudaStream_t st) {
+  axpy_dev_kernel<<<vec_grid(n), 256, 0, st>>>(n, sign, a, b, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_axpby(long long n, double a, const float *x, double b, float *y, cudaStream_t st) {
+  axpby_kernel<<<vec_grid(n), 256, 0, st>>>(n, (float)a, x, (float)b, y);
+  return cudaGetLastError();
+}
+
+// Two-loop recursion (Nocedal & Wright Algorithm 7.4): r = -H g.
+cudaError_t lbfgs_direction(long long n, int m, const int *order, const float *S, const float *Y,
+                            const double *rho, const double *gamma, const float *g, float *r,
+                            double *alpha, void *scratch, cudaStream_t st) {
+  double *beta = (double *)((char *)scratch + VEC_BLOCKS * sizeof(double));
+  cudaError_t e;
+  // q = g (held in r)
+  axpby_kernel<<<vec_grid(n), 256, 0, st>>>(n, 1.0f, g, 0.0f, r);
+  for (int k = m - 1; k >= 0; k--) {  // newest to oldest
+    const long long s = order[k];
+    if ((e = vec_dot(n, S + s * n, r, alpha + k, rho + s, scratch, st)) != cudaSuccess) return e;
+    axpy_dev_kernel<<<vec_grid(n), 256, 0, st>>>(n, -1.0, alpha + k, nullptr, Y + s * n, r);
+  }
+  scale_dev_kernel<<<vec_grid(n), 256, 0, st>>>(n, gamma, r, r);
+  for (int k = 0; k < m; k++) {  // oldest to newest
+    const long long s = order[k];
+    if ((e = vec_dot(n, Y + s * n, r, beta, rho + s, scratch, st)) != cudaSuccess) return e;
+    axpy_dev_kernel<<<vec_grid(n), 256, 0, st>>>(n, 1.0, alpha + k, beta, S + s * n, r);
+  }
+  axpby_kernel<<<vec_grid(n), 256, 0, st>>>(n, -1.0f, r, 0.0f, r);
+  return cudaGetLastError();
+}
+
+}  // namespace dsm

@@ -1,0 +1,593 @@
+// dsm_lb_impl.cuh -- lattice Boltzmann kernels of the Diffuse Solid Method
+// (Sec. II.B of the paper), templated on lattice (D2Q9 / D3Q19), arithmetic
+// type T and population storage type S.  Each dsm_lb_<precision>.cu includes
+// this file and instantiates one storage type.
+//
+// State: POST-COLLISION populations f*, g* in two ping-pong buffers,
+// structure-of-arrays (plane i at offset i*pitch).  One step =
+//   moments pass   C(x) = sum_i g*_i(x - c_i)                       (K1)
+//   fused pass     pull f, g (interpolated bounce-back at the diffuse solid),
+//                  mu, forces, moments, BGK collision of f and g     (K2)
+// The fused pass needs C and C1 on the node's 1-neighbourhood only, because
+// the capillary force is taken in its potential form mu G[C] (see below).
+#pragma once
+
+#include "dsm_common.cuh"
+
+namespace dsm {
+
+enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_OBS = 2 };
+constexpr int OBS_K = 5;  // sum C, sum C1, kinetic, max |u|, nonfinite
+
+template <class T>
+__device__ __forceinline__ T bwell(T c) {
+  // d/dc [c^2 (1-c)^2 / 2] = c (1 - c)(1 - 2c)   (Sec. II.B)
+  return c * (T(1) - c) * (T(1) - T(2) * c);
+}
+
+// Periodic neighbourhood of node (x, y, z): linear index of x + c.
+struct Hood {
+  int ox[3], oy[3], oz[3];
+  __device__ __forceinline__ void init(int x, int y, int z, int nx, int ny, int nz) {
+    ox[0] = x == 0 ? nx - 1 : x - 1;
+    ox[1] = x;
+    ox[2] = x + 1 == nx ? 0 : x + 1;
+    int ym = y == 0 ? ny - 1 : y - 1, yp = y + 1 == ny ? 0 : y + 1;
+    oy[0] = ym * nx;
+    oy[1] = y * nx;
+    oy[2] = yp * nx;
+    int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
+    const int s = nx * ny;
+    oz[0] = zm * s;
+    oz[1] = z * s;
+    oz[2] = zp * s;
+  }
+  template <class L>
+  __device__ __forceinline__ int plus(int i) const {  // x + c_i
+    return ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
+  }
+  template <class L>
+  __device__ __forceinline__ int minus(int i) const {  // x - c_i
+    return ox[1 - L::cx(i)] + oy[1 - L::cy(i)] + oz[1 - L::cz(i)];
+  }
+};
+
+template <class T, class S>
+__device__ __forceinline__ T load_f(const S *base, long long off, int i, double w) {
+  if constexpr (Store<S>::k16) return T(w) + T(Store<S>::dec(base[off]));
+  else return T(Store<S>::dec(__ldg(base + off)));
+}
+template <class T, class S>
+__device__ __forceinline__ T load_g(const S *base, long long off) {
+  if constexpr (Store<S>::k16) return T(Store<S>::dec(base[off]));
+  else return T(__ldg(base + off));
+}
+
+// Link fraction of the interpolated bounce-back (Sec. II.B, Eq. [eqn:tanh] and
+// D = |x / (n.d)|): the fluid node sits x_s = 2 alpha_s artanh(2 C1 - 1) <= 0
+// from the C1 = 1/2 surface; along link i the wall is q |c_i| away with
+// q = |x_s / (n.d)| / |c_i|, n = G[C1]/|G[C1]|, d = c_i/|c_i|.  C1 is clamped to
+// [1e-9, 1/2]; a degenerate normal, a link not pointing into the solid or
+// q > 1 gives q = 1/2 (halfway bounce-back).
+template <class L, class T>
+__device__ __forceinline__ T link_q(T c1x, const T (&gc1)[3], int i, T alpha_s) {
+  T c = c1x < T(1e-9) ? T(1e-9) : (c1x > T(0.5) ? T(0.5) : c1x);
+  T xs = T(2) * alpha_s * atanh(T(2) * c - T(1));
+  T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
+  if (!(gn >= T(1e-12))) return T(0.5);
+  const int l2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+  T cl = l2 == 1 ? T(1) : sqrt(T(l2));
+  T nd = (gc1[0] * T(L::cx(i)) + gc1[1] * T(L::cy(i)) + gc1[2] * T(L::cz(i))) / (gn * cl);
+  if (!(nd > T(1e-6))) return T(0.5);
+  T q = fabs(xs / nd) / cl;
+  return q > T(1) ? T(0.5) : q;
+}
+
+// ---------------------------------------------------------------------------
+// K1: moments pass.  C(x) = sum_i g_i after streaming (Sec. II.B, C = sum g).
+// ---------------------------------------------------------------------------
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
+  using L = Lat<K>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init(x, y, z, a.nx, a.ny, a.nz);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
+    else s += load_g<T, S>(a.g_in, (long long)i * a.pitch + h.minus<L>(i));
+  }
+  a.C[n] = s;
+}
+
+// ---------------------------------------------------------------------------
+// K2: fused pass.  STAGE 2: fluids on the frozen diffuse solid C1.
+// STAGE 1: relaxation of C1 itself (g carries C1; rho = 1, tau = tau_g = 1,
+// every node fluid).  MODE_STEP collides and writes the next state;
+// MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
+// ---------------------------------------------------------------------------
+template <int K, class T, class S, int STAGE, int MODE>
+__global__ void __launch_bounds__(256) node_kernel(LBArgs<T, S> a, int field_sel) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  int z = blockIdx.z * blockDim.z + threadIdx.z;
+  const bool valid = x < a.nx && y < a.ny && z < a.nz;
+  if (MODE != MODE_OBS && !valid) return;
+  if (!valid) x = y = z = 0;
+  Hood h;
+  h.init(x, y, z, a.nx, a.ny, a.nz);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  const StepParams &P = a.p;
+
+  // ---- neighbourhood of C and C1: mu, G[C], G[rho], solid links ----------
+  T C, c1, mu, rho, tau, taug;
+  T gC[3] = {T(0), T(0), T(0)}, gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
+  unsigned nb_solid = 0;  // bit k: x + c_k is solid (stage 2)
+  {
+    T Cn[Q], C1n[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const int m = h.plus<L>(i);
+      Cn[i] = __ldg(a.C + m);
+      C1n[i] = (STAGE == 2) ? __ldg(a.C1 + m) : T(0);
+    }
+    C = Cn[0];
+    c1 = C1n[0];
+    T lapC = T(0), lapS = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+      const T w = T(L::w(i));
+      lapC += w * (Cn[i] - C);
+      if (STAGE == 2) lapS += w * ((C1n[i] + Cn[i]) - (c1 + C));
+      gC[0] += w * T(L::cx(i)) * Cn[i];
+      gC[1] += w * T(L::cy(i)) * Cn[i];
+      gC[2] += w * T(L::cz(i)) * Cn[i];
+    }
+    lapC *= T(6);  // 2 / c_s^2
+    lapS *= T(6);
+#pragma unroll
+    for (int d = 0; d < 3; d++) gC[d] *= T(3);  // 1 / c_s^2
+    if (STAGE == 2) {
+      // Chemical potential of the frozen-solid free energy (Sec. II.B,
+      // Eq. [eqn:fefrozen]), taken as its exact derivative in C2:
+      //   mu = k2 b(C) + k3 b(C1 + C) - a^2 k2 L[C] - a^2 k3 L[C1 + C]
+      mu = T(P.kappa2) * bwell(C) + T(P.kappa3) * bwell(c1 + C) -
+           T(P.a2 * P.kappa2) * lapC - T(P.a2 * P.kappa3) * lapS;
+      // density map rho = rho3 + (rho2 - rho3) C2/(C2 + C3), the ratio clamped
+      // to [0, 1] and 0 where C2 + C3 = 1 - C1 <= 1e-6 (inside the solid)
+      auto rho_of = [&](T cc, T s1) -> T {
+        const T den = T(1) - s1;
+        T ph = T(0);
+        if (den > T(1e-6)) {
+          ph = cc / den;
+          ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
+        }
+        return T(P.rho3) + T(P.rho2 - P.rho3) * ph;
+      };
+      rho = rho_of(C, c1);
+      if (P.rho_contrast) {
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+          const T r = T(L::w(i)) * rho_of(Cn[i], C1n[i]);
+          gR[0] += r * T(L::cx(i));
+          gR[1] += r * T(L::cy(i));
+          gR[2] += r * T(L::cz(i));
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) gR[d] *= T(3);
+      }
+      // relaxation time map tau = tau3 + (tau2 - tau3) H(C2 - C3), H(0) = 0
+      tau = (C - (T(1) - c1 - C) > T(0)) ? T(P.tau2) : T(P.tau3);
+      taug = T(P.tau_g);
+#pragma unroll
+      for (int i = 0; i < Q; i++) nb_solid |= (C1n[i] >= T(0.5) ? 1u : 0u) << i;
+      if ((nb_solid & ~1u) && !(nb_solid & 1u)) {
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+          const T w = T(L::w(i));
+          gc1[0] += w * T(L::cx(i)) * C1n[i];
+          gc1[1] += w * T(L::cy(i)) * C1n[i];
+          gc1[2] += w * T(L::cz(i)) * C1n[i];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) gc1[d] *= T(3);
+      }
+    } else {
+      // Solid relaxation (Sec. II.B, Eq. [Free Energy1] and its chemical
+      // potential): mu1 = (k1+k3) b(C1) - a^2 (k1+k3) L[C1]
+      //   + 2 beta (C1 - 1/2) chi + 2 Omega C1 H(-C1) - 2 Omega (1 - C1) H(C1 - 1)
+      // chi = 1 where the solid leaks out of S or the fluid into it (the
+      // printed case labels of Eq. [frozen:poly-quadratic_lbm] read swapped).
+      const T k13 = T(P.kappa1 + P.kappa3);
+      mu = k13 * bwell(C) - T(P.a2) * k13 * lapC;
+      const bool inS = a.mask[n] != 0;
+      if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += T(2 * P.beta) * (C - T(0.5));
+      if (C < T(0)) mu += T(2 * P.omega) * C;
+      if (C > T(1)) mu -= T(2 * P.omega) * (T(1) - C);
+      rho = T(1);
+      tau = T(1);
+      taug = T(1);
+    }
+  }
+  const bool solid_x = (STAGE == 2) && (nb_solid & 1u);
+
+  // ---- pull streaming ------------------------------------------------------
+  T f[Q], g[Q];
+#pragma unroll
+  for (int j = 0; j < Q; j++) {
+    if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
+    else g[j] = load_g<T, S>(a.g_in, (long long)j * a.pitch + h.minus<L>(j));
+  }
+  if (!solid_x) {
+#pragma unroll
+    for (int j = 0; j < Q; j++) {
+      const int i = L::opp(j);  // upstream x - c_j = x + c_i
+      if (STAGE == 1 || !((nb_solid >> i) & 1u)) {
+        f[j] = load_f<T, S>(a.f_in, (long long)j * a.pitch + h.minus<L>(j), j, L::w(j));
+      } else {
+        // interpolated bounce-back (linear, Bouzidi et al. 2001) on link i
+        const T q = link_q<L, T>(c1, gc1, i, T(P.alpha_s));
+        const T fi_x = load_f<T, S>(a.f_in, (long long)i * a.pitch + n, i, L::w(i));
+        if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
+          const T fi_z = load_f<T, S>(a.f_in, (long long)i * a.pitch + h.plus<L>(j), i, L::w(i));
+          f[j] = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
+        } else if (q < T(0.5)) {
+          f[j] = fi_x;  // no second fluid node: halfway rule
+        } else {
+          const T fj_x = load_f<T, S>(a.f_in, (long long)j * a.pitch + n, j, L::w(j));
+          f[j] = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
+        }
+      }
+    }
+  }
+
+  // ---- moments and forces --------------------------------------------------
+  // Capillary force in its potential form mu G[C] (the form of the printed
+  // velocity moment; it differs from -C G[mu] by the gradient G[C mu], a
+  // pressure shift) plus the body force on the liquid, one total F in both the
+  // forcing term and the velocity moment:
+  //   rho u = sum_i c_i f_i + F/2,   pt = sum_i f_i + u.G[rho]/2  (pt = P/c_s^2)
+  T u[3] = {T(0), T(0), T(0)}, pt = T(1), Fv[3];
+  Fv[0] = mu * gC[0];
+  Fv[1] = mu * gC[1];
+  Fv[2] = mu * gC[2];
+  if (STAGE == 2) {
+    Fv[0] += C * T(P.body[0]);
+    Fv[1] += C * T(P.body[1]);
+    Fv[2] += C * T(P.body[2]);
+  }
+  if (!solid_x) {
+    T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < Q; j++) {
+      m0 += f[j];
+      if (L::cx(j)) m1[0] += T(L::cx(j)) * f[j];
+      if (L::cy(j)) m1[1] += T(L::cy(j)) * f[j];
+      if (L::cz(j)) m1[2] += T(L::cz(j)) * f[j];
+    }
+    const T ir = T(1) / rho;
+    u[0] = (m1[0] + T(0.5) * Fv[0]) * ir;
+    u[1] = (m1[1] + T(0.5) * Fv[1]) * ir;
+    u[2] = (m1[2] + T(0.5) * Fv[2]) * ir;
+    pt = m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]);
+  }
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+
+  if constexpr (MODE == MODE_FIELDS) {
+    T v;
+    switch (field_sel) {
+      case DSM_FIELD_C1: v = (STAGE == 2) ? c1 : C; break;
+      case DSM_FIELD_C2: v = (STAGE == 2) ? C : T(0); break;
+      case DSM_FIELD_C3: v = T(1) - ((STAGE == 2) ? c1 + C : C); break;
+      case DSM_FIELD_MU: v = mu; break;
+      case DSM_FIELD_UX: v = u[0]; break;
+      case DSM_FIELD_UY: v = u[1]; break;
+      case DSM_FIELD_UZ: v = u[2]; break;
+      case DSM_FIELD_PT: v = pt; break;
+      case DSM_FIELD_RHO: v = rho; break;
+      default: v = tau; break;
+    }
+    a.fields[n] = v;
+    return;
+  }
+
+  if constexpr (MODE == MODE_OBS) {
+    double vals[OBS_K];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < Q; j++) bad |= !isfinite(g[j]) || (!solid_x && !isfinite(f[j]));
+    vals[0] = valid ? double(C) : 0.0;
+    vals[1] = valid ? double((STAGE == 2) ? c1 : C) : 0.0;
+    vals[2] = valid ? 0.5 * double(rho) * double(uu) : 0.0;
+    vals[3] = valid ? sqrt(double(uu)) : 0.0;
+    vals[4] = (valid && bad) ? 1.0 : 0.0;
+    // deterministic block reduction: warp shuffles then one shared pass
+    __shared__ double sh[OBS_K][32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < OBS_K; k++) {
+      double v = vals[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double w2 = __shfl_down_sync(0xffffffffu, v, o);
+        v = (k == 3 || k == 4) ? fmax(v, w2) : v + w2;
+      }
+      if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (tid < OBS_K) {
+      double v = sh[tid][0];
+      for (int w2 = 1; w2 < nw; w2++) v = (tid == 3 || tid == 4) ? fmax(v, sh[tid][w2]) : v + sh[tid][w2];
+      const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+      a.partials[b * OBS_K + tid] = v;
+    }
+    return;
+  }
+
+  // ---- BGK collision (Sec. II.B) -------------------------------------------
+  //   s_i = c_i.u/c_s^2 + (c_i.u)^2/(2 c_s^4) - u.u/(2 c_s^2)
+  //   f_eq_i = w_i (pt + rho s_i)                                 Eq. [eqn:feq]
+  //   F_i = (1 - 1/(2 tau)) w_i [((c_i - u).G[rho]) s_i + c_i.F/c_s^2]
+  //                                                       Eq. [eqn:hydroforce]
+  //   g_eq_i = w_i (mu + C s_i) (i != 0),  g_eq_0 = C - (1 - w_0) mu + w_0 C s_0
+  // (the minus signs read where the printed forms would break sum f_eq = pt and
+  // sum g_eq = C).  Solid nodes: f* = w_i; g collides with u = 0.
+  if (!isfinite(pt + mu + u[0] + u[1] + u[2])) atomicOr(a.err, ERR_NONFINITE);
+  const T omf = T(1) / tau, omg = T(1) / taug;
+  const T kF = T(1) - T(0.5) * omf;
+  const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
+  T gsum16 = T(0);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const T w = T(L::w(i));
+    const T cu = T(L::cx(i)) * u[0] + T(L::cy(i)) * u[1] + T(L::cz(i)) * u[2];
+    const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+    const long long off = (long long)i * a.pitch + n;
+    // f
+    T fo;
+    if (solid_x) {
+      fo = w;
+    } else {
+      const T feq = w * (pt + rho * s);
+      const T cg = T(L::cx(i)) * gR[0] + T(L::cy(i)) * gR[1] + T(L::cz(i)) * gR[2] - ug;
+      const T cF = T(L::cx(i)) * Fv[0] + T(L::cy(i)) * Fv[1] + T(L::cz(i)) * Fv[2];
+      const T Fi = kF * w * (cg * s + T(3) * cF);
+      fo = f[i] - (f[i] - feq) * omf + Fi;
+    }
+    if constexpr (Store<S>::k16) a.f_out[off] = Store<S>::enc(float(fo - w));
+    else a.f_out[off] = S(fo);
+    // g
+    const T geq = (i == 0) ? C - (T(1) - w) * mu + w * C * s : w * (mu + C * s);
+    const T go = g[i] - (g[i] - geq) * omg;
+    if constexpr (Store<S>::k16) {
+      if (i > 0) {
+        const S e = Store<S>::enc(float(go));
+        a.g_out[off] = e;
+        gsum16 += T(Store<S>::dec(e));
+      }
+    } else {
+      a.g_out[off] = S(go);
+    }
+  }
+  // 16-bit storage: the rest population takes the rounding of the others so
+  // that sum_i g*_i = C holds at every node (sum_i g_eq_i = C, so the exact
+  // post-collision sum is C) and the liquid mass is conserved.
+  if constexpr (Store<S>::k16) a.g0_out[n] = float(C - gsum16);
+}
+
+// ---------------------------------------------------------------------------
+// K3: initial state at rest (reading of the unstated initial condition):
+// f_i = w_i, g_i = g_eq_i(C, mu(C), u = 0), stored as the post-collision state.
+// ---------------------------------------------------------------------------
+template <int K, class T, class S, int STAGE>
+__global__ void __launch_bounds__(256) init_kernel(LBArgs<T, S> a, const T *cfield) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init(x, y, z, a.nx, a.ny, a.nz);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  const StepParams &P = a.p;
+  const T C = cfield[n];
+  const T c1 = (STAGE == 2) ? a.C1[n] : T(0);
+  T lapC = T(0), lapS = T(0);
+#pragma unroll
+  for (int i = 1; i < Q; i++) {
+    const int m = h.plus<L>(i);
+    const T w = T(L::w(i));
+    lapC += w * (cfield[m] - C);
+    if (STAGE == 2) lapS += w * ((a.C1[m] + cfield[m]) - (c1 + C));
+  }
+  lapC *= T(6);
+  lapS *= T(6);
+  T mu;
+  if (STAGE == 2) {
+    mu = T(P.kappa2) * bwell(C) + T(P.kappa3) * bwell(c1 + C) - T(P.a2 * P.kappa2) * lapC -
+         T(P.a2 * P.kappa3) * lapS;
+  } else {
+    const T k13 = T(P.kappa1 + P.kappa3);
+    mu = k13 * bwell(C) - T(P.a2) * k13 * lapC;
+    const bool inS = a.mask[n] != 0;
+    if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += T(2 * P.beta) * (C - T(0.5));
+    if (C < T(0)) mu += T(2 * P.omega) * C;
+    if (C > T(1)) mu -= T(2 * P.omega) * (T(1) - C);
+  }
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const T w = T(L::w(i));
+    const long long off = (long long)i * a.pitch + n;
+    if constexpr (Store<S>::k16) a.f_out[off] = Store<S>::enc(0.0f);
+    else a.f_out[off] = S(w);
+    const T geq = (i == 0) ? C - (T(1) - w) * mu : w * mu;
+    if constexpr (Store<S>::k16) {
+      if (i > 0) a.g_out[off] = Store<S>::enc(float(geq));
+    } else {
+      a.g_out[off] = S(geq);
+    }
+  }
+  if constexpr (Store<S>::k16) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; i++) s += T(Store<S>::dec(a.g_out[(long long)i * a.pitch + n]));
+    a.g0_out[n] = float(C - s);
+  }
+}
+
+// K7: analytic solid.  C1 = 1/2 + tanh(d / (2 alpha_s)) / 2 from the signed
+// distance d (positive inside S): the planar profile of Sec. II.A,
+// Eq. [frozen:interface_profile].
+template <class T>
+__global__ void __launch_bounds__(256) solid_profile_kernel(const T *sd, T *c1, long long N,
+                                                            T alpha_s) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < N;
+       k += (long long)gridDim.x * blockDim.x)
+    c1[k] = T(0.5) + T(0.5) * tanh(sd[k] / (T(2) * alpha_s));
+}
+
+// Population codecs (test/checkpoint path): storage <-> reals, q-major N-stride.
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) pops_get_kernel(LBArgs<T, S> a, T *fo, T *go) {
+  using L = Lat<K>;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+      const long long off = (long long)i * a.pitch + k;
+      if constexpr (Store<S>::k16) {
+        fo[i * a.N + k] = T(L::w(i)) + T(Store<S>::dec(a.f_in[off]));
+        go[i * a.N + k] = (i == 0) ? T(a.g0_in[k]) : T(Store<S>::dec(a.g_in[off]));
+      } else {
+        fo[i * a.N + k] = T(a.f_in[off]);
+        go[i * a.N + k] = T(a.g_in[off]);
+      }
+    }
+  }
+}
+
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *fi, const T *gi) {
+  using L = Lat<K>;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gridDim.x * blockDim.x) {
+    T gs = T(0), g0 = T(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+      const long long off = (long long)i * a.pitch + k;
+      const T fv = fi[i * a.N + k], gv = gi[i * a.N + k];
+      if constexpr (Store<S>::k16) {
+        a.f_out[off] = Store<S>::enc(float(fv - T(L::w(i))));
+        if (i == 0) {
+          g0 = gv;
+        } else {
+          a.g_out[off] = Store<S>::enc(float(gv));
+          gs += T(Store<S>::dec(a.g_out[off])) - gv;
+        }
+      } else {
+        a.f_out[off] = S(fv);
+        a.g_out[off] = S(gv);
+      }
+    }
+    // 16-bit: keep the node's sum of g as given
+    if constexpr (Store<S>::k16) a.g0_out[k] = float(g0 - gs);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: typed launchers behind a type-erased table.
+// ---------------------------------------------------------------------------
+inline dim3 lb_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+inline dim3 lb_grid(int kind, int nx, int ny, int nz) {
+  const dim3 b = lb_block(kind);
+  return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
+}
+
+template <class T, class S>
+LBArgs<T, S> typed(const LBRaw &r) {
+  LBArgs<T, S> a;
+  a.nx = r.nx; a.ny = r.ny; a.nz = r.nz; a.N = r.N; a.pitch = r.pitch;
+  a.f_in = (const S *)r.f_in; a.g_in = (const S *)r.g_in; a.g0_in = r.g0_in;
+  a.f_out = (S *)r.f_out; a.g_out = (S *)r.g_out; a.g0_out = r.g0_out;
+  a.C = (T *)r.C; a.C1 = (const T *)r.C1; a.mask = r.mask;
+  a.fields = (T *)r.out; a.partials = r.partials; a.err = r.err; a.p = r.p;
+  return a;
+}
+
+template <int K, class T, class S>
+struct LBOps {
+  static cudaError_t moments(const LBRaw &r, cudaStream_t st) {
+    moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r));
+    return cudaGetLastError();
+  }
+  template <int STAGE, int MODE>
+  static void node_launch(const LBRaw &r, cudaStream_t st) {
+    node_kernel<K, T, S, STAGE, MODE>
+        <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
+  }
+  static cudaError_t node(const LBRaw &r, int stage, int mode, cudaStream_t st) {
+    if (stage == 2) {
+      if (mode == MODE_STEP) node_launch<2, MODE_STEP>(r, st);
+      else if (mode == MODE_FIELDS) node_launch<2, MODE_FIELDS>(r, st);
+      else node_launch<2, MODE_OBS>(r, st);
+    } else {
+      if (mode == MODE_STEP) node_launch<1, MODE_STEP>(r, st);
+      else if (mode == MODE_FIELDS) node_launch<1, MODE_FIELDS>(r, st);
+      else node_launch<1, MODE_OBS>(r, st);
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t init(const LBRaw &r, const void *cfield, int stage, cudaStream_t st) {
+    if (stage == 2)
+      init_kernel<K, T, S, 2><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(
+          typed<T, S>(r), (const T *)cfield);
+    else
+      init_kernel<K, T, S, 1><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(
+          typed<T, S>(r), (const T *)cfield);
+    return cudaGetLastError();
+  }
+  static cudaError_t solid(const void *sd, void *c1, long long N, double alpha_s, cudaStream_t st) {
+    const int blocks = (int)((N + 255) / 256 < 152 * 32 ? (N + 255) / 256 : 152 * 32);
+    solid_profile_kernel<T><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((const T *)sd, (T *)c1, N,
+                                                                     T(alpha_s));
+    return cudaGetLastError();
+  }
+  static cudaError_t get_pops(const LBRaw &r, void *fo, void *go, cudaStream_t st) {
+    const int blocks = (int)((r.N + 255) / 256 < 152 * 32 ? (r.N + 255) / 256 : 152 * 32);
+    pops_get_kernel<K, T, S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(typed<T, S>(r), (T *)fo,
+                                                                      (T *)go);
+    return cudaGetLastError();
+  }
+  static cudaError_t set_pops(const LBRaw &r, const void *fi, const void *gi, cudaStream_t st) {
+    const int blocks = (int)((r.N + 255) / 256 < 152 * 32 ? (r.N + 255) / 256 : 152 * 32);
+    pops_set_kernel<K, T, S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(typed<T, S>(r),
+                                                                      (const T *)fi, (const T *)gi);
+    return cudaGetLastError();
+  }
+  static LBTable table() {
+    LBTable t;
+    t.moments = &moments;
+    t.node = &node;
+    t.init = &init;
+    t.solid = &solid;
+    t.get_pops = &get_pops;
+    t.set_pops = &set_pops;
+    t.q = Lat<K>::Q;
+    t.real_bytes = sizeof(T);
+    t.store_bytes = sizeof(S);
+    t.k16 = Store<S>::k16;
+    return t;
+  }
+};
+
+}  // namespace dsm

@@ -1,0 +1,129 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that
+include/dsm.h declares, and its host-side logic (argument checks, kappa mapping,
+lattice tables, workspace sizing) is right.  No compute call is made."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_19941_gb300.build import build
+    build()
+    from paper_2504_19941_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(dsm_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    L = lib.load()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared <= set(lib.EXPORTED), declared - set(lib.EXPORTED)
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.status_string(s) not in ("", "unknown status")
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_lattice_table_matches_oracle(lib, kind):
+    c, w = lib.dsm_lattice_table(kind)
+    co, wo = O.lattice(kind)
+    got = sorted(zip(map(tuple, c), w))
+    ref = sorted(zip(map(tuple, co), wo))
+    assert len(got) == len(ref)
+    for (ca, wa), (cb, wb) in zip(got, ref):
+        assert ca == tuple(cb) and abs(wa - wb) < 1e-17
+    if kind == 0:  # the paper's D2Q9 order is kept
+        assert [tuple(x) for x in c] == [tuple(x) for x in co]
+
+
+def test_kappa_matches_oracle(lib):
+    import paper_2504_19941_gb300 as P
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        th, g23, g12, a = rng.uniform(5, 175), rng.uniform(1e-3, 1), rng.uniform(1e-3, 1), \
+            rng.uniform(0.5, 2)
+        p = P.make_params("D3Q19", (4, 4, 4), theta_deg=th, g23=g23, g12=g12, alpha=a)
+        k_ref, rc = O.kappa_from_angle(th, g23, g12, a)
+        if rc != 0:
+            with pytest.raises(P.DSMError):
+                lib.dsm_kappa(p)
+            continue
+        np.testing.assert_allclose(lib.dsm_kappa(p), k_ref, rtol=1e-13, atol=1e-16)
+    p = P.make_params("D2Q9", (4, 4), g12=0.3, g13=0.5, g23=0.4)
+    np.testing.assert_allclose(lib.dsm_kappa(p), O.kappa_from_tensions(0.3, 0.5, 0.4)[0])
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(0, 4, 4)), dict(shape=(4, -1, 4)), dict(lattice="D2Q9", shape=(4, 4, 2)),
+    dict(tau2=0.5), dict(tau_g=0.4), dict(rho3=0.0), dict(theta_deg=180.0),
+    dict(precision=7), dict(alpha=0.0), dict(shape=(2048, 2048, 1024)), dict(alpha_s=-1.0)])
+def test_invalid_parameters_rejected(lib, bad):
+    import paper_2504_19941_gb300 as P
+    kw = dict(lattice="D3Q19", shape=(8, 8, 8), theta_deg=90.0)
+    kw.update(bad)
+    lat, shape = kw.pop("lattice"), kw.pop("shape")
+    prec = kw.pop("precision", "f32")
+    p = P.make_params(lat, shape, prec, **kw)
+    with pytest.raises(P.DSMError) as e:
+        lib.dsm_workspace_bytes(p)
+    assert e.value.status == lib.DSM_E_INVAL
+
+
+@pytest.mark.parametrize("prec,sb,extra", [("f64", 8, 0), ("f32", 4, 0), ("bf16", 2, 1),
+                                           ("f16", 2, 1)])
+def test_workspace_size(lib, prec, sb, extra):
+    import paper_2504_19941_gb300 as P
+    shape = (37, 29, 23)
+    n = 37 * 29 * 23
+    p = P.make_params("D3Q19", shape, prec, theta_deg=100.0)
+    nbytes = lib.dsm_workspace_bytes(p)
+    pops = 4 * 19 * n * sb + extra * 2 * 4 * n
+    assert pops <= nbytes <= pops + 2 * n * (8 if prec == "f64" else 4) + n + 10 * 2 ** 16
+
+
+def test_create_rejects_bad_workspace_without_touching_the_gpu(lib):
+    import paper_2504_19941_gb300 as P
+    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90)
+    nb = lib.dsm_workspace_bytes(p)
+    for ptr, size in [(None, nb), (4096, nb - 1), (4096 + 16, nb)]:
+        with pytest.raises(P.DSMError) as e:
+            lib.dsm_create(p, ptr, size, stream=0)
+        assert e.value.status == lib.DSM_E_WORKSPACE
+
+
+def test_scratch_sizes(lib):
+    assert lib.dsm_fe_scratch_bytes(1, 128, 128, 128) >= 8 * 5 * (128 // 32) * (128 // 4) * 64
+    assert lib.dsm_vec_scratch_bytes(10 ** 7) >= 8 * 152 * 4
+    import paper_2504_19941_gb300 as P
+    with pytest.raises(P.DSMError):
+        lib.dsm_fe_scratch_bytes(0, 4, 4, 2)
+
+
+def test_null_arguments_rejected(lib):
+    L = lib.load()
+    assert L.dsm_step(None, 1) == lib.DSM_E_INVAL
+    assert L.dsm_destroy(None) == lib.DSM_E_INVAL
+    assert L.dsm_get_observables(None, None) == lib.DSM_E_INVAL
+    assert L.dsm_batch_step(None, 1, None) == lib.DSM_E_INVAL

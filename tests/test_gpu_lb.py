@@ -1,0 +1,294 @@
+"""GPU parity of the lattice Boltzmann step: the CUDA library (through its C ABI)
+against the FP64 oracle on the same seeded inputs.
+
+Tolerances (parity metric max|a-b| / max|b| per field):
+  FP64 path ...... 1e-12 on every field and population (steps 1, 10, 2000 of the
+                   128x64 D2Q9 wall-drop case; D3Q19 small cases)
+  FP32 path ...... 1e-5 on C and pt, 2e-4 on u, 1e-5 on populations, after
+                   50 steps of a ragged D3Q19 case (FP32 rounding of the
+                   velocity moment, a sum of nineteen O(0.05) terms whose result
+                   is O(1e-4), bounds the relative velocity error)
+Sampled parity at the full 256x256x192 size recomputes single nodes with the
+oracle on 9^3 periodic blocks (a node's post-collision state depends only on
+the state within distance 3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from oracle import analysis as A
+
+from dsm_helpers import (compare, direction_map, gpu_fields, gpu_lattice, gpu_pops,
+                         oracle_params, rel_err)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2504_19941_gb300 as P  # noqa: E402
+
+
+def _oracle_case(case, kind):
+    p = oracle_params(case, kind)
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+    f, g = O.lb_init(p, 2, c1, case.c2)
+    return p, c1, f, g
+
+
+def _oracle_fields(p, c1, f, g):
+    return O.lb_fields(p, 2, c1, f, g)
+
+
+# ---------------------------------------------------------------- FP64 D2Q9
+def test_wall_drop_fp64_parity():
+    case = S.wall_drop_2d()
+    perm = direction_map(O.D2Q9)
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, O.D2Q9)
+    # C1 from the signed distance
+    assert rel_err(lat.field("C1").cpu().numpy(), c1) < 1e-14
+    # initial state
+    gf, gg = gpu_pops(lat, perm)
+    assert rel_err(gf, f) < 1e-15 and rel_err(gg, g) < 1e-14
+    done = 0
+    obs0 = lat.observables()
+    for upto in (1, 10, 2000):
+        lat.step(upto - done)
+        f, g = O.lb_run(p, 2, c1, f, g, upto - done)
+        done = upto
+        errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g), ("C", "mu", "ux", "uy", "pt"))
+        gf, gg = gpu_pops(lat, perm)
+        errs["f"], errs["g"] = rel_err(gf, f), rel_err(gg, g)
+        assert max(errs.values()) < 1e-12, (upto, errs)
+    obs = lat.observables()
+    assert obs["step"] == 2000
+    assert abs(obs["mass_c2"] - obs0["mass_c2"]) / obs0["mass_c2"] < 1e-12
+    ob_or = O.observables(p, c1, f, g)
+    assert abs(obs["mass_c2"] - ob_or["mass_c2"]) / ob_or["mass_c2"] < 1e-12
+    assert abs(obs["kinetic"] - ob_or["kinetic"]) / ob_or["kinetic"] < 1e-9
+    # contact angle of both after 2000 steps, measured the same way
+    ny, nx = case.shape[1], case.shape[0]
+    th_g = A.contact_angle_flat(lat.field("C2").cpu().numpy().reshape(ny, nx), c1.reshape(ny, nx))
+    th_o = A.contact_angle_flat(_oracle_fields(p, c1, f, g)["C"].reshape(ny, nx),
+                                c1.reshape(ny, nx))
+    assert abs(th_g - th_o) < 0.5
+
+
+# ---------------------------------------------------------------- D3Q19 small
+def _small_3d(shape=(37, 29, 23), theta=120.0, g=0.01, body=(2e-6, -1e-6, -5e-6)):
+    nx, ny, nz = shape
+    sd = S.pillars_sd(shape, 4, 6, 16, 8, offset=3)
+    a_s = S.width_to_alpha(3.0)
+    c2 = S.layer_c2(shape, 2, 12, 19, 1.0, sd, a_s) + \
+        S.drop_c2(shape, (nx / 2, ny / 2, 8.0), 5.0, 1.0, sd, a_s) * 0.5
+    c2 = c2.ravel() + S.perturbation(3, nx * ny * nz)
+    return S.Case("small3d", "D3Q19", shape, sd.ravel(), c2, theta_deg=theta, g23=g, g12=g,
+                  alpha_s=a_s, body=body)
+
+
+def test_d3q19_fp64_parity():
+    case = _small_3d()
+    perm = direction_map(O.D3Q19)
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, O.D3Q19)
+    lat.step(20)
+    f, g = O.lb_run(p, 2, c1, f, g, 20)
+    errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    gf, gg = gpu_pops(lat, perm)
+    errs["f"], errs["g"] = rel_err(gf, f), rel_err(gg, g)
+    assert max(errs.values()) < 1e-12, errs
+
+
+def test_d3q19_fp32_parity():
+    case = _small_3d()
+    perm = direction_map(O.D3Q19)
+    lat = gpu_lattice(case, "f32")
+    p, c1, f, g = _oracle_case(case, O.D3Q19)
+    lat.step(50)
+    f, g = O.lb_run(p, 2, c1, f, g, 50)
+    e = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    gf, gg = gpu_pops(lat, perm)
+    assert e["C"] < 1e-5 and e["pt"] < 1e-5 and e["mu"] < 1e-4, e
+    assert max(e["ux"], e["uy"], e["uz"]) < 2e-4, e
+    assert rel_err(gf, f) < 1e-5 and rel_err(gg, g) < 1e-5
+
+
+def test_density_viscosity_contrast_fp64():
+    case = _small_3d(shape=(20, 18, 16), body=(0.0, 0.0, -1e-5))
+    case.rho2, case.rho3, case.tau2, case.tau3, case.tau_g = 1.0, 0.5, 1.0, 0.7, 0.8
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, O.D3Q19)
+    lat.step(15)
+    f, g = O.lb_run(p, 2, c1, f, g, 15)
+    errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    assert max(errs.values()) < 1e-12, errs
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 1), (1, 5), (5, 4)])
+def test_tiny_2d_lattices_fp64(shape):
+    # degenerate periodic sizes: every neighbour may be the node itself
+    n = shape[0] * shape[1]
+    sd = np.full(n, -3.0)
+    sd[0] = 1.0
+    c2 = 0.3 + S.perturbation(1, n, 0.2)
+    case = S.Case("tiny", "D2Q9", shape, sd, c2, theta_deg=70.0, g23=0.01, g12=0.01,
+                  alpha_s=1.0, body=(1e-4, -1e-4, 0.0))
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, O.D2Q9)
+    lat.step(7)
+    f, g = O.lb_run(p, 2, c1, f, g, 7)
+    perm = direction_map(O.D2Q9)
+    gf, gg = gpu_pops(lat, perm)
+    assert rel_err(gf, f) < 1e-12 and rel_err(gg, g) < 1e-12
+
+
+def test_no_solid_and_pure_gas():
+    # degenerate inputs: no solid anywhere (C1 = 0), and no liquid (C2 = 0)
+    shape = (16, 12, 10)
+    n = 16 * 12 * 10
+    for c2 in (S.drop_c2(shape, (8, 6, 5), 4.0).ravel(), np.zeros(n)):
+        case = S.Case("deg", "D3Q19", shape, np.full(n, -50.0), c2, theta_deg=90.0, g23=0.01,
+                      g12=0.01, alpha_s=1.0)
+        lat = gpu_lattice(case, "f64")
+        p, c1, f, g = _oracle_case(case, O.D3Q19)
+        lat.step(10)
+        f, g = O.lb_run(p, 2, c1, f, g, 10)
+        perm = direction_map(O.D3Q19)
+        gf, gg = gpu_pops(lat, perm)
+        assert rel_err(gf, f) < 1e-12 and rel_err(gg, g) < 1e-12
+
+
+# ---------------------------------------------------------------- stage 1
+@pytest.mark.parametrize("kind,shape", [(O.D2Q9, (24, 20)), (O.D3Q19, (14, 12, 10))])
+def test_solid_relaxation_fp64_parity(kind, shape):
+    n = int(np.prod(shape))
+    d = len(shape)
+    sd = S.slab_sd(shape, d - 1, 0, 5) if d == 2 else S.sphere_sd(shape, (7, 6, 5), 3.5)
+    Smask = (sd.ravel() > 0).astype(np.uint8)
+    k, _ = O.kappa_from_angle(60.0, 0.01, 0.01)
+    beta, omega = 1e-3, 2e-4
+    po = O.make_params(kind, shape, k, beta=beta, omega=omega)
+    f, g = O.lb_init(po, 1, None, Smask.astype(float), S=Smask)
+    f, g = O.lb_run(po, 1, None, f, g, 300, S=Smask)
+    c1_o = O.lb_fields(po, 1, None, f, g, S=Smask)["C"]
+    pp = P.make_params("D2Q9" if d == 2 else "D3Q19", shape, "f64", theta_deg=60.0, g12=0.01,
+                       g23=0.01)
+    lat = P.Lattice(pp)
+    lat.set_solid_c1(torch.as_tensor(Smask.astype(float), device="cuda"))
+    lat.relax_solid(torch.as_tensor(Smask, device="cuda"), 300, beta, omega)
+    c1_g = lat.field("C1").cpu().numpy()
+    assert rel_err(c1_g, c1_o) < 1e-12
+
+
+# ---------------------------------------------------------------- full size
+def _block_indices(shape, centre, r=4):
+    nx, ny, nz = shape
+    x0, y0, z0 = centre
+    xs = (np.arange(x0 - r, x0 + r + 1) % nx)
+    ys = (np.arange(y0 - r, y0 + r + 1) % ny)
+    zs = (np.arange(z0 - r, z0 + r + 1) % nz)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return (X + nx * (Y + ny * Z)).ravel()
+
+
+def test_full_size_sampled_fp32():
+    case = S.pillar_slab_3d()
+    shape = case.shape
+    perm = direction_map(O.D3Q19)
+    lat = gpu_lattice(case, "f32")
+    lat.step(30)
+    q = 19
+    f_before, g_before = lat.populations()
+    c1_full = lat.field("C1")
+    lat.step(1)
+    f_after, g_after = lat.populations()
+    obs = lat.observables()
+    assert obs["nonfinite"] == 0
+    rng = np.random.default_rng(0)
+    nx, ny, nz = shape
+    # samples: random nodes plus nodes next to a pillar top and the base plate
+    pts = [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz)))
+           for _ in range(12)]
+    pts += [(16, 16, 38), (11, 16, 20), (16, 11, 20), (3, 3, 8), (255, 0, 191), (0, 255, 37)]
+    po = oracle_params(case, O.D3Q19)
+    po.nx = po.ny = po.nz = 9
+    inv = np.empty(q, dtype=int)
+    inv[perm] = np.arange(q)
+    worst_f = worst_g = 0.0
+    for (x, y, z) in pts:
+        idx = torch.as_tensor(_block_indices(shape, (x, y, z)), device="cuda")
+        n_all = nx * ny * nz
+        fb = f_before.view(q, n_all)[:, idx].double().cpu().numpy()[inv]
+        gb = g_before.view(q, n_all)[:, idx].double().cpu().numpy()[inv]
+        c1b = c1_full[idx].double().cpu().numpy()
+        fo, go = O.lb_run(po, 2, c1b, fb, gb, 1)
+        centre = x + nx * (y + ny * z)
+        fa = f_after.view(q, n_all)[:, centre].double().cpu().numpy()[inv]
+        ga = g_after.view(q, n_all)[:, centre].double().cpu().numpy()[inv]
+        c = 4 + 9 * (4 + 9 * 4)
+        worst_f = max(worst_f, np.max(np.abs(fa - fo[:, c])))
+        worst_g = max(worst_g, np.max(np.abs(ga - go[:, c])))
+    assert worst_f < 2e-7 and worst_g < 2e-7, (worst_f, worst_g)
+
+
+def test_full_size_mass_conservation_fp32():
+    case = S.pillar_slab_3d()
+    lat = gpu_lattice(case, "f32")
+    m0 = lat.observables()["mass_c2"]
+    lat.step(200)
+    ob = lat.observables()
+    assert ob["nonfinite"] == 0
+    assert abs(ob["mass_c2"] - m0) / m0 < 1e-5
+
+
+# ---------------------------------------------------------------- state, errors
+def test_state_roundtrip_bitwise():
+    case = _small_3d(shape=(20, 18, 16))
+    a = gpu_lattice(case, "f32")
+    a.step(10)
+    f, g = a.populations()
+    a.step(10)
+    ref = a.populations()
+    b = gpu_lattice(case, "f32")
+    b.set_populations(f, g)
+    b.step(10)
+    out = b.populations()
+    assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1])
+
+
+def test_nonfinite_is_reported():
+    case = _small_3d(shape=(12, 10, 8))
+    lat = gpu_lattice(case, "f32")
+    f, g = lat.populations()
+    f[5] = float("nan")
+    lat.set_populations(f, g)
+    lat.step(2)
+    ob = lat.observables(check=False)
+    assert ob["nonfinite"] == 1 and ob["status"] == P._lib.DSM_E_NONFINITE
+    with pytest.raises(P.DSMError):
+        lat.step(1)  # latched until the state is reset
+    lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float32, device="cuda"))
+    lat.step(1)
+    assert lat.observables()["nonfinite"] == 0
+
+
+def test_workspace_checks():
+    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90)
+    nb = P._lib.dsm_workspace_bytes(p)
+    ws = torch.empty(nb + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.DSMError) as e:
+        P._lib.dsm_create(p, ws, nb - 1)
+    assert e.value.status == P._lib.DSM_E_WORKSPACE
+    with pytest.raises(P.DSMError) as e:
+        P._lib.dsm_create(p, ws.data_ptr() + 16, nb)
+    assert e.value.status == P._lib.DSM_E_WORKSPACE
+    h = P._lib.dsm_create(p, ws, nb)
+    with pytest.raises(P.DSMError) as e:
+        P._lib.dsm_step(h, 1)  # no fluid yet
+    assert e.value.status == P._lib.DSM_E_STATE
+    P._lib.dsm_destroy(h)
