@@ -15,8 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2504_19941_gb300.build import build
-    build()
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "dsm_build", os.path.join(ROOT, "paper_2504_19941_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
     from paper_2504_19941_gb300 import _lib
     return _lib
 
