@@ -64,7 +64,14 @@ def test_wall_drop_fp64_parity():
         errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g), ("C", "mu", "ux", "uy", "pt"))
         gf, gg = gpu_pops(lat, perm)
         errs["f"], errs["g"] = rel_err(gf, f), rel_err(gg, g)
-        assert max(errs.values()) < 1e-12, (upto, errs)
+        if upto == 1:
+            assert max(errs.values()) < 1e-14, (upto, errs)
+        # FP64 floor of the velocity: u (~1e-4) is a cancelling sum of O(0.1)
+        # populations; the oracle built with and without FMA contraction differs
+        # from itself by 1.0e-12 in u_y at step 2000 (7.7e-14 at step 10)
+        tol_u = 1e-12 if upto <= 10 else 5e-12
+        assert max(errs["ux"], errs["uy"]) < tol_u, (upto, errs)
+        assert max(v for k_, v in errs.items() if k_ not in ("ux", "uy")) < 1e-12, (upto, errs)
     obs = lat.observables()
     assert obs["step"] == 2000
     assert abs(obs["mass_c2"] - obs0["mass_c2"]) / obs0["mass_c2"] < 1e-12
@@ -265,7 +272,10 @@ def test_nonfinite_is_reported():
     case = _small_3d(shape=(12, 10, 8))
     lat = gpu_lattice(case, "f32")
     f, g = lat.populations()
-    f[5] = float("nan")
+    n = 12 * 10 * 8
+    fluid = 1 + 12 * (1 + 10 * 6)  # above the base plate, beside a pillar
+    assert lat.field("C1")[fluid].item() < 0.5
+    f[2 * n + fluid] = float("nan")
     lat.set_populations(f, g)
     lat.step(2)
     ob = lat.observables(check=False)
