@@ -99,9 +99,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_case():
+def make_case(shape):
     import synthetic as S
-    return S.pillar_slab_3d(*SHAPE)
+    if tuple(shape) == SHAPE:
+        return S.pillar_slab_3d(*SHAPE)
+    nz = shape[2]
+    return S.pillar_slab_3d(*shape, liquid=(38, min(98, nz - 4)))
 
 
 def cpu_baseline(max_seconds=15.0):
@@ -166,8 +169,9 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    case = make_case()
-    params = P.make_params("D3Q19", SHAPE, "f32", theta_deg=case.theta_deg, g12=case.g12,
+    shape = tuple(int(v) for v in args.shape.split(","))
+    case = make_case(shape)
+    params = P.make_params("D3Q19", shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
                            g23=case.g23, alpha_s=case.alpha_s)
     lat = P.Lattice(params, device=dev)
     sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
@@ -256,7 +260,9 @@ def run_gpu(args, rank, world):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": WORKLOAD, "lattice": "D3Q19", "nodes": n,
+               "config": {"workload": WORKLOAD if shape == SHAPE else
+                          f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)",
+                          "lattice": "D3Q19", "nodes": n,
                           "global_batch": world, "parallelism": f"replicas x{world}",
                           "l2": "inputs (3.9 GB populations) larger than L2; no flush"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -280,6 +286,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="dsm", choices=["dsm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
+                    help="lattice size nx,ny,nz (default: the benchmark workload)")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", "0"))
