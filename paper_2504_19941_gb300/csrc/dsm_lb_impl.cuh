@@ -50,6 +50,14 @@ struct Hood {
   __device__ __forceinline__ int minus(int i) const {  // x - c_i
     return ox[1 - L::cx(i)] + oy[1 - L::cy(i)] + oz[1 - L::cz(i)];
   }
+  // x + c_i for a direction known only at run time (selects without indexing
+  // the offset arrays dynamically, so they stay in registers)
+  template <class L>
+  __device__ __forceinline__ int plus_rt(int i) const {
+    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+    return (cx < 0 ? ox[0] : cx > 0 ? ox[2] : ox[1]) + (cy < 0 ? oy[0] : cy > 0 ? oy[2] : oy[1]) +
+           (cz < 0 ? oz[0] : cz > 0 ? oz[2] : oz[1]);
+  }
 };
 
 template <class T, class S>
@@ -83,6 +91,13 @@ __device__ __forceinline__ T link_q(T c1x, const T (&gc1)[3], int i, T alpha_s) 
   return q > T(1) ? T(0.5) : q;
 }
 
+// link_q for a direction known only at run time (the wall-link loop is rolled).
+template <class L, class T>
+__device__ __noinline__ T link_q_rt(T c1x, T g0, T g1, T g2, int i, T alpha_s) {
+  const T gc1[3] = {g0, g1, g2};
+  return link_q<L, T>(c1x, gc1, i, alpha_s);
+}
+
 // ---------------------------------------------------------------------------
 // K1: moments pass.  C(x) = sum_i g_i after streaming (Sec. II.B, C = sum g).
 // ---------------------------------------------------------------------------
@@ -112,7 +127,7 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
 template <int K, class T, class S, int STAGE, int MODE>
-__global__ void __launch_bounds__(256) node_kernel(LBArgs<T, S> a, int field_sel) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
   int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,10 +141,14 @@ __global__ void __launch_bounds__(256) node_kernel(LBArgs<T, S> a, int field_sel
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   const StepParams &P = a.p;
 
-  // ---- neighbourhood of C and C1: mu, G[C], G[rho], solid links ----------
+  // ---- every load of the node, issued up front ------------------------------
+  // The populations are pulled from x - c_j for all j without a branch (a link
+  // whose upstream node is solid is corrected below), so the 2Q population
+  // loads and the 2Q neighbourhood loads are all in flight together.
   T C, c1, mu, rho, tau, taug;
   T gC[3] = {T(0), T(0), T(0)}, gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
   unsigned nb_solid = 0;  // bit k: x + c_k is solid (stage 2)
+  T f[Q], g[Q];
   {
     T Cn[Q], C1n[Q];
 #pragma unroll
@@ -137,6 +156,13 @@ __global__ void __launch_bounds__(256) node_kernel(LBArgs<T, S> a, int field_sel
       const int m = h.plus<L>(i);
       Cn[i] = __ldg(a.C + m);
       C1n[i] = (STAGE == 2) ? __ldg(a.C1 + m) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; j++) {
+      const int src = h.minus<L>(j);
+      if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
+      else g[j] = load_g<T, S>(a.g_in, (long long)j * a.pitch + src);
+      f[j] = load_f<T, S>(a.f_in, (long long)j * a.pitch + src, j, L::w(j));
     }
     C = Cn[0];
     c1 = C1n[0];
@@ -218,33 +244,29 @@ __global__ void __launch_bounds__(256) node_kernel(LBArgs<T, S> a, int field_sel
   }
   const bool solid_x = (STAGE == 2) && (nb_solid & 1u);
 
-  // ---- pull streaming ------------------------------------------------------
-  T f[Q], g[Q];
-#pragma unroll
-  for (int j = 0; j < Q; j++) {
-    if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
-    else g[j] = load_g<T, S>(a.g_in, (long long)j * a.pitch + h.minus<L>(j));
-  }
-  if (!solid_x) {
-#pragma unroll
-    for (int j = 0; j < Q; j++) {
-      const int i = L::opp(j);  // upstream x - c_j = x + c_i
-      if (STAGE == 1 || !((nb_solid >> i) & 1u)) {
-        f[j] = load_f<T, S>(a.f_in, (long long)j * a.pitch + h.minus<L>(j), j, L::w(j));
+  // ---- interpolated bounce-back at the diffuse solid ------------------------
+  // (rare: only fluid nodes with a solid neighbour) -- one rolled loop replaces
+  // the pulled value of every link whose upstream node x - c_j is solid.
+  if (STAGE == 2 && !solid_x && (nb_solid & ~1u)) {
+    for (int j = 1; j < Q; j++) {
+      const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
+      if (!((nb_solid >> i) & 1u)) continue;
+      const T q = link_q_rt<L, T>(c1, gc1[0], gc1[1], gc1[2], i, T(P.alpha_s));
+      const T fi_x = load_f<T, S>(a.f_in, (long long)i * a.pitch + n, i, L::w(i));
+      T v;
+      if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
+        const int z2 = h.plus_rt<L>(j);  // x - c_i, the next fluid node away from the wall
+        const T fi_z = load_f<T, S>(a.f_in, (long long)i * a.pitch + z2, i, L::w(i));
+        v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
+      } else if (q < T(0.5)) {
+        v = fi_x;  // no second fluid node: halfway rule
       } else {
-        // interpolated bounce-back (linear, Bouzidi et al. 2001) on link i
-        const T q = link_q<L, T>(c1, gc1, i, T(P.alpha_s));
-        const T fi_x = load_f<T, S>(a.f_in, (long long)i * a.pitch + n, i, L::w(i));
-        if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
-          const T fi_z = load_f<T, S>(a.f_in, (long long)i * a.pitch + h.plus<L>(j), i, L::w(i));
-          f[j] = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
-        } else if (q < T(0.5)) {
-          f[j] = fi_x;  // no second fluid node: halfway rule
-        } else {
-          const T fj_x = load_f<T, S>(a.f_in, (long long)j * a.pitch + n, j, L::w(j));
-          f[j] = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
-        }
+        const T fj_x = load_f<T, S>(a.f_in, (long long)j * a.pitch + n, j, L::w(j));
+        v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
       }
+#pragma unroll
+      for (int k = 1; k < Q; k++)
+        if (k == j) f[k] = v;
     }
   }
 
