@@ -11,6 +11,8 @@
 
 namespace dsm {
 
+constexpr int QMAX = 19;
+
 // --------------------------------------------------------------------------
 // Lattices.  D2Q9: the velocity/weight table printed in Sec. II.B of the
 // paper.  D3Q19: textbook set (rest 1/3, six axis links 1/18, twelve face
@@ -128,6 +130,9 @@ struct LBArgs {
   double *partials;    // OBS mode: per-block partial sums
   int *err;            // latched error word
   StepParams p;
+  // per-direction plane pointers (kernel parameters: one address op per access)
+  const S *fin[QMAX], *gin[QMAX];
+  S *fout[QMAX], *gout[QMAX];
 };
 
 // Error bits latched in the workspace error word.

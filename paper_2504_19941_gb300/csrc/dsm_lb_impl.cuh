@@ -61,12 +61,12 @@ struct Hood {
 };
 
 template <class T, class S>
-__device__ __forceinline__ T load_f(const S *base, long long off, int i, double w) {
+__device__ __forceinline__ T load_f(const S *base, int off, int i, double w) {
   if constexpr (Store<S>::k16) return T(w) + T(Store<S>::dec(base[off]));
   else return T(Store<S>::dec(__ldg(base + off)));
 }
 template <class T, class S>
-__device__ __forceinline__ T load_g(const S *base, long long off) {
+__device__ __forceinline__ T load_g(const S *base, int off) {
   if constexpr (Store<S>::k16) return T(Store<S>::dec(base[off]));
   else return T(__ldg(base + off));
 }
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
     if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
-    else s += load_g<T, S>(a.g_in, (long long)i * a.pitch + h.minus<L>(i));
+    else s += load_g<T, S>(a.gin[i], h.minus<L>(i));
   }
   a.C[n] = s;
 }
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 // every node fluid).  MODE_STEP collides and writes the next state;
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S, int STAGE, int MODE>
+template <int K, class T, class S, int STAGE, int MODE, bool RC>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
     for (int j = 0; j < Q; j++) {
       const int src = h.minus<L>(j);
       if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
-      else g[j] = load_g<T, S>(a.g_in, (long long)j * a.pitch + src);
-      f[j] = load_f<T, S>(a.f_in, (long long)j * a.pitch + src, j, L::w(j));
+      else g[j] = load_g<T, S>(a.gin[j], src);
+      f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
     }
     C = Cn[0];
     c1 = C1n[0];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
         return T(P.rho3) + T(P.rho2 - P.rho3) * ph;
       };
       rho = rho_of(C, c1);
-      if (P.rho_contrast) {
+      if (RC) {
 #pragma unroll
         for (int i = 1; i < Q; i++) {
           const T r = T(L::w(i)) * rho_of(Cn[i], C1n[i]);
@@ -252,16 +252,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
       const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
       if (!((nb_solid >> i) & 1u)) continue;
       const T q = link_q_rt<L, T>(c1, gc1[0], gc1[1], gc1[2], i, T(P.alpha_s));
-      const T fi_x = load_f<T, S>(a.f_in, (long long)i * a.pitch + n, i, L::w(i));
+      const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
       T v;
       if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
         const int z2 = h.plus_rt<L>(j);  // x - c_i, the next fluid node away from the wall
-        const T fi_z = load_f<T, S>(a.f_in, (long long)i * a.pitch + z2, i, L::w(i));
+        const T fi_z = load_f<T, S>(a.fin[i], z2, i, L::w(i));
         v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
       } else if (q < T(0.5)) {
         v = fi_x;  // no second fluid node: halfway rule
       } else {
-        const T fj_x = load_f<T, S>(a.f_in, (long long)j * a.pitch + n, j, L::w(j));
+        const T fj_x = load_f<T, S>(a.fin[j], n, j, L::w(j));
         v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
       }
 #pragma unroll
@@ -363,42 +363,69 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   //   g_eq_i = w_i (mu + C s_i) (i != 0),  g_eq_0 = C - (1 - w_0) mu + w_0 C s_0
   // (the minus signs read where the printed forms would break sum f_eq = pt and
   // sum g_eq = C).  Solid nodes: f* = w_i; g collides with u = 0.
+  // Directions come in opposite pairs (i, i+1): c_{i+1} = -c_i, so s splits
+  // into a shared even part and an odd part of opposite sign.  Without a density
+  // contrast (RC = false) G[rho] = 0 and its forcing terms vanish exactly.
   if (!isfinite(pt + mu + u[0] + u[1] + u[2])) atomicOr(a.err, ERR_NONFINITE);
   const T omf = T(1) / tau, omg = T(1) / taug;
   const T kF = T(1) - T(0.5) * omf;
-  const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
+  const T kF3 = T(3) * kF;
+  const T ug = RC ? u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2] : T(0);
+  const T m15uu = T(1.5) * uu;
   T gsum16 = T(0);
+  auto put_f = [&](int i, T fo) {
+    if constexpr (Store<S>::k16) a.fout[i][n] = Store<S>::enc(float(fo - T(L::w(i))));
+    else a.fout[i][n] = S(fo);
+  };
+  auto put_g = [&](int i, T go) {
+    if constexpr (Store<S>::k16) {
+      const S e = Store<S>::enc(float(go));
+      a.gout[i][n] = e;
+      gsum16 += T(Store<S>::dec(e));
+    } else {
+      a.gout[i][n] = S(go);
+    }
+  };
+  {  // rest population
+    const T w = T(L::w(0));
+    const T s = -m15uu;
+    T fo = w;
+    if (!solid_x) {
+      T Fi = T(0);
+      if (RC) Fi = kF * w * (-ug * s);
+      fo = f[0] + (w * (pt + rho * s) - f[0]) * omf + Fi;
+    }
+    put_f(0, fo);
+    const T geq = C - (T(1) - w) * mu + w * C * s;
+    const T go = g[0] + (geq - g[0]) * omg;
+    if constexpr (!Store<S>::k16) a.gout[0][n] = S(go);
+  }
 #pragma unroll
-  for (int i = 0; i < Q; i++) {
+  for (int i = 1; i < Q; i += 2) {
+    const int ib = i + 1;  // opposite direction
     const T w = T(L::w(i));
     const T cu = T(L::cx(i)) * u[0] + T(L::cy(i)) * u[1] + T(L::cz(i)) * u[2];
-    const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
-    const long long off = (long long)i * a.pitch + n;
-    // f
-    T fo;
-    if (solid_x) {
-      fo = w;
-    } else {
-      const T feq = w * (pt + rho * s);
-      const T cg = T(L::cx(i)) * gR[0] + T(L::cy(i)) * gR[1] + T(L::cz(i)) * gR[2] - ug;
+    const T even = T(4.5) * cu * cu - m15uu;
+    const T odd = T(3) * cu;
+    const T sp = even + odd, sm = even - odd;
+    T fp = w, fm = w;
+    if (!solid_x) {
+      const T wpt = w * pt, wr = w * rho;
       const T cF = T(L::cx(i)) * Fv[0] + T(L::cy(i)) * Fv[1] + T(L::cz(i)) * Fv[2];
-      const T Fi = kF * w * (cg * s + T(3) * cF);
-      fo = f[i] - (f[i] - feq) * omf + Fi;
-    }
-    if constexpr (Store<S>::k16) a.f_out[off] = Store<S>::enc(float(fo - w));
-    else a.f_out[off] = S(fo);
-    // g
-    const T geq = (i == 0) ? C - (T(1) - w) * mu + w * C * s : w * (mu + C * s);
-    const T go = g[i] - (g[i] - geq) * omg;
-    if constexpr (Store<S>::k16) {
-      if (i > 0) {
-        const S e = Store<S>::enc(float(go));
-        a.g_out[off] = e;
-        gsum16 += T(Store<S>::dec(e));
+      T Fp = w * kF3 * cF, Fm = -Fp;
+      if (RC) {
+        const T cg = T(L::cx(i)) * gR[0] + T(L::cy(i)) * gR[1] + T(L::cz(i)) * gR[2];
+        Fp += kF * w * ((cg - ug) * sp);
+        Fm += kF * w * ((-cg - ug) * sm);
       }
-    } else {
-      a.g_out[off] = S(go);
+      fp = f[i] + (wpt + wr * sp - f[i]) * omf + Fp;
+      fm = f[ib] + (wpt + wr * sm - f[ib]) * omf + Fm;
     }
+    put_f(i, fp);
+    put_f(ib, fm);
+    const T wmu = w * mu, wC = w * C;
+    put_g(i, g[i] + (wmu + wC * sp - g[i]) * omg);
+    put_g(ib, g[ib] + (wmu + wC * sm - g[ib]) * omg);
   }
   // 16-bit storage: the rest population takes the rounding of the others so
   // that sum_i g*_i = C holds at every node (sum_i g_eq_i = C, so the exact
@@ -543,6 +570,13 @@ LBArgs<T, S> typed(const LBRaw &r) {
   a.f_out = (S *)r.f_out; a.g_out = (S *)r.g_out; a.g0_out = r.g0_out;
   a.C = (T *)r.C; a.C1 = (const T *)r.C1; a.mask = r.mask;
   a.fields = (T *)r.out; a.partials = r.partials; a.err = r.err; a.p = r.p;
+  for (int i = 0; i < QMAX; i++) {
+    const long long o = (long long)i * r.pitch;
+    a.fin[i] = a.f_in ? a.f_in + o : nullptr;
+    a.gin[i] = a.g_in ? a.g_in + o : nullptr;
+    a.fout[i] = a.f_out ? a.f_out + o : nullptr;
+    a.gout[i] = a.g_out ? a.g_out + o : nullptr;
+  }
   return a;
 }
 
@@ -554,8 +588,12 @@ struct LBOps {
   }
   template <int STAGE, int MODE>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
-    node_kernel<K, T, S, STAGE, MODE>
-        <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
+    if (STAGE == 2 && r.p.rho_contrast)
+      node_kernel<K, T, S, STAGE, MODE, true>
+          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
+    else
+      node_kernel<K, T, S, STAGE, MODE, false>
+          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
   }
   static cudaError_t node(const LBRaw &r, int stage, int mode, cudaStream_t st) {
     if (stage == 2) {
