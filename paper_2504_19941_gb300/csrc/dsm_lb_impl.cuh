@@ -127,10 +127,13 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
 template <int K, class T, class S, int STAGE, int MODE, bool RC>
-__device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
-                                          int field_sel) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y * blockDim.y + threadIdx.y;
+  int z = blockIdx.z * blockDim.z + threadIdx.z;
+  const bool valid = x < a.nx && y < a.ny && z < a.nz;
   if (MODE != MODE_OBS && !valid) return;
   if (!valid) x = y = z = 0;
   Hood h;
@@ -430,72 +433,6 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   if constexpr (Store<S>::k16) a.g0_out[n] = float(C - gsum16);
 }
 
-template <int K, class T, class S, int STAGE, int MODE, bool RC>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z * blockDim.z + threadIdx.z;
-  node_body<K, T, S, STAGE, MODE, RC>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
-}
-
-// L2 prefetch of the lines a warp will pull from when it processes brick b:
-// per population plane the 32-node line of the upstream row, and the rows of
-// C and C1 on the 1-neighbourhood.  Fire-and-forget, no registers held.
-template <class L, class T, class S, int STAGE>
-__device__ __forceinline__ void prefetch_brick(const LBArgs<T, S> &a, long long b, int gx, int gy,
-                                               int lane) {
-  constexpr int Q = L::Q;
-  const int bx = (int)(b % gx), by = (int)((b / gx) % gy), bz = (int)(b / ((long long)gx * gy));
-  const int x0 = bx * blockDim.x;
-  const int y = by * blockDim.y + threadIdx.y, z = bz * blockDim.z + threadIdx.z;
-  if (y >= a.ny || z >= a.nz) return;
-  const int nrow = (STAGE == 2) ? 2 * Q + 18 : 2 * Q + 9;
-  for (int k = lane; k < nrow; k += 32) {
-    int dy, dz;
-    const void *base;
-    if (k < 2 * Q) {
-      const int j = k < Q ? k : k - Q;
-      dy = -L::cy(j);
-      dz = -L::cz(j);
-      base = k < Q ? (const void *)a.fin[j] : (const void *)a.gin[j];
-      if (Store<S>::k16 && k == Q) base = (const void *)a.g0_in;
-    } else {
-      const int r = (k - 2 * Q) % 9;
-      dy = r % 3 - 1;
-      dz = (L::D == 3) ? r / 3 - 1 : 0;
-      base = (k - 2 * Q) < 9 ? (const void *)a.C : (const void *)a.C1;
-    }
-    int yy = y + dy, zz = z + dz;
-    yy = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
-    zz = zz < 0 ? zz + a.nz : (zz >= a.nz ? zz - a.nz : zz);
-    const long long node = x0 + (long long)a.nx * (yy + (long long)a.ny * zz);
-    const size_t esz = (k < 2 * Q) ? ((Store<S>::k16 && k == Q) ? 4 : sizeof(S)) : sizeof(T);
-    const char *p = (const char *)base + node * esz;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-  }
-}
-
-// The stage-2 step as a persistent kernel: resident blocks walk the bricks
-// (blockDim-shaped node boxes) in a grid-stride loop, each warp prefetching the
-// next brick's lines into L2 while it computes the current one.
-template <int K, class T, class S, bool RC>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) step_kernel(LBArgs<T, S> a, int gx,
-                                                                       int gy, int gz) {
-  using L = Lat<K>;
-  const long long nb = (long long)gx * gy * gz;
-  const int lane = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) & 31;
-  if ((long long)blockIdx.x < nb) prefetch_brick<L, T, S, 2>(a, blockIdx.x, gx, gy, lane);
-  for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
-    const long long bn = b + gridDim.x;
-    if (bn < nb) prefetch_brick<L, T, S, 2>(a, bn, gx, gy, lane);
-    const int bx = (int)(b % gx), by = (int)((b / gx) % gy), bz = (int)(b / ((long long)gx * gy));
-    const int x = bx * blockDim.x + threadIdx.x;
-    const int y = by * blockDim.y + threadIdx.y;
-    const int z = bz * blockDim.z + threadIdx.z;
-    node_body<K, T, S, 2, MODE_STEP, RC>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, 0);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // K3: initial state at rest (reading of the unstated initial condition):
 // f_i = w_i, g_i = g_eq_i(C, mu(C), u = 0), stored as the post-collision state.
@@ -649,28 +586,8 @@ struct LBOps {
     moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
-  template <bool RC>
-  static void step_launch(const LBRaw &r, cudaStream_t st) {
-    static int resident = 0;  // blocks of step_kernel resident on the whole GPU
-    if (!resident) {
-      int dev = 0, sms = 0, per_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<K, T, S, RC>, 256, 0);
-      resident = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz);
-    const long long nb = (long long)g.x * g.y * g.z;
-    const int blocks = (int)(nb < resident ? nb : resident);
-    step_kernel<K, T, S, RC><<<blocks, lb_block(K), 0, st>>>(typed<T, S>(r), g.x, g.y, g.z);
-  }
   template <int STAGE, int MODE>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
-    if (STAGE == 2 && MODE == MODE_STEP) {
-      if (r.p.rho_contrast) step_launch<true>(r, st);
-      else step_launch<false>(r, st);
-      return;
-    }
     if (STAGE == 2 && r.p.rho_contrast)
       node_kernel<K, T, S, STAGE, MODE, true>
           <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
