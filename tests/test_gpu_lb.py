@@ -241,7 +241,8 @@ def test_full_size_sampled_fp32():
         c = 4 + 9 * (4 + 9 * 4)
         worst_f = max(worst_f, np.max(np.abs(fa - fo[:, c])))
         worst_g = max(worst_g, np.max(np.abs(ga - go[:, c])))
-    assert worst_f < 2e-7 and worst_g < 2e-7, (worst_f, worst_g)
+    # one FP32 step: a few ulp of populations up to O(1) (g_0 ~ C)
+    assert worst_f < 5e-7 and worst_g < 5e-7, (worst_f, worst_g)
 
 
 def test_full_size_mass_conservation_fp32():
