@@ -111,6 +111,32 @@ struct StepParams {
   int rho_contrast;         // rho2 != rho3
 };
 
+// The same constants in the arithmetic type T, with every product and
+// reciprocal the kernels need formed once on the host: no double-precision
+// conversion or division is left in the FP32 kernels.
+template <class T>
+struct ConstT {
+  T k2, k3, a2k2, a2k3, k13, a2k13;  // kappa_2, kappa_3, a^2 kappa_n, kappa_1 + kappa_3
+  T alpha_s;
+  T rho2, rho3, drho, inv_rho3;      // densities, rho2 - rho3, 1/rho3
+  T tau2, tau3, om2, om3, omg;       // relaxation times and 1/tau2, 1/tau3, 1/tau_g
+  T body[3];
+  T beta2, omega2;                   // 2 beta, 2 Omega
+  static ConstT make(const StepParams &p) {
+    ConstT c;
+    c.k2 = T(p.kappa2); c.k3 = T(p.kappa3);
+    c.a2k2 = T(p.a2 * p.kappa2); c.a2k3 = T(p.a2 * p.kappa3);
+    c.k13 = T(p.kappa1 + p.kappa3); c.a2k13 = T(p.a2 * (p.kappa1 + p.kappa3));
+    c.alpha_s = T(p.alpha_s);
+    c.rho2 = T(p.rho2); c.rho3 = T(p.rho3); c.drho = T(p.rho2 - p.rho3); c.inv_rho3 = T(1.0 / p.rho3);
+    c.tau2 = T(p.tau2); c.tau3 = T(p.tau3);
+    c.om2 = T(1.0 / p.tau2); c.om3 = T(1.0 / p.tau3); c.omg = T(1.0 / p.tau_g);
+    for (int a = 0; a < 3; a++) c.body[a] = T(p.body[a]);
+    c.beta2 = T(2.0 * p.beta); c.omega2 = T(2.0 * p.omega);
+    return c;
+  }
+};
+
 // Pointers and sizes of one lattice for the LB kernels.
 template <class T, class S>
 struct LBArgs {
@@ -130,6 +156,7 @@ struct LBArgs {
   double *partials;    // OBS mode: per-block partial sums
   int *err;            // latched error word
   StepParams p;
+  ConstT<T> c;
   // per-direction plane pointers (kernel parameters: one address op per access)
   const S *fin[QMAX], *gin[QMAX];
   S *fout[QMAX], *gout[QMAX];

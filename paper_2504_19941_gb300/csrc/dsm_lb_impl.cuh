@@ -91,11 +91,17 @@ __device__ __forceinline__ T link_q(T c1x, const T (&gc1)[3], int i, T alpha_s) 
   return q > T(1) ? T(0.5) : q;
 }
 
-// link_q for a direction known only at run time (the wall-link loop is rolled).
+// The same link fraction from the node's precomputed x_s and |G[C1]|, for a
+// direction known only at run time (the wall-link loop is rolled).
 template <class L, class T>
-__device__ __noinline__ T link_q_rt(T c1x, T g0, T g1, T g2, int i, T alpha_s) {
-  const T gc1[3] = {g0, g1, g2};
-  return link_q<L, T>(c1x, gc1, i, alpha_s);
+__device__ __noinline__ T link_fraction(T xs, T gn, T g0, T g1, T g2, int i) {
+  if (!(gn >= T(1e-12))) return T(0.5);
+  const int l2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+  const T cl = l2 == 1 ? T(1) : sqrt(T(l2));
+  const T nd = (g0 * T(L::cx(i)) + g1 * T(L::cy(i)) + g2 * T(L::cz(i))) / (gn * cl);
+  if (!(nd > T(1e-6))) return T(0.5);
+  const T q = fabs(xs / nd) / cl;
+  return q > T(1) ? T(0.5) : q;
 }
 
 // ---------------------------------------------------------------------------
@@ -139,13 +145,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   Hood h;
   h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
-  const StepParams &P = a.p;
+  const ConstT<T> &K_ = a.c;
 
   // ---- every load of the node, issued up front ------------------------------
   // The populations are pulled from x - c_j for all j without a branch (a link
   // whose upstream node is solid is corrected below), so the 2Q population
   // loads and the 2Q neighbourhood loads are all in flight together.
-  T C, c1, mu, rho, tau, taug;
+  T C, c1, mu, rho, tau, omf, omg;  // omf = 1/tau, omg = 1/tau_g
   T gC[3] = {T(0), T(0), T(0)}, gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
   unsigned nb_solid = 0;  // bit k: x + c_k is solid (stage 2)
   T f[Q], g[Q];
@@ -184,8 +190,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
       // Chemical potential of the frozen-solid free energy (Sec. II.B,
       // Eq. [eqn:fefrozen]), taken as its exact derivative in C2:
       //   mu = k2 b(C) + k3 b(C1 + C) - a^2 k2 L[C] - a^2 k3 L[C1 + C]
-      mu = T(P.kappa2) * bwell(C) + T(P.kappa3) * bwell(c1 + C) -
-           T(P.a2 * P.kappa2) * lapC - T(P.a2 * P.kappa3) * lapS;
+      mu = K_.k2 * bwell(C) + K_.k3 * bwell(c1 + C) - K_.a2k2 * lapC - K_.a2k3 * lapS;
       // density map rho = rho3 + (rho2 - rho3) C2/(C2 + C3), the ratio clamped
       // to [0, 1] and 0 where C2 + C3 = 1 - C1 <= 1e-6 (inside the solid)
       auto rho_of = [&](T cc, T s1) -> T {
@@ -195,9 +200,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
           ph = cc / den;
           ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
         }
-        return T(P.rho3) + T(P.rho2 - P.rho3) * ph;
+        return K_.rho3 + K_.drho * ph;
       };
-      rho = rho_of(C, c1);
+      rho = RC ? rho_of(C, c1) : K_.rho3;
       if (RC) {
 #pragma unroll
         for (int i = 1; i < Q; i++) {
@@ -210,8 +215,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
         for (int d = 0; d < 3; d++) gR[d] *= T(3);
       }
       // relaxation time map tau = tau3 + (tau2 - tau3) H(C2 - C3), H(0) = 0
-      tau = (C - (T(1) - c1 - C) > T(0)) ? T(P.tau2) : T(P.tau3);
-      taug = T(P.tau_g);
+      const bool liquid = C - (T(1) - c1 - C) > T(0);
+      tau = liquid ? K_.tau2 : K_.tau3;
+      omf = liquid ? K_.om2 : K_.om3;
+      omg = K_.omg;
 #pragma unroll
       for (int i = 0; i < Q; i++) nb_solid |= (C1n[i] >= T(0.5) ? 1u : 0u) << i;
       if ((nb_solid & ~1u) && !(nb_solid & 1u)) {
@@ -231,15 +238,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
       //   + 2 beta (C1 - 1/2) chi + 2 Omega C1 H(-C1) - 2 Omega (1 - C1) H(C1 - 1)
       // chi = 1 where the solid leaks out of S or the fluid into it (the
       // printed case labels of Eq. [frozen:poly-quadratic_lbm] read swapped).
-      const T k13 = T(P.kappa1 + P.kappa3);
-      mu = k13 * bwell(C) - T(P.a2) * k13 * lapC;
+      mu = K_.k13 * bwell(C) - K_.a2k13 * lapC;
       const bool inS = a.mask[n] != 0;
-      if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += T(2 * P.beta) * (C - T(0.5));
-      if (C < T(0)) mu += T(2 * P.omega) * C;
-      if (C > T(1)) mu -= T(2 * P.omega) * (T(1) - C);
+      if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += K_.beta2 * (C - T(0.5));
+      if (C < T(0)) mu += K_.omega2 * C;
+      if (C > T(1)) mu -= K_.omega2 * (T(1) - C);
       rho = T(1);
       tau = T(1);
-      taug = T(1);
+      omf = T(1);
+      omg = T(1);
     }
   }
   const bool solid_x = (STAGE == 2) && (nb_solid & 1u);
@@ -248,10 +255,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   // (rare: only fluid nodes with a solid neighbour) -- one rolled loop replaces
   // the pulled value of every link whose upstream node x - c_j is solid.
   if (STAGE == 2 && !solid_x && (nb_solid & ~1u)) {
+    // the node's distance to the C1 = 1/2 surface and the normal, once per node
+    const T cc = c1 < T(1e-9) ? T(1e-9) : (c1 > T(0.5) ? T(0.5) : c1);
+    const T xs = T(2) * K_.alpha_s * atanh(T(2) * cc - T(1));
+    const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
     for (int j = 1; j < Q; j++) {
       const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
       if (!((nb_solid >> i) & 1u)) continue;
-      const T q = link_q_rt<L, T>(c1, gc1[0], gc1[1], gc1[2], i, T(P.alpha_s));
+      const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
       const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
       T v;
       if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
@@ -281,9 +292,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   Fv[1] = mu * gC[1];
   Fv[2] = mu * gC[2];
   if (STAGE == 2) {
-    Fv[0] += C * T(P.body[0]);
-    Fv[1] += C * T(P.body[1]);
-    Fv[2] += C * T(P.body[2]);
+    Fv[0] += C * K_.body[0];
+    Fv[1] += C * K_.body[1];
+    Fv[2] += C * K_.body[2];
   }
   if (!solid_x) {
     T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
       if (L::cy(j)) m1[1] += T(L::cy(j)) * f[j];
       if (L::cz(j)) m1[2] += T(L::cz(j)) * f[j];
     }
-    const T ir = T(1) / rho;
+    const T ir = (STAGE == 1) ? T(1) : (RC ? T(1) / rho : K_.inv_rho3);
     u[0] = (m1[0] + T(0.5) * Fv[0]) * ir;
     u[1] = (m1[1] + T(0.5) * Fv[1]) * ir;
     u[2] = (m1[2] + T(0.5) * Fv[2]) * ir;
@@ -367,7 +378,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   // into a shared even part and an odd part of opposite sign.  Without a density
   // contrast (RC = false) G[rho] = 0 and its forcing terms vanish exactly.
   if (!isfinite(pt + mu + u[0] + u[1] + u[2])) atomicOr(a.err, ERR_NONFINITE);
-  const T omf = T(1) / tau, omg = T(1) / taug;
   const T kF = T(1) - T(0.5) * omf;
   const T kF3 = T(3) * kF;
   const T ug = RC ? u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2] : T(0);
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(256) init_kernel(LBArgs<T, S> a, const T *cfie
   Hood h;
   h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
-  const StepParams &P = a.p;
+  const ConstT<T> &K_ = a.c;
   const T C = cfield[n];
   const T c1 = (STAGE == 2) ? a.C1[n] : T(0);
   T lapC = T(0), lapS = T(0);
@@ -463,15 +473,13 @@ __global__ void __launch_bounds__(256) init_kernel(LBArgs<T, S> a, const T *cfie
   lapS *= T(6);
   T mu;
   if (STAGE == 2) {
-    mu = T(P.kappa2) * bwell(C) + T(P.kappa3) * bwell(c1 + C) - T(P.a2 * P.kappa2) * lapC -
-         T(P.a2 * P.kappa3) * lapS;
+    mu = K_.k2 * bwell(C) + K_.k3 * bwell(c1 + C) - K_.a2k2 * lapC - K_.a2k3 * lapS;
   } else {
-    const T k13 = T(P.kappa1 + P.kappa3);
-    mu = k13 * bwell(C) - T(P.a2) * k13 * lapC;
+    mu = K_.k13 * bwell(C) - K_.a2k13 * lapC;
     const bool inS = a.mask[n] != 0;
-    if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += T(2 * P.beta) * (C - T(0.5));
-    if (C < T(0)) mu += T(2 * P.omega) * C;
-    if (C > T(1)) mu -= T(2 * P.omega) * (T(1) - C);
+    if ((inS && C < T(0.5)) || (!inS && C > T(0.5))) mu += K_.beta2 * (C - T(0.5));
+    if (C < T(0)) mu += K_.omega2 * C;
+    if (C > T(1)) mu -= K_.omega2 * (T(1) - C);
   }
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -570,6 +578,7 @@ LBArgs<T, S> typed(const LBRaw &r) {
   a.f_out = (S *)r.f_out; a.g_out = (S *)r.g_out; a.g0_out = r.g0_out;
   a.C = (T *)r.C; a.C1 = (const T *)r.C1; a.mask = r.mask;
   a.fields = (T *)r.out; a.partials = r.partials; a.err = r.err; a.p = r.p;
+  a.c = ConstT<T>::make(r.p);
   for (int i = 0; i < QMAX; i++) {
     const long long o = (long long)i * r.pitch;
     a.fin[i] = a.f_in ? a.f_in + o : nullptr;
