@@ -99,6 +99,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    or None when the kernel source has changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "node_kernel_d3q19_f32_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("dsm_lb_impl.cuh", "dsm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2504_19941_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != rec.get("kernel_source_sha256_16"):
+        return None
+    return float(rec["bytes_per_launch"])
+
+
 def make_case(shape):
     import synthetic as S
     if tuple(shape) == SHAPE:
@@ -248,11 +269,7 @@ def run_gpu(args, rank, world):
 
     peak, peak_kind = _peaks()
     achieved = B_MIN_F32_D3Q19 * n / t_k2 / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        with open(tp) as f:
-            traffic = json.load(f).get("node_kernel_d3q19_f32_bytes_per_launch")
+    traffic = measured_traffic() if shape == SHAPE else None
 
     if rank == 0:
         cb = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
