@@ -193,13 +193,27 @@ def _trial(a, x, d, xt, Et, gt, evaluate, V, host):
     return host(Et, V.dot(gt, d))
 
 
-def _wolfe(phi, f0, dg0, c1=1e-4, c2=0.9, max_trials=20):
+def _wolfe(phi, f0, dg0, c1=1e-4, c2=0.9, max_trials=20, eps=1e-6):
     """Strong-Wolfe step length along a descent direction (Nocedal & Wright,
     Numerical Optimization, Algorithms 3.5 and 3.6): expand until the minimum is
     bracketed, then shrink the bracket with a safeguarded cubic.  phi(a) ->
     (f, f') evaluates the trial point and leaves it in the trial buffers.
     Returns (a, trials, f(a), f'(a)); f(a) is None when the accepted point is
-    not the last one evaluated."""
+    not the last one evaluated.
+
+    Near a minimum the energy change of a step falls below the rounding noise
+    of an energy summed from FP32 node densities, so the sufficient-decrease
+    test on f stops being informative.  There (|f - f0| <= eps |f0|) the test
+    is replaced by its derivative form, f'(a) <= (2 c1 - 1) f'(0) (the
+    approximate Wolfe condition of Hager & Zhang 2005), using the FP64
+    directional derivatives."""
+    noise = eps * abs(f0)
+
+    def too_high(a, f, df):
+        if abs(f - f0) <= noise:
+            return df > (2.0 * c1 - 1.0) * dg0
+        return f > f0 + c1 * a * dg0
+
     trials = 0
     a_prev, f_prev, d_prev = 0.0, f0, dg0
     a = 1.0
@@ -207,7 +221,7 @@ def _wolfe(phi, f0, dg0, c1=1e-4, c2=0.9, max_trials=20):
     while trials < max_trials:
         f, df = phi(a)
         trials += 1
-        if f > f0 + c1 * a * dg0 or (trials > 1 and f >= f_prev):
+        if too_high(a, f, df) or (trials > 1 and f >= f_prev and abs(f - f0) > noise):
             lo, hi = (a_prev, f_prev, d_prev), (a, f, df)
             break
         if abs(df) <= -c2 * dg0:
@@ -225,7 +239,7 @@ def _wolfe(phi, f0, dg0, c1=1e-4, c2=0.9, max_trials=20):
         f, df = phi(a)
         trials += 1
         last = a
-        if f > f0 + c1 * a * dg0 or f >= lo[1]:
+        if too_high(a, f, df) or (f >= lo[1] and abs(f - f0) > noise):
             hi = (a, f, df)
         else:
             if abs(df) <= -c2 * dg0:

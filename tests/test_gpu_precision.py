@@ -1,0 +1,142 @@
+"""16-bit population storage (BF16 / FP16 offsets f_i - w_i and g_i, FP32 g_0 and
+FP32 arithmetic) against FP64 on the same GPU, the FP64 run itself checked
+against the oracle.
+
+Measured on a GB300 (reduced capillary rise between plates, 96x64x48, 3000
+steps; errors against the GPU FP64 run; velocity error relative to max |u|):
+
+  form   C2       pt       |du|/max|u|   mass drift
+  FP32   1.3e-5   4.9e-5   6.5e-4        7.4e-6
+  BF16   2.6e-3   5.0e-4   2.1e-2        6.3e-8
+  FP16   6.4e-4   1.9e-4   3.3e-3        3.8e-8
+
+The tolerances below are about three times these.  The one-step tests bound
+each stored population by its own encoding rounding: 2^-9 relative for BF16
+(8 stored mantissa bits), 2^-12 for FP16 (11 bits, values scaled by 2^10 so
+they stay normal).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+from oracle import analysis as A
+
+from dsm_helpers import direction_map, gpu_lattice, gpu_pops, oracle_params, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2504_19941_gb300 as P  # noqa: E402
+
+
+def _plates():
+    return S.plates_rise_3d(96, 64, 48, gap=16, thick=6, x0=12, x1=84, reservoir=24, lid=4,
+                            target_rise=30.0)
+
+
+def test_fp64_reference_matches_oracle():
+    case = _plates()
+    lat = gpu_lattice(case, "f64")
+    p = oracle_params(case, O.D3Q19)
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+    f, g = O.lb_init(p, 2, c1, case.c2)
+    lat.step(60)
+    f, g = O.lb_run(p, 2, c1, f, g, 60)
+    perm = direction_map(O.D3Q19)
+    gf, gg = gpu_pops(lat, perm)
+    assert rel_err(gf, f) < 1e-12 and rel_err(gg, g) < 1e-12
+    fo = O.lb_fields(p, 2, c1, f, g)
+    assert rel_err(lat.field("C2").cpu().numpy(), fo["C"]) < 1e-12
+
+
+TOL = {"f32": dict(C2=5e-5, pt=2e-4, u=3e-3, mass=3e-5),
+       "bf16": dict(C2=1e-2, pt=2e-3, u=7e-2, mass=1e-6),
+       "f16": dict(C2=2e-3, pt=6e-4, u=1e-2, mass=1e-6)}
+
+
+def test_storage_forms_against_fp64():
+    case = _plates()
+    lats = {p: gpu_lattice(case, p) for p in ("f64", "f32", "bf16", "f16")}
+    m0 = {p: lat.observables()["mass_c2"] for p, lat in lats.items()}
+    for lat in lats.values():
+        lat.step(3000)
+    ref = {k: lats["f64"].field(k).double().cpu().numpy() for k in ("C2", "pt", "ux", "uy", "uz")}
+    umax = max(np.abs(ref[k]).max() for k in ("ux", "uy", "uz"))
+    for prec in ("f32", "bf16", "f16"):
+        lat = lats[prec]
+        ob = lat.observables()
+        assert ob["nonfinite"] == 0
+        t = TOL[prec]
+        got = {k: lat.field(k).double().cpu().numpy() for k in ref}
+        assert rel_err(got["C2"], ref["C2"]) < t["C2"], prec
+        assert rel_err(got["pt"], ref["pt"]) < t["pt"], prec
+        du = max(np.abs(got[k] - ref[k]).max() for k in ("ux", "uy", "uz"))
+        assert du / umax < t["u"], (prec, du / umax)
+        assert abs(ob["mass_c2"] - m0[prec]) / m0[prec] < t["mass"], prec
+
+
+@pytest.mark.parametrize("prec,bits", [("bf16", 9), ("f16", 12)])
+def test_one_step_within_encoding_rounding(prec, bits):
+    # from a state representable in the storage, one step in FP32 arithmetic
+    # differs from the FP64 oracle's step only by the rounding of the stored
+    # result (and FP32 arithmetic, far smaller)
+    case = _plates()
+    case.shape = (24, 20, 16)
+    n = 24 * 20 * 16
+    sd = S.box_sd(case.shape, (4, 5, 0), (20, 9, 16))
+    case.solid_sd = sd.ravel()
+    case.c2 = S.drop_c2(case.shape, (12, 14, 8), 5.0, 1.0, sd, case.alpha_s).ravel()
+    case.body = (-1e-5, 0.0, 0.0)
+    lat = gpu_lattice(case, prec)
+    lat.step(20)
+    f, g = lat.populations()          # decoded reals of the stored state
+    perm = direction_map(O.D3Q19)
+    inv = np.empty(19, dtype=int)
+    inv[perm] = np.arange(19)
+    fo0 = f.double().cpu().numpy().reshape(19, n)[inv]
+    go0 = g.double().cpu().numpy().reshape(19, n)[inv]
+    lat.step(1)
+    gf, gg = gpu_pops(lat, perm)
+    p = oracle_params(case, O.D3Q19)
+    c1 = lat.field("C1").double().cpu().numpy()
+    f1, g1 = O.lb_run(p, 2, c1, fo0, go0, 1)
+    _, w = O.lattice(O.D3Q19)
+    u = 2.0 ** -bits
+    bound_f = u * np.abs(f1 - w[:, None]) + 1e-7
+    assert np.all(np.abs(gf - f1) <= bound_f), np.max(np.abs(gf - f1) - bound_f)
+    bound_g = u * np.abs(g1[1:]) + 1e-8
+    assert np.all(np.abs(gg[1:] - g1[1:]) <= bound_g), np.max(np.abs(gg[1:] - g1[1:]) - bound_g)
+    # the rest population absorbs the others' rounding: the node sums of g agree
+    np.testing.assert_allclose(gg.sum(axis=0), g1.sum(axis=0), rtol=0, atol=5e-7)
+
+
+def _sessile(theta, steps=4000):
+    shape = (64, 64, 40)
+    sd = S.slab_sd(shape, 2, 0, 6)
+    a_s = S.width_to_alpha(3.0)
+    c2 = S.cap_c2(shape, 5.5, 14.0, theta, 1.0, sd, a_s).ravel()
+    return S.Case("sessile", "D3Q19", shape, sd.ravel(), c2, theta_deg=theta, g23=0.02, g12=0.02,
+                  alpha_s=a_s)
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_contact_angle_of_storage_forms(theta):
+    # the 16-bit forms reproduce the FP64 drop's contact angle within 0.5 degree
+    case = _sessile(theta + 8.0)
+    case.theta_deg = theta
+    nx, ny, nz = case.shape
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s).reshape(nz, ny, nx)
+    ang = {}
+    for prec in ("f64", "f32", "bf16", "f16"):
+        lat = gpu_lattice(case, prec)
+        lat.step(4000)
+        c2 = lat.field("C2").double().cpu().numpy().reshape(nz, ny, nx)
+        ang[prec] = A.contact_angle_flat(c2, c1)
+    for prec in ("f32", "bf16", "f16"):
+        assert abs(ang[prec] - ang["f64"]) < 0.5, ang
+    assert abs(ang["f64"] - theta) < 5.0, ang  # relaxing toward Young's angle
