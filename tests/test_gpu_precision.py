@@ -11,9 +11,9 @@ steps; errors against the GPU FP64 run; velocity error relative to max |u|):
   FP16   6.4e-4   1.9e-4   3.3e-3        3.8e-8
 
 The tolerances below are about three times these.  The one-step tests bound
-each stored population by its own encoding rounding: 2^-9 relative for BF16
-(8 stored mantissa bits), 2^-12 for FP16 (11 bits, values scaled by 2^10 so
-they stay normal).
+each stored population by its own encoding rounding, 2^-9 relative for BF16
+(8 stored mantissa bits) and 2^-12 for FP16 (11 bits, values scaled by 2^10 so
+they stay normal), plus a few FP32 ulp of the arithmetic.
 """
 import math
 
@@ -107,9 +107,10 @@ def test_one_step_within_encoding_rounding(prec, bits):
     f1, g1 = O.lb_run(p, 2, c1, fo0, go0, 1)
     _, w = O.lattice(O.D3Q19)
     u = 2.0 ** -bits
-    bound_f = u * np.abs(f1 - w[:, None]) + 1e-7
+    # plus FP32 arithmetic on O(1/3) values: a handful of ulp (6e-8 each)
+    bound_f = u * np.abs(f1 - w[:, None]) + 1e-6
     assert np.all(np.abs(gf - f1) <= bound_f), np.max(np.abs(gf - f1) - bound_f)
-    bound_g = u * np.abs(g1[1:]) + 1e-8
+    bound_g = u * np.abs(g1[1:]) + 1e-7
     assert np.all(np.abs(gg[1:] - g1[1:]) <= bound_g), np.max(np.abs(gg[1:] - g1[1:]) - bound_g)
     # the rest population absorbs the others' rounding: the node sums of g agree
     np.testing.assert_allclose(gg.sum(axis=0), g1.sum(axis=0), rtol=0, atol=5e-7)
