@@ -25,7 +25,7 @@ EXPORTED = (
     "dsm_set_solid", "dsm_relax_solid", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
     "dsm_step_collide", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_fe_scratch_bytes",
-    "dsm_fe_energy_grad", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
+    "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
     "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_step", "dsm_destroy",
 )
 
@@ -85,6 +85,8 @@ def load():
         "dsm_fe_scratch_bytes": (st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_fe_energy_grad": (st, [P, fp, fp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
                                     C.c_double, vp, fp, vp, vp, C.c_size_t, vp]),
+        "dsm_fe_energy_grad_noalloc": (st, [P, fp, fp, vp, C.c_int, C.c_double, C.c_double,
+                                            C.c_double, C.c_double, vp, fp, vp, vp]),
         "dsm_vec_scratch_bytes": (st, [C.c_longlong, C.POINTER(C.c_size_t)]),
         "dsm_vec_dot": (st, [C.c_longlong, fp, fp, vp, vp, C.c_size_t, vp]),
         "dsm_vec_axpy_dev": (st, [C.c_longlong, C.c_double, vp, vp, fp, fp, vp]),
@@ -220,6 +222,15 @@ def dsm_fe_energy_grad(params: dsm_params, c1, c2, mask, active: int, dP: float,
                                      dP, kcs, V0, fg, _ptr(energy), _ptr(grad), _ptr(terms),
                                      _ptr(scratch), scratch_bytes, _stream(stream)),
            "dsm_fe_energy_grad")
+
+
+def dsm_fe_energy_grad_noalloc(params: dsm_params, c1, c2, mask, active: int, dP: float,
+                               kcs: float, V0: float, fg: float, energy, grad, terms,
+                               stream=None):
+    _check(load().dsm_fe_energy_grad_noalloc(C.byref(params), _ptr(c1), _ptr(c2), _ptr(mask),
+                                             active, dP, kcs, V0, fg, _ptr(energy), _ptr(grad),
+                                             _ptr(terms), _stream(stream)),
+           "dsm_fe_energy_grad_noalloc")
 
 
 def dsm_vec_scratch_bytes(n: int) -> int:
