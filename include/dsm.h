@@ -236,11 +236,25 @@ dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float
                                const float *d_g, float *d_r, double *d_alpha,
                                void *d_scratch, size_t scratch_bytes, void *cuda_stream);
 
-/* Batched step: advance every handle by nsteps[i] steps in fused launches
- * (many small lattices per launch, one persistent grid).  All handles must
- * share lattice kind and precision and have the same stream.  Each lattice's
- * result equals its solo dsm_step result bitwise. */
-dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps);
+/* Batched step: advance handle i by nsteps[i] stage-2 steps, all handles in
+ * ONE persistent cooperative launch.  Resident blocks walk a work list of
+ * (lattice, 32-node-wide brick) pairs of every lattice: per step a moments
+ * phase and a fused phase, each followed by a grid-wide barrier whose waits are
+ * bounded (a barrier that does not complete within a few seconds latches
+ * DSM_E_TIMEOUT in every handle of the batch, reported by the next
+ * dsm_get_observables).  For many small lattices this replaces two launches per
+ * lattice per step by one launch per call.  Each lattice's result equals its
+ * solo dsm_step result bitwise (same per-node arithmetic).
+ * Requirements: n >= 1; every handle with fluid set and no latched error; all
+ * share the lattice kind, the precision, the stream, and whether rho2 != rho3;
+ * otherwise DSM_E_INVAL.  d_scratch: caller-owned device memory of at least
+ * dsm_batch_scratch_bytes(hs, n) bytes, 256-byte aligned (work list, per-lattice
+ * arguments, barrier words); DSM_E_WORKSPACE if short.  The call waits for its
+ * small host-to-device copies of the work list, then returns with the launch
+ * queued on the stream. */
+dsm_status dsm_batch_scratch_bytes(dsm_lattice *const *hs, int n, size_t *bytes);
+dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps, void *d_scratch,
+                          size_t scratch_bytes);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
 dsm_status dsm_destroy(dsm_lattice *h);

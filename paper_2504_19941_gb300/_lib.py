@@ -26,7 +26,8 @@ EXPORTED = (
     "dsm_step_collide", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
-    "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_step", "dsm_destroy",
+    "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_scratch_bytes", "dsm_batch_step",
+    "dsm_destroy",
 )
 
 
@@ -93,7 +94,8 @@ def load():
         "dsm_vec_axpby": (st, [C.c_longlong, C.c_double, fp, C.c_double, fp, vp]),
         "dsm_lbfgs_direction": (st, [C.c_longlong, C.c_int, C.POINTER(C.c_int), fp, fp, vp, vp, fp,
                                      fp, vp, vp, C.c_size_t, vp]),
-        "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong)]),
+        "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
         "dsm_destroy": (st, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -262,11 +264,19 @@ def dsm_lbfgs_direction(n: int, order, S, Y, rho, gamma, g, r, alpha, scratch, s
                                       _stream(stream)), "dsm_lbfgs_direction")
 
 
-def dsm_batch_step(handles, nsteps):
+def dsm_batch_scratch_bytes(handles) -> int:
+    n = len(handles)
+    hs = (C.c_void_p * max(n, 1))(*handles)
+    b = C.c_size_t()
+    _check(load().dsm_batch_scratch_bytes(hs, n, C.byref(b)), "dsm_batch_scratch_bytes")
+    return b.value
+
+
+def dsm_batch_step(handles, nsteps, scratch, scratch_bytes: int):
     n = len(handles)
     hs = (C.c_void_p * max(n, 1))(*handles)
     ns = (C.c_longlong * max(n, 1))(*nsteps)
-    _check(load().dsm_batch_step(hs, n, ns), "dsm_batch_step")
+    _check(load().dsm_batch_step(hs, n, ns, _ptr(scratch), scratch_bytes), "dsm_batch_step")
 
 
 def dsm_destroy(h: int):

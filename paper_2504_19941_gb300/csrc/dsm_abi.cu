@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "dsm_em.cuh"
 #include "dsm_lb_impl.cuh"
@@ -536,11 +537,54 @@ dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float
                                      d_scratch, (cudaStream_t)cuda_stream));
 }
 
-dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps) {
-  if (!hs || n < 0 || (n > 0 && !nsteps)) return DSM_E_INVAL;
+// Batch admission: common kind, precision, stream and density-contrast flag.
+static dsm_status batch_items(dsm_lattice *const *hs, int n, const long long *nsteps,
+                              std::vector<BatchRaw> &items) {
+  if (!hs || n < 1) return DSM_E_INVAL;
+  const dsm_lattice *h0 = hs[0];
+  if (!h0) return DSM_E_INVAL;
+  items.resize(n);
   for (int i = 0; i < n; i++) {
-    dsm_status s = dsm_step(hs[i], nsteps[i]);
-    if (s != DSM_OK) return s;
+    const dsm_lattice *h = hs[i];
+    if (!h) return DSM_E_INVAL;
+    if (h->kind != h0->kind || h->prm.precision != h0->prm.precision ||
+        h->stream != h0->stream || h->sp.rho_contrast != h0->sp.rho_contrast)
+      return DSM_E_INVAL;
+    if (nsteps && (nsteps[i] < 0 || nsteps[i] > (1ll << 30))) return DSM_E_INVAL;
+    items[i].r[0] = raw_of(h, 0);
+    items[i].r[1] = raw_of(h, 1);
+    items[i].nsteps = nsteps ? nsteps[i] : 0;
+    items[i].cur0 = h->cur;
+  }
+  return DSM_OK;
+}
+
+dsm_status dsm_batch_scratch_bytes(dsm_lattice *const *hs, int n, size_t *bytes) {
+  if (!bytes) return DSM_E_INVAL;
+  std::vector<BatchRaw> items;
+  dsm_status s = batch_items(hs, n, nullptr, items);
+  if (s != DSM_OK) return s;
+  *bytes = hs[0]->tab.batch_bytes(items.data(), n);
+  return DSM_OK;
+}
+
+dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps, void *d_scratch,
+                          size_t scratch_bytes) {
+  if (!nsteps || !d_scratch) return DSM_E_INVAL;
+  std::vector<BatchRaw> items;
+  dsm_status s = batch_items(hs, n, nsteps, items);
+  if (s != DSM_OK) return s;
+  for (int i = 0; i < n; i++)
+    if (!hs[i]->has_fluid || hs[i]->latched) return DSM_E_STATE;
+  if (scratch_bytes < hs[0]->tab.batch_bytes(items.data(), n) || ((uintptr_t)d_scratch & 255u))
+    return DSM_E_WORKSPACE;
+  cudaError_t e = hs[0]->tab.batch(items.data(), n, d_scratch, scratch_bytes,
+                                   hs[0]->sp.rho_contrast != 0, hs[0]->stream);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  for (int i = 0; i < n; i++) {
+    hs[i]->cur ^= (int)(nsteps[i] & 1);
+    hs[i]->step += nsteps[i];
+    hs[i]->moments_ready = false;
   }
   return DSM_OK;
 }

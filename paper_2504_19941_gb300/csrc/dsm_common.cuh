@@ -188,6 +188,13 @@ struct LBRaw {
   StepParams p;
 };
 
+// One lattice of a batched launch: its arguments for either current buffer.
+struct BatchRaw {
+  LBRaw r[2];         // r[p]: reads buffer p, writes buffer 1 - p
+  long long nsteps;
+  int cur0;
+};
+
 struct LBTable {
   cudaError_t (*moments)(const LBRaw &, cudaStream_t);
   cudaError_t (*node)(const LBRaw &, int stage, int mode, cudaStream_t);
@@ -195,6 +202,9 @@ struct LBTable {
   cudaError_t (*solid)(const void *sd, void *c1, long long N, double alpha_s, cudaStream_t);
   cudaError_t (*get_pops)(const LBRaw &, void *f, void *g, cudaStream_t);
   cudaError_t (*set_pops)(const LBRaw &, const void *f, const void *g, cudaStream_t);
+  cudaError_t (*batch)(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
+                       cudaStream_t);
+  size_t (*batch_bytes)(const BatchRaw *items, int n);
   int q, real_bytes, store_bytes;
   bool k16;
 };

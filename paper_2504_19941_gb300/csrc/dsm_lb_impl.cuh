@@ -12,6 +12,8 @@
 // the capillary force is taken in its potential form mu G[C] (see below).
 #pragma once
 
+#include <vector>
+
 #include "dsm_common.cuh"
 
 namespace dsm {
@@ -108,11 +110,8 @@ __device__ __noinline__ T link_fraction(T xs, T gn, T g0, T g1, T g2, int i) {
 // K1: moments pass.  C(x) = sum_i g_i after streaming (Sec. II.B, C = sum g).
 // ---------------------------------------------------------------------------
 template <int K, class T, class S>
-__global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
+__device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y, int z) {
   using L = Lat<K>;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   h.init(x, y, z, a.nx, a.ny, a.nz);
@@ -126,6 +125,12 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
   a.C[n] = s;
 }
 
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
+  moments_body<K, T, S>(a, blockIdx.x * blockDim.x + threadIdx.x,
+                        blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z * blockDim.z + threadIdx.z);
+}
+
 // ---------------------------------------------------------------------------
 // K2: fused pass.  STAGE 2: fluids on the frozen diffuse solid C1.
 // STAGE 1: relaxation of C1 itself (g carries C1; rho = 1, tau = tau_g = 1,
@@ -133,13 +138,10 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
 template <int K, class T, class S, int STAGE, int MODE, bool RC>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
+__device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
+                                          int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int y = blockIdx.y * blockDim.y + threadIdx.y;
-  int z = blockIdx.z * blockDim.z + threadIdx.z;
-  const bool valid = x < a.nx && y < a.ny && z < a.nz;
   if (MODE != MODE_OBS && !valid) return;
   if (!valid) x = y = z = 0;
   Hood h;
@@ -443,6 +445,98 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
   if constexpr (Store<S>::k16) a.g0_out[n] = float(C - gsum16);
 }
 
+template <int K, class T, class S, int STAGE, int MODE, bool RC>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  node_body<K, T, S, STAGE, MODE, RC>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
+}
+
+// ---------------------------------------------------------------------------
+// K9: batched persistent step.  One cooperative launch advances many lattices
+// (same lattice kind and precision) by up to tmax steps: per step a moments
+// phase and a fused phase over the work list of (lattice, brick) pairs, each
+// phase followed by a grid-wide barrier.  Resident blocks walk the list in a
+// grid-stride loop.  Every barrier wait is bounded: after kBarrierSpins polls
+// the block latches ERR_TIMEOUT in every lattice's error word and returns, so
+// a lost block can never hang the GPU.  Per-node arithmetic is node_body /
+// moments_body, the same code as the single-lattice step, so each lattice's
+// result equals its solo result bitwise.
+// ---------------------------------------------------------------------------
+template <class T, class S>
+struct BatchItem {
+  LBArgs<T, S> a[2];  // a[p]: arguments while the lattice's current buffer is p
+  int gx, gy, gz;     // bricks per axis
+  int brick0;         // first brick of this lattice in the work list
+  int nsteps;         // steps this launch takes for this lattice
+  int cur0;           // current buffer at launch
+};
+
+constexpr unsigned long long kBarrierSpins = 20000000ull;  // ~2-4 s of polling
+
+template <class T, class S>
+__device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int nitems) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+    ok = 1;
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*gen == g) {
+        __nanosleep(100);
+        if (++spins > kBarrierSpins) {
+          for (int i = 0; i < nitems; i++) atomicOr(items[i].a[0].err, ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int K, class T, class S, bool RC>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
+    batch_kernel(const BatchItem<T, S> *items, int nitems, const int *owner, int nbricks, int tmax,
+                 unsigned *bar) {
+  __shared__ LBArgs<T, S> sa;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  for (int t = 0; t < tmax; t++) {
+    for (int phase = 0; phase < 2; phase++) {
+      for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        const BatchItem<T, S> *it = items + __ldg(owner + b);
+        if (t >= it->nsteps) continue;  // uniform over the block
+        __syncthreads();
+        {  // this lattice's arguments for this step, into shared memory
+          const int *src = (const int *)&it->a[(it->cur0 + t) & 1];
+          int *dst = (int *)&sa;
+          for (int w = tid; w < (int)(sizeof(LBArgs<T, S>) / sizeof(int)); w += nthr) dst[w] = src[w];
+        }
+        __syncthreads();
+        const int lb = b - it->brick0;
+        const int bx = lb % it->gx, by = (lb / it->gx) % it->gy, bz = lb / (it->gx * it->gy);
+        const int x = bx * blockDim.x + threadIdx.x;
+        const int y = by * blockDim.y + threadIdx.y;
+        const int z = bz * blockDim.z + threadIdx.z;
+        if (phase == 0) moments_body<K, T, S>(sa, x, y, z);
+        else node_body<K, T, S, 2, MODE_STEP, RC>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
+      }
+      if (!grid_barrier<T, S>(bar, items, nitems)) return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K3: initial state at rest (reading of the unstated initial condition):
 // f_i = w_i, g_i = g_eq_i(C, mu(C), u = 0), stored as the post-collision state.
@@ -643,8 +737,70 @@ struct LBOps {
                                                                       (const T *)fi, (const T *)gi);
     return cudaGetLastError();
   }
+  static size_t batch_bytes(const BatchRaw *items, int n) {
+    long long bricks = 0;
+    for (int i = 0; i < n; i++) {
+      const dim3 g = lb_grid(K, items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
+      bricks += (long long)g.x * g.y * g.z;
+    }
+    return 256 + (size_t)round_up((long long)n * sizeof(BatchItem<T, S>), 256) +
+           (size_t)round_up(bricks * (long long)sizeof(int), 256);
+  }
+  static cudaError_t batch(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
+                           cudaStream_t st) {
+    if (bytes < batch_bytes(items, n)) return cudaErrorInvalidValue;
+    std::vector<BatchItem<T, S>> hi(n);
+    std::vector<int> owner;
+    int tmax = 0;
+    for (int i = 0; i < n; i++) {
+      BatchItem<T, S> &b = hi[i];
+      b.a[0] = typed<T, S>(items[i].r[0]);
+      b.a[1] = typed<T, S>(items[i].r[1]);
+      const dim3 g = lb_grid(K, items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
+      b.gx = g.x;
+      b.gy = g.y;
+      b.gz = g.z;
+      b.brick0 = (int)owner.size();
+      b.nsteps = (int)items[i].nsteps;
+      b.cur0 = items[i].cur0;
+      if (b.nsteps > tmax) tmax = b.nsteps;
+      owner.insert(owner.end(), (size_t)g.x * g.y * g.z, i);
+    }
+    if (tmax == 0 || owner.empty()) return cudaSuccess;
+    char *base = (char *)scratch;
+    unsigned *bar = (unsigned *)base;
+    BatchItem<T, S> *d_items = (BatchItem<T, S> *)(base + 256);
+    int *d_owner = (int *)(base + 256 + round_up((long long)n * sizeof(BatchItem<T, S>), 256));
+    cudaError_t e = cudaMemsetAsync(bar, 0, 256, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_items, hi.data(), n * sizeof(BatchItem<T, S>), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_owner, owner.data(), owner.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    // the copies above read pageable host memory: finish them before the
+    // host vectors go out of scope
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    const void *fn = rc ? (const void *)batch_kernel<K, T, S, true>
+                        : (const void *)batch_kernel<K, T, S, false>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const dim3 blk = lb_block(K);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, blk.x * blk.y * blk.z, 0)) !=
+        cudaSuccess)
+      return e;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > (long long)owner.size()) grid = (long long)owner.size();
+    int nb = (int)owner.size();
+    const BatchItem<T, S> *pi = d_items;
+    const int *po = d_owner;
+    void *args[] = {(void *)&pi, (void *)&n, (void *)&po, (void *)&nb, (void *)&tmax, (void *)&bar};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), blk, args, 0, st);
+  }
   static LBTable table() {
     LBTable t;
+    t.batch = &batch;
+    t.batch_bytes = &batch_bytes;
     t.moments = &moments;
     t.node = &node;
     t.init = &init;

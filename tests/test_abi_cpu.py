@@ -130,4 +130,5 @@ def test_null_arguments_rejected(lib):
     assert L.dsm_step(None, 1) == lib.DSM_E_INVAL
     assert L.dsm_destroy(None) == lib.DSM_E_INVAL
     assert L.dsm_get_observables(None, None) == lib.DSM_E_INVAL
-    assert L.dsm_batch_step(None, 1, None) == lib.DSM_E_INVAL
+    assert L.dsm_batch_step(None, 1, None, None, 0) == lib.DSM_E_INVAL
+    assert L.dsm_batch_scratch_bytes(None, 1, None) == lib.DSM_E_INVAL

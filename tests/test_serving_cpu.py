@@ -1,0 +1,140 @@
+"""Host logic of the serving loop, on the CPU with a fake executor and a fake
+clock: admission by HBM budget, FIFO order, rejection of malformed and
+oversized requests, failures injected on the host, quantum accounting,
+latency percentiles."""
+import math
+from dataclasses import dataclass
+
+import pytest
+
+from paper_2504_19941_gb300.serving import Scheduler, serial_run, summarize  # noqa: E402
+
+
+@dataclass
+class Req:
+    rid: int
+    arrival: float
+    steps: int
+    n: int
+    nbytes: int = 100
+    bad: bool = False
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+class FakeExecutor:
+    """Each step of a lattice costs `cost` seconds of fake time; a quantum over
+    several lattices costs the sum (one device)."""
+
+    def __init__(self, clock, cost=1e-3, fail=(), nan=()):
+        self.clock = clock
+        self.cost = cost
+        self.fail = set(fail)      # rids whose advance reports an error
+        self.nan = set(nan)        # rids whose finish reports a non-finite state
+        self.live = {}
+        self.steps = {}
+        self.peak = 0
+
+    def bytes_needed(self, req):
+        if req.bad:
+            raise ValueError("malformed request")
+        return req.nbytes
+
+    def admit(self, req):
+        h = ("h", req.rid)
+        self.live[h] = req
+        self.steps[req.rid] = 0
+        self.peak = max(self.peak, sum(r.nbytes for r in self.live.values()))
+        return h
+
+    def advance(self, work):
+        errs = {}
+        for h, k in work:
+            self.steps[h[1]] += k
+            self.clock.t += self.cost * k
+            if h[1] in self.fail:
+                errs[h] = "injected device error"
+        return errs
+
+    def finish(self, h):
+        req = self.live.pop(h)
+        if req.rid in self.nan:
+            return {"error": "non-finite population"}
+        return {"steps": self.steps[req.rid]}
+
+    def release(self, h):
+        self.live.pop(h, None)
+
+
+def _run(reqs, budget=1000, quantum=10, **kw):
+    clk = Clock()
+    ex = FakeExecutor(clk, **kw)
+    sch = Scheduler(ex, budget, quantum, clock=clk, sleep=clk.sleep)
+    recs = sch.run(reqs)
+    return recs, ex, clk
+
+
+def test_every_request_gets_exactly_its_steps():
+    reqs = [Req(i, 0.01 * i, steps=7 + 13 * i, n=10) for i in range(8)]
+    recs, ex, _ = _run(reqs, quantum=10)
+    assert all(r.status == "done" for r in recs)
+    assert all(ex.steps[r.rid] == r.steps for r in reqs)
+    assert all(r.finished >= r.admitted >= r.arrival - 1e-12 for r in recs)
+
+
+def test_budget_is_never_exceeded_and_admission_is_fifo():
+    reqs = [Req(i, 0.0, steps=50, n=10, nbytes=400) for i in range(6)]
+    recs, ex, _ = _run(reqs, budget=1000, quantum=10)
+    assert ex.peak <= 1000
+    adm = [r.admitted for r in recs]
+    assert adm == sorted(adm)               # FIFO
+    assert adm[2] > adm[1] and adm[1] == adm[0]  # only two fit at a time
+
+
+def test_rejections_and_failures_do_not_stop_the_loop():
+    reqs = [Req(0, 0.0, 30, 10), Req(1, 0.0, 30, 10, bad=True),
+            Req(2, 0.0, 30, 10, nbytes=5000), Req(3, 0.0, 30, 10), Req(4, 0.0, 30, 10),
+            Req(5, 0.0, 30, 10)]
+    recs, ex, _ = _run(reqs, budget=1000, fail={3}, nan={4})
+    st = {r.rid: r.status for r in recs}
+    assert st == {0: "done", 1: "rejected", 2: "rejected", 3: "failed", 4: "failed", 5: "done"}
+    assert not ex.live                      # everything released
+    s = summarize(recs, 1.0)
+    assert s["solves"] == 2 and s["rejected"] == 2 and s["failed"] == 2
+
+
+def test_continuous_batching_admits_arrivals_between_quanta():
+    # a long request is running when a short one arrives; the short one must
+    # not wait for the long one to finish
+    reqs = [Req(0, 0.0, steps=1000, n=10), Req(1, 0.05, steps=20, n=10)]
+    recs, _, _ = _run(reqs, quantum=10, cost=1e-3)
+    r0, r1 = recs
+    assert r1.finished < r0.finished
+    assert r1.admitted < 0.08
+
+
+def test_serial_baseline_serves_in_order():
+    reqs = [Req(i, 0.0, steps=100, n=10) for i in range(4)]
+    clk = Clock()
+    ex = FakeExecutor(clk)
+    recs = serial_run(ex, reqs, clock=clk, sleep=clk.sleep)
+    fin = [r.finished for r in recs]
+    assert fin == sorted(fin)
+    assert math.isclose(fin[-1], 4 * 100 * 1e-3)
+
+
+def test_percentiles():
+    from paper_2504_19941_gb300.serving import Record
+    recs = [Record(i, 0.0, finished=float(i + 1), status="done", steps=1, nodes=1)
+            for i in range(100)]
+    s = summarize(recs, 10.0)
+    assert s["p50_s"] == 50.0 and s["p99_s"] == 99.0 and s["solves_per_s"] == 10.0
