@@ -296,6 +296,49 @@ def run_gpu(args, rank, world):
     return 0
 
 
+def run_serve(args, rank, world):
+    """Served form: a Poisson stream of wetting studies through the
+    continuous-batching scheduler, against serving the same stream one request
+    at a time.  Requests: 50 % D2Q9 (side 64..512), 50 % D3Q19 (side 64..160),
+    random pillars / sinusoidal walls / sphere packings, contact angle
+    U[30, 150] degrees, step budgets U[2000, 20000] scaled by --serve-scale."""
+    import torch
+    import synthetic as S
+    from paper_2504_19941_gb300.serving import GpuExecutor, Scheduler, serial_run, summarize
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reqs = S.serving_stream(n_req=args.serve_requests, rate=args.serve_rate, seed=0,
+                            scale_steps=args.serve_scale)
+    mine = [r for r in reqs if r.rid % world == rank]   # replicas: requests sharded by id
+    warm = S.serving_stream(n_req=4, rate=1000.0, seed=99, max_side_2d=96, max_side_3d=48,
+                            steps=(20, 40))
+    Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(warm)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        recs = Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(mine)
+        wall = time.perf_counter() - t0
+    s = summarize(recs, wall)
+    base = None
+    if not args.no_serial_baseline:
+        t0 = time.perf_counter()
+        srecs = serial_run(GpuExecutor("f32"), mine)
+        base = summarize(srecs, time.perf_counter() - t0)
+    if rank == 0:
+        out = {"metric": "served wetting sweeps: solves/s (p50/p99 latency)",
+               "value": s["solves_per_s"] * world, "unit": "solves/s", "n_gpus": world,
+               "steps": len(mine), "warmup": len(warm), "ms_per_step": None,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"{args.serve_requests} requests, Poisson {args.serve_rate}/s, "
+                                      f"steps x{args.serve_scale}", "quantum": args.serve_quantum,
+                          "parallelism": f"replicas x{world}"},
+               "serving": s, "one_at_a_time": base, "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,12 +348,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
+    ap.add_argument("--workload", default="lb", choices=["lb", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-scale", type=float, default=0.05)
+    ap.add_argument("--serve-quantum", type=int, default=100)
+    ap.add_argument("--no-serial-baseline", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
     return run_gpu(args, rank, world)
 
 
