@@ -311,7 +311,7 @@ def run_serve(args, rank, world):
     reqs = S.serving_stream(n_req=args.serve_requests, rate=args.serve_rate, seed=0,
                             scale_steps=args.serve_scale)
     mine = [r for r in reqs if r.rid % world == rank]   # replicas: requests sharded by id
-    warm = S.serving_stream(n_req=4, rate=1000.0, seed=99, max_side_2d=96, max_side_3d=48,
+    warm = S.serving_stream(n_req=4, rate=1000.0, seed=99, min_side=32, max_side_2d=96, max_side_3d=48,
                             steps=(20, 40))
     Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(warm)
     torch.cuda.synchronize()

@@ -91,7 +91,7 @@ def test_batch_argument_checks():
 
 
 def test_serving_results_equal_solo_runs():
-    reqs = S.serving_stream(n_req=10, rate=200.0, seed=3, max_side_2d=160, max_side_3d=48,
+    reqs = S.serving_stream(n_req=10, rate=200.0, seed=3, min_side=24, max_side_2d=160, max_side_3d=48,
                             steps=(40, 200))
     ex = GpuExecutor("f32", small_nodes=20_000)
     recs = Scheduler(ex, budget_bytes=8 << 30, quantum=32).run(reqs)
