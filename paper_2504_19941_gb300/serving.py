@@ -180,8 +180,9 @@ def summarize(records, wall: float) -> dict:
 
 class GpuExecutor:
     """Device work of the scheduler through libdsm: one Lattice per request,
-    small lattices advanced together by dsm_batch_step on the current stream,
-    large ones by dsm_step, each on a stream of its own."""
+    small lattices advanced together by dsm_batch_step on the current stream
+    (one launch per lattice kind), large ones by dsm_step, each on a stream of
+    its own."""
 
     def __init__(self, precision="f32", small_nodes=300_000, device="cuda"):
         import torch
@@ -229,13 +230,15 @@ class GpuExecutor:
         large = [(h, k) for h, k in work if h.n > self.small_nodes and k > 0]
         for h, k in large:  # queued on each lattice's own stream
             _lib.dsm_step(h.h, k)
-        if small:
-            hs = [h.h for h, _ in small]
+        # one batched launch per lattice kind (a batch shares kind and precision)
+        for kind in sorted({h.params.lattice for h, _ in small}):
+            grp = [(h, k) for h, k in small if h.params.lattice == kind]
+            hs = [h.h for h, _ in grp]
             nb = _lib.dsm_batch_scratch_bytes(hs)
             if self.batch_scratch is None or self.batch_scratch.numel() < nb:
                 self.batch_scratch = torch.empty(max(nb, 1 << 20), dtype=torch.uint8,
                                                  device=self.device)
-            _lib.dsm_batch_step(hs, [k for _, k in small], self.batch_scratch,
+            _lib.dsm_batch_step(hs, [k for _, k in grp], self.batch_scratch,
                                 self.batch_scratch.numel())
         torch.cuda.synchronize(self.device)
         return {}
