@@ -343,6 +343,160 @@ def run_serve(args, rank, world):
     return 0
 
 
+def _time_steps(lat, steps, warmup):
+    """Per-step and fused-pass times (CUDA events) of `steps` steps."""
+    import torch
+    from paper_2504_19941_gb300 import _lib
+    for _ in range(warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+    stream = lat.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        _lib.dsm_step_moments(lat.h)
+        ev[k][0].record(stream)
+        _lib.dsm_step_collide(lat.h)
+        ev[k][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / steps, sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+
+
+def run_precision(args, rank, world):
+    """Precision forms on the 384x384x256 capillary-rise lattice (D3Q19): FP32
+    storage and BF16 / FP16 storage of the populations, FP32 arithmetic."""
+    import torch
+    import synthetic as S
+    import paper_2504_19941_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    case = S.plates_rise_3d()
+    peak, peak_kind = _peaks()
+    out = {}
+    for prec, bmin in (("f32", 308), ("bf16", 160), ("f16", 160)):
+        p = P.make_params("D3Q19", case.shape, prec, theta_deg=case.theta_deg, g12=case.g12,
+                          g23=case.g23, alpha_s=case.alpha_s, body=case.body)
+        lat = P.Lattice(p, device=dev)
+        lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
+        lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float32, device=dev))
+        t_step, t_k2 = _time_steps(lat, args.steps, args.warmup)
+        ob = lat.observables()
+        out[prec] = {"MLUPS": lat.n / t_step / 1e6, "ms_per_step": t_step * 1e3,
+                     "k2_ms": t_k2 * 1e3, "bytes_per_lu": bmin,
+                     "roofline_frac": bmin * lat.n / t_k2 / 1e9 / peak,
+                     "nonfinite": ob["nonfinite"]}
+        del lat
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"metric": "D3Q19 precision forms MLUPS (384x384x256 capillary rise)",
+                          "value": out["bf16"]["MLUPS"], "unit": "MLUPS", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "dtype": "bf16-storage/f32",
+                          "higher_is_better": True, "data": "synthetic", "peak_gbs": peak,
+                          "peak_source": peak_kind, "forms": out}), flush=True)
+    return 0
+
+
+def run_plain_fp64(args, rank, world):
+    """The plain FP64 D2Q9 128x64 wall-drop case: per-step launches against one
+    persistent batched launch of all its steps."""
+    import torch
+    import synthetic as S
+    import paper_2504_19941_gb300 as P
+    from paper_2504_19941_gb300 import _lib
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    case = S.wall_drop_2d()
+    res = {}
+    for mode in ("per_step_launches", "persistent_launch"):
+        p = P.make_params("D2Q9", case.shape, "f64", theta_deg=case.theta_deg, g12=case.g12,
+                          g23=case.g23, alpha_s=case.alpha_s)
+        lat = P.Lattice(p, device=dev)
+        lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float64, device=dev))
+        lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float64, device=dev))
+        nb = _lib.dsm_batch_scratch_bytes([lat.h])
+        scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+        lat.step(10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "per_step_launches":
+            lat.step(case.steps)
+        else:
+            _lib.dsm_batch_step([lat.h], [case.steps], scratch, nb)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[mode] = {"us_per_step": dt / case.steps * 1e6, "MLUPS": lat.n * case.steps / dt / 1e6}
+    if rank == 0:
+        print(json.dumps({"metric": "D2Q9 FP64 128x64 wall drop, 2000 steps", "unit": "us/step",
+                          "value": res["persistent_launch"]["us_per_step"],
+                          "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+                          "data": "synthetic", "modes": res}), flush=True)
+    return 0
+
+
+def run_em(args, rank, world):
+    """Energy-minimisation twin on a 128^3 grid (sphere of radius 20 at a flat
+    liquid/gas interface): energy + gradient evaluations per second, and L-BFGS
+    iterations per second with the time to an rms gradient of 1e-6."""
+    import torch
+    import synthetic as S
+    import paper_2504_19941_gb300 as P
+    from paper_2504_19941_gb300.energy import FreeEnergy, lbfgs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    case = S.em_sphere_interface()
+    n = case.n
+    p = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg, g23=case.g23,
+                      g12=case.g12)
+    # the solid's tanh profile of Sec. II.A, written by the library from the distance
+    lat_p = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg, g23=case.g23,
+                          g12=case.g12, alpha_s=1.0)
+    lat = P.Lattice(lat_p, device=dev)
+    lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
+    c1 = lat.field("C1")
+    del lat
+    c2 = torch.as_tensor(case.c2, dtype=torch.float32, device=dev)
+    fe = FreeEnergy(p, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        fe(c1, c2, energy=E, grad=g, kcs=1e-2, V0=float(c2.double().sum()))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    V0 = float(c2.double().sum())
+    e0.record()
+    for _ in range(reps):
+        fe(c1, c2, energy=E, grad=g, kcs=1e-2, V0=V0)
+    e1.record()
+    torch.cuda.synchronize()
+    t_eval = e0.elapsed_time(e1) / 1e3 / reps
+    peak, peak_kind = _peaks()
+    t0 = time.perf_counter()
+    x, Emin, info = lbfgs(fe, c2, c1, active=2, kcs=1e-2, V0=V0, tol=1e-6,
+                          max_iter=args.em_iters)
+    torch.cuda.synchronize()
+    t_lb = time.perf_counter() - t0
+    if rank == 0:
+        print(json.dumps({"metric": "EM energy+gradient evaluations/s (128^3, D3Q19 stencil)",
+                          "value": 1.0 / t_eval, "unit": "evals/s", "n_gpus": 1,
+                          "higher_is_better": True, "dtype": "f32 fields / f64 energy",
+                          "data": "synthetic",
+                          "roofline": {"bound": "hbm", "bytes_per_node": 12,
+                                       "achieved": 12 * n / t_eval / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": 12 * n / t_eval / 1e9 / peak,
+                                       "peak_source": peak_kind},
+                          "eval_ms": t_eval * 1e3,
+                          "lbfgs": {"iterations": info["iterations"],
+                                    "evaluations": info["evaluations"],
+                                    "rms_grad": info["rms_grad"], "energy": Emin,
+                                    "seconds": t_lb, "iters_per_s": info["iterations"] / t_lb,
+                                    "tol": 1e-6}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,7 +506,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
-    ap.add_argument("--workload", default="lb", choices=["lb", "serve"])
+    ap.add_argument("--workload", default="lb", choices=["lb", "serve", "precision", "fp64", "em"])
+    ap.add_argument("--em-iters", type=int, default=3000)
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-scale", type=float, default=0.05)
@@ -366,6 +521,12 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "precision":
+        return run_precision(args, rank, world)
+    if args.workload == "fp64":
+        return run_plain_fp64(args, rank, world)
+    if args.workload == "em":
+        return run_em(args, rank, world)
     return run_gpu(args, rank, world)
 
 
