@@ -2,6 +2,7 @@
 // minimisation (Sec. II.A of the paper) and the FP64-accumulating vector
 // kernels of its L-BFGS driver.
 #include "dsm_em.cuh"
+#include "dsm_reduce.cuh"
 
 namespace dsm {
 
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
   int y = blockIdx.y * blockDim.y + threadIdx.y;
   int z = blockIdx.z * blockDim.z + threadIdx.z;
   const bool valid = x < a.nx && y < a.ny && z < a.nz;
-  double acc[FE_K] = {0, 0, 0, 0, 0};
+  float acc[FE_K] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (valid) {
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x + 1 == a.nx ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y + 1 == a.ny ? 0 : y + 1;
@@ -83,13 +84,13 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
     const float A2 = a.a2;
     // per-node densities in FP32, accumulated in FP64
     const float q1 = c1 * (1.0f - c1), q2 = c2 * (1.0f - c2), q3 = c3 * (1.0f - c3);
-    acc[0] = (double)(0.5f * (k1 * q1 * q1 + k2 * q2 * q2 + k3 * q3 * q3));
-    acc[1] = (double)(1.5f * A2 * (k1 * p1 + k2 * p2 + k3 * p3));
+    acc[0] = 0.5f * (k1 * q1 * q1 + k2 * q2 * q2 + k3 * q3 * q3);
+    acc[1] = 1.5f * A2 * (k1 * p1 + k2 * p2 + k3 * p3);
     const bool inS = a.mask ? a.mask[n] != 0 : false;
     const bool chi = (inS && c1 < 0.5f) || (!inS && c1 > 0.5f);
-    if (a.active == 1 && chi) acc[2] = (double)(a.beta * (c1 - 0.5f) * (c1 - 0.5f));
+    if (a.active == 1 && chi) acc[2] = a.beta * (c1 - 0.5f) * (c1 - 0.5f);
     const int hgt = (a.d == 2) ? y : z;
-    acc[3] = (double)(a.fg * c2 * (float)hgt);
+    acc[3] = a.fg * c2 * (float)hgt;
     acc[4] = c2;
     const float dd1 = k1 * bw(c1) - A2 * k1 * l1;
     const float dd2 = k2 * bw(c2) - A2 * k2 * l2;
@@ -99,13 +100,11 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
     else gr = dd1 - dd3 + (chi ? 2.0f * a.beta * (c1 - 0.5f) : 0.0f);
     a.grad[n] = gr;
   }
-  double out[FE_K];
-  block_sum<FE_K>(acc, out);
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  if (tid < FE_K) {
-    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    a.partials[b * FE_K + tid] = out[tid];
-  }
+  // per-node FP32 densities, summed with carried rounding errors inside a warp
+  // and in FP64 across warps and blocks
+  const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+  const int sums[FE_K] = {0, 0, 0, 0, 0};
+  block_reduce_ff<FE_K>(acc, sums, a.partials + b * FE_K);
 }
 
 // Sum the per-block partials in block order; assemble E and the constraint.

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dsm_common.cuh"
+#include "dsm_reduce.cuh"
 
 namespace dsm {
 
@@ -334,36 +335,44 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   }
 
   if constexpr (MODE == MODE_OBS) {
-    double vals[OBS_K];
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < Q; j++) bad |= !isfinite(g[j]) || (!solid_x && !isfinite(f[j]));
-    vals[0] = valid ? double(C) : 0.0;
-    vals[1] = valid ? double((STAGE == 2) ? c1 : C) : 0.0;
-    vals[2] = valid ? 0.5 * double(rho) * double(uu) : 0.0;
-    vals[3] = valid ? sqrt(double(uu)) : 0.0;
-    vals[4] = (valid && bad) ? 1.0 : 0.0;
-    // deterministic block reduction: warp shuffles then one shared pass
-    __shared__ double sh[OBS_K][32];
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    if constexpr (sizeof(T) == 4) {
+      // FP32 lattices: carried-error sums in FP32 within a warp, FP64 beyond
+      const float vals[OBS_K] = {valid ? float(C) : 0.f, valid ? float((STAGE == 2) ? c1 : C) : 0.f,
+                                 valid ? 0.5f * float(rho) * float(uu) : 0.f,
+                                 valid ? sqrtf(float(uu)) : 0.f, (valid && bad) ? 1.f : 0.f};
+      const int is_max[OBS_K] = {0, 0, 0, 1, 1};
+      block_reduce_ff<OBS_K>(vals, is_max, a.partials + b * OBS_K);
+    } else {
+      double vals[OBS_K];
+      vals[0] = valid ? double(C) : 0.0;
+      vals[1] = valid ? double((STAGE == 2) ? c1 : C) : 0.0;
+      vals[2] = valid ? 0.5 * double(rho) * double(uu) : 0.0;
+      vals[3] = valid ? sqrt(double(uu)) : 0.0;
+      vals[4] = (valid && bad) ? 1.0 : 0.0;
+      __shared__ double sh[OBS_K][32];
+      const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+      const int lane = tid & 31, warp = tid >> 5;
+      const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < OBS_K; k++) {
-      double v = vals[k];
+      for (int k = 0; k < OBS_K; k++) {
+        double v = vals[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double w2 = __shfl_down_sync(0xffffffffu, v, o);
-        v = (k == 3 || k == 4) ? fmax(v, w2) : v + w2;
+        for (int o = 16; o > 0; o >>= 1) {
+          const double w2 = __shfl_down_sync(0xffffffffu, v, o);
+          v = (k == 3 || k == 4) ? fmax(v, w2) : v + w2;
+        }
+        if (lane == 0) sh[k][warp] = v;
       }
-      if (lane == 0) sh[k][warp] = v;
-    }
-    __syncthreads();
-    if (tid < OBS_K) {
-      double v = sh[tid][0];
-      for (int w2 = 1; w2 < nw; w2++) v = (tid == 3 || tid == 4) ? fmax(v, sh[tid][w2]) : v + sh[tid][w2];
-      const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-      a.partials[b * OBS_K + tid] = v;
+      __syncthreads();
+      if (tid < OBS_K) {
+        double v = sh[tid][0];
+        for (int w2 = 1; w2 < nw; w2++) v = (tid == 3 || tid == 4) ? fmax(v, sh[tid][w2]) : v + sh[tid][w2];
+        a.partials[b * OBS_K + tid] = v;
+      }
     }
     return;
   }
@@ -658,9 +667,20 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
 // ---------------------------------------------------------------------------
 // Host side: typed launchers behind a type-erased table.
 // ---------------------------------------------------------------------------
-inline dim3 lb_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+// Block shape of the per-lattice launches.  Lattices too small to give every SM
+// a 256-thread block (fewer than ~2 x 152 x 256 nodes) use 64-thread blocks so
+// that their work spreads over four times as many SMs.  The batched launch keeps
+// the 256-thread shape for every lattice (lb_block_batch).
+inline dim3 lb_block_batch(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+inline dim3 lb_block(int kind, int nx, int ny, int nz) {
+  if ((long long)nx * ny * nz < 2ll * 152 * 256) return kind == 0 ? dim3(32, 2, 1) : dim3(32, 1, 2);
+  return lb_block_batch(kind);
+}
+inline dim3 lb_grid_of(dim3 b, int nx, int ny, int nz) {
+  return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
+}
 inline dim3 lb_grid(int kind, int nx, int ny, int nz) {
-  const dim3 b = lb_block(kind);
+  const dim3 b = lb_block(kind, nx, ny, nz);
   return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
 }
 
@@ -686,17 +706,17 @@ LBArgs<T, S> typed(const LBRaw &r) {
 template <int K, class T, class S>
 struct LBOps {
   static cudaError_t moments(const LBRaw &r, cudaStream_t st) {
-    moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r));
+    moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
   template <int STAGE, int MODE>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
     if (STAGE == 2 && r.p.rho_contrast)
       node_kernel<K, T, S, STAGE, MODE, true>
-          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
+          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r), r.field_sel);
     else
       node_kernel<K, T, S, STAGE, MODE, false>
-          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(typed<T, S>(r), r.field_sel);
+          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r), r.field_sel);
   }
   static cudaError_t node(const LBRaw &r, int stage, int mode, cudaStream_t st) {
     if (stage == 2) {
@@ -712,10 +732,10 @@ struct LBOps {
   }
   static cudaError_t init(const LBRaw &r, const void *cfield, int stage, cudaStream_t st) {
     if (stage == 2)
-      init_kernel<K, T, S, 2><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(
+      init_kernel<K, T, S, 2><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(
           typed<T, S>(r), (const T *)cfield);
     else
-      init_kernel<K, T, S, 1><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K), 0, st>>>(
+      init_kernel<K, T, S, 1><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(
           typed<T, S>(r), (const T *)cfield);
     return cudaGetLastError();
   }
@@ -740,7 +760,7 @@ struct LBOps {
   static size_t batch_bytes(const BatchRaw *items, int n) {
     long long bricks = 0;
     for (int i = 0; i < n; i++) {
-      const dim3 g = lb_grid(K, items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
+      const dim3 g = lb_grid_of(lb_block_batch(K), items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
       bricks += (long long)g.x * g.y * g.z;
     }
     return 256 + (size_t)round_up((long long)n * sizeof(BatchItem<T, S>), 256) +
@@ -756,7 +776,7 @@ struct LBOps {
       BatchItem<T, S> &b = hi[i];
       b.a[0] = typed<T, S>(items[i].r[0]);
       b.a[1] = typed<T, S>(items[i].r[1]);
-      const dim3 g = lb_grid(K, items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
+      const dim3 g = lb_grid_of(lb_block_batch(K), items[i].r[0].nx, items[i].r[0].ny, items[i].r[0].nz);
       b.gx = g.x;
       b.gy = g.y;
       b.gz = g.z;
@@ -785,7 +805,7 @@ struct LBOps {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const dim3 blk = lb_block(K);
+    const dim3 blk = lb_block_batch(K);
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, blk.x * blk.y * blk.z, 0)) !=
         cudaSuccess)
       return e;
