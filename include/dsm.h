@@ -195,18 +195,20 @@ dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const floa
  * is owned by an allocator that forbids side allocations).  The paper has no
  * counterpart: it is a service of this library.
  * Same arguments and results as dsm_fe_energy_grad minus the scratch buffer:
- * the reduction scratch is a fixed array of DSM_NOALLOC_SCRATCH_BYTES inside
- * the library's device image, which every GPU that loads the library holds
- * until the process exits.  Lattices whose reduction needs more (above about
- * 6.7 million nodes) are refused with DSM_E_WORKSPACE.  No device memory
- * is allocated or freed by this call.
+ * the reduction scratch is a fixed array of DSM_NOALLOC_SCRATCH_BYTES (64 KiB)
+ * inside the library's device image, which every GPU that loads the library
+ * holds until the process exits.  The energy kernel leaves at most one partial
+ * sum per resident block (608), about 25 KB, whatever the lattice size, so every
+ * lattice the library accepts fits; a lattice whose reduction did not fit would
+ * be refused with DSM_E_WORKSPACE.  Invalid sizes are refused with DSM_E_INVAL
+ * before any device work.  No device memory is allocated or freed by this call.
  * The first call on a device resolves the array's device address (a one-time
  * set-up per device, with that device current); make that first call before
  * any stream capture.  All calls on a device share the array: calls whose work
  * overlaps on the GPU (different streams, or several host threads) race on it
  * and must be serialised by the caller.  Every scratch word a call reads is
  * written earlier in the same call, so nothing needs clearing between calls. */
-#define DSM_NOALLOC_SCRATCH_BYTES ((size_t)1 << 20)
+#define DSM_NOALLOC_SCRATCH_BYTES ((size_t)1 << 16)
 dsm_status dsm_fe_energy_grad_noalloc(const dsm_params *p, const float *d_c1, const float *d_c2,
                                       const unsigned char *d_mask, int active, double dP,
                                       double kcs, double V0, double fg, double *d_energy,

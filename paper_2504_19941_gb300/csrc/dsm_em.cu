@@ -11,29 +11,6 @@ __device__ __forceinline__ T bw(T c) {
   return c * (T(1) - c) * (T(1) - T(2) * c);
 }
 
-// Deterministic block sum of NV doubles: warp shuffles, then warp 0 over the
-// per-warp results in order; thread 0 writes out[0..NV).
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
-  __shared__ double sh[NV][32];
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int lane = tid & 31, warp = tid >> 5;
-  const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
-    double s = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[k][warp] = s;
-  }
-  __syncthreads();
-  if (tid < NV) {
-    double s = 0.0;
-    for (int w = 0; w < nw; w++) s += sh[tid][w];
-    out[tid] = s;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // K4: per-node energy density and gradient (FP32), per-block FP64 partials.
 //   bulk     sum_n kappa_n/2 C_n^2 (1 - C_n)^2                Eq. [frozen:bulk_energy]
@@ -46,15 +23,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
 // d_n = kappa_n b(C_n) - a^2 kappa_n L[C_n],  C3 = 1 - C1 - C2.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
+__global__ void __launch_bounds__(256) fe_kernel(FEArgs a, int gx, int gy, int nbricks) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int y = blockIdx.y * blockDim.y + threadIdx.y;
-  int z = blockIdx.z * blockDim.z + threadIdx.z;
-  const bool valid = x < a.nx && y < a.ny && z < a.nz;
-  float acc[FE_K] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (valid) {
+  FF acc[FE_K];
+#pragma unroll
+  for (int k = 0; k < FE_K; k++) acc[k] = FF{0.0f, 0.0f};
+  // resident blocks walk the node bricks (blockDim-shaped boxes) in a fixed
+  // grid-stride order, so each block leaves one partial sum
+  for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+    const int bx = b % gx, by = (b / gx) % gy, bz = b / (gx * gy);
+    const int x = bx * blockDim.x + threadIdx.x;
+    const int y = by * blockDim.y + threadIdx.y;
+    const int z = bz * blockDim.z + threadIdx.z;
+    if (!(x < a.nx && y < a.ny && z < a.nz)) continue;
     const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x + 1 == a.nx ? 0 : x + 1;
     const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y + 1 == a.ny ? 0 : y + 1;
     const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z + 1 == a.nz ? 0 : z + 1;
@@ -82,16 +64,16 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
     l2 *= 6.f;
     l3 *= 6.f;
     const float A2 = a.a2;
-    // per-node densities in FP32, accumulated in FP64
+    // per-node densities in FP32, accumulated with carried rounding errors
     const float q1 = c1 * (1.0f - c1), q2 = c2 * (1.0f - c2), q3 = c3 * (1.0f - c3);
-    acc[0] = 0.5f * (k1 * q1 * q1 + k2 * q2 * q2 + k3 * q3 * q3);
-    acc[1] = 1.5f * A2 * (k1 * p1 + k2 * p2 + k3 * p3);
+    acc[0] = ff_add(acc[0], FF{0.5f * (k1 * q1 * q1 + k2 * q2 * q2 + k3 * q3 * q3), 0.0f});
+    acc[1] = ff_add(acc[1], FF{1.5f * A2 * (k1 * p1 + k2 * p2 + k3 * p3), 0.0f});
     const bool inS = a.mask ? a.mask[n] != 0 : false;
     const bool chi = (inS && c1 < 0.5f) || (!inS && c1 > 0.5f);
-    if (a.active == 1 && chi) acc[2] = a.beta * (c1 - 0.5f) * (c1 - 0.5f);
+    if (a.active == 1 && chi) acc[2] = ff_add(acc[2], FF{a.beta * (c1 - 0.5f) * (c1 - 0.5f), 0.0f});
     const int hgt = (a.d == 2) ? y : z;
-    acc[3] = a.fg * c2 * (float)hgt;
-    acc[4] = c2;
+    acc[3] = ff_add(acc[3], FF{a.fg * c2 * (float)hgt, 0.0f});
+    acc[4] = ff_add(acc[4], FF{c2, 0.0f});
     const float dd1 = k1 * bw(c1) - A2 * k1 * l1;
     const float dd2 = k2 * bw(c2) - A2 * k2 * l2;
     const float dd3 = k3 * bw(c3) - A2 * k3 * l3;
@@ -100,11 +82,8 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a) {
     else gr = dd1 - dd3 + (chi ? 2.0f * a.beta * (c1 - 0.5f) : 0.0f);
     a.grad[n] = gr;
   }
-  // per-node FP32 densities, summed with carried rounding errors inside a warp
-  // and in FP64 across warps and blocks
-  const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
   const int sums[FE_K] = {0, 0, 0, 0, 0};
-  block_reduce_ff<FE_K>(acc, sums, a.partials + b * FE_K);
+  block_reduce_ff<FE_K>(acc, sums, a.partials + (long long)blockIdx.x * FE_K);
 }
 
 // Sum the per-block partials in block order; assemble E and the constraint.
@@ -146,14 +125,17 @@ __global__ void add_dev_scalar_kernel(long long n, const double *c, float *g) {
 }
 
 static dim3 fe_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
-static dim3 fe_grid(int kind, int nx, int ny, int nz) {
+static dim3 fe_bricks(int kind, int nx, int ny, int nz) {
   const dim3 b = fe_block(kind);
   return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
 }
+constexpr long long FE_MAX_BLOCKS = 152 * 4;  // fixed grid: four blocks per SM
 
+// blocks (= partial sums) of one evaluation
 long long fe_blocks(int kind, int nx, int ny, int nz) {
-  const dim3 g = fe_grid(kind, nx, ny, nz);
-  return (long long)g.x * g.y * g.z;
+  const dim3 g = fe_bricks(kind, nx, ny, nz);
+  const long long nb = (long long)g.x * g.y * g.z;
+  return nb < FE_MAX_BLOCKS ? nb : FE_MAX_BLOCKS;
 }
 
 size_t fe_scratch_bytes(int kind, int nx, int ny, int nz) {
@@ -167,8 +149,10 @@ cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, doub
   double *dEcs = (double *)((char *)scratch + round_up(nb * FE_K * sizeof(double), 256));
   a.partials = partials;
   a.const_grad = (kcs == 0.0) ? (float)(-dP) : 0.0f;
-  if (kind == 0) fe_kernel<0><<<fe_grid(0, a.nx, a.ny, a.nz), fe_block(0), 0, st>>>(a);
-  else fe_kernel<1><<<fe_grid(1, a.nx, a.ny, a.nz), fe_block(1), 0, st>>>(a);
+  const dim3 g = fe_bricks(kind, a.nx, a.ny, a.nz);
+  const int nbricks = (int)((long long)g.x * g.y * g.z);
+  if (kind == 0) fe_kernel<0><<<(unsigned)nb, fe_block(0), 0, st>>>(a, g.x, g.y, nbricks);
+  else fe_kernel<1><<<(unsigned)nb, fe_block(1), 0, st>>>(a, g.x, g.y, nbricks);
   fe_finalize_kernel<<<1, 256, 0, st>>>(partials, nb, dP, kcs, V0, energy, terms, dEcs);
   if (kcs != 0.0 && a.active == 2) {
     const long long N = (long long)a.nx * a.ny * a.nz;
@@ -186,13 +170,14 @@ cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, doub
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) dot_kernel(long long n, const float *x, const float *y,
                                                   double *partials) {
-  double s[1] = {0.0};
+  // exact FP32 products (TwoProd) summed with carried errors: FP64 accuracy
+  // without FP64 instructions per element
+  FF s[1] = {FF{0.0f, 0.0f}};
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
-    s[0] += (double)x[k] * (double)y[k];
-  double out[1];
-  block_sum<1>(s, out);
-  if (threadIdx.x == 0) partials[blockIdx.x] = out[0];
+    s[0] = ff_add(s[0], two_prod(x[k], y[k]));
+  const int sums[1] = {0};
+  block_reduce_ff<1>(s, sums, partials + blockIdx.x);
 }
 
 __global__ void dot_finalize_kernel(const double *partials, int nb, const double *scale,

@@ -23,6 +23,7 @@ import paper_2504_19941_gb300 as P  # noqa: E402
 from paper_2504_19941_gb300 import _lib  # noqa: E402
 
 DEV = "cuda"
+NOALLOC_BYTES = 1 << 16  # DSM_NOALLOC_SCRATCH_BYTES in include/dsm.h
 
 
 def _fields(n, seed):
@@ -59,8 +60,15 @@ def test_noalloc_matches_caller_scratch_entry_point(lat, shape):
         torch.testing.assert_close(t, t_ref, rtol=1e-6, atol=1e-9)
 
 
-def test_noalloc_refuses_lattices_beyond_its_array():
-    p = P.make_params("D3Q19", (256, 256, 128), "f32", theta_deg=90.0)
+def test_noalloc_array_holds_every_accepted_lattice():
+    # the energy kernel leaves at most one partial sum per resident block, so
+    # the scratch it needs does not grow with the lattice: the largest lattice
+    # the library accepts fits the fixed array
+    need = _lib.dsm_fe_scratch_bytes(1, 1290, 1290, 1290)  # ~2^31 - 1 nodes
+    assert need <= NOALLOC_BYTES
+    # an invalid lattice is refused on the host, before any device work
+    # (the pointers are never touched)
+    p = P.make_params("D3Q19", (2048, 2048, 1024), "f32", theta_deg=90.0)
     with pytest.raises(P.DSMError) as e:
         _lib.dsm_fe_energy_grad_noalloc(p, 16, 16, None, 2, 0.0, 0.0, 0.0, 0.0, 16, 16, None)
-    assert e.value.status == _lib.DSM_E_WORKSPACE
+    assert e.value.status == _lib.DSM_E_INVAL
