@@ -46,23 +46,25 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a, int gx, int gy, int n
     const int n = x + y * a.nx + z * s;
     const float k1 = a.kappa[0], k2 = a.kappa[1], k3 = a.kappa[2];
     const float c1 = a.c1[n], c2 = a.c2[n], c3 = 1.0f - c1 - c2;
-    float l1 = 0.f, l2 = 0.f, l3 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    // C3 = 1 - C1 - C2, so its differences are -(d1 + d2): L[C3] = -L[C1] - L[C2]
+    // and its pair sum is p1 + p2 + 2 x12 with x12 = sum_i w_i d1 d2
+    float l1 = 0.f, l2 = 0.f, p1 = 0.f, p2 = 0.f, x12 = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
       const int m = ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
       const float w = float(L::w(i));
-      const float a1 = __ldg(a.c1 + m), a2v = __ldg(a.c2 + m);
-      const float d1 = a1 - c1, d2 = a2v - c2, d3 = (1.0f - a1 - a2v) - c3;
-      l1 += w * d1;
-      l2 += w * d2;
-      l3 += w * d3;
-      p1 += w * d1 * d1;
-      p2 += w * d2 * d2;
-      p3 += w * d3 * d3;
+      const float d1 = __ldg(a.c1 + m) - c1, d2 = __ldg(a.c2 + m) - c2;
+      const float t1 = w * d1, t2 = w * d2;
+      l1 += t1;
+      l2 += t2;
+      p1 = fmaf(t1, d1, p1);
+      p2 = fmaf(t2, d2, p2);
+      x12 = fmaf(t1, d2, x12);
     }
+    const float p3 = p1 + p2 + 2.0f * x12;
     l1 *= 6.f;
     l2 *= 6.f;
-    l3 *= 6.f;
+    const float l3 = -(l1 + l2);
     const float A2 = a.a2;
     // per-node densities in FP32, accumulated with carried rounding errors
     const float q1 = c1 * (1.0f - c1), q2 = c2 * (1.0f - c2), q3 = c3 * (1.0f - c3);
