@@ -99,6 +99,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(t_local: float, units_local: float, dist=None):
+    """Replica timing over ranks: the job time is the slowest rank's, the
+    throughput all ranks' units over that time.  Returns (t_max, units/t_max)."""
+    t_max, units = t_local, units_local
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+            else torch.device("cpu")
+        tt = torch.tensor([t_local, units_local], dtype=torch.float64, device=dev)
+        t = tt[:1].clone()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = tt[1:].clone()
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_max, units = float(t.item()), float(u.item())
+    return t_max, units / t_max
+
+
+def shard(items, rank: int, world: int):
+    """Independent problems are split across replicas by index."""
+    return [it for i, it in enumerate(items) if i % world == rank]
+
+
 def measured_traffic():
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     or None when the kernel source has changed since the counters were taken."""
@@ -234,12 +256,8 @@ def run_gpu(args, rank, world):
     t_k2 = sum(a.elapsed_time(b) for a, b in ev) / len(ev) / 1e3
     obs = lat.observables()
     assert obs["nonfinite"] == 0, "non-finite state after the timed steps"
-    t_max = t_total
-    if dist:
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n * args.steps / t_max / 1e6
+    t_max, lups = aggregate(t_total, float(n * args.steps), dist)
+    value = lups / 1e6
 
     # end to end through the public API with host buffers: H2D of the geometry
     # and the liquid field, set_solid, set_fluid, K steps, D2H of the liquid field
@@ -259,12 +277,8 @@ def run_gpu(args, rank, world):
     out_h.copy_(f_out, non_blocking=True)
     s1.record(stream)
     torch.cuda.synchronize()
-    t_e2e = s0.elapsed_time(s1) / 1e3
-    if dist:
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = {"value": world * n * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+    t_e2e, lups_e2e = aggregate(s0.elapsed_time(s1) / 1e3, float(n * args.steps), dist)
+    e2e = {"value": lups_e2e / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 2 * 4 * n / args.steps, "d2h_bytes_per_step": 4 * n / args.steps}
 
     peak, peak_kind = _peaks()
@@ -310,7 +324,7 @@ def run_serve(args, rank, world):
     torch.cuda.set_device(local)
     reqs = S.serving_stream(n_req=args.serve_requests, rate=args.serve_rate, seed=0,
                             scale_steps=args.serve_scale)
-    mine = [r for r in reqs if r.rid % world == rank]   # replicas: requests sharded by id
+    mine = shard(reqs, rank, world)   # replicas: requests split across ranks
     # a request arrives with its fields (geometry and liquid), as a client sends
     # them: build them before the clock starts
     for r in mine:
