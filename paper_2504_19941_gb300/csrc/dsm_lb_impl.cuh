@@ -138,10 +138,9 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
 // every node fluid).  MODE_STEP collides and writes the next state;
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S, int STAGE, int MODE, bool RC, bool SMEM = false>
+template <int K, class T, class S, int STAGE, int MODE, bool RC>
 __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
-                                          int field_sel, const S *sf = nullptr,
-                                          const S *sg = nullptr, int sstride = 0) {
+                                          int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
   if (MODE != MODE_OBS && !valid) return;
@@ -170,14 +169,9 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 #pragma unroll
     for (int j = 0; j < Q; j++) {
       const int src = h.minus<L>(j);
-      if constexpr (SMEM) {  // pulled earlier by this thread's own async copies
-        f[j] = T(sf[j * sstride]);
-        g[j] = T(sg[j * sstride]);
-      } else {
-        if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
-        else g[j] = load_g<T, S>(a.gin[j], src);
-        f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
-      }
+      if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
+      else g[j] = load_g<T, S>(a.gin[j], src);
+      f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
     }
     C = Cn[0];
     c1 = C1n[0];
@@ -469,87 +463,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArg
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined stage-2 step (4- and 8-byte storage).  Resident blocks walk the
-// bricks in a grid-stride loop.  While a thread computes its node of brick k,
-// the 2Q populations its node of brick k+1 will pull are already on their way
-// into shared memory through per-thread asynchronous copies (cp.async), so the
-// DRAM latency of the next brick overlaps this brick's arithmetic without
-// holding registers.  A thread only ever reads the copies it issued itself,
-// so waiting on its own copy groups is all the synchronisation needed.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-template <int K, class T, class S>
-__device__ __forceinline__ bool brick_node(const LBArgs<T, S> &a, int b, int gx, int gy, int &x,
-                                           int &y, int &z) {
-  const int bx = b % gx, by = (b / gx) % gy, bz = b / (gx * gy);
-  x = bx * blockDim.x + threadIdx.x;
-  y = by * blockDim.y + threadIdx.y;
-  z = bz * blockDim.z + threadIdx.z;
-  return x < a.nx && y < a.ny && z < a.nz;
-}
-
-// issue the async copies of the populations node (x, y, z) pulls
-template <int K, class T, class S>
-__device__ __forceinline__ void pull_async(const LBArgs<T, S> &a, int x, int y, int z, S *sf, S *sg,
-                                           int sstride) {
-  using L = Lat<K>;
-  Hood h;
-  h.init(x, y, z, a.nx, a.ny, a.nz);
-#pragma unroll
-  for (int j = 0; j < L::Q; j++) {
-    const int src = h.minus<L>(j);
-    if constexpr (sizeof(S) == 4) {
-      cp_async_4(sf + j * sstride, a.fin[j] + src);
-      cp_async_4(sg + j * sstride, a.gin[j] + src);
-    } else {
-      cp_async_8(sf + j * sstride, a.fin[j] + src);
-      cp_async_8(sg + j * sstride, a.gin[j] + src);
-    }
-  }
-}
-
-template <int K, class T, class S, bool RC>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
-    step_pipelined_kernel(LBArgs<T, S> a, int gx, int gy, int nbricks) {
-  using L = Lat<K>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  S *const stage0 = (S *)smem_raw;
-  S *const stage1 = stage0 + 2 * L::Q * nthr;
-  int b = blockIdx.x;
-  int x, y, z;
-  bool valid = b < nbricks && brick_node<K, T, S>(a, b, gx, gy, x, y, z);
-  if (valid) pull_async<K, T, S>(a, x, y, z, stage0 + tid, stage0 + L::Q * nthr + tid, nthr);
-  cp_async_commit();
-  for (int k = 0; b < nbricks; b += gridDim.x, k ^= 1) {
-    const int bn = b + gridDim.x;
-    int xn, yn, zn;
-    const bool vn = bn < nbricks && brick_node<K, T, S>(a, bn, gx, gy, xn, yn, zn);
-    S *nx_f = (k ? stage0 : stage1) + tid;
-    if (vn) pull_async<K, T, S>(a, xn, yn, zn, nx_f, nx_f + L::Q * nthr, nthr);
-    cp_async_commit();
-    cp_async_wait_1();  // this thread's copies of brick b have landed
-    const S *cf = (k ? stage1 : stage0) + tid;
-    node_body<K, T, S, 2, MODE_STEP, RC, true>(a, x, y, z, valid, 0, cf, cf + L::Q * nthr, nthr);
-    x = xn;
-    y = yn;
-    z = zn;
-    valid = vn;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // K9: batched persistent step.  One cooperative launch advances many lattices
 // (same lattice kind and precision) by up to tmax steps: per step a moments
 // phase and a fused phase over the work list of (lattice, brick) pairs, each
@@ -796,44 +709,8 @@ struct LBOps {
     moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
-  template <bool RC>
-  static void pipelined_launch(const LBRaw &r, cudaStream_t st) {
-    static int resident = 0;
-    const dim3 blk = lb_block(K, r.nx, r.ny, r.nz);
-    const int nthr = blk.x * blk.y * blk.z;
-    const size_t smem = 2 * 2 * Lat<K>::Q * nthr * sizeof(S);
-    const void *fn = (const void *)step_pipelined_kernel<K, T, S, RC>;
-    static int attr_set = 0;
-    if (!attr_set) {
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(2 * 2 * Lat<K>::Q * 256 * sizeof(S)));
-      attr_set = 1;
-    }
-    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz);
-    const long long nb = (long long)g.x * g.y * g.z;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (!resident || nthr != 256) {
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nthr, smem);
-      const int res = sms * (per_sm > 0 ? per_sm : 1);
-      if (nthr == 256) resident = res;
-      per_sm = res;
-    } else {
-      per_sm = resident;
-    }
-    const int blocks = (int)(nb < per_sm ? nb : per_sm);
-    step_pipelined_kernel<K, T, S, RC><<<blocks, blk, smem, st>>>(typed<T, S>(r), g.x, g.y, (int)nb);
-  }
   template <int STAGE, int MODE>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
-    if constexpr (!Store<S>::k16) {
-      if (STAGE == 2 && MODE == MODE_STEP) {
-        if (r.p.rho_contrast) pipelined_launch<true>(r, st);
-        else pipelined_launch<false>(r, st);
-        return;
-      }
-    }
     if (STAGE == 2 && r.p.rho_contrast)
       node_kernel<K, T, S, STAGE, MODE, true>
           <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r), r.field_sel);
