@@ -32,7 +32,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 N+1-phase LBM MLUPS & HBM-roofline %; sweep solves/s with p50/p99 latency"
-B_MIN_F32_D3Q19 = 308  # algorithmic bytes per lattice update: f, g read + write, C1 read
+
+
+def lu_bytes(lattice: str, prec: str, g_eq: bool):
+    """Algorithmic bytes per lattice update of the fused pass and of the moments
+    pass.  Population form: read and write f and g once, read C1 (FP32 D3Q19:
+    308 B; 16-bit storage with FP32 g_0: 160 B).  g held as g_eq (tau_g = 1):
+    read and write f, read C1, write A and u in the fused pass; read A, u and the
+    previous C and write C in the moments pass.  The fused pass's read of C, just
+    written by the moments pass, is not counted (an L2-resident field)."""
+    q, d = (19, 3) if lattice == "D3Q19" else (9, 2)
+    real = 8 if prec == "f64" else 4
+    st = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[prec]
+    g_read = (q - 1) * st + 4 if st == 2 else q * st
+    if g_eq:
+        return 2 * q * st + real + (1 + d) * real, (1 + d) * real + 2 * real
+    return 2 * q * st + 2 * g_read + real, g_read + real
 SHAPE = (256, 256, 192)
 WORKLOAD = "D3Q19 FP32 pillar-slab 256x256x192 (12.58M nodes), plain method, stage-2 LB step"
 
@@ -121,11 +136,11 @@ def shard(items, rank: int, world: int):
     return [it for i, it in enumerate(items) if i % world == rank]
 
 
-def measured_traffic():
+def measured_traffic(name="node_kernel_d3q19_f32_geq"):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     or None when the kernel source has changed since the counters were taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "node_kernel_d3q19_f32_traffic.txt")
+    path = os.path.join(ROOT, "profiles", name + "_traffic.txt")
     if not os.path.exists(path):
         return None
     rec = {}
@@ -217,6 +232,7 @@ def run_gpu(args, rank, world):
     params = P.make_params("D3Q19", shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
                            g23=case.g23, alpha_s=case.alpha_s)
     lat = P.Lattice(params, device=dev)
+    lat.set_g_storage(args.g_storage)
     sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
     c2_h = torch.as_tensor(case.c2, dtype=torch.float32).pin_memory()
     sd_d = sd_h.to(dev, non_blocking=True)
@@ -233,6 +249,8 @@ def run_gpu(args, rank, world):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
+    g_eq = lat.g_implicit
+    k2_b, k1_b = lu_bytes("D3Q19", "f32", g_eq)
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -282,8 +300,10 @@ def run_gpu(args, rank, world):
            "h2d_bytes_per_step": 2 * 4 * n / args.steps, "d2h_bytes_per_step": 4 * n / args.steps}
 
     peak, peak_kind = _peaks()
-    achieved = B_MIN_F32_D3Q19 * n / t_k2 / 1e9
-    traffic = measured_traffic() if shape == SHAPE else None
+    achieved = k2_b * n / t_k2 / 1e9
+    traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
+               if shape == SHAPE else None)
+    step_achieved = (k2_b + k1_b) * n / (t_max / args.steps) / 1e9
 
     if rank == 0:
         cb = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
@@ -295,12 +315,15 @@ def run_gpu(args, rank, world):
                           f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)",
                           "lattice": "D3Q19", "nodes": n,
                           "global_batch": world, "parallelism": f"replicas x{world}",
-                          "l2": "inputs (3.9 GB populations) larger than L2; no flush"},
+                          "g_storage": "g_eq (tau_g = 1): A, u per node" if g_eq else "populations",
+                          "l2": "f populations alone 1.9 GB per buffer, larger than L2; no flush"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic,
-                            "kernel": "node_kernel<D3Q19,f32,stage2,step>",
-                            "bytes_per_lu": B_MIN_F32_D3Q19, "peak_source": peak_kind,
-                            "k2_ms": t_k2 * 1e3},
+                            "kernel": "node_kernel<D3Q19,f32,stage2,step,%s>" %
+                                      ("g_eq" if g_eq else "populations"),
+                            "bytes_per_lu": k2_b, "peak_source": peak_kind,
+                            "k2_ms": t_k2 * 1e3, "step_bytes_per_lu": k1_b + k2_b,
+                            "step_achieved": step_achieved, "step_frac": step_achieved / peak},
                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
                "cpu_baseline": cb,
                "observables": {"mass_c2": obs["mass_c2"], "max_u": obs["max_u"]}}
@@ -390,13 +413,15 @@ def run_precision(args, rank, world):
     case = S.plates_rise_3d()
     peak, peak_kind = _peaks()
     out = {}
-    for prec, bmin in (("f32", 308), ("bf16", 160), ("f16", 160)):
+    for prec in ("f32", "bf16", "f16"):
         p = P.make_params("D3Q19", case.shape, prec, theta_deg=case.theta_deg, g12=case.g12,
                           g23=case.g23, alpha_s=case.alpha_s, body=case.body)
         lat = P.Lattice(p, device=dev)
+        lat.set_g_storage(args.g_storage)
         lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
         lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float32, device=dev))
         t_step, t_k2 = _time_steps(lat, args.steps, args.warmup)
+        bmin = lu_bytes("D3Q19", prec, lat.g_implicit)[0]
         ob = lat.observables()
         out[prec] = {"MLUPS": lat.n / t_step / 1e6, "ms_per_step": t_step * 1e3,
                      "k2_ms": t_k2 * 1e3, "bytes_per_lu": bmin,
@@ -409,7 +434,8 @@ def run_precision(args, rank, world):
                           "value": out["bf16"]["MLUPS"], "unit": "MLUPS", "n_gpus": 1,
                           "steps": args.steps, "warmup": args.warmup, "dtype": "bf16-storage/f32",
                           "higher_is_better": True, "data": "synthetic", "peak_gbs": peak,
-                          "peak_source": peak_kind, "forms": out}), flush=True)
+                          "peak_source": peak_kind, "g_storage": args.g_storage,
+                          "forms": out}), flush=True)
     return 0
 
 
@@ -518,6 +544,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="dsm", choices=["dsm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],
+                    help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
     ap.add_argument("--workload", default="lb", choices=["lb", "serve", "precision", "fp64", "em"])

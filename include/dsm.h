@@ -23,7 +23,7 @@
  *     Device-detected errors (non-finite populations, a persistent-kernel
  *     barrier that timed out) are latched in the workspace and reported by the
  *     next synchronising call; the handle then stays in DSM_E_STATE until
- *     dsm_set_populations or dsm_set_fluid resets it.
+ *     dsm_set_populations, dsm_set_state or dsm_set_fluid resets it.
  *   - One handle belongs to one stream; calls on different handles are
  *     independent.  The library is not thread-safe for one handle.
  */
@@ -110,7 +110,8 @@ dsm_status dsm_lattice_table(int lattice, int *q_out, int *c_out, double *w_out)
 dsm_status dsm_kappa(const dsm_params *p, double kappa_out[3]);
 
 /* Workspace bytes a lattice of these parameters needs (populations, two
- * buffers each; C1; C; solid mask; reduction scratch). */
+ * buffers each; C1; C, two buffers; the four g_eq planes; solid mask;
+ * reduction scratch). */
 dsm_status dsm_workspace_bytes(const dsm_params *p, size_t *bytes);
 
 /* Create a handle over a caller-owned device workspace (>= the size above,
@@ -162,12 +163,49 @@ dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out);
 dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst);
 
 /* Post-collision populations of the current state as reals, q-major
- * (d_f[i*N + n], d_g[i*N + n], N = nx*ny*nz, q-order of dsm_lattice_table). */
+ * (d_f[i*N + n], d_g[i*N + n], N = nx*ny*nz, q-order of dsm_lattice_table).
+ * A state holding g as g_eq (dsm_set_g_storage) returns g_eq_i evaluated from
+ * the stored A, u and C in the lattice's arithmetic. */
 dsm_status dsm_get_populations(dsm_lattice *h, void *d_f, void *d_g);
 
 /* Replace the state by the given post-collision populations (reals, layout as
- * above); 16-bit precisions encode them.  Clears a latched error. */
+ * above); 16-bit precisions encode them.  Clears a latched error.  The state
+ * holds g as populations until the next step. */
 dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g);
+
+/* Storage form of the order-parameter populations g (stage 2).
+ *
+ * The g collision of Sec. II.B relaxes g_i toward g_eq_i with rate 1/tau_g; at
+ * tau_g = 1 (the paper's value) it replaces g_i by g_eq_i outright, and g_eq_i
+ * is fixed by the node's C, mu and u:
+ *   g_eq_i = w_i (mu + C s_i)  (i != 0),  g_eq_0 = C - (1 - w_0) mu + w_0 C s_0.
+ * DSM_G_AUTO (the default) then keeps four reals per node (A = mu - 3/2 C u.u,
+ * u) instead of the Q populations, and the moments pass rebuilds
+ * C = sum_i g_eq_i(x - c_i) from the neighbours' values: the same step up to
+ * rounding, with less than half the memory traffic.  With tau_g != 1 AUTO
+ * keeps populations.  DSM_G_POPULATIONS always keeps populations.
+ *
+ * dsm_set_g_storage may be called at any time; switching a state that holds g
+ * as g_eq to populations writes them out (on the stream).  dsm_get_g_storage
+ * reports the form set and whether the current state holds g as g_eq
+ * (either output pointer may be NULL).  DSM_E_INVAL for an unknown form. */
+enum { DSM_G_AUTO = 0, DSM_G_POPULATIONS = 1 };
+dsm_status dsm_set_g_storage(dsm_lattice *h, int form);
+dsm_status dsm_get_g_storage(dsm_lattice *h, int *form, int *implicit_now);
+
+/* Checkpoint of the current state (not in the paper: restart support).
+ * dsm_state_bytes gives the size; dsm_get_state copies the state into the
+ * caller's device buffer d_dst (256-byte aligned, >= that size): a header
+ * (lattice, precision, sizes, step, storage form) and the raw population /
+ * g_eq buffers.  dsm_set_state restores such a buffer into a handle of the
+ * same lattice, precision and size, clears a latched error, and the run then
+ * continues bitwise as the saved one would have.  Both synchronise the stream
+ * (the header passes through host memory).  DSM_E_WORKSPACE for a short or
+ * misaligned buffer, DSM_E_INVAL for a header that does not match the handle,
+ * DSM_E_STATE for dsm_get_state before dsm_set_fluid. */
+dsm_status dsm_state_bytes(dsm_lattice *h, size_t *bytes);
+dsm_status dsm_get_state(dsm_lattice *h, void *d_dst, size_t bytes);
+dsm_status dsm_set_state(dsm_lattice *h, const void *d_src, size_t bytes);
 
 /* Free-energy twin (Sec. II.A, Eqs. [frozen:total_energy], [frozen:bulk_energy],
  * [frozen:interface_energy], [frozen:pressure_const] / [frozen:volume_const],

@@ -117,3 +117,24 @@ class Lattice:
         assert f.dtype == self.real and g.dtype == self.real
         assert f.numel() == self.q * self.n and g.numel() == self.q * self.n
         _lib.dsm_set_populations(self.h, f.contiguous(), g.contiguous())
+
+    def set_g_storage(self, form: str):
+        """'auto' (g held as g_eq when tau_g = 1) or 'populations'."""
+        _lib.dsm_set_g_storage(self.h, {"auto": _lib.DSM_G_AUTO,
+                                        "populations": _lib.DSM_G_POPULATIONS}[form])
+
+    @property
+    def g_implicit(self) -> bool:
+        """True when the current state holds g as g_eq (A, u) rather than populations."""
+        return bool(_lib.dsm_get_g_storage(self.h)[1])
+
+    def state(self):
+        """Checkpoint of the current state (a device byte tensor)."""
+        import torch
+        nb = _lib.dsm_state_bytes(self.h)
+        buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        _lib.dsm_get_state(self.h, buf, nb)
+        return buf
+
+    def set_state(self, buf):
+        _lib.dsm_set_state(self.h, buf, buf.numel())

@@ -17,6 +17,7 @@ DSM_OK, DSM_E_INVAL, DSM_E_WORKSPACE, DSM_E_CUDA, DSM_E_NONFINITE, DSM_E_TIMEOUT
     DSM_E_STATE, DSM_E_UNSUPPORTED = range(8)
 DSM_D2Q9, DSM_D3Q19 = 0, 1
 DSM_F64, DSM_F32, DSM_BF16_STORE, DSM_F16_STORE = 0, 1, 2, 3
+DSM_G_AUTO, DSM_G_POPULATIONS = 0, 1
 (DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_UX, DSM_FIELD_UY,
  DSM_FIELD_UZ, DSM_FIELD_PT, DSM_FIELD_RHO, DSM_FIELD_TAU) = range(10)
 
@@ -24,7 +25,8 @@ EXPORTED = (
     "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
     "dsm_set_solid", "dsm_relax_solid", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
     "dsm_step_collide", "dsm_get_observables",
-    "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_fe_scratch_bytes",
+    "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
+    "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
     "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_scratch_bytes", "dsm_batch_step",
     "dsm_destroy",
@@ -83,6 +85,11 @@ def load():
         "dsm_get_field": (st, [vp, C.c_int, vp]),
         "dsm_get_populations": (st, [vp, vp, vp]),
         "dsm_set_populations": (st, [vp, vp, vp]),
+        "dsm_set_g_storage": (st, [vp, C.c_int]),
+        "dsm_get_g_storage": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "dsm_state_bytes": (st, [vp, C.POINTER(C.c_size_t)]),
+        "dsm_get_state": (st, [vp, vp, C.c_size_t]),
+        "dsm_set_state": (st, [vp, vp, C.c_size_t]),
         "dsm_fe_scratch_bytes": (st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_fe_energy_grad": (st, [P, fp, fp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
                                     C.c_double, vp, fp, vp, vp, C.c_size_t, vp]),
@@ -209,6 +216,31 @@ def dsm_get_populations(h: int, f, g):
 
 def dsm_set_populations(h: int, f, g):
     _check(load().dsm_set_populations(h, _ptr(f), _ptr(g)), "dsm_set_populations")
+
+
+def dsm_set_g_storage(h: int, form: int):
+    _check(load().dsm_set_g_storage(h, form), "dsm_set_g_storage")
+
+
+def dsm_get_g_storage(h: int):
+    """(form, 1 if the current state holds g as g_eq else 0)."""
+    form, imp = C.c_int(), C.c_int()
+    _check(load().dsm_get_g_storage(h, C.byref(form), C.byref(imp)), "dsm_get_g_storage")
+    return form.value, imp.value
+
+
+def dsm_state_bytes(h: int) -> int:
+    n = C.c_size_t()
+    _check(load().dsm_state_bytes(h, C.byref(n)), "dsm_state_bytes")
+    return n.value
+
+
+def dsm_get_state(h: int, dst, nbytes: int):
+    _check(load().dsm_get_state(h, _ptr(dst), nbytes), "dsm_get_state")
+
+
+def dsm_set_state(h: int, src, nbytes: int):
+    _check(load().dsm_set_state(h, _ptr(src), nbytes), "dsm_set_state")
 
 
 def dsm_fe_scratch_bytes(lattice: int, nx: int, ny: int, nz: int) -> int:

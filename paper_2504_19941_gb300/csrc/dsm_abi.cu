@@ -23,7 +23,9 @@ struct dsm_lattice {
   size_t ws_bytes;
   void *f[2], *g[2];
   float *g0[2];
-  void *C, *C1;
+  void *Cb[2];   // Cb[cur]: C of the state's last collision; Cb[cur ^ 1]: moments output
+  void *M;       // g held as g_eq: A, u_x, u_y, u_z planes
+  void *C1;
   unsigned char *mask;
   double *partials, *obs;
   int *err;
@@ -32,6 +34,9 @@ struct dsm_lattice {
   cudaStream_t stream;
   long long step;
   bool has_solid, has_fluid, latched, moments_ready;
+  int g_form;      // DSM_G_AUTO or DSM_G_POPULATIONS
+  bool eq;         // the fused pass stores g as g_eq (tau_g = 1 and DSM_G_AUTO)
+  bool g_implicit; // the current g are held as g_eq
   StepParams sp;
 };
 
@@ -79,7 +84,7 @@ dsm_status check_params(const dsm_params *p) {
 }
 
 struct Layout {
-  size_t f[2], g[2], g0[2], C, C1, mask, partials, obs, err, total;
+  size_t f[2], g[2], g0[2], C[2], M, C1, mask, partials, obs, err, total;
 };
 
 long long obs_blocks_of(int kind, int nx, int ny, int nz) {
@@ -102,7 +107,9 @@ Layout layout_of(const dsm_params *p, const LBTable &t, long long N, long long p
   L.g[1] = take(pop);
   L.g0[0] = take(t.k16 ? pitch * sizeof(float) : 0);
   L.g0[1] = take(t.k16 ? pitch * sizeof(float) : 0);
-  L.C = take(pitch * t.real_bytes);
+  L.C[0] = take(pitch * t.real_bytes);
+  L.C[1] = take(pitch * t.real_bytes);
+  L.M = take(4 * pitch * t.real_bytes);
   L.C1 = take(pitch * t.real_bytes);
   L.mask = take(pitch);
   L.partials = take(obs_blocks_of(p->lattice, p->nx, p->ny, p->nz) * OBS_K * sizeof(double));
@@ -147,7 +154,11 @@ LBRaw raw_of(const dsm_lattice *h, int src) {
   r.f_out = h->f[src ^ 1];
   r.g_out = h->g[src ^ 1];
   r.g0_out = h->g0[src ^ 1];
-  r.C = h->C;
+  r.C = h->Cb[src ^ 1];
+  r.Cprev = h->Cb[src];
+  r.M = h->M;
+  r.eq = h->eq;
+  r.implicit = h->g_implicit;
   r.C1 = h->C1;
   r.mask = h->mask;
   r.partials = h->partials;
@@ -275,7 +286,9 @@ dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void
     h->g[b] = h->ws + L.g[b];
     h->g0[b] = t.k16 ? (float *)(h->ws + L.g0[b]) : nullptr;
   }
-  h->C = h->ws + L.C;
+  h->Cb[0] = h->ws + L.C[0];
+  h->Cb[1] = h->ws + L.C[1];
+  h->M = h->ws + L.M;
   h->C1 = h->ws + L.C1;
   h->mask = (unsigned char *)(h->ws + L.mask);
   h->partials = (double *)(h->ws + L.partials);
@@ -284,6 +297,8 @@ dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void
   h->obs_blocks = obs_blocks_of(p->lattice, p->nx, p->ny, p->nz);
   h->stream = (cudaStream_t)cuda_stream;
   h->sp = step_params(p, h->kappa);
+  h->g_form = DSM_G_AUTO;
+  h->eq = p->tau_g == 1.0;
   // no solid yet: C1 = 0 everywhere; clear the error word and the mask
   cudaError_t e = cudaMemsetAsync(h->C1, 0, pitch * t.real_bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->mask, 0, pitch, h->stream);
@@ -317,11 +332,16 @@ dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int step
   h->sp.beta = beta;
   h->sp.omega = omega;
   // initial state of stage 1 from the current C1, written into buffer 0
+  // (stage 1 keeps g as populations)
   h->cur = 0;
+  h->g_implicit = false;
+  h->has_fluid = false;
   LBRaw r = raw_of(h, 1);  // out = buffer 0
+  r.eq = 0;
   if ((e = h->tab.init(r, h->C1, 1, h->stream)) != cudaSuccess) return DSM_E_CUDA;
   for (int t = 0; t < steps; t++) {
     LBRaw a = raw_of(h, h->cur);
+    a.eq = 0;
     if ((e = h->tab.moments(a, h->stream)) != cudaSuccess) return DSM_E_CUDA;
     if ((e = h->tab.node(a, 1, MODE_STEP, h->stream)) != cudaSuccess) return DSM_E_CUDA;
     h->cur ^= 1;
@@ -329,7 +349,7 @@ dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int step
   // relaxed C1 = the concentration the next step would see
   LBRaw a = raw_of(h, h->cur);
   if ((e = h->tab.moments(a, h->stream)) != cudaSuccess) return DSM_E_CUDA;
-  e = cudaMemcpyAsync(h->C1, h->C, h->N * h->tab.real_bytes, cudaMemcpyDeviceToDevice, h->stream);
+  e = cudaMemcpyAsync(h->C1, a.C, h->N * h->tab.real_bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return DSM_E_CUDA;
   h->sp.beta = h->prm.beta;
   h->sp.omega = h->prm.omega;
@@ -349,6 +369,7 @@ dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2) {
   h->has_fluid = true;
   h->latched = false;
   h->moments_ready = false;
+  h->g_implicit = false;  // the initial g are written as populations
   return DSM_OK;
 }
 
@@ -362,6 +383,7 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
     if (e != cudaSuccess) return DSM_E_CUDA;
     h->cur ^= 1;
     h->step++;
+    h->g_implicit = h->eq;
   }
   h->moments_ready = false;
   return DSM_OK;
@@ -383,6 +405,7 @@ dsm_status dsm_step_collide(dsm_lattice *h) {
   if (h->tab.node(a, 2, MODE_STEP, h->stream) != cudaSuccess) return DSM_E_CUDA;
   h->cur ^= 1;
   h->step++;
+  h->g_implicit = h->eq;
   h->moments_ready = false;
   return DSM_OK;
 }
@@ -451,6 +474,137 @@ dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g)
   h->has_fluid = true;
   h->latched = false;
   h->moments_ready = false;
+  h->g_implicit = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_set_g_storage(dsm_lattice *h, int form) {
+  if (!h || (form != DSM_G_AUTO && form != DSM_G_POPULATIONS)) return DSM_E_INVAL;
+  const bool eq = form == DSM_G_AUTO && h->prm.tau_g == 1.0;
+  if (h->g_implicit && !eq) {
+    // write the current g_eq out as populations of the current buffer
+    LBRaw a = raw_of(h, h->cur ^ 1);  // g_out = current buffer
+    a.Cprev = h->Cb[h->cur];
+    if (h->tab.materialize(a, h->stream) != cudaSuccess) return DSM_E_CUDA;
+    h->g_implicit = false;
+    h->moments_ready = false;
+  }
+  h->g_form = form;
+  h->eq = eq;
+  return DSM_OK;
+}
+
+dsm_status dsm_get_g_storage(dsm_lattice *h, int *form, int *implicit_now) {
+  if (!h) return DSM_E_INVAL;
+  if (form) *form = h->g_form;
+  if (implicit_now) *implicit_now = h->g_implicit ? 1 : 0;
+  return DSM_OK;
+}
+
+// Raw state (checkpoint): a 256-byte header, then the current buffer's f, g,
+// 16-bit g_0, C of the last collision and the g_eq planes, each region
+// 256-byte aligned.  Restoring it continues the run bitwise.
+namespace {
+constexpr unsigned kStateMagic = 0x53534d44u;  // "DSMS"
+struct StateHeader {
+  unsigned magic, version;
+  int lattice, precision, nx, ny, nz, implicit;
+  long long step, pitch;
+};
+struct StateLayout {
+  size_t f, g, g0, C, M, total;
+};
+StateLayout state_layout(const dsm_lattice *h) {
+  StateLayout L;
+  size_t o = 256;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += (size_t)round_up((long long)bytes, 256);
+    return at;
+  };
+  const size_t pop = (size_t)h->q * h->pitch * h->tab.store_bytes;
+  L.f = take(pop);
+  L.g = take(pop);
+  L.g0 = take(h->tab.k16 ? h->pitch * sizeof(float) : 0);
+  L.C = take(h->pitch * h->tab.real_bytes);
+  L.M = take(4 * h->pitch * h->tab.real_bytes);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+dsm_status dsm_state_bytes(dsm_lattice *h, size_t *bytes) {
+  if (!h || !bytes) return DSM_E_INVAL;
+  *bytes = state_layout(h).total;
+  return DSM_OK;
+}
+
+dsm_status dsm_get_state(dsm_lattice *h, void *d_dst, size_t bytes) {
+  if (!h || !d_dst) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  const StateLayout L = state_layout(h);
+  if (bytes < L.total || ((uintptr_t)d_dst & 255u)) return DSM_E_WORKSPACE;
+  StateHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  hd.magic = kStateMagic;
+  hd.version = 1;
+  hd.lattice = h->kind;
+  hd.precision = h->prm.precision;
+  hd.nx = h->prm.nx;
+  hd.ny = h->prm.ny;
+  hd.nz = h->prm.nz;
+  hd.implicit = h->g_implicit ? 1 : 0;
+  hd.step = h->step;
+  hd.pitch = h->pitch;
+  char *d = (char *)d_dst;
+  const size_t pop = (size_t)h->q * h->pitch * h->tab.store_bytes;
+  const size_t real = h->pitch * h->tab.real_bytes;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemcpyAsync(d, &hd, sizeof(hd), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + L.f, h->f[h->cur], pop, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + L.g, h->g[h->cur], pop, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && h->tab.k16)
+    e = cudaMemcpyAsync(d + L.g0, h->g0[h->cur], h->pitch * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + L.C, h->Cb[h->cur], real, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + L.M, h->M, 4 * real, cudaMemcpyDeviceToDevice, st);
+  // the header copy reads host stack memory
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return cuda_status(e);
+}
+
+dsm_status dsm_set_state(dsm_lattice *h, const void *d_src, size_t bytes) {
+  if (!h || !d_src) return DSM_E_INVAL;
+  const StateLayout L = state_layout(h);
+  if (bytes < L.total || ((uintptr_t)d_src & 255u)) return DSM_E_WORKSPACE;
+  StateHeader hd;
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaMemcpyAsync(&hd, d_src, sizeof(hd), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  if (hd.magic != kStateMagic || hd.version != 1 || hd.lattice != h->kind ||
+      hd.precision != h->prm.precision || hd.nx != h->prm.nx || hd.ny != h->prm.ny ||
+      hd.nz != h->prm.nz || hd.pitch != h->pitch || (hd.implicit != 0 && hd.implicit != 1) ||
+      hd.step < 0)
+    return DSM_E_INVAL;
+  const char *d = (const char *)d_src;
+  const size_t pop = (size_t)h->q * h->pitch * h->tab.store_bytes;
+  const size_t real = h->pitch * h->tab.real_bytes;
+  e = cudaMemcpyAsync(h->f[0], d + L.f, pop, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->g[0], d + L.g, pop, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && h->tab.k16)
+    e = cudaMemcpyAsync(h->g0[0], d + L.g0, h->pitch * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->Cb[0], d + L.C, real, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->M, d + L.M, 4 * real, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->cur = 0;
+  h->step = hd.step;
+  h->g_implicit = hd.implicit != 0;
+  h->has_fluid = true;
+  h->latched = false;
+  h->moments_ready = false;
+  // a state holding g as g_eq, restored into a handle that keeps populations
+  if (h->g_implicit && !h->eq) return dsm_set_g_storage(h, h->g_form);
   return DSM_OK;
 }
 
@@ -548,7 +702,7 @@ static dsm_status batch_items(dsm_lattice *const *hs, int n, const long long *ns
     const dsm_lattice *h = hs[i];
     if (!h) return DSM_E_INVAL;
     if (h->kind != h0->kind || h->prm.precision != h0->prm.precision ||
-        h->stream != h0->stream || h->sp.rho_contrast != h0->sp.rho_contrast)
+        h->stream != h0->stream || h->sp.rho_contrast != h0->sp.rho_contrast || h->eq != h0->eq)
       return DSM_E_INVAL;
     if (nsteps && (nsteps[i] < 0 || nsteps[i] > (1ll << 30))) return DSM_E_INVAL;
     items[i].r[0] = raw_of(h, 0);
@@ -579,12 +733,13 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
   if (scratch_bytes < hs[0]->tab.batch_bytes(items.data(), n) || ((uintptr_t)d_scratch & 255u))
     return DSM_E_WORKSPACE;
   cudaError_t e = hs[0]->tab.batch(items.data(), n, d_scratch, scratch_bytes,
-                                   hs[0]->sp.rho_contrast != 0, hs[0]->stream);
+                                   hs[0]->sp.rho_contrast != 0, hs[0]->eq, hs[0]->stream);
   if (e != cudaSuccess) return DSM_E_CUDA;
   for (int i = 0; i < n; i++) {
     hs[i]->cur ^= (int)(nsteps[i] & 1);
     hs[i]->step += nsteps[i];
     hs[i]->moments_ready = false;
+    if (nsteps[i] > 0) hs[i]->g_implicit = hs[i]->eq;
   }
   return DSM_OK;
 }

@@ -154,6 +154,7 @@ struct LBArgs {
   S *g_out;
   float *g0_out;
   T *C;                // concentration (moments pass output)
+  const T *Cprev;      // concentration of the state's last collision (g held as g_eq)
   const T *C1;         // frozen solid (stage 2)
   const unsigned char *mask;  // solid region S (stage 1)
   T *fields;           // FIELDS mode output: 10 x N
@@ -164,6 +165,8 @@ struct LBArgs {
   // per-direction plane pointers (kernel parameters: one address op per access)
   const S *fin[QMAX], *gin[QMAX];
   S *fout[QMAX], *gout[QMAX];
+  // g held as g_eq (tau_g = 1): planes A = mu - 3/2 C u.u, u_x, u_y, u_z
+  T *Mp[4];
 };
 
 // Error bits latched in the workspace error word.
@@ -179,8 +182,12 @@ struct LBRaw {
   void *f_out, *g_out;
   float *g0_out;
   void *C;
+  const void *Cprev;
   const void *C1;
   const unsigned char *mask;
+  void *M;          // 4 planes of pitch reals (see LBArgs::Mp)
+  int eq;           // the fused pass stores g as g_eq (A, u) instead of populations
+  int implicit;     // the current g are held as g_eq (A, u, Cprev)
   void *out;
   int field_sel;
   double *partials;
@@ -202,8 +209,9 @@ struct LBTable {
   cudaError_t (*solid)(const void *sd, void *c1, long long N, double alpha_s, cudaStream_t);
   cudaError_t (*get_pops)(const LBRaw &, void *f, void *g, cudaStream_t);
   cudaError_t (*set_pops)(const LBRaw &, const void *f, const void *g, cudaStream_t);
+  cudaError_t (*materialize)(const LBRaw &, cudaStream_t);  // g_eq -> populations of g_out
   cudaError_t (*batch)(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
-                       cudaStream_t);
+                       bool eq, cudaStream_t);
   size_t (*batch_bytes)(const BatchRaw *items, int n);
   int q, real_bytes, store_bytes;
   bool k16;

@@ -10,6 +10,14 @@
 //                  mu, forces, moments, BGK collision of f and g     (K2)
 // The fused pass needs C and C1 on the node's 1-neighbourhood only, because
 // the capillary force is taken in its potential form mu G[C] (see below).
+//
+// g held as g_eq.  With tau_g = 1 the g collision replaces g_i by g_eq_i
+// entirely, and g_eq_i depends on the node's C, mu and u only.  The fused pass
+// then stores A = mu - 3/2 C u.u and u instead of the Q populations, and the
+// moments pass rebuilds C(x) = sum_i g_eq_i(x - c_i) from the neighbours'
+// (A, C, u): for i != 0, g_eq_i = w_i (A + C c_i.u (3 + 9/2 c_i.u)), and the
+// rest population holds the remainder C - (1 - w_0) A - 3/2 C u.u.  Same
+// trajectory, up to rounding; 4 + 1 reals per node move instead of 2Q.
 #pragma once
 
 #include <vector>
@@ -132,17 +140,80 @@ __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
                         blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z * blockDim.z + threadIdx.z);
 }
 
+// c_i . u for a direction known at compile time (adds only the non-zero
+// components, in x, y, z order)
+template <class L, class T>
+__device__ __forceinline__ T cdot(int i, T ux, T uy, T uz) {
+  T s = L::cx(i) == 0 ? T(0) : (L::cx(i) > 0 ? ux : -ux);
+  if (L::cy(i)) s += L::cy(i) > 0 ? uy : -uy;
+  if (L::cz(i)) s += L::cz(i) > 0 ? uz : -uz;
+  return s;
+}
+
+// g_eq_i / w_i for i != 0 from a node's A = mu - 3/2 C u.u, C and cu = c_i.u:
+//   mu + C s_i = A + C cu (3 + 9/2 cu)        (s_i of Eq. [eqn:feq], c_s^2 = 1/3)
+template <class T>
+__device__ __forceinline__ T geq_core(T A, T C, T cu) {
+  return A + C * (cu * (T(3) + T(4.5) * cu));
+}
+
+// K1 with g held as g_eq: C(x) = sum_i g_eq_i(x - c_i), written as the node's
+// own C plus the net inflow, so that the O(1) value is rounded once:
+//   C(x) + [ sum_{i != 0} w_i (A + C cu (3 + 9/2 cu))(x - c_i)
+//            - (1 - w_0) A(x) - 3/2 C(x) u(x).u(x) ]
+// (sum_{i != 0} w_i c_i.u (3 + 9/2 c_i.u) = 3/2 u.u reduces the node's own
+// outflow to its last two terms).
+template <int K, class T, class S>
+__device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, int y, int z) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init(x, y, z, a.nx, a.ny, a.nz);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  const T *pA = a.Mp[0], *pux = a.Mp[1], *puy = a.Mp[2], *puz = a.Mp[3];
+  T Ay[Q], Cy[Q], uy[Q][3];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const int m = i == 0 ? n : h.minus<L>(i);
+    Ay[i] = __ldg(pA + m);
+    Cy[i] = __ldg(a.Cprev + m);
+    uy[i][0] = (i == 0 || L::cx(i)) ? __ldg(pux + m) : T(0);
+    uy[i][1] = (i == 0 || L::cy(i)) ? __ldg(puy + m) : T(0);
+    uy[i][2] = (L::D == 3 && (i == 0 || L::cz(i))) ? __ldg(puz + m) : T(0);
+  }
+  T sa = T(0), sd = T(0);  // axis and diagonal links (one weight each)
+#pragma unroll
+  for (int i = 1; i < Q; i++) {
+    const T v = geq_core(Ay[i], Cy[i], cdot<L>(i, uy[i][0], uy[i][1], uy[i][2]));
+    if (L::w(i) == L::w(1)) sa += v;
+    else sd += v;
+  }
+  const T uu0 = uy[0][0] * uy[0][0] + uy[0][1] * uy[0][1] + uy[0][2] * uy[0][2];
+  const T out = T(1.0 - L::w(0)) * Ay[0] + T(1.5) * Cy[0] * uu0;
+  a.C[n] = Cy[0] + ((T(L::w(1)) * sa + T(L::w(Q - 1)) * sd) - out);
+}
+
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) moments_eq_kernel(LBArgs<T, S> a) {
+  moments_eq_body<K, T, S>(a, blockIdx.x * blockDim.x + threadIdx.x,
+                           blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z * blockDim.z + threadIdx.z);
+}
+
 // ---------------------------------------------------------------------------
 // K2: fused pass.  STAGE 2: fluids on the frozen diffuse solid C1.
 // STAGE 1: relaxation of C1 itself (g carries C1; rho = 1, tau = tau_g = 1,
 // every node fluid).  MODE_STEP collides and writes the next state;
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S, int STAGE, int MODE, bool RC>
+template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ = false>
 __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
                                           int field_sel) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
+  // the pulled g enter only the g collision (C comes from the moments pass)
+  constexpr bool LOAD_G = MODE == MODE_STEP && !EQ;
+  static_assert(!EQ || STAGE == 2, "g as g_eq is a stage-2 form");
   if (MODE != MODE_OBS && !valid) return;
   if (!valid) x = y = z = 0;
   Hood h;
@@ -169,7 +240,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 #pragma unroll
     for (int j = 0; j < Q; j++) {
       const int src = h.minus<L>(j);
-      if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
+      if (!LOAD_G) g[j] = T(0);
+      else if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
       else g[j] = load_g<T, S>(a.gin[j], src);
       f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
     }
@@ -337,7 +409,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   if constexpr (MODE == MODE_OBS) {
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < Q; j++) bad |= !isfinite(g[j]) || (!solid_x && !isfinite(f[j]));
+    for (int j = 0; j < Q; j++) bad |= !solid_x && !isfinite(f[j]);
+    bad |= !isfinite(C);  // C sums every pulled g
     const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
     if constexpr (sizeof(T) == 4) {
       // FP32 lattices: carried-error sums in FP32 within a warp, FP64 beyond
@@ -417,9 +490,11 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       fo = f[0] + (w * (pt + rho * s) - f[0]) * omf + Fi;
     }
     put_f(0, fo);
-    const T geq = C - (T(1) - w) * mu + w * C * s;
-    const T go = g[0] + (geq - g[0]) * omg;
-    if constexpr (!Store<S>::k16) a.gout[0][n] = S(go);
+    if constexpr (!EQ) {
+      const T geq = C - (T(1) - w) * mu + w * C * s;
+      const T go = g[0] + (geq - g[0]) * omg;
+      if constexpr (!Store<S>::k16) a.gout[0][n] = S(go);
+    }
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -444,22 +519,34 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     }
     put_f(i, fp);
     put_f(ib, fm);
-    const T wmu = w * mu, wC = w * C;
-    put_g(i, g[i] + (wmu + wC * sp - g[i]) * omg);
-    put_g(ib, g[ib] + (wmu + wC * sm - g[ib]) * omg);
+    if constexpr (!EQ) {
+      const T wmu = w * mu, wC = w * C;
+      put_g(i, g[i] + (wmu + wC * sp - g[i]) * omg);
+      put_g(ib, g[ib] + (wmu + wC * sm - g[ib]) * omg);
+    }
   }
-  // 16-bit storage: the rest population takes the rounding of the others so
-  // that sum_i g*_i = C holds at every node (sum_i g_eq_i = C, so the exact
-  // post-collision sum is C) and the liquid mass is conserved.
-  if constexpr (Store<S>::k16) a.g0_out[n] = float(C - gsum16);
+  if constexpr (EQ) {
+    // g* = g_eq (tau_g = 1): store what fixes it.  The C of this collision is
+    // this step's moments output a.C, which the next step reads as Cprev.
+    a.Mp[0][n] = mu - T(1.5) * C * uu;
+    a.Mp[1][n] = u[0];
+    a.Mp[2][n] = u[1];
+    if (L::D == 3) a.Mp[3][n] = u[2];
+  } else if constexpr (Store<S>::k16) {
+    // 16-bit storage: the rest population takes the rounding of the others so
+    // that sum_i g*_i = C holds at every node (sum_i g_eq_i = C, so the exact
+    // post-collision sum is C) and the liquid mass is conserved.
+    a.g0_out[n] = float(C - gsum16);
+  }
+  (void)gsum16;
 }
 
-template <int K, class T, class S, int STAGE, int MODE, bool RC>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) node_kernel(LBArgs<T, S> a, int field_sel) {
+template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
-  node_body<K, T, S, STAGE, MODE, RC>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
+  node_body<K, T, S, STAGE, MODE, RC, EQ>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
 }
 
 // ---------------------------------------------------------------------------
@@ -480,6 +567,7 @@ struct BatchItem {
   int brick0;         // first brick of this lattice in the work list
   int nsteps;         // steps this launch takes for this lattice
   int cur0;           // current buffer at launch
+  int implicit0;      // g held as g_eq at launch
 };
 
 constexpr unsigned long long kBarrierSpins = 20000000ull;  // ~2-4 s of polling
@@ -514,7 +602,7 @@ __device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int ni
   return ok != 0;
 }
 
-template <int K, class T, class S, bool RC>
+template <int K, class T, class S, bool RC, bool EQ>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
     batch_kernel(const BatchItem<T, S> *items, int nitems, const int *owner, int nbricks, int tmax,
                  unsigned *bar) {
@@ -538,8 +626,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
         const int x = bx * blockDim.x + threadIdx.x;
         const int y = by * blockDim.y + threadIdx.y;
         const int z = bz * blockDim.z + threadIdx.z;
-        if (phase == 0) moments_body<K, T, S>(sa, x, y, z);
-        else node_body<K, T, S, 2, MODE_STEP, RC>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
+        if (phase == 0) {
+          if (EQ && (t > 0 || it->implicit0)) moments_eq_body<K, T, S>(sa, x, y, z);
+          else moments_body<K, T, S>(sa, x, y, z);
+        } else {
+          node_body<K, T, S, 2, MODE_STEP, RC, EQ>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
+        }
       }
       if (!grid_barrier<T, S>(bar, items, nitems)) return;
     }
@@ -617,22 +709,63 @@ __global__ void __launch_bounds__(256) solid_profile_kernel(const T *sd, T *c1, 
 }
 
 // Population codecs (test/checkpoint path): storage <-> reals, q-major N-stride.
+// With g held as g_eq (implicit), g is rebuilt from (A, u, Cprev) with the
+// arithmetic of the moments pass: g_i = w_i (A + C c_i.u (3 + 9/2 c_i.u)),
+// g_0 = C - (1 - w_0) A - 3/2 C u.u.
 template <int K, class T, class S>
-__global__ void __launch_bounds__(256) pops_get_kernel(LBArgs<T, S> a, T *fo, T *go) {
+__global__ void __launch_bounds__(256) pops_get_kernel(LBArgs<T, S> a, T *fo, T *go, int implicit) {
   using L = Lat<K>;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < a.N;
        k += (long long)gridDim.x * blockDim.x) {
+    T A = T(0), Cx = T(0), ux = T(0), uy = T(0), uz = T(0);
+    if (implicit) {
+      A = a.Mp[0][k];
+      Cx = a.Cprev[k];
+      ux = a.Mp[1][k];
+      uy = a.Mp[2][k];
+      uz = L::D == 3 ? a.Mp[3][k] : T(0);
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
       const long long off = (long long)i * a.pitch + k;
-      if constexpr (Store<S>::k16) {
-        fo[i * a.N + k] = T(L::w(i)) + T(Store<S>::dec(a.f_in[off]));
+      if constexpr (Store<S>::k16) fo[i * a.N + k] = T(L::w(i)) + T(Store<S>::dec(a.f_in[off]));
+      else fo[i * a.N + k] = T(a.f_in[off]);
+      if (implicit) {
+        go[i * a.N + k] = i == 0 ? Cx - (T(1.0 - L::w(0)) * A + T(1.5) * Cx * (ux * ux + uy * uy + uz * uz))
+                                 : T(L::w(i)) * geq_core(A, Cx, cdot<L>(i, ux, uy, uz));
+      } else if constexpr (Store<S>::k16) {
         go[i * a.N + k] = (i == 0) ? T(a.g0_in[k]) : T(Store<S>::dec(a.g_in[off]));
       } else {
-        fo[i * a.N + k] = T(a.f_in[off]);
         go[i * a.N + k] = T(a.g_in[off]);
       }
     }
+  }
+}
+
+// g held as g_eq -> stored populations of the current buffer (a.g_out), for a
+// switch to the population form.  16-bit storage keeps the node's sum exact
+// through g_0 as the fused pass does.
+template <int K, class T, class S>
+__global__ void __launch_bounds__(256) g_materialize_kernel(LBArgs<T, S> a) {
+  using L = Lat<K>;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < a.N;
+       k += (long long)gridDim.x * blockDim.x) {
+    const T A = a.Mp[0][k], Cx = a.Cprev[k], ux = a.Mp[1][k], uy = a.Mp[2][k];
+    const T uz = L::D == 3 ? a.Mp[3][k] : T(0);
+    T s16 = T(0);
+#pragma unroll
+    for (int i = 1; i < L::Q; i++) {
+      const T gi = T(L::w(i)) * geq_core(A, Cx, cdot<L>(i, ux, uy, uz));
+      const long long off = (long long)i * a.pitch + k;
+      if constexpr (Store<S>::k16) {
+        a.g_out[off] = Store<S>::enc(float(gi));
+        s16 += T(Store<S>::dec(a.g_out[off]));
+      } else {
+        a.g_out[off] = S(gi);
+      }
+    }
+    if constexpr (Store<S>::k16) a.g0_out[k] = float(Cx - s16);
+    else a.g_out[k] = S(Cx - (T(1.0 - L::w(0)) * A + T(1.5) * Cx * (ux * ux + uy * uy + uz * uz)));
   }
 }
 
@@ -690,7 +823,8 @@ LBArgs<T, S> typed(const LBRaw &r) {
   a.nx = r.nx; a.ny = r.ny; a.nz = r.nz; a.N = r.N; a.pitch = r.pitch;
   a.f_in = (const S *)r.f_in; a.g_in = (const S *)r.g_in; a.g0_in = r.g0_in;
   a.f_out = (S *)r.f_out; a.g_out = (S *)r.g_out; a.g0_out = r.g0_out;
-  a.C = (T *)r.C; a.C1 = (const T *)r.C1; a.mask = r.mask;
+  a.C = (T *)r.C; a.Cprev = (const T *)r.Cprev; a.C1 = (const T *)r.C1; a.mask = r.mask;
+  for (int k = 0; k < 4; k++) a.Mp[k] = r.M ? (T *)r.M + (long long)k * r.pitch : nullptr;
   a.fields = (T *)r.out; a.partials = r.partials; a.err = r.err; a.p = r.p;
   a.c = ConstT<T>::make(r.p);
   for (int i = 0; i < QMAX; i++) {
@@ -706,21 +840,23 @@ LBArgs<T, S> typed(const LBRaw &r) {
 template <int K, class T, class S>
 struct LBOps {
   static cudaError_t moments(const LBRaw &r, cudaStream_t st) {
-    moments_kernel<K, T, S><<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r));
+    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz), b = lb_block(K, r.nx, r.ny, r.nz);
+    if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
+    else moments_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
-  template <int STAGE, int MODE>
+  template <int STAGE, int MODE, bool EQ = false>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
+    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz), b = lb_block(K, r.nx, r.ny, r.nz);
     if (STAGE == 2 && r.p.rho_contrast)
-      node_kernel<K, T, S, STAGE, MODE, true>
-          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r), r.field_sel);
+      node_kernel<K, T, S, STAGE, MODE, STAGE == 2, EQ><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
     else
-      node_kernel<K, T, S, STAGE, MODE, false>
-          <<<lb_grid(K, r.nx, r.ny, r.nz), lb_block(K, r.nx, r.ny, r.nz), 0, st>>>(typed<T, S>(r), r.field_sel);
+      node_kernel<K, T, S, STAGE, MODE, false, EQ><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
   }
   static cudaError_t node(const LBRaw &r, int stage, int mode, cudaStream_t st) {
     if (stage == 2) {
-      if (mode == MODE_STEP) node_launch<2, MODE_STEP>(r, st);
+      if (mode == MODE_STEP && r.eq) node_launch<2, MODE_STEP, true>(r, st);
+      else if (mode == MODE_STEP) node_launch<2, MODE_STEP>(r, st);
       else if (mode == MODE_FIELDS) node_launch<2, MODE_FIELDS>(r, st);
       else node_launch<2, MODE_OBS>(r, st);
     } else {
@@ -748,7 +884,12 @@ struct LBOps {
   static cudaError_t get_pops(const LBRaw &r, void *fo, void *go, cudaStream_t st) {
     const int blocks = (int)((r.N + 255) / 256 < 152 * 32 ? (r.N + 255) / 256 : 152 * 32);
     pops_get_kernel<K, T, S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(typed<T, S>(r), (T *)fo,
-                                                                      (T *)go);
+                                                                      (T *)go, r.implicit);
+    return cudaGetLastError();
+  }
+  static cudaError_t materialize(const LBRaw &r, cudaStream_t st) {
+    const int blocks = (int)((r.N + 255) / 256 < 152 * 32 ? (r.N + 255) / 256 : 152 * 32);
+    g_materialize_kernel<K, T, S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
   static cudaError_t set_pops(const LBRaw &r, const void *fi, const void *gi, cudaStream_t st) {
@@ -767,7 +908,7 @@ struct LBOps {
            (size_t)round_up(bricks * (long long)sizeof(int), 256);
   }
   static cudaError_t batch(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
-                           cudaStream_t st) {
+                           bool eq, cudaStream_t st) {
     if (bytes < batch_bytes(items, n)) return cudaErrorInvalidValue;
     std::vector<BatchItem<T, S>> hi(n);
     std::vector<int> owner;
@@ -783,6 +924,7 @@ struct LBOps {
       b.brick0 = (int)owner.size();
       b.nsteps = (int)items[i].nsteps;
       b.cur0 = items[i].cur0;
+      b.implicit0 = items[i].r[0].implicit;
       if (b.nsteps > tmax) tmax = b.nsteps;
       owner.insert(owner.end(), (size_t)g.x * g.y * g.z, i);
     }
@@ -800,8 +942,10 @@ struct LBOps {
     // the copies above read pageable host memory: finish them before the
     // host vectors go out of scope
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    const void *fn = rc ? (const void *)batch_kernel<K, T, S, true>
-                        : (const void *)batch_kernel<K, T, S, false>;
+    const void *fn = rc ? (eq ? (const void *)batch_kernel<K, T, S, true, true>
+                              : (const void *)batch_kernel<K, T, S, true, false>)
+                        : (eq ? (const void *)batch_kernel<K, T, S, false, true>
+                              : (const void *)batch_kernel<K, T, S, false, false>);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -827,6 +971,7 @@ struct LBOps {
     t.solid = &solid;
     t.get_pops = &get_pops;
     t.set_pops = &set_pops;
+    t.materialize = &materialize;
     t.q = Lat<K>::Q;
     t.real_bytes = sizeof(T);
     t.store_bytes = sizeof(S);

@@ -39,7 +39,7 @@ def oracle_params(case: S.Case, kind: int):
                          tau_g=case.tau_g, body=case.body)
 
 
-def gpu_lattice(case: S.Case, precision: str, device="cuda"):
+def gpu_lattice(case: S.Case, precision: str, device="cuda", g_storage="auto"):
     import torch
     import paper_2504_19941_gb300 as P
     p = P.make_params(case.lattice, case.shape, precision, theta_deg=case.theta_deg, g12=case.g12,
@@ -47,6 +47,7 @@ def gpu_lattice(case: S.Case, precision: str, device="cuda"):
                       rho3=case.rho3, tau2=case.tau2, tau3=case.tau3, tau_g=case.tau_g,
                       body=case.body)
     lat = P.Lattice(p, device=device)
+    lat.set_g_storage(g_storage)
     real = lat.real
     lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=real, device=device))
     lat.set_fluid(torch.as_tensor(case.c2, dtype=real, device=device))

@@ -20,7 +20,7 @@ from paper_2504_19941_gb300.serving import GpuExecutor, Scheduler, serial_run, s
 DEV = "cuda"
 
 
-def _lattice(shape, seed, prec="f32"):
+def _lattice(shape, seed, prec="f32", form="auto"):
     rng = np.random.default_rng(seed)
     d = len(shape)
     sd = S.pillars_sd(shape, 3, int(rng.integers(3, 6)), int(rng.integers(8, 14)), 5, offset=2)
@@ -32,6 +32,7 @@ def _lattice(shape, seed, prec="f32"):
                       theta_deg=float(rng.uniform(40, 140)), g12=0.01, g23=0.01, alpha_s=a_s,
                       body=(1e-6, -2e-6, 0.0))
     lat = P.Lattice(p)
+    lat.set_g_storage(form)
     lat.set_solid_distance(torch.as_tensor(sd.ravel(), dtype=lat.real, device=DEV))
     lat.set_fluid(torch.as_tensor(c2, dtype=lat.real, device=DEV))
     return lat
@@ -43,13 +44,15 @@ SETS = {
 }
 
 
-@pytest.mark.parametrize("kind", ["2d", "3d"])
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_batch_equals_solo_bitwise(kind, prec):
+@pytest.mark.parametrize("kind,prec,form", [("2d", "f32", "auto"), ("3d", "f32", "auto"),
+                                            ("2d", "bf16", "auto"), ("3d", "bf16", "auto"),
+                                            ("3d", "f32", "populations"),
+                                            ("2d", "bf16", "populations")])
+def test_batch_equals_solo_bitwise(kind, prec, form):
     shapes = SETS[kind]
     nsteps = [30, 17, 0, 45, 8][:len(shapes)]
-    batch = [_lattice(s, i, prec) for i, s in enumerate(shapes)]
-    solo = [_lattice(s, i, prec) for i, s in enumerate(shapes)]
+    batch = [_lattice(s, i, prec, form) for i, s in enumerate(shapes)]
+    solo = [_lattice(s, i, prec, form) for i, s in enumerate(shapes)]
     hs = [lat.h for lat in batch]
     nb = _lib.dsm_batch_scratch_bytes(hs)
     scratch = torch.empty(nb, dtype=torch.uint8, device=DEV)
@@ -82,6 +85,10 @@ def test_batch_argument_checks():
     torch.cuda.synchronize()
     with pytest.raises(P.DSMError) as e:
         _lib.dsm_batch_scratch_bytes([a.h, c.h])  # different streams
+    assert e.value.status == _lib.DSM_E_INVAL
+    d = _lattice((16, 16), 2, "f32", form="populations")
+    with pytest.raises(P.DSMError) as e:
+        _lib.dsm_batch_scratch_bytes([a.h, d.h])  # g held as g_eq in one only
     assert e.value.status == _lib.DSM_E_INVAL
     nb = _lib.dsm_batch_scratch_bytes([a.h])
     scratch = torch.empty(nb, dtype=torch.uint8, device=DEV)

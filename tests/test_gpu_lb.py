@@ -99,12 +99,16 @@ def _small_3d(shape=(37, 29, 23), theta=120.0, g=0.01, body=(2e-6, -1e-6, -5e-6)
                   alpha_s=a_s, body=body)
 
 
-def test_d3q19_fp64_parity():
+# Both storage forms of g: "auto" holds g as g_eq (A, u) since tau_g = 1 here,
+# "populations" stores the Q populations.
+@pytest.mark.parametrize("form", ["auto", "populations"])
+def test_d3q19_fp64_parity(form):
     case = _small_3d()
     perm = direction_map(O.D3Q19)
-    lat = gpu_lattice(case, "f64")
+    lat = gpu_lattice(case, "f64", g_storage=form)
     p, c1, f, g = _oracle_case(case, O.D3Q19)
     lat.step(20)
+    assert lat.g_implicit == (form == "auto")
     f, g = O.lb_run(p, 2, c1, f, g, 20)
     errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
     gf, gg = gpu_pops(lat, perm)
@@ -112,12 +116,14 @@ def test_d3q19_fp64_parity():
     assert max(errs.values()) < 1e-12, errs
 
 
-def test_d3q19_fp32_parity():
+@pytest.mark.parametrize("form", ["auto", "populations"])
+def test_d3q19_fp32_parity(form):
     case = _small_3d()
     perm = direction_map(O.D3Q19)
-    lat = gpu_lattice(case, "f32")
+    lat = gpu_lattice(case, "f32", g_storage=form)
     p, c1, f, g = _oracle_case(case, O.D3Q19)
     lat.step(50)
+    assert lat.g_implicit == (form == "auto")
     f, g = O.lb_run(p, 2, c1, f, g, 50)
     e = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
     gf, gg = gpu_pops(lat, perm)
@@ -257,17 +263,91 @@ def test_full_size_mass_conservation_fp32():
 
 # ---------------------------------------------------------------- state, errors
 def test_state_roundtrip_bitwise():
+    # population form: populations out and back in continue the run bitwise
+    case = _small_3d(shape=(20, 18, 16))
+    a = gpu_lattice(case, "f32", g_storage="populations")
+    a.step(10)
+    f, g = a.populations()
+    a.step(10)
+    ref = a.populations()
+    b = gpu_lattice(case, "f32", g_storage="populations")
+    b.set_populations(f, g)
+    b.step(10)
+    out = b.populations()
+    assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1])
+
+
+def test_populations_roundtrip_g_eq_form():
+    # g held as g_eq: populations rebuilt from (A, u, C) restart the run up to
+    # FP32 rounding (the first moments pass then sums stored g_i)
     case = _small_3d(shape=(20, 18, 16))
     a = gpu_lattice(case, "f32")
     a.step(10)
+    assert a.g_implicit
     f, g = a.populations()
     a.step(10)
     ref = a.populations()
     b = gpu_lattice(case, "f32")
     b.set_populations(f, g)
+    assert not b.g_implicit
     b.step(10)
+    assert b.g_implicit
+    out = b.populations()
+    assert rel_err(out[0].cpu().numpy(), ref[0].cpu().numpy()) < 1e-6
+    assert rel_err(out[1].cpu().numpy(), ref[1].cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("form", ["auto", "populations"])
+def test_checkpoint_bitwise(prec, form):
+    case = _small_3d(shape=(20, 18, 16))
+    a = gpu_lattice(case, prec, g_storage=form)
+    a.step(7)
+    st = a.state()
+    a.step(9)
+    ref = a.populations()
+    b = gpu_lattice(case, prec, g_storage=form)
+    b.step(3)  # a different state, overwritten by the checkpoint
+    b.set_state(st)
+    assert b.g_implicit == a.g_implicit
+    b.step(9)
     out = b.populations()
     assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1])
+    assert b.observables()["step"] == a.observables()["step"] == 16
+
+
+def test_checkpoint_checks():
+    a = gpu_lattice(_small_3d(shape=(20, 18, 16)), "f32")
+    st = a.state()
+    b = gpu_lattice(_small_3d(shape=(20, 18, 14)), "f32")  # another size
+    with pytest.raises(P.DSMError) as e:
+        b.set_state(st)
+    assert e.value.status == P._lib.DSM_E_INVAL
+    with pytest.raises(P.DSMError) as e:
+        P._lib.dsm_set_state(a.h, st, st.numel() - 1)
+    assert e.value.status == P._lib.DSM_E_WORKSPACE
+
+
+def test_g_storage_switch_mid_run_fp64():
+    # g_eq form -> populations (written out from A, u, C) -> g_eq form: the
+    # trajectory matches an uninterrupted run to FP64 rounding
+    case = _small_3d(shape=(20, 18, 16))
+    perm = direction_map(O.D3Q19)
+    ref = gpu_lattice(case, "f64")
+    ref.step(30)
+    a = gpu_lattice(case, "f64")
+    a.step(10)
+    assert a.g_implicit
+    a.set_g_storage("populations")
+    assert not a.g_implicit
+    a.step(10)
+    assert not a.g_implicit
+    a.set_g_storage("auto")
+    a.step(10)
+    assert a.g_implicit
+    fa, ga = gpu_pops(a, perm)
+    fr, gr = gpu_pops(ref, perm)
+    assert rel_err(fa, fr) < 1e-13 and rel_err(ga, gr) < 1e-13
 
 
 def test_nonfinite_is_reported():
