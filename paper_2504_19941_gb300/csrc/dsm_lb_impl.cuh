@@ -162,7 +162,24 @@ __device__ __forceinline__ T geq_core(T A, T C, T cu) {
 //   C(x) + [ sum_{i != 0} w_i (A + C cu (3 + 9/2 cu))(x - c_i)
 //            - (1 - w_0) A(x) - 3/2 C(x) u(x).u(x) ]
 // (sum_{i != 0} w_i c_i.u (3 + 9/2 c_i.u) = 3/2 u.u reduces the node's own
-// outflow to its last two terms).
+// outflow to its last two terms).  Ay, Cy, uy hold the values at x - c_i
+// (index 0: the node itself).  Every moments pass of this form goes through
+// this function, so that all of them round alike.
+template <class L, class T>
+__device__ __forceinline__ T moments_eq_node(const T (&Ay)[L::Q], const T (&Cy)[L::Q],
+                                             const T (&uy)[L::Q][3]) {
+  T sa = T(0), sd = T(0);  // axis and diagonal links (one weight each)
+#pragma unroll
+  for (int i = 1; i < L::Q; i++) {
+    const T v = geq_core(Ay[i], Cy[i], cdot<L>(i, uy[i][0], uy[i][1], uy[i][2]));
+    if (L::w(i) == L::w(1)) sa += v;
+    else sd += v;
+  }
+  const T uu0 = uy[0][0] * uy[0][0] + uy[0][1] * uy[0][1] + uy[0][2] * uy[0][2];
+  const T out = T(1.0 - L::w(0)) * Ay[0] + T(1.5) * Cy[0] * uu0;
+  return Cy[0] + ((T(L::w(1)) * sa + T(L::w(L::Q - 1)) * sd) - out);
+}
+
 template <int K, class T, class S>
 __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, int y, int z) {
   using L = Lat<K>;
@@ -182,16 +199,133 @@ __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, in
     uy[i][1] = (i == 0 || L::cy(i)) ? __ldg(puy + m) : T(0);
     uy[i][2] = (L::D == 3 && (i == 0 || L::cz(i))) ? __ldg(puz + m) : T(0);
   }
-  T sa = T(0), sd = T(0);  // axis and diagonal links (one weight each)
+  a.C[n] = moments_eq_node<L, T>(Ay, Cy, uy);
+}
+
+// The same pass for D3Q19, tiled: a 32 x 8 block walks a run of z planes.
+// Each plane of (A, C, u) over the tile and a one-node halo is copied once into
+// a five-plane shared ring by asynchronous copies (cp.async), three planes
+// ahead of the plane being summed, and the five in-plane "cross" points (0,0),
+// (+-1,0), (0,+-1) a node needs from planes z-1, z, z+1 stay in registers from
+// one z to the next: per node 37 shared reads instead of 71 scattered loads.
+// One barrier per plane.
+constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_Z = 16, MT_RING = 5;
+
+template <class T>
+struct EqPt {
+  T A, C, ux, uy, uz;
+};
+template <class T>
+struct EqCross {
+  EqPt<T> c, xm, xp, ym, yp;  // (0,0), (-1,0), (+1,0), (0,-1), (0,+1)
+};
+
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <class T, class S>
+__global__ void __launch_bounds__(MT_X * MT_Y, sizeof(T) == 8 ? 1 : 3)
+    moments_eq_tiled_kernel(LBArgs<T, S> a) {
+  using L = Lat<1>;
+  constexpr int NH = MT_HX * MT_HY;          // nodes of one staged plane
+  constexpr int PER = (NH + MT_X * MT_Y - 1) / (MT_X * MT_Y);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T(*sm)[MT_RING][NH] = reinterpret_cast<T(*)[MT_RING][NH]>(sm_raw);  // [field][slot][node]
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + MT_X * ty;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int x0 = blockIdx.x * MT_X, y0 = blockIdx.y * MT_Y;
+  const int z0 = blockIdx.z * MT_Z, z1 = min(z0 + MT_Z, nz);
+  const T *src[5] = {a.Mp[0], a.Cprev, a.Mp[1], a.Mp[2], a.Mp[3]};  // A, C, ux, uy, uz
+  auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+  // in-plane global index of the staged nodes this thread copies (-1: none)
+  int hrow[PER];
 #pragma unroll
-  for (int i = 1; i < Q; i++) {
-    const T v = geq_core(Ay[i], Cy[i], cdot<L>(i, uy[i][0], uy[i][1], uy[i][2]));
-    if (L::w(i) == L::w(1)) sa += v;
-    else sd += v;
+  for (int r = 0; r < PER; r++) {
+    const int k = tid + r * MT_X * MT_Y;
+    hrow[r] = k < NH ? wrap(x0 - 1 + k % MT_HX, nx) + nx * wrap(y0 - 1 + k / MT_HX, ny) : -1;
   }
-  const T uu0 = uy[0][0] * uy[0][0] + uy[0][1] * uy[0][1] + uy[0][2] * uy[0][2];
-  const T out = T(1.0 - L::w(0)) * Ay[0] + T(1.5) * Cy[0] * uu0;
-  a.C[n] = Cy[0] + ((T(L::w(1)) * sa + T(L::w(Q - 1)) * sd) - out);
+  auto issue = [&](int zz) {  // plane zz -> ring slot zz mod MT_RING, one copy group
+    const int slot = wrap(zz, MT_RING);
+    const long long zo = (long long)wrap(zz, nz) * nx * ny;
+#pragma unroll
+    for (int r = 0; r < PER; r++)
+      if (hrow[r] >= 0) {
+        const int k = tid + r * MT_X * MT_Y;
+#pragma unroll
+        for (int f = 0; f < 5; f++) cp_async_elem(&sm[f][slot][k], src[f] + zo + hrow[r]);
+      }
+    cp_async_commit();
+  };
+  auto pt = [&](int zz, int dx, int dy) {
+    const int slot = wrap(zz, MT_RING);
+    const int k = (tx + 1 + dx) + MT_HX * (ty + 1 + dy);
+    EqPt<T> p;
+    p.A = sm[0][slot][k];
+    p.C = sm[1][slot][k];
+    p.ux = sm[2][slot][k];
+    p.uy = sm[3][slot][k];
+    p.uz = sm[4][slot][k];
+    return p;
+  };
+  auto cross = [&](int zz) {
+    EqCross<T> c;
+    c.c = pt(zz, 0, 0);
+    c.xm = pt(zz, -1, 0);
+    c.xp = pt(zz, 1, 0);
+    c.ym = pt(zz, 0, -1);
+    c.yp = pt(zz, 0, 1);
+    return c;
+  };
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < nx && y < ny;
+  // one plane: wait for plane z + 1, refill the ring with plane z + 4 (into the
+  // slot of plane z - 1, read for the last time in the previous step), then the
+  // node's sum from the cross points of z - 1, z, z + 1 and the diagonals of z
+  auto step = [&](int z, const EqCross<T> &Pm, const EqCross<T> &P0, EqCross<T> &Pp) {
+    cp_async_wait<2>();  // planes up to z + 1 have landed (z + 2, z + 3 may be in flight)
+    __syncthreads();
+    issue(z + 4);
+    Pp = cross(z + 1);
+    if (active) {
+      T Ay[L::Q], Cy[L::Q], uy[L::Q][3];
+#pragma unroll
+      for (int i = 0; i < L::Q; i++) {
+        // the value at x - c_i: plane by -c_z, in-plane point by (-c_x, -c_y)
+        const int sx = -L::cx(i), sy = -L::cy(i), sz = -L::cz(i);
+        const EqCross<T> &Pl = sz < 0 ? Pm : (sz > 0 ? Pp : P0);
+        EqPt<T> v;
+        if (sx != 0 && sy != 0) v = pt(z, sx, sy);  // in-plane diagonal
+        else v = sx < 0 ? Pl.xm : sx > 0 ? Pl.xp : sy < 0 ? Pl.ym : sy > 0 ? Pl.yp : Pl.c;
+        Ay[i] = v.A;
+        Cy[i] = v.C;
+        uy[i][0] = (i == 0 || L::cx(i)) ? v.ux : T(0);
+        uy[i][1] = (i == 0 || L::cy(i)) ? v.uy : T(0);
+        uy[i][2] = (i == 0 || L::cz(i)) ? v.uz : T(0);
+      }
+      a.C[(long long)z * nx * ny + x + (long long)nx * y] = moments_eq_node<L, T>(Ay, Cy, uy);
+    }
+  };
+  // prologue: planes z0 - 1 .. z0 + 3 in flight, the cross points of z0 - 1 and z0
+  for (int d = -1; d <= 3; d++) issue(z0 + d);
+  cp_async_wait<3>();
+  __syncthreads();
+  EqCross<T> Pa = cross(z0 - 1), Pb = cross(z0), Pc;
+  // unrolled by three so that the rotating cross points stay in registers
+  for (int z = z0; z < z1; z += 3) {
+    step(z, Pa, Pb, Pc);
+    if (z + 1 < z1) step(z + 1, Pb, Pc, Pa);
+    if (z + 2 < z1) step(z + 2, Pc, Pa, Pb);
+  }
+  cp_async_wait<0>();  // no copy outlives the block
 }
 
 template <int K, class T, class S>
@@ -253,6 +387,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       const T w = T(L::w(i));
       lapC += w * (Cn[i] - C);
       if (STAGE == 2) lapS += w * ((C1n[i] + Cn[i]) - (c1 + C));
+      // (zero components skipped: without fast-math 0 * x is not folded away)
       gC[0] += w * T(L::cx(i)) * Cn[i];
       gC[1] += w * T(L::cy(i)) * Cn[i];
       gC[2] += w * T(L::cz(i)) * Cn[i];
@@ -282,9 +417,9 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 #pragma unroll
         for (int i = 1; i < Q; i++) {
           const T r = T(L::w(i)) * rho_of(Cn[i], C1n[i]);
-          gR[0] += r * T(L::cx(i));
-          gR[1] += r * T(L::cy(i));
-          gR[2] += r * T(L::cz(i));
+          if (L::cx(i)) gR[0] += r * T(L::cx(i));
+          if (L::cy(i)) gR[1] += r * T(L::cy(i));
+          if (L::cz(i)) gR[2] += r * T(L::cz(i));
         }
 #pragma unroll
         for (int d = 0; d < 3; d++) gR[d] *= T(3);
@@ -300,9 +435,9 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 #pragma unroll
         for (int i = 1; i < Q; i++) {
           const T w = T(L::w(i));
-          gc1[0] += w * T(L::cx(i)) * C1n[i];
-          gc1[1] += w * T(L::cy(i)) * C1n[i];
-          gc1[2] += w * T(L::cz(i)) * C1n[i];
+          if (L::cx(i)) gc1[0] += w * T(L::cx(i)) * C1n[i];
+          if (L::cy(i)) gc1[1] += w * T(L::cy(i)) * C1n[i];
+          if (L::cz(i)) gc1[2] += w * T(L::cz(i)) * C1n[i];
         }
 #pragma unroll
         for (int d = 0; d < 3; d++) gc1[d] *= T(3);
@@ -510,7 +645,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       const T cF = T(L::cx(i)) * Fv[0] + T(L::cy(i)) * Fv[1] + T(L::cz(i)) * Fv[2];
       T Fp = w * kF3 * cF, Fm = -Fp;
       if (RC) {
-        const T cg = T(L::cx(i)) * gR[0] + T(L::cy(i)) * gR[1] + T(L::cz(i)) * gR[2];
+        const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);
         Fp += kF * w * ((cg - ug) * sp);
         Fm += kF * w * ((-cg - ug) * sm);
       }
@@ -542,7 +677,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 }
 
 template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ && !RC ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
@@ -837,11 +972,30 @@ LBArgs<T, S> typed(const LBRaw &r) {
   return a;
 }
 
+template <class T>
+constexpr size_t moments_eq_smem() {
+  return sizeof(T) * 5 * MT_RING * MT_HX * MT_HY;
+}
+
 template <int K, class T, class S>
 struct LBOps {
   static cudaError_t moments(const LBRaw &r, cudaStream_t st) {
     const dim3 g = lb_grid(K, r.nx, r.ny, r.nz), b = lb_block(K, r.nx, r.ny, r.nz);
-    if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
+    if (r.implicit && K == 1 && moments_eq_smem<T>() > 48 * 1024) {
+      static bool opted_in = false;  // above 48 KB of dynamic shared memory
+      if (!opted_in) {
+        const cudaError_t e = cudaFuncSetAttribute(moments_eq_tiled_kernel<T, S>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)moments_eq_smem<T>());
+        if (e != cudaSuccess) return e;
+        opted_in = true;
+      }
+    }
+    if (r.implicit && K == 1)
+      moments_eq_tiled_kernel<T, S><<<dim3((r.nx + MT_X - 1) / MT_X, (r.ny + MT_Y - 1) / MT_Y,
+                                           (r.nz + MT_Z - 1) / MT_Z),
+                                      dim3(MT_X, MT_Y, 1), moments_eq_smem<T>(), st>>>(typed<T, S>(r));
+    else if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     else moments_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
