@@ -387,7 +387,6 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       const T w = T(L::w(i));
       lapC += w * (Cn[i] - C);
       if (STAGE == 2) lapS += w * ((C1n[i] + Cn[i]) - (c1 + C));
-      // (zero components skipped: without fast-math 0 * x is not folded away)
       gC[0] += w * T(L::cx(i)) * Cn[i];
       gC[1] += w * T(L::cy(i)) * Cn[i];
       gC[2] += w * T(L::cz(i)) * Cn[i];
