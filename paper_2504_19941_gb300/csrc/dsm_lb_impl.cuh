@@ -209,7 +209,7 @@ __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, in
 // (+-1,0), (0,+-1) a node needs from planes z-1, z, z+1 stay in registers from
 // one z to the next: per node 37 shared reads instead of 71 scattered loads.
 // One barrier per plane.
-constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_Z = 16, MT_RING = 5;
+constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_Z = 32, MT_RING = 5;
 
 template <class T>
 struct EqPt {
@@ -936,11 +936,19 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
 // ---------------------------------------------------------------------------
 // Block shape of the per-lattice launches.  Lattices too small to give every SM
 // a 256-thread block (fewer than ~2 x 152 x 256 nodes) use 64-thread blocks so
-// that their work spreads over four times as many SMs.  The batched launch keeps
-// the 256-thread shape for every lattice (lb_block_batch).
+// that their work spreads over four times as many SMs.  Larger lattices use the
+// widest row (256, 128, 64 or 32 nodes) that divides nx: the warps of one row
+// then share, in L1, the cache lines their shifted pulls straddle (measured at
+// 256x256x192, fused pass: 32x4x2 blocks 0.510 ms, 128x2x1 0.486 ms,
+// 256x1x1 0.484 ms).
+// The batched launch keeps 32-wide bricks for every lattice (lb_block_batch),
+// which suits its small lattices.
 inline dim3 lb_block_batch(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
 inline dim3 lb_block(int kind, int nx, int ny, int nz) {
   if ((long long)nx * ny * nz < 2ll * 152 * 256) return kind == 0 ? dim3(32, 2, 1) : dim3(32, 1, 2);
+  if (nx % 256 == 0) return dim3(256, 1, 1);
+  if (nx % 128 == 0) return dim3(128, 2, 1);
+  if (nx % 64 == 0) return dim3(64, 4, 1);
   return lb_block_batch(kind);
 }
 inline dim3 lb_grid_of(dim3 b, int nx, int ny, int nz) {
