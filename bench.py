@@ -441,7 +441,7 @@ def run_precision(args, rank, world):
 
 def run_plain_fp64(args, rank, world):
     """The plain FP64 D2Q9 128x64 wall-drop case: per-step launches against one
-    persistent batched launch of all its steps."""
+    persistent batched launch of all its steps, in both storage forms of g."""
     import torch
     import synthetic as S
     import paper_2504_19941_gb300 as P
@@ -450,27 +450,31 @@ def run_plain_fp64(args, rank, world):
     torch.cuda.set_device(dev)
     case = S.wall_drop_2d()
     res = {}
-    for mode in ("per_step_launches", "persistent_launch"):
-        p = P.make_params("D2Q9", case.shape, "f64", theta_deg=case.theta_deg, g12=case.g12,
-                          g23=case.g23, alpha_s=case.alpha_s)
-        lat = P.Lattice(p, device=dev)
-        lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float64, device=dev))
-        lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float64, device=dev))
-        nb = _lib.dsm_batch_scratch_bytes([lat.h])
-        scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
-        lat.step(10)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        if mode == "per_step_launches":
-            lat.step(case.steps)
-        else:
-            _lib.dsm_batch_step([lat.h], [case.steps], scratch, nb)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        res[mode] = {"us_per_step": dt / case.steps * 1e6, "MLUPS": lat.n * case.steps / dt / 1e6}
+    for form in ("auto", "populations"):
+        for mode in ("per_step_launches", "persistent_launch"):
+            p = P.make_params("D2Q9", case.shape, "f64", theta_deg=case.theta_deg, g12=case.g12,
+                              g23=case.g23, alpha_s=case.alpha_s)
+            lat = P.Lattice(p, device=dev)
+            lat.set_g_storage(form)
+            lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float64, device=dev))
+            lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float64, device=dev))
+            nb = _lib.dsm_batch_scratch_bytes([lat.h])
+            scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+            lat.step(10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "per_step_launches":
+                lat.step(case.steps)
+            else:
+                _lib.dsm_batch_step([lat.h], [case.steps], scratch, nb)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            key = ("g_eq" if form == "auto" else "populations") + "/" + mode
+            res[key] = {"us_per_step": dt / case.steps * 1e6, "MLUPS": lat.n * case.steps / dt / 1e6}
+    best = min(res, key=lambda k: res[k]["us_per_step"])
     if rank == 0:
         print(json.dumps({"metric": "D2Q9 FP64 128x64 wall drop, 2000 steps", "unit": "us/step",
-                          "value": res["persistent_launch"]["us_per_step"],
+                          "value": res[best]["us_per_step"], "best": best,
                           "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
                           "data": "synthetic", "modes": res}), flush=True)
     return 0

@@ -936,19 +936,19 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
 // ---------------------------------------------------------------------------
 // Block shape of the per-lattice launches.  Lattices too small to give every SM
 // a 256-thread block (fewer than ~2 x 152 x 256 nodes) use 64-thread blocks so
-// that their work spreads over four times as many SMs.  Larger lattices use the
-// widest row (256, 128, 64 or 32 nodes) that divides nx: the warps of one row
-// then share, in L1, the cache lines their shifted pulls straddle (measured at
-// 256x256x192, fused pass: 32x4x2 blocks 0.510 ms, 128x2x1 0.486 ms,
-// 256x1x1 0.484 ms).
-// The batched launch keeps 32-wide bricks for every lattice (lb_block_batch),
-// which suits its small lattices.
+// that their work spreads over four times as many SMs.  Larger lattices: shapes
+// measured on the fused pass (D3Q19 FP32, g held as g_eq), best kept --
+//   256x256x192:  32x4x2 0.510 ms, 64x4x1 0.494, 128x2x1 0.486, 256x1x1 0.484;
+//   384x384x256:  32x4x2 1.784 ms, 64x4x1 1.784, 64x2x2 1.772, 128x2x1 2.025,
+//                 128x1x2 2.017.
+// Whole 256-node rows where nx allows, else 64x2x2, else 32-wide bricks.  The
+// batched launch keeps 32-wide bricks for every lattice (lb_block_batch), which
+// suits its small lattices.
 inline dim3 lb_block_batch(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
 inline dim3 lb_block(int kind, int nx, int ny, int nz) {
   if ((long long)nx * ny * nz < 2ll * 152 * 256) return kind == 0 ? dim3(32, 2, 1) : dim3(32, 1, 2);
   if (nx % 256 == 0) return dim3(256, 1, 1);
-  if (nx % 128 == 0) return dim3(128, 2, 1);
-  if (nx % 64 == 0) return dim3(64, 4, 1);
+  if (nx % 64 == 0) return kind == 0 ? dim3(64, 4, 1) : dim3(64, 2, 2);
   return lb_block_batch(kind);
 }
 inline dim3 lb_grid_of(dim3 b, int nx, int ny, int nz) {
