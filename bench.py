@@ -165,53 +165,88 @@ def make_case(shape):
     return S.pillar_slab_3d(*shape, liquid=(38, min(98, nz - 4)))
 
 
+class OracleSlice:
+    """The FP64 oracle, as it stands, on a 64x64x48 slice of the workload: the
+    bounded sample both the CPU baseline and the reference arm time."""
+    SHAPE = (64, 64, 48)
+
+    def __init__(self):
+        import numpy as np
+        import oracle as O
+        import synthetic as S
+        self.O = O
+        case = S.pillar_slab_3d(*self.SHAPE, pitch=32, width=10, height=12, base=4, liquid=(16, 32))
+        k, _ = O.kappa_from_angle(case.theta_deg, case.g23, case.g12)
+        self.p = O.make_params(O.D3Q19, self.SHAPE, k, alpha_s=case.alpha_s)
+        self.c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+        self.f, self.g = O.lb_init(self.p, 2, self.c1, case.c2)
+        self.n = int(np.prod(self.SHAPE))
+
+    def run(self, max_seconds):
+        """Oracle steps, two at a time, until max_seconds have passed: (steps, seconds)."""
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            self.f, self.g = self.O.lb_run(self.p, 2, self.c1, self.f, self.g, 2)
+            steps += 2
+            if time.perf_counter() - t0 > max_seconds:
+                break
+        return steps, time.perf_counter() - t0
+
+    @staticmethod
+    def cores():
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
 def cpu_baseline(max_seconds=15.0):
     """The FP64 oracle, as it stands, on a 64x64x48 slice of the workload."""
-    import numpy as np
-    import oracle as O
-    import synthetic as S
-    shape = (64, 64, 48)
-    case = S.pillar_slab_3d(*shape, pitch=32, width=10, height=12, base=4, liquid=(16, 32))
-    k, _ = O.kappa_from_angle(case.theta_deg, case.g23, case.g12)
-    p = O.make_params(O.D3Q19, shape, k, alpha_s=case.alpha_s)
-    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
-    f, g = O.lb_init(p, 2, c1, case.c2)
-    O.lb_run(p, 2, c1, f, g, 1)  # warm
-    n = int(np.prod(shape))
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        f, g = O.lb_run(p, 2, c1, f, g, 2)
-        steps += 2
-        if time.perf_counter() - t0 > max_seconds:
-            break
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+    sl = OracleSlice()
+    sl.run(0.0)  # warm
+    steps, dt = sl.run(max_seconds)
+    return {"value": sl.n * steps / dt / 1e6, "unit": "MLUPS", "cores": sl.cores(), "kind": "oracle",
             "sample": f"D3Q19 FP64 oracle, 64x64x48 pillar-slab slice, {steps} steps, {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle timed on the host cores.  Each of the K
+    timed steps (after W untimed ones) is a bounded sample of the workload --
+    oracle steps on the 64x64x48 slice for about 100 s / (K + W), at least 0.2 s
+    -- so that the whole run takes about two minutes."""
     if rank != 0:
         return 0
-    per_step = max(5.0, 60.0 / max(args.steps + args.warmup, 1))
-    cb = None
-    times = []
+    per_step = min(20.0, max(0.2, 100.0 / max(args.steps + args.warmup, 1)))
+    sl = OracleSlice()
+    lu, secs, steps_done = 0, 0.0, 0
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(max_seconds=min(per_step, 20.0))
+        steps, dt = sl.run(per_step)
         if i >= args.warmup:
-            times.append(r["value"])
-            cb = r
-    value = sum(times) / len(times)
+            lu += sl.n * steps
+            secs += dt
+            steps_done += steps
+    value = lu / secs / 1e6
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "D3Q19 FP64 CPU oracle on a 64x64x48 slice of the "
-                                  "pillar-slab workload", "parallelism": "host cores"},
-           "cpu_baseline": dict(cb, value=value),
+           "warmup": args.warmup,
+           # one step of the full workload at the sampled rate
+           "ms_per_step": SHAPE[0] * SHAPE[1] * SHAPE[2] / (value * 1e6) * 1e3,
+           "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference", "config": gpu_config(SHAPE, world, "populations"),
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": sl.cores(), "kind": "oracle",
+                            "sample": f"each step: D3Q19 FP64 oracle LB steps on a 64x64x48 "
+                                      f"pillar-slab slice for {per_step:.2f} s ({steps_done} oracle "
+                                      f"steps in {secs:.1f} s timed)"},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def gpu_config(shape, world, g_storage):
+    return {"workload": WORKLOAD if tuple(shape) == SHAPE else
+            f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)",
+            "lattice": "D3Q19", "nodes": int(shape[0] * shape[1] * shape[2]),
+            "global_batch": world, "parallelism": f"replicas x{world}",
+            "g_storage": g_storage,
+            "l2": "f populations alone 1.9 GB per buffer, larger than L2; no flush"}
 
 
 def run_gpu(args, rank, world):
@@ -311,12 +346,8 @@ def run_gpu(args, rank, world):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": WORKLOAD if shape == SHAPE else
-                          f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)",
-                          "lattice": "D3Q19", "nodes": n,
-                          "global_batch": world, "parallelism": f"replicas x{world}",
-                          "g_storage": "g_eq (tau_g = 1): A, u per node" if g_eq else "populations",
-                          "l2": "f populations alone 1.9 GB per buffer, larger than L2; no flush"},
+               "config": gpu_config(shape, world,
+                                    "g_eq (tau_g = 1): A, u per node" if g_eq else "populations"),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic,
                             "kernel": "node_kernel<D3Q19,f32,stage2,step,%s>" %

@@ -202,14 +202,14 @@ __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, in
   a.C[n] = moments_eq_node<L, T>(Ay, Cy, uy);
 }
 
-// The same pass for D3Q19, tiled: a 32 x 8 block walks a run of z planes.
+// The same pass for D3Q19, tiled: a 32 x 8 block walks a run of zrun z planes.
 // Each plane of (A, C, u) over the tile and a one-node halo is copied once into
 // a five-plane shared ring by asynchronous copies (cp.async), three planes
 // ahead of the plane being summed, and the five in-plane "cross" points (0,0),
 // (+-1,0), (0,+-1) a node needs from planes z-1, z, z+1 stay in registers from
 // one z to the next: per node 37 shared reads instead of 71 scattered loads.
 // One barrier per plane.
-constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_Z = 32, MT_RING = 5;
+constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_RING = 5;
 
 template <class T>
 struct EqPt {
@@ -234,7 +234,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <class T, class S>
 __global__ void __launch_bounds__(MT_X * MT_Y, sizeof(T) == 8 ? 1 : 3)
-    moments_eq_tiled_kernel(LBArgs<T, S> a) {
+    moments_eq_tiled_kernel(LBArgs<T, S> a, int zrun) {
   using L = Lat<1>;
   constexpr int NH = MT_HX * MT_HY;          // nodes of one staged plane
   constexpr int PER = (NH + MT_X * MT_Y - 1) / (MT_X * MT_Y);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(MT_X * MT_Y, sizeof(T) == 8 ? 1 : 3)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + MT_X * ty;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int x0 = blockIdx.x * MT_X, y0 = blockIdx.y * MT_Y;
-  const int z0 = blockIdx.z * MT_Z, z1 = min(z0 + MT_Z, nz);
+  const int z0 = blockIdx.z * zrun, z1 = min(z0 + zrun, nz);
   const T *src[5] = {a.Mp[0], a.Cprev, a.Mp[1], a.Mp[2], a.Mp[3]};  // A, C, ux, uy, uz
   auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
   // in-plane global index of the staged nodes this thread copies (-1: none)
@@ -361,7 +361,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   // loads and the 2Q neighbourhood loads are all in flight together.
   T C, c1, mu, rho, tau, omf, omg;  // omf = 1/tau, omg = 1/tau_g
   T gC[3] = {T(0), T(0), T(0)}, gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
-  unsigned nb_solid = 0;  // bit k: x + c_k is solid (stage 2)
+  unsigned nb_solid = 0;  // bit k: x + c_k is solid (stage 2, fluid nodes next to the solid)
   T f[Q], g[Q];
   {
     T Cn[Q], C1n[Q];
@@ -387,9 +387,9 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       const T w = T(L::w(i));
       lapC += w * (Cn[i] - C);
       if (STAGE == 2) lapS += w * ((C1n[i] + Cn[i]) - (c1 + C));
-      gC[0] += w * T(L::cx(i)) * Cn[i];
-      gC[1] += w * T(L::cy(i)) * Cn[i];
-      gC[2] += w * T(L::cz(i)) * Cn[i];
+      if (L::cx(i)) gC[0] += w * T(L::cx(i)) * Cn[i];
+      if (L::cy(i)) gC[1] += w * T(L::cy(i)) * Cn[i];
+      if (L::cz(i)) gC[2] += w * T(L::cz(i)) * Cn[i];
     }
     lapC *= T(6);  // 2 / c_s^2
     lapS *= T(6);
@@ -428,9 +428,14 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       tau = liquid ? K_.tau2 : K_.tau3;
       omf = liquid ? K_.om2 : K_.om3;
       omg = K_.omg;
+      // solid links (bit k: x + c_k is solid) only for a fluid node with a solid
+      // neighbour -- rare; elsewhere one running max of C1 settles it
+      T c1max = C1n[1];
 #pragma unroll
-      for (int i = 0; i < Q; i++) nb_solid |= (C1n[i] >= T(0.5) ? 1u : 0u) << i;
-      if ((nb_solid & ~1u) && !(nb_solid & 1u)) {
+      for (int i = 2; i < Q; i++) c1max = c1max > C1n[i] ? c1max : C1n[i];
+      if (c1max >= T(0.5) && !(c1 >= T(0.5))) {
+#pragma unroll
+        for (int i = 1; i < Q; i++) nb_solid |= (C1n[i] >= T(0.5) ? 1u : 0u) << i;
 #pragma unroll
         for (int i = 1; i < Q; i++) {
           const T w = T(L::w(i));
@@ -458,7 +463,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       omg = T(1);
     }
   }
-  const bool solid_x = (STAGE == 2) && (nb_solid & 1u);
+  const bool solid_x = (STAGE == 2) && c1 >= T(0.5);
 
   // ---- interpolated bounce-back at the diffuse solid ------------------------
   // (rare: only fluid nodes with a solid neighbour) -- one rolled loop replaces
@@ -998,11 +1003,16 @@ struct LBOps {
         opted_in = true;
       }
     }
-    if (r.implicit && K == 1)
+    if (r.implicit && K == 1) {
+      // the longest run of z planes (fewer ring refills per plane) that still
+      // fills one wave of three 256-thread blocks per SM
+      const int tiles = ((r.nx + MT_X - 1) / MT_X) * ((r.ny + MT_Y - 1) / MT_Y);
+      int zrun = 32;
+      while (zrun > 4 && (long long)tiles * ((r.nz + zrun - 1) / zrun) < 3 * 152) zrun /= 2;
       moments_eq_tiled_kernel<T, S><<<dim3((r.nx + MT_X - 1) / MT_X, (r.ny + MT_Y - 1) / MT_Y,
-                                           (r.nz + MT_Z - 1) / MT_Z),
-                                      dim3(MT_X, MT_Y, 1), moments_eq_smem<T>(), st>>>(typed<T, S>(r));
-    else if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
+                                           (r.nz + zrun - 1) / zrun),
+                                      dim3(MT_X, MT_Y, 1), moments_eq_smem<T>(), st>>>(typed<T, S>(r), zrun);
+    } else if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     else moments_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
   }
