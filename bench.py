@@ -511,6 +511,44 @@ def run_plain_fp64(args, rank, world):
     return 0
 
 
+def run_critical(args, rank, world):
+    """Critical pressure of the Cassie-Baxter to Wenzel transition on 2D pillars
+    (Sec. III) by bisection over GPU energy minimisations, for a sweep of five
+    contact angles on a 160x200 box with gap s = 81, the cases run concurrently
+    (one host thread and CUDA stream each): the value is sweep points per second;
+    each point reports dP_c against -2 gamma cos(theta) / s.  The same sweep run
+    one case after another is reported beside it."""
+    import torch
+    import synthetic as S
+    from paper_2504_19941_gb300 import critical as C
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    thetas = (60.0, 80.0, 100.0, 112.0, 135.0)
+    cases = [S.pillar_gap_2d(period=160, height=200, width=79, pillar=100, base=6, theta=t)
+             for t in thetas]
+    C.critical_pressure(S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4))  # warm
+    t0 = time.perf_counter()
+    res = C.critical_sweep(cases)
+    wall = time.perf_counter() - t0
+    serial = None
+    if not args.no_serial_baseline:
+        t1 = time.perf_counter()
+        for c in cases:
+            C.critical_pressure(c)
+        serial = len(cases) / (time.perf_counter() - t1)
+    pts = [{"theta": t, "dP_c": r["dP_c"], "theory": r["theory"], "ratio": r["ratio"],
+            "probes": r["probes"], "lbfgs_iterations": r["iterations"], "seconds": r["seconds"]}
+           for t, r in zip(thetas, res)]
+    if rank == 0:
+        print(json.dumps({"metric": "critical-pressure sweep points/s (2D pillars, bisection to 1e-4)",
+                          "value": len(pts) / wall, "unit": "points/s", "n_gpus": 1,
+                          "higher_is_better": True, "dtype": "f32 fields / f64 energy",
+                          "data": "synthetic",
+                          "config": {"workload": "160x200 box, pillar width 79, gap 81, height 100, "
+                                                 "5 contact angles concurrently"},
+                          "one_at_a_time_points_per_s": serial, "points": pts}), flush=True)
+    return 0
+
+
 def run_em(args, rank, world):
     """Energy-minimisation twin on a 128^3 grid (sphere of radius 20 at a flat
     liquid/gas interface): energy + gradient evaluations per second, and L-BFGS
@@ -583,7 +621,8 @@ def main():
                     help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
-    ap.add_argument("--workload", default="lb", choices=["lb", "serve", "precision", "fp64", "em"])
+    ap.add_argument("--workload", default="lb",
+                    choices=["lb", "serve", "precision", "fp64", "em", "critical"])
     ap.add_argument("--em-iters", type=int, default=3000)
     ap.add_argument("--serve-requests", type=int, default=96)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -604,6 +643,8 @@ def main():
         return run_plain_fp64(args, rank, world)
     if args.workload == "em":
         return run_em(args, rank, world)
+    if args.workload == "critical":
+        return run_critical(args, rank, world)
     return run_gpu(args, rank, world)
 
 

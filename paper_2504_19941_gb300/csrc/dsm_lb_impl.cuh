@@ -386,13 +386,13 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     for (int i = 1; i < Q; i++) {
       const T w = T(L::w(i));
       lapC += w * (Cn[i] - C);
-      if (STAGE == 2) lapS += w * ((C1n[i] + Cn[i]) - (c1 + C));
+      if (STAGE == 2) lapS += w * (C1n[i] - c1);
       if (L::cx(i)) gC[0] += w * T(L::cx(i)) * Cn[i];
       if (L::cy(i)) gC[1] += w * T(L::cy(i)) * Cn[i];
       if (L::cz(i)) gC[2] += w * T(L::cz(i)) * Cn[i];
     }
     lapC *= T(6);  // 2 / c_s^2
-    lapS *= T(6);
+    lapS = lapC + T(6) * lapS;  // L[C1 + C] = L[C] + L[C1]
 #pragma unroll
     for (int d = 0; d < 3; d++) gC[d] *= T(3);  // 1 / c_s^2
     if (STAGE == 2) {
@@ -639,14 +639,14 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   for (int i = 1; i < Q; i += 2) {
     const int ib = i + 1;  // opposite direction
     const T w = T(L::w(i));
-    const T cu = T(L::cx(i)) * u[0] + T(L::cy(i)) * u[1] + T(L::cz(i)) * u[2];
+    const T cu = cdot<L>(i, u[0], u[1], u[2]);
     const T even = T(4.5) * cu * cu - m15uu;
     const T odd = T(3) * cu;
     const T sp = even + odd, sm = even - odd;
     T fp = w, fm = w;
     if (!solid_x) {
       const T wpt = w * pt, wr = w * rho;
-      const T cF = T(L::cx(i)) * Fv[0] + T(L::cy(i)) * Fv[1] + T(L::cz(i)) * Fv[2];
+      const T cF = cdot<L>(i, Fv[0], Fv[1], Fv[2]);
       T Fp = w * kF3 * cF, Fm = -Fp;
       if (RC) {
         const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);

@@ -293,6 +293,31 @@ def em_sinusoid_drop(n=128, amplitude=6.0, wavelength=32.0, base=16.0, radius=30
                 extra={"kcs": 1e-2})
 
 
+def pillar_gap_2d(period=64, height=120, width=24, pillar=40, base=6, theta=112.0,
+                  g23=math.sqrt(8.0 / 9.0), g12=1.0, solid_width=1.0) -> Case:
+    """Energy minimisation, critical pressure on micropillars (Sec. III, 2D): one
+    period of a row of rectangular pillars of width `width` and height `pillar`
+    on a base plate y < `base` (the pillar split across the periodic x
+    boundary, so the gap s = period - width is centred), gas in the gap and a
+    liquid layer on the pillar tops up to the box top (periodic in y: the box
+    top meets the underside of the base plate).  extra['gap'] holds the nodes of
+    the lower half of the gap, extra['s'] the gap width."""
+    shape = (period, height)
+    half = width // 2
+    sd = union_sd(slab_sd(shape, 1, 0, base),
+                  box_sd(shape, (0, base), (half, base + pillar)),
+                  box_sd(shape, (period - (width - half), base), (period, base + pillar)))
+    top = base + pillar
+    # liquid from the pillar tops through the periodic top to the base's underside
+    c2 = layer_c2(shape, 1, top, height + 8, 1.0, sd, solid_width).ravel()
+    x, y = _coords(shape)
+    s = period - width
+    lo_x, hi_x = half + s // 4, period - (width - half) - s // 4
+    gap = ((x >= lo_x) & (x < hi_x) & (y >= base + 2) & (y < base + pillar // 2)).ravel()
+    return Case("pillar_gap_2d", "D2Q9", shape, sd.ravel(), c2, theta_deg=theta, g23=g23, g12=g12,
+                alpha_s=solid_width, extra={"gap": np.flatnonzero(gap), "s": s})
+
+
 def random_fields(n, seed=0, lo=0.05, hi=0.95):
     """Independent uniform fields in [lo, hi) for finite-difference checks."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,60 @@
+"""Critical pressure on micropillars by energy minimisation on the GPU (Sec. III):
+bisection over L-BFGS minimisations of the pressure-constrained free energy
+(FP32 fields, FP64 energy) against the FP64 oracle's bisection on the same
+grid, and against the closed form dP_c = -2 gamma cos(theta) / s."""
+import math
+
+import pytest
+
+import oracle as O
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_19941_gb300 import critical as C  # noqa: E402
+from oracle import critical as OC  # noqa: E402
+
+
+@pytest.mark.parametrize("theta", [112.0, 60.0])
+def test_critical_pressure_matches_oracle(theta):
+    c = S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=theta)
+    r = C.critical_pressure(c, tol=1e-4)
+    k, _ = O.kappa_from_angle(theta, c.g23, c.g12)
+    p = O.make_params(O.D2Q9, c.shape, k, alpha_s=c.alpha_s)
+    c1 = O.solid_profile(c.solid_sd, c.alpha_s)
+    lo, hi = r["bracket"]
+    # the oracle's bisection from the GPU's final bracket widened by 4 tolerances
+    dpc_o = OC.critical_pressure(p, c1, c.c2, c.extra["gap"], lo - 4e-4, hi + 4e-4)
+    # both bisections stop within 1e-4 of their own switch point; FP32 fields
+    # may move the switch by a fraction of that
+    assert abs(r["dP_c"] - dpc_o) < 2e-4, (r, dpc_o)
+
+
+@pytest.mark.parametrize("theta", [60.0, 135.0])
+def test_critical_pressure_closed_form(theta):
+    c = S.pillar_gap_2d(period=64, height=120, width=24, pillar=40, base=6, theta=theta)
+    r = C.critical_pressure(c, tol=1e-4)
+    assert abs(r["ratio"] - 1) < 0.03, r
+
+
+def test_suspended_and_collapsed_states():
+    c = S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=120.0)
+    pg = C.PillarGap(c)
+    th = C.critical_theory(c.g23, 120.0, c.extra["s"])
+    x, E_lo, info = pg.relax(0.5 * th)
+    assert pg.gap_liquid(x) < 0.1 and info["rms_grad"] < 1e-6
+    x, E_hi, info = pg.relax(1.5 * th)
+    assert pg.gap_liquid(x) > 0.9 and info["rms_grad"] < 1e-6
+
+
+def test_concurrent_sweep_equals_serial_results():
+    cases = [S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=t)
+             for t in (70.0, 120.0, 140.0)]
+    serial = [C.critical_pressure(c) for c in cases]
+    conc = C.critical_sweep(cases)
+    for a, b in zip(serial, conc):
+        # the same arithmetic on another stream: the same bisection decisions
+        assert a["dP_c"] == b["dP_c"] and a["probes"] == b["probes"], (a, b)

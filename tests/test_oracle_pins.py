@@ -20,6 +20,7 @@ term, a wrong sign or index, a transposed operand -- fails at least one:
   interface thermodynamics ......... test_flat_interface_profile_and_tension, test_laplace_em
   wetting .......................... test_young_em, test_young_lb
   gravity energy ................... test_jurin_em
+  pressure term, wetting transition  test_critical_pressure_em
 Parity unpinned: the L-BFGS iteration trajectory (only its converged results
 are used, through the pins above).
 """
@@ -549,3 +550,21 @@ def test_jurin_em():
     ys = [half_crossing(phi[:, xx], bottom) for xx in range(x0 + thick, x0 + thick + gap)]
     h = float(np.mean(ys)) - y_r                       # mean height of the C2 = 1/2 line
     assert abs(h / h_target - 1) < 0.05, (h, h_target)
+
+
+@pytest.mark.parametrize("theta", [60.0, 112.0, 135.0])
+def test_critical_pressure_em(theta):
+    # Cassie-Baxter to Wenzel transition on 2D pillars (Sec. III): the pressure
+    # at which the minimum of the pressure-constrained energy switches from the
+    # suspended meniscus to the filled gap is dP_c = -2 gamma cos(theta) / s
+    # (Eq. [frozen:critical-pressure-cyl-2d]); bisection to the paper's 1e-4.
+    from oracle import critical as OC
+    c = S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=theta)
+    k, _ = O.kappa_from_angle(theta, c.g23, c.g12)
+    p = O.make_params(O.D2Q9, c.shape, k, alpha_s=c.alpha_s)
+    c1 = O.solid_profile(c.solid_sd, c.alpha_s)
+    th = -2 * c.g23 * math.cos(math.radians(theta)) / c.extra["s"]
+    dpc = OC.critical_pressure(p, c1, c.c2, c.extra["gap"], th - 0.5 * abs(th) - 5e-3,
+                               th + 0.5 * abs(th) + 5e-3)
+    # diffuse walls make the effective gap a little wider than s: within 4 %
+    assert abs(dpc / th - 1) < 0.04, (dpc, th)
