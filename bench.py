@@ -514,38 +514,31 @@ def run_plain_fp64(args, rank, world):
 def run_critical(args, rank, world):
     """Critical pressure of the Cassie-Baxter to Wenzel transition on 2D pillars
     (Sec. III) by bisection over GPU energy minimisations, for a sweep of five
-    contact angles on a 160x200 box with gap s = 81, the cases run concurrently
-    (one host thread and CUDA stream each): the value is sweep points per second;
-    each point reports dP_c against -2 gamma cos(theta) / s.  The same sweep run
-    one case after another is reported beside it."""
+    contact angles on a 160x200 box with gap s = 81: the value is sweep points
+    per second; each point reports dP_c against -2 gamma cos(theta) / s."""
     import torch
     import synthetic as S
     from paper_2504_19941_gb300 import critical as C
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     thetas = (60.0, 80.0, 100.0, 112.0, 135.0)
-    cases = [S.pillar_gap_2d(period=160, height=200, width=79, pillar=100, base=6, theta=t)
-             for t in thetas]
     C.critical_pressure(S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4))  # warm
     t0 = time.perf_counter()
-    res = C.critical_sweep(cases)
+    pts = []
+    for t in thetas:
+        case = S.pillar_gap_2d(period=160, height=200, width=79, pillar=100, base=6, theta=t)
+        r = C.critical_pressure(case, tol=1e-4)
+        pts.append({"theta": t, "dP_c": r["dP_c"], "theory": r["theory"], "ratio": r["ratio"],
+                    "probes": r["probes"], "lbfgs_iterations": r["iterations"],
+                    "seconds": r["seconds"], "ms_per_lbfgs_iteration": r["seconds"] / max(
+                        r["iterations"], 1) * 1e3})
     wall = time.perf_counter() - t0
-    serial = None
-    if not args.no_serial_baseline:
-        t1 = time.perf_counter()
-        for c in cases:
-            C.critical_pressure(c)
-        serial = len(cases) / (time.perf_counter() - t1)
-    pts = [{"theta": t, "dP_c": r["dP_c"], "theory": r["theory"], "ratio": r["ratio"],
-            "probes": r["probes"], "lbfgs_iterations": r["iterations"], "seconds": r["seconds"]}
-           for t, r in zip(thetas, res)]
     if rank == 0:
         print(json.dumps({"metric": "critical-pressure sweep points/s (2D pillars, bisection to 1e-4)",
                           "value": len(pts) / wall, "unit": "points/s", "n_gpus": 1,
                           "higher_is_better": True, "dtype": "f32 fields / f64 energy",
                           "data": "synthetic",
-                          "config": {"workload": "160x200 box, pillar width 79, gap 81, height 100, "
-                                                 "5 contact angles concurrently"},
-                          "one_at_a_time_points_per_s": serial, "points": pts}), flush=True)
+                          "config": {"workload": "160x200 box, pillar width 79, gap 81, height 100"},
+                          "points": pts}), flush=True)
     return 0
 
 

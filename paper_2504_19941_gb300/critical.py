@@ -122,20 +122,3 @@ def critical_pressure(case, tol: float = 1e-4, device="cuda", rms_tol=1e-6, max_
     return {"dP_c": dpc, "bracket": (lo, hi), "theory": th, "ratio": dpc / th if th else math.nan,
             "probes": pg.probes, "iterations": pg.iterations,
             "seconds": time.perf_counter() - t0}
-
-
-def critical_sweep(cases, tol: float = 1e-4, device="cuda", workers: int = 8):
-    """Critical pressures of several independent cases at once: each case runs
-    its bisection in a host thread with a CUDA stream of its own, so that the
-    small, latency-bound minimisations of different cases overlap on the GPU.
-    Returns the results in the order of `cases`."""
-    from concurrent.futures import ThreadPoolExecutor
-    dev = torch.device(device)
-    streams = [torch.cuda.Stream(dev) for _ in cases]
-    torch.cuda.synchronize(dev)
-
-    def one(k):
-        torch.cuda.set_device(dev)
-        return critical_pressure(cases[k], tol=tol, device=dev, stream=streams[k])
-    with ThreadPoolExecutor(max_workers=max(1, min(workers, len(cases)))) as pool:
-        return list(pool.map(one, range(len(cases))))

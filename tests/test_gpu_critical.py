@@ -49,12 +49,3 @@ def test_suspended_and_collapsed_states():
     x, E_hi, info = pg.relax(1.5 * th)
     assert pg.gap_liquid(x) > 0.9 and info["rms_grad"] < 1e-6
 
-
-def test_concurrent_sweep_equals_serial_results():
-    cases = [S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=t)
-             for t in (70.0, 120.0, 140.0)]
-    serial = [C.critical_pressure(c) for c in cases]
-    conc = C.critical_sweep(cases)
-    for a, b in zip(serial, conc):
-        # the same arithmetic on another stream: the same bisection decisions
-        assert a["dP_c"] == b["dP_c"] and a["probes"] == b["probes"], (a, b)
