@@ -276,6 +276,25 @@ dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float
                                const float *d_g, float *d_r, double *d_alpha,
                                void *d_scratch, size_t scratch_bytes, void *cuda_stream);
 
+/* Batched vector kernels for the compact form of the L-BFGS matrix (Byrd,
+ * Nocedal & Schnabel 1994: H = gamma I + [S gamma Y] M [S^T; gamma Y^T], the
+ * same matrix as the two-loop recursion over the same pairs), which needs the
+ * history only through two batched passes per iteration.
+ * dsm_vec_dots: d_out[k] = V_k . x for k < nv, V_k = d_V + k * stride (FP32
+ *   vectors of n elements), results as device doubles, each equal bitwise to a
+ *   dsm_vec_dot of the same two vectors.  d_scratch >= dsm_vec_dots_scratch_bytes(n, nv).
+ * dsm_vec_lincomb: y = cx x + sum_k coef[k] V_k (coef: host array of nv
+ *   doubles, 0 <= nv <= 64, applied in FP32); y must not overlap x or any V_k.
+ * Both asynchronous on the stream; DSM_E_INVAL for negative sizes, nv out of
+ * range or a missing pointer. */
+dsm_status dsm_vec_dots_scratch_bytes(long long n, int nv, size_t *bytes);
+dsm_status dsm_vec_dots(long long n, int nv, const float *d_V, long long stride,
+                        const float *d_x, double *d_out, void *d_scratch, size_t scratch_bytes,
+                        void *cuda_stream);
+dsm_status dsm_vec_lincomb(long long n, int nv, const float *d_V, long long stride,
+                           const double *coef, const float *d_x, double cx, float *d_y,
+                           void *cuda_stream);
+
 /* Batched step: advance handle i by nsteps[i] stage-2 steps, all handles in
  * ONE persistent cooperative launch.  Resident blocks walk a work list of
  * (lattice, 32-node-wide brick) pairs of every lattice: per step a moments

@@ -28,7 +28,8 @@ EXPORTED = (
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
-    "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_batch_scratch_bytes", "dsm_batch_step",
+    "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_vec_dots_scratch_bytes", "dsm_vec_dots",
+    "dsm_vec_lincomb", "dsm_batch_scratch_bytes", "dsm_batch_step",
     "dsm_destroy",
 )
 
@@ -101,6 +102,11 @@ def load():
         "dsm_vec_axpby": (st, [C.c_longlong, C.c_double, fp, C.c_double, fp, vp]),
         "dsm_lbfgs_direction": (st, [C.c_longlong, C.c_int, C.POINTER(C.c_int), fp, fp, vp, vp, fp,
                                      fp, vp, vp, C.c_size_t, vp]),
+        "dsm_vec_dots_scratch_bytes": (st, [C.c_longlong, C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_vec_dots": (st, [C.c_longlong, C.c_int, fp, C.c_longlong, fp, vp, vp, C.c_size_t,
+                              vp]),
+        "dsm_vec_lincomb": (st, [C.c_longlong, C.c_int, fp, C.c_longlong, dp, fp, C.c_double, fp,
+                                 vp]),
         "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
         "dsm_destroy": (st, [vp]),
@@ -294,6 +300,24 @@ def dsm_lbfgs_direction(n: int, order, S, Y, rho, gamma, g, r, alpha, scratch, s
     _check(load().dsm_lbfgs_direction(n, m, arr, _ptr(S), _ptr(Y), _ptr(rho), _ptr(gamma),
                                       _ptr(g), _ptr(r), _ptr(alpha), _ptr(scratch), scratch_bytes,
                                       _stream(stream)), "dsm_lbfgs_direction")
+
+
+def dsm_vec_dots_scratch_bytes(n: int, nv: int) -> int:
+    b = C.c_size_t()
+    _check(load().dsm_vec_dots_scratch_bytes(n, nv, C.byref(b)), "dsm_vec_dots_scratch_bytes")
+    return b.value
+
+
+def dsm_vec_dots(n: int, nv: int, V, stride: int, x, out, scratch, scratch_bytes: int,
+                 stream=None):
+    _check(load().dsm_vec_dots(n, nv, _ptr(V), stride, _ptr(x), _ptr(out), _ptr(scratch),
+                               scratch_bytes, _stream(stream)), "dsm_vec_dots")
+
+
+def dsm_vec_lincomb(n: int, nv: int, V, stride: int, coef, x, cx: float, y, stream=None):
+    arr = (C.c_double * max(nv, 1))(*[float(v) for v in coef[:nv]])
+    _check(load().dsm_vec_lincomb(n, nv, _ptr(V), stride, arr, _ptr(x), float(cx), _ptr(y),
+                                  _stream(stream)), "dsm_vec_lincomb")
 
 
 def dsm_batch_scratch_bytes(handles) -> int:

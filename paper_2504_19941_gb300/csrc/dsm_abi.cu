@@ -691,6 +691,32 @@ dsm_status dsm_lbfgs_direction(long long n, int m, const int *order, const float
                                      d_scratch, (cudaStream_t)cuda_stream));
 }
 
+dsm_status dsm_vec_dots_scratch_bytes(long long n, int nv, size_t *bytes) {
+  if (!bytes || n < 0 || nv < 0) return DSM_E_INVAL;
+  *bytes = vec_dots_scratch_bytes(n, nv);
+  return DSM_OK;
+}
+
+dsm_status dsm_vec_dots(long long n, int nv, const float *d_V, long long stride,
+                        const float *d_x, double *d_out, void *d_scratch, size_t scratch_bytes,
+                        void *cuda_stream) {
+  if (n < 0 || nv < 0 || stride < 0 || (nv > 0 && (!d_V || !d_x || !d_out || !d_scratch)))
+    return DSM_E_INVAL;
+  if (nv > 1 && stride < n) return DSM_E_INVAL;
+  if (scratch_bytes < vec_dots_scratch_bytes(n, nv)) return DSM_E_WORKSPACE;
+  return cuda_status(vec_dots(n, nv, d_V, stride, d_x, d_out, d_scratch, (cudaStream_t)cuda_stream));
+}
+
+dsm_status dsm_vec_lincomb(long long n, int nv, const float *d_V, long long stride,
+                           const double *coef, const float *d_x, double cx, float *d_y,
+                           void *cuda_stream) {
+  if (n < 0 || nv < 0 || nv > LINCOMB_MAX || stride < 0 || !d_x || !d_y ||
+      (nv > 0 && (!d_V || !coef)))
+    return DSM_E_INVAL;
+  if (nv > 1 && stride < n) return DSM_E_INVAL;
+  return cuda_status(vec_lincomb(n, nv, d_V, stride, coef, d_x, cx, d_y, (cudaStream_t)cuda_stream));
+}
+
 // Batch admission: common kind, precision, stream and density-contrast flag.
 static dsm_status batch_items(dsm_lattice *const *hs, int n, const long long *nsteps,
                               std::vector<BatchRaw> &items) {

@@ -196,6 +196,47 @@ __global__ void dot_finalize_kernel(const double *partials, int nb, const double
   if (threadIdx.x == 0) out[0] = (scale ? scale[0] : 1.0) * sh[0];
 }
 
+// Batched dot products V_k . x for k < nv (V_k at V + k * stride): one launch,
+// grid (blocks, nv); the same fixed grid-stride order and carried-error sums as
+// dot_kernel, so each result equals a separate vec_dot of the same vectors.
+__global__ void __launch_bounds__(256) dots_kernel(long long n, const float *V, long long stride,
+                                                   const float *x, double *partials) {
+  const float *v = V + blockIdx.y * stride;
+  FF s[1] = {FF{0.0f, 0.0f}};
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    s[0] = ff_add(s[0], two_prod(v[k], x[k]));
+  const int sums[1] = {0};
+  block_reduce_ff<1>(s, sums, partials + (long long)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// one block per dot product: its block partials summed in block order
+__global__ void dots_finalize_kernel(const double *partials, int nb, double *out) {
+  __shared__ double sh[256];
+  const double *p = partials + (long long)blockIdx.x * nb;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// y = cx x + sum_k c_k V_k, coefficients passed by value, the sum in k order
+__global__ void __launch_bounds__(256) lincomb_kernel(long long n, int nv, const float *V,
+                                                      long long stride, LinCoef c,
+                                                      const float *x, float *y) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    float acc = c.cx * x[k];
+    for (int j = 0; j < nv; j++) acc += c.c[j] * V[j * stride + k];
+    y[k] = acc;
+  }
+}
+
 // y += sign * (a[0] - (b ? b[0] : 0)) * x
 __global__ void __launch_bounds__(256) axpy_dev_kernel(long long n, double sign, const double *a,
                                                        const double *b, const float *x, float *y) {
@@ -227,6 +268,29 @@ static int vec_grid(long long n) {
 }
 
 size_t vec_scratch_bytes(long long) { return VEC_BLOCKS * sizeof(double) + 256; }
+
+size_t vec_dots_scratch_bytes(long long n, int nv) {
+  return (size_t)(nv > 0 ? nv : 1) * vec_grid(n) * sizeof(double) + 256;
+}
+
+cudaError_t vec_dots(long long n, int nv, const float *V, long long stride, const float *x,
+                     double *out, void *scratch, cudaStream_t st) {
+  if (nv <= 0) return cudaSuccess;
+  double *partials = (double *)scratch;
+  const int g = vec_grid(n);
+  dots_kernel<<<dim3(g, nv), 256, 0, st>>>(n, V, stride, x, partials);
+  dots_finalize_kernel<<<nv, 256, 0, st>>>(partials, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_lincomb(long long n, int nv, const float *V, long long stride, const double *coef,
+                        const float *x, double cx, float *y, cudaStream_t st) {
+  LinCoef c;
+  c.cx = (float)cx;
+  for (int j = 0; j < LINCOMB_MAX; j++) c.c[j] = j < nv ? (float)coef[j] : 0.0f;
+  lincomb_kernel<<<vec_grid(n), 256, 0, st>>>(n, nv, V, stride, c, x, y);
+  return cudaGetLastError();
+}
 
 cudaError_t vec_dot(long long n, const float *x, const float *y, double *out, const double *scale,
                     void *scratch, cudaStream_t st) {

@@ -28,7 +28,18 @@ size_t fe_scratch_bytes(int kind, int nx, int ny, int nz);
 cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, double *energy,
                       double *terms, void *scratch, cudaStream_t st);
 
+constexpr int LINCOMB_MAX = 64;  // most vectors one dsm_vec_lincomb combines
+struct LinCoef {
+  float cx;
+  float c[LINCOMB_MAX];
+};
+
 size_t vec_scratch_bytes(long long n);
+size_t vec_dots_scratch_bytes(long long n, int nv);
+cudaError_t vec_dots(long long n, int nv, const float *V, long long stride, const float *x,
+                     double *out, void *scratch, cudaStream_t st);
+cudaError_t vec_lincomb(long long n, int nv, const float *V, long long stride, const double *coef,
+                        const float *x, double cx, float *y, cudaStream_t st);
 cudaError_t vec_dot(long long n, const float *x, const float *y, double *out, const double *scale,
                     void *scratch, cudaStream_t st);
 cudaError_t vec_axpy_dev(long long n, double sign, const double *a, const double *b,

@@ -92,10 +92,35 @@ class _Vec:
         _lib.dsm_vec_axpby(self.n, a, x, b, y, self.stream)
 
 
+def compact_direction(SY, YY, a, b, gamma):
+    """Coefficients of d = -H g for the L-BFGS inverse Hessian in its compact
+    form (Byrd, Nocedal & Schnabel 1994, Theorem 2.2), the same matrix the
+    two-loop recursion applies:
+      H = gamma I + [S  gamma Y] [[R^-T (D + gamma Y^T Y) R^-1, -R^-T], [-R^-1, 0]] [S^T; gamma Y^T]
+    with R the upper triangle of S^T Y (pairs oldest first) and D its diagonal.
+    SY[i, j] = s_i.y_j, YY[i, j] = y_i.y_j, a = S^T g, b = Y^T g (host float64).
+    Solving R w = a and R^T u = (D + gamma Y^T Y) w - gamma b gives
+    H g = gamma g + S u - gamma Y w, so d = cx g + sum cs_i s_i + sum cy_i y_i with
+    (cx, cs, cy) = (-gamma, -u, gamma w)."""
+    import numpy as np
+    R = np.triu(SY)
+    w = np.linalg.solve(R, a)
+    z = (np.diag(np.diag(SY)) + gamma * YY) @ w - gamma * b
+    u = np.linalg.solve(R.T, z)
+    return -gamma, -u, gamma * w
+
+
 def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0=0.0, fg=0.0,
           m=10, tol=1e-6, max_iter=10000, callback=None):
     """Minimise E over the active field from x0 (FP32 device vector, not
-    modified).  Stops when sqrt(mean(grad^2)) < tol.  Returns (x, E, info)."""
+    modified).  Stops when sqrt(mean(grad^2)) < tol.  Returns (x, E, info).
+
+    The direction uses the compact form of the L-BFGS matrix
+    (compact_direction): per iteration one batched pass of dot products over the
+    stored pairs and one linear combination, instead of the 2m dependent dot and
+    axpy passes of the two-loop recursion.  The small m x m solves run on the
+    host, which reads the dot products once per iteration."""
+    import numpy as np
     n = x0.numel()
     dev = x0.device
     V = _Vec(n, dev, fe.stream)
@@ -105,14 +130,17 @@ def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0
     g = torch.empty(n, **f32)
     gt = torch.empty(n, **f32)
     d = torch.empty(n, **f32)
-    S = torch.empty(m * n, **f32)
-    Y = torch.empty(m * n, **f32)
-    rho = torch.zeros(m, dtype=torch.float64, device=dev)
-    gamma = torch.ones(1, dtype=torch.float64, device=dev)
-    alpha = torch.zeros(m, dtype=torch.float64, device=dev)
+    hist = torch.zeros(2 * m * n, **f32)        # slots: s_0..s_{m-1}, y_0..y_{m-1}
+    dots = torch.zeros(4 * m, dtype=torch.float64, device=dev)
+    dsb = _lib.dsm_vec_dots_scratch_bytes(n, 2 * m)
+    dscratch = torch.empty(dsb, dtype=torch.uint8, device=dev)
     E = torch.empty(1, dtype=torch.float64, device=dev)
     Et = torch.empty(1, dtype=torch.float64, device=dev)
     kw = dict(active=active, mask=mask, dP=dP, kcs=kcs, V0=V0, fg=fg)
+    SY = np.zeros((m, m))   # SY[i, j] = s_i . y_j by slot (j's column set when y_j is stored)
+    YY = np.zeros((m, m))
+    Ag = np.zeros(m)        # s_i . g and y_i . g for the current g, by slot
+    Bg = np.zeros(m)
 
     def evaluate(point, e_out, g_out):
         c1, c2 = (other, point) if active == 2 else (point, other)
@@ -121,27 +149,37 @@ def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0
     def host(*ts):
         return [float(v) for v in torch.cat([t.reshape(-1) for t in ts]).cpu()]
 
+    def slot_s(k):
+        return hist[k * n:(k + 1) * n]
+
+    def slot_y(k):
+        return hist[(m + k) * n:(m + k + 1) * n]
+
     evaluate(x, E, g)
     f_val, gg = host(E, V.dot(g, g))
-    order = []   # ring slots, oldest first
+    order = []   # slots of the stored pairs, oldest first
     nxt = 0
+    gamma = 1.0
     it = evals = 0
+    coef = np.zeros(2 * m)
     while it < max_iter:
         rms = math.sqrt(gg / n)
         if rms < tol:
             break
-        # search direction d = -H g
-        if not order:
-            gamma.fill_(1.0 / max(math.sqrt(gg), 1e-300))
-        _lib.dsm_lbfgs_direction(n, order, S, Y, rho, gamma, g, d, alpha, V.scratch, V.sb,
-                                 fe.stream)
-        (dg0,) = host(V.dot(d, g))
-        if not dg0 < 0.0:  # not a descent direction: restart from steepest descent
+        if order:
+            ix = np.array(order)
+            cx, cs, cy = compact_direction(SY[np.ix_(ix, ix)], YY[np.ix_(ix, ix)], Ag[ix], Bg[ix],
+                                           gamma)
+            coef[:] = 0.0
+            coef[ix] = cs
+            coef[m + ix] = cy
+            dg0 = cx * gg + float(cs @ Ag[ix]) + float(cy @ Bg[ix])
+        if not order or not dg0 < 0.0:  # no pairs, or not a descent direction
             order = []
-            gamma.fill_(1.0 / max(math.sqrt(gg), 1e-300))
-            _lib.dsm_lbfgs_direction(n, [], S, Y, rho, gamma, g, d, alpha, V.scratch, V.sb,
-                                     fe.stream)
-            (dg0,) = host(V.dot(d, g))
+            cx = -1.0 / max(math.sqrt(gg), 1e-300)
+            coef[:] = 0.0
+            dg0 = cx * gg
+        _lib.dsm_vec_lincomb(n, 2 * m if order else 0, hist, n, coef, g, cx, d, fe.stream)
         step, trials, ft, dgt = _wolfe(lambda a: _trial(a, x, d, xt, Et, gt, evaluate, V, host),
                                        f_val, dg0)
         evals += trials
@@ -150,35 +188,37 @@ def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0
                 order = []
                 continue
             break
-        # the accepted trial point is in (xt, gt, Et) only if it was the last
-        # evaluated; re-evaluate at the accepted step otherwise
         if ft is None:
             _trial(step, x, d, xt, Et, gt, evaluate, V, host)
             evals += 1
-            ft, dgt = host(Et, V.dot(gt, d))
-        s_slot = S[nxt * n:(nxt + 1) * n]
-        y_slot = Y[nxt * n:(nxt + 1) * n]
-        V.axpby(step, d, 0.0, s_slot)           # s = step d
-        V.axpby(1.0, gt, 0.0, y_slot)           # y = g_new - g
-        V.axpby(-1.0, g, 1.0, y_slot)
-        V.dot(s_slot, y_slot, 1)
-        V.dot(y_slot, y_slot, 2)
-        V.dot(s_slot, s_slot, 3)
-        sy, yy, ss = host(V.out[1:4])
+            (ft,) = host(Et)
+        # the new pair s = step d, y = g_new - g into slot nxt
+        if nxt in order:  # the ring is full: the oldest pair leaves
+            order.remove(nxt)
+        V.axpby(step, d, 0.0, slot_s(nxt))
+        V.axpby(1.0, gt, 0.0, slot_y(nxt))
+        V.axpby(-1.0, g, 1.0, slot_y(nxt))
+        # one batched pass each: every stored s, y against y_new and against g_new
+        _lib.dsm_vec_dots(n, 2 * m, hist, n, slot_y(nxt), dots[0:2 * m], dscratch, dsb, fe.stream)
+        _lib.dsm_vec_dots(n, 2 * m, hist, n, gt, dots[2 * m:4 * m], dscratch, dsb, fe.stream)
+        V.dot(slot_s(nxt), slot_s(nxt), 1)
+        V.dot(gt, gt, 2)
+        hv = host(dots, V.out[1:3])
+        ss, gg = hv[4 * m], hv[4 * m + 1]
+        sy, yy = hv[nxt], hv[m + nxt]
+        Ag[:] = hv[2 * m:3 * m]
+        Bg[:] = hv[3 * m:4 * m]
         if sy > 1e-12 * math.sqrt(ss * yy):
-            rho[nxt:nxt + 1].fill_(1.0 / sy)
-            gamma.fill_(sy / yy)
-            if nxt in order:
-                order.remove(nxt)
+            SY[:, nxt] = hv[0:m]          # s_i . y_new
+            YY[:, nxt] = hv[m:2 * m]      # y_i . y_new
+            YY[nxt, :] = hv[m:2 * m]
+            gamma = sy / yy
             order.append(nxt)
-            if len(order) > m:
-                order.pop(0)
             nxt = (nxt + 1) % m
         x, xt = xt, x
         g, gt = gt, g
         E, Et = Et, E
         f_val = ft
-        (gg,) = host(V.dot(g, g))
         it += 1
         if callback is not None:
             callback(it, x, f_val, math.sqrt(gg / n))

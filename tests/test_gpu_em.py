@@ -125,6 +125,34 @@ def test_vector_kernels():
     np.testing.assert_allclose(z.cpu().numpy(), y - 1.25 * x, rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("n,nv", [(1_000_003, 20), (4097, 7), (33, 1)])
+def test_batched_dots_and_lincomb(n, nv):
+    rng = np.random.default_rng(nv)
+    V = rng.normal(size=(nv, n)).astype(np.float32)
+    x = rng.normal(size=n).astype(np.float32)
+    Vd, xd = _t(V.ravel()), _t(x)
+    sb = _lib.dsm_vec_dots_scratch_bytes(n, nv)
+    sc = torch.empty(sb, dtype=torch.uint8, device=DEV)
+    out = torch.zeros(nv, dtype=torch.float64, device=DEV)
+    _lib.dsm_vec_dots(n, nv, Vd, n, xd, out, sc, sb)
+    ref = V.astype(np.float64) @ x.astype(np.float64)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # each equals the single dot of the same vectors bitwise
+    sb1 = _lib.dsm_vec_scratch_bytes(n)
+    sc1 = torch.empty(sb1, dtype=torch.uint8, device=DEV)
+    one = torch.zeros(1, dtype=torch.float64, device=DEV)
+    for k in (0, nv - 1):
+        _lib.dsm_vec_dot(n, Vd[k * n:(k + 1) * n], xd, one, sc1, sb1)
+        assert one.item() == out[k].item()
+    coef = rng.normal(size=nv)
+    y = torch.empty(n, dtype=torch.float32, device=DEV)
+    _lib.dsm_vec_lincomb(n, nv, Vd, n, coef, xd, -0.75, y)
+    ref = -0.75 * x.astype(np.float64) + coef @ V.astype(np.float64)
+    np.testing.assert_allclose(y.cpu().numpy(), ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+    with pytest.raises(P.DSMError):
+        _lib.dsm_vec_lincomb(n, 65, Vd, n, np.zeros(65), xd, 1.0, y)
+
+
 def test_two_loop_recursion_matches_dense_inverse_hessian():
     # with m pairs from a quadratic, the two-loop product equals the textbook
     # recursion H_{k+1} = (I - rho s y^T) H_k (I - rho y s^T) + rho s s^T
