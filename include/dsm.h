@@ -295,6 +295,39 @@ dsm_status dsm_vec_lincomb(long long n, int nv, const float *d_V, long long stri
                            const double *coef, const float *d_x, double cx, float *d_y,
                            void *cuda_stream);
 
+/* The energy minimiser, native: L-BFGS over the active field (C2 for active = 2,
+ * C1 for active = 1, the other field fixed in d_fixed) of the free energy of
+ * dsm_fe_energy_grad with the same constraint arguments, from the start point
+ * in d_x (FP32, nx*ny*nz, overwritten with the final point), until the rms
+ * gradient sqrt(sum g^2 / N) < tol or max_iter iterations.  Sec. II.A cites
+ * L-BFGS (Nocedal 1980; Liu & Nocedal 1989) with an rms-gradient stop; the
+ * rest is this library's reading: m stored pairs (1 <= m <= 32), initial
+ * matrix (s.y / y.y) I, pairs with s.y <= 1e-12 |s||y| dropped, a strong-Wolfe
+ * line search (c1 = 1e-4, c2 = 0.9, cubic interpolation, at most 20 trials)
+ * whose decrease test takes its derivative form when the energy change is
+ * below 1e-6 |E| (FP32 noise), steepest descent after a non-descent direction,
+ * and the direction from the compact form of the L-BFGS matrix (Byrd, Nocedal
+ * & Schnabel 1994).  d_work: caller-owned device memory of at least
+ * dsm_lbfgs_workspace_bytes(p, m), 256-byte aligned.  Runs on the stream and
+ * returns when done (host reads each iteration).  DSM_E_NONFINITE if the energy
+ * or gradient turns non-finite.  dsm_lbfgs_compact is the host-only
+ * compact-form solve, exposed for tests: for k pairs (oldest first),
+ * SY[i*k+j] = s_i.y_j, YY[i*k+j] = y_i.y_j, a = S^T g, b = Y^T g, it returns the
+ * coefficients of -H g = cx g + sum cs_i s_i + sum cy_i y_i. */
+typedef struct dsm_lbfgs_info {
+  long long iterations, evaluations;
+  double energy, rms_grad;
+  int converged;  /* 1 if the rms gradient fell below tol */
+} dsm_lbfgs_info;
+dsm_status dsm_lbfgs_workspace_bytes(const dsm_params *p, int m, size_t *bytes);
+dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
+                              const unsigned char *d_mask, int active, double dP, double kcs,
+                              double V0, double fg, float *d_x, int m, double tol,
+                              long long max_iter, void *d_work, size_t work_bytes,
+                              dsm_lbfgs_info *info, void *cuda_stream);
+dsm_status dsm_lbfgs_compact(int k, const double *SY, const double *YY, const double *a,
+                             const double *b, double gamma, double *cx, double *cs, double *cy);
+
 /* Batched step: advance handle i by nsteps[i] stage-2 steps, all handles in
  * ONE persistent cooperative launch.  Resident blocks walk a work list of
  * (lattice, 32-node-wide brick) pairs of every lattice: per step a moments

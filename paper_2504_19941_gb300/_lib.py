@@ -29,7 +29,8 @@ EXPORTED = (
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
     "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_vec_dots_scratch_bytes", "dsm_vec_dots",
-    "dsm_vec_lincomb", "dsm_batch_scratch_bytes", "dsm_batch_step",
+    "dsm_vec_lincomb", "dsm_lbfgs_workspace_bytes", "dsm_lbfgs_minimize", "dsm_lbfgs_compact",
+    "dsm_batch_scratch_bytes", "dsm_batch_step",
     "dsm_destroy",
 )
 
@@ -48,6 +49,11 @@ class dsm_params(C.Structure):
                 ("rho3", C.c_double), ("tau2", C.c_double), ("tau3", C.c_double),
                 ("tau_g", C.c_double), ("body_force", C.c_double * 3), ("beta", C.c_double),
                 ("omega", C.c_double)]
+
+
+class dsm_lbfgs_info(C.Structure):
+    _fields_ = [("iterations", C.c_longlong), ("evaluations", C.c_longlong),
+                ("energy", C.c_double), ("rms_grad", C.c_double), ("converged", C.c_int)]
 
 
 class dsm_observables(C.Structure):
@@ -107,6 +113,11 @@ def load():
                               vp]),
         "dsm_vec_lincomb": (st, [C.c_longlong, C.c_int, fp, C.c_longlong, dp, fp, C.c_double, fp,
                                  vp]),
+        "dsm_lbfgs_workspace_bytes": (st, [P, C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_lbfgs_minimize": (st, [P, fp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, fp, C.c_int, C.c_double, C.c_longlong, vp,
+                                    C.c_size_t, C.POINTER(dsm_lbfgs_info), vp]),
+        "dsm_lbfgs_compact": (st, [C.c_int, dp, dp, dp, dp, C.c_double, dp, dp, dp]),
         "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
         "dsm_destroy": (st, [vp]),
@@ -318,6 +329,38 @@ def dsm_vec_lincomb(n: int, nv: int, V, stride: int, coef, x, cx: float, y, stre
     arr = (C.c_double * max(nv, 1))(*[float(v) for v in coef[:nv]])
     _check(load().dsm_vec_lincomb(n, nv, _ptr(V), stride, arr, _ptr(x), float(cx), _ptr(y),
                                   _stream(stream)), "dsm_vec_lincomb")
+
+
+def dsm_lbfgs_workspace_bytes(params: dsm_params, m: int) -> int:
+    b = C.c_size_t()
+    _check(load().dsm_lbfgs_workspace_bytes(C.byref(params), m, C.byref(b)),
+           "dsm_lbfgs_workspace_bytes")
+    return b.value
+
+
+def dsm_lbfgs_minimize(params: dsm_params, fixed, mask, active: int, dP: float, kcs: float,
+                       V0: float, fg: float, x, m: int, tol: float, max_iter: int, work,
+                       work_bytes: int, stream=None, check=True) -> dict:
+    info = dsm_lbfgs_info()
+    s = load().dsm_lbfgs_minimize(C.byref(params), _ptr(fixed), _ptr(mask), active, dP, kcs, V0,
+                                  fg, _ptr(x), m, tol, max_iter, _ptr(work), work_bytes,
+                                  C.byref(info), _stream(stream))
+    if check:
+        _check(s, "dsm_lbfgs_minimize")
+    return dict(iterations=info.iterations, evaluations=info.evaluations, energy=info.energy,
+                rms_grad=info.rms_grad, converged=bool(info.converged), status=s)
+
+
+def dsm_lbfgs_compact(SY, YY, a, b, gamma: float):
+    """Host-only compact-form solve: (cx, cs, cy) of -H g (see the header)."""
+    import numpy as np
+    k = len(a)
+    arr = lambda v: (C.c_double * max(len(v), 1))(*[float(t) for t in v])  # noqa: E731
+    cx = C.c_double()
+    cs, cy = (C.c_double * k)(), (C.c_double * k)()
+    _check(load().dsm_lbfgs_compact(k, arr(np.ravel(SY)), arr(np.ravel(YY)), arr(a), arr(b),
+                                    float(gamma), C.byref(cx), cs, cy), "dsm_lbfgs_compact")
+    return cx.value, np.array(cs[:]), np.array(cy[:])
 
 
 def dsm_batch_scratch_bytes(handles) -> int:
