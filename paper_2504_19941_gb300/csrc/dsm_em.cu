@@ -30,9 +30,26 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a, int gx, int gy, int n
 #pragma unroll
   for (int k = 0; k < FE_K; k++) acc[k] = FF{0.0f, 0.0f};
   // resident blocks walk the node bricks (blockDim-shaped boxes) in a fixed
-  // grid-stride order, so each block leaves one partial sum
-  for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
-    const int bx = b % gx, by = (b / gx) % gy, bz = b / (gx * gy);
+  // grid-stride order, so each block leaves one partial sum; the brick
+  // coordinates advance by the stride's own (x, y, z) digits with carries
+  // instead of three divisions per brick
+  const int G = gridDim.x;
+  const int sx = G % gx, sy = (G / gx) % gy, sz = G / (gx * gy);
+  int bx = blockIdx.x % gx, by = (blockIdx.x / gx) % gy, bz = blockIdx.x / (gx * gy);
+  for (int b = blockIdx.x; b < nbricks; b += G) {
+    if (b != blockIdx.x) {
+      bx += sx;
+      by += sy;
+      bz += sz;
+      if (bx >= gx) {
+        bx -= gx;
+        by++;
+      }
+      if (by >= gy) {
+        by -= gy;
+        bz++;
+      }
+    }
     const int x = bx * blockDim.x + threadIdx.x;
     const int y = by * blockDim.y + threadIdx.y;
     const int z = bz * blockDim.z + threadIdx.z;
