@@ -369,7 +369,12 @@ def run_serve(args, rank, world):
     continuous-batching scheduler, against serving the same stream one request
     at a time.  Requests: 50 % D2Q9 (side 64..512), 50 % D3Q19 (side 64..160),
     random pillars / sinusoidal walls / sphere packings, contact angle
-    U[30, 150] degrees, step budgets U[2000, 20000] scaled by --serve-scale."""
+    U[30, 150] degrees, step budgets U[2000, 20000] scaled by --serve-scale.
+    By default 48 requests arrive at once with full step budgets, which
+    saturates the GPU (throughput and the latency of a burst); a rate below
+    capacity (e.g. --serve-rate 1.0) measures latency under load.  Policy: at
+    most --serve-max-large large lattices active together, taken shortest work
+    first (--serve-order sjf)."""
     import torch
     import synthetic as S
     from paper_2504_19941_gb300.serving import GpuExecutor, Scheduler, serial_run, summarize
@@ -385,11 +390,14 @@ def run_serve(args, rank, world):
         r.payload = r.case()
     warm = S.serving_stream(n_req=4, rate=1000.0, seed=99, min_side=32, max_side_2d=96, max_side_3d=48,
                             steps=(20, 40))
-    Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(warm)
+    policy = dict(max_large=args.serve_max_large if args.serve_max_large > 0 else None,
+                  order=args.serve_order)
+    Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum, **policy).run(warm)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        recs = Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum).run(mine)
+        recs = Scheduler(GpuExecutor("f32"), 200 << 30, quantum=args.serve_quantum,
+                         **policy).run(mine)
         wall = time.perf_counter() - t0
     s = summarize(recs, wall)
     base = None
@@ -405,6 +413,7 @@ def run_serve(args, rank, world):
                "data": "synthetic",
                "config": {"workload": f"{args.serve_requests} requests, Poisson {args.serve_rate}/s, "
                                       f"steps x{args.serve_scale}", "quantum": args.serve_quantum,
+                          "max_large": policy["max_large"], "order": policy["order"],
                           "parallelism": f"replicas x{world}"},
                "serving": s, "one_at_a_time": base, "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
@@ -617,10 +626,14 @@ def main():
     ap.add_argument("--workload", default="lb",
                     choices=["lb", "serve", "precision", "fp64", "em", "critical"])
     ap.add_argument("--em-iters", type=int, default=3000)
-    ap.add_argument("--serve-requests", type=int, default=96)
-    ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-scale", type=float, default=0.05)
+    # default: a saturating burst (every request at once, full step budgets)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=1000.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0)
     ap.add_argument("--serve-quantum", type=int, default=200)
+    ap.add_argument("--serve-max-large", type=int, default=2,
+                    help="large lattices active at once (0: no cap)")
+    ap.add_argument("--serve-order", default="sjf", choices=["fifo", "sjf"])
     ap.add_argument("--no-serial-baseline", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3, "at least 3 warm-up steps"

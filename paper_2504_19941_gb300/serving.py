@@ -9,6 +9,12 @@ their work overlaps on the device.  Between quanta finished requests retire and
 free their memory, and new arrivals are admitted.  A request's latency is
 finish time minus arrival time.
 
+One large lattice nearly fills the GPU by itself, so advancing every admitted
+large lattice at once only makes them all finish late.  ``max_large`` caps how
+many large lattices are active together (small ones are still admitted
+freely), and ``order="sjf"`` takes waiting large requests shortest work
+(nodes x steps) first.
+
 ``Scheduler`` is host logic only; ``GpuExecutor`` does the device work through
 libdsm.  Tests drive the scheduler with a fake executor on the CPU.
 """
@@ -50,6 +56,7 @@ class Scheduler:
 
     executor interface:
       bytes_needed(req) -> int            workspace bytes (host-side, no device work)
+      is_large(req) -> bool               (optional) counts against max_large
       admit(req) -> handle                 create and initialise the lattice
       advance([(handle, steps)]) -> {handle: error-or-None}
                                            advance every active lattice, wait for it
@@ -58,12 +65,20 @@ class Scheduler:
     """
 
     def __init__(self, executor, budget_bytes: int, quantum: int = 200, clock=time.perf_counter,
-                 sleep=time.sleep):
+                 sleep=time.sleep, max_large=None, order: str = "fifo"):
+        if order not in ("fifo", "sjf"):
+            raise ValueError("order must be 'fifo' or 'sjf'")
         self.ex = executor
         self.budget = int(budget_bytes)
         self.quantum = int(quantum)
         self.clock = clock
         self.sleep = sleep
+        self.max_large = max_large
+        self.order = order
+
+    def _large(self, req) -> bool:
+        f = getattr(self.ex, "is_large", None)
+        return bool(f(req)) if f is not None else False
 
     def run(self, requests):
         pending = deque(sorted(requests, key=lambda r: r.arrival))
@@ -76,25 +91,35 @@ class Scheduler:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            # FIFO admission while the next request fits in the budget
-            while waiting:
-                req = waiting[0]
+            # admission in arrival order (large requests shortest work first
+            # under "sjf") while the next request fits in the budget; a large
+            # request waits for a free large slot without holding up the rest
+            if self.order == "sjf":
+                queue = sorted(waiting, key=lambda r: (1, r.n * r.steps, r.arrival)
+                               if self._large(r) else (0, r.arrival, 0))
+            else:
+                queue = list(waiting)
+            n_large = sum(1 for sl in active if self._large(sl.req))
+            for req in queue:
                 rec = recs[req.rid]
                 try:
                     need = int(self.ex.bytes_needed(req))
                 except Exception as e:  # malformed request: reject, keep serving
-                    waiting.popleft()
+                    waiting.remove(req)
                     rec.status, rec.finished = "rejected", self.clock() - t0
                     rec.result = {"error": str(e)}
                     continue
                 if need > self.budget:
-                    waiting.popleft()
+                    waiting.remove(req)
                     rec.status, rec.finished = "rejected", self.clock() - t0
                     rec.result = {"error": f"needs {need} bytes, budget {self.budget}"}
                     continue
                 if used + need > self.budget:
                     break
-                waiting.popleft()
+                large = self._large(req)
+                if large and self.max_large is not None and n_large >= self.max_large:
+                    continue
+                waiting.remove(req)
                 try:
                     h = self.ex.admit(req)
                 except Exception as e:
@@ -102,6 +127,7 @@ class Scheduler:
                     rec.result = {"error": str(e)}
                     continue
                 used += need
+                n_large += large
                 rec.admitted = self.clock() - t0
                 active.append(_Slot(req, rec, h, need, int(req.steps)))
             if not active:
@@ -198,6 +224,9 @@ class GpuExecutor:
                            g12=case.g12, g23=case.g23, alpha=case.alpha, alpha_s=case.alpha_s,
                            rho2=case.rho2, rho3=case.rho3, tau2=case.tau2, tau3=case.tau3,
                            tau_g=case.tau_g, body=case.body)
+
+    def is_large(self, req) -> bool:
+        return req.n > self.small_nodes
 
     def bytes_needed(self, req):
         from . import _lib, make_params

@@ -1,7 +1,8 @@
 """Host logic of the serving loop, on the CPU with a fake executor and a fake
 clock: admission by HBM budget, FIFO order, rejection of malformed and
 oversized requests, failures injected on the host, quantum accounting,
-latency percentiles."""
+latency percentiles, the cap on concurrent large lattices and shortest-job-first
+order."""
 import math
 from dataclasses import dataclass
 
@@ -35,14 +36,19 @@ class FakeExecutor:
     """Each step of a lattice costs `cost` seconds of fake time; a quantum over
     several lattices costs the sum (one device)."""
 
-    def __init__(self, clock, cost=1e-3, fail=(), nan=()):
+    def __init__(self, clock, cost=1e-3, fail=(), nan=(), large_n=None):
         self.clock = clock
         self.cost = cost
         self.fail = set(fail)      # rids whose advance reports an error
         self.nan = set(nan)        # rids whose finish reports a non-finite state
+        self.large_n = large_n     # requests with n above this count as large
         self.live = {}
         self.steps = {}
         self.peak = 0
+        self.peak_large = 0
+
+    def is_large(self, req):
+        return self.large_n is not None and req.n > self.large_n
 
     def bytes_needed(self, req):
         if req.bad:
@@ -54,6 +60,7 @@ class FakeExecutor:
         self.live[h] = req
         self.steps[req.rid] = 0
         self.peak = max(self.peak, sum(r.nbytes for r in self.live.values()))
+        self.peak_large = max(self.peak_large, sum(self.is_large(r) for r in self.live.values()))
         return h
 
     def advance(self, work):
@@ -75,10 +82,11 @@ class FakeExecutor:
         self.live.pop(h, None)
 
 
-def _run(reqs, budget=1000, quantum=10, **kw):
+def _run(reqs, budget=1000, quantum=10, max_large=None, order="fifo", **kw):
     clk = Clock()
     ex = FakeExecutor(clk, **kw)
-    sch = Scheduler(ex, budget, quantum, clock=clk, sleep=clk.sleep)
+    sch = Scheduler(ex, budget, quantum, clock=clk, sleep=clk.sleep, max_large=max_large,
+                    order=order)
     recs = sch.run(reqs)
     return recs, ex, clk
 
@@ -138,3 +146,29 @@ def test_percentiles():
             for i in range(100)]
     s = summarize(recs, 10.0)
     assert s["p50_s"] == 50.0 and s["p99_s"] == 99.0 and s["solves_per_s"] == 10.0
+
+
+def test_large_cap_lets_small_requests_through():
+    # three large requests (n = 1000) and two small ones, all at once, cap 1:
+    # never two large lattices at a time, and the small ones do not wait
+    reqs = [Req(0, 0.0, 200, 1000), Req(1, 0.0, 200, 1000), Req(2, 0.0, 200, 1000),
+            Req(3, 0.0, 30, 10), Req(4, 0.0, 30, 10)]
+    recs, ex, _ = _run(reqs, budget=10 ** 6, quantum=10, max_large=1, large_n=100)
+    assert all(r.status == "done" for r in recs)
+    assert ex.peak_large == 1
+    assert recs[3].admitted == 0.0 and recs[4].admitted == 0.0
+    fin = [recs[i].finished for i in range(3)]
+    assert fin == sorted(fin)              # FIFO among the large ones
+    assert recs[3].finished < recs[0].finished
+
+
+def test_shortest_job_first_for_large_requests():
+    reqs = [Req(0, 0.0, 300, 1000), Req(1, 0.0, 100, 1000), Req(2, 0.0, 200, 1000)]
+    recs, ex, _ = _run(reqs, budget=10 ** 6, quantum=10, max_large=1, order="sjf", large_n=100)
+    order = sorted(range(3), key=lambda i: recs[i].finished)
+    assert order == [1, 2, 0]
+    # shortest first lowers the mean latency against arrival order
+    fifo, _, _ = _run(reqs, budget=10 ** 6, quantum=10, max_large=1, large_n=100)
+    assert sum(r.latency for r in recs) < sum(r.latency for r in fifo)
+    with pytest.raises(ValueError):
+        Scheduler(ex, 1, order="lifo")
