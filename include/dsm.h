@@ -44,7 +44,7 @@ typedef enum {
   DSM_E_NONFINITE = 4,   /* a NaN/Inf appeared in the populations */
   DSM_E_TIMEOUT = 5,     /* a bounded device wait ran out */
   DSM_E_STATE = 6,       /* call out of order, or handle latched in error */
-  DSM_E_UNSUPPORTED = 7  /* valid request this build does not implement */
+  DSM_E_UNSUPPORTED = 7  /* a valid request the library does not implement */
 } dsm_status;
 
 typedef enum { DSM_D2Q9 = 0, DSM_D3Q19 = 1 } dsm_lattice_kind;
