@@ -157,8 +157,10 @@ def measured_traffic(name="node_kernel_d3q19_f32_geq"):
     return float(rec["bytes_per_launch"])
 
 
-def make_case(shape):
+def make_case(shape, lattice="D3Q19"):
     import synthetic as S
+    if lattice == "D2Q9":
+        return S.pillar_row_2d(*shape, liquid=(38, min(98, shape[1] - 4)))
     if tuple(shape) == SHAPE:
         return S.pillar_slab_3d(*SHAPE)
     nz = shape[2]
@@ -240,13 +242,23 @@ def run_reference(args, rank, world):
     return 0
 
 
-def gpu_config(shape, world, g_storage):
-    return {"workload": WORKLOAD if tuple(shape) == SHAPE else
-            f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)",
-            "lattice": "D3Q19", "nodes": int(shape[0] * shape[1] * shape[2]),
+def gpu_config(shape, world, g_storage, lattice="D3Q19", rho3=1.0, tau3=1.0):
+    nodes = 1
+    for v in shape:
+        nodes *= int(v)
+    if lattice == "D2Q9":
+        name = f"D2Q9 FP32 pillar-row {shape[0]}x{shape[1]}"
+    elif tuple(shape) == SHAPE:
+        name = WORKLOAD
+    else:
+        name = f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)"
+    if rho3 != 1.0 or tau3 != 1.0:
+        name += f", gas density {rho3}, gas tau {tau3} (liquid 1, 1)"
+    return {"workload": name, "lattice": lattice, "nodes": nodes,
             "global_batch": world, "parallelism": f"replicas x{world}",
             "g_storage": g_storage,
-            "l2": "f populations alone 1.9 GB per buffer, larger than L2; no flush"}
+            "l2": f"f populations alone {nodes * (9 if lattice == 'D2Q9' else 19) * 4 / 1e9:.1f} GB "
+                  "per buffer, larger than L2; no flush"}
 
 
 def run_gpu(args, rank, world):
@@ -263,9 +275,12 @@ def run_gpu(args, rank, world):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
     shape = tuple(int(v) for v in args.shape.split(","))
-    case = make_case(shape)
-    params = P.make_params("D3Q19", shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
-                           g23=case.g23, alpha_s=case.alpha_s)
+    lattice = args.lattice
+    if lattice == "D2Q9" and len(shape) != 2:
+        shape = (4096, 4096)
+    case = make_case(shape, lattice)
+    params = P.make_params(lattice, shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
+                           g23=case.g23, alpha_s=case.alpha_s, rho3=args.rho3, tau3=args.tau3)
     lat = P.Lattice(params, device=dev)
     lat.set_g_storage(args.g_storage)
     sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
@@ -285,7 +300,7 @@ def run_gpu(args, rank, world):
         one_step()
     torch.cuda.synchronize()
     g_eq = lat.g_implicit
-    k2_b, k1_b = lu_bytes("D3Q19", "f32", g_eq)
+    k2_b, k1_b = lu_bytes(lattice, "f32", g_eq)
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -336,8 +351,9 @@ def run_gpu(args, rank, world):
 
     peak, peak_kind = _peaks()
     achieved = k2_b * n / t_k2 / 1e9
+    default = shape == SHAPE and lattice == "D3Q19" and args.rho3 == 1.0 and args.tau3 == 1.0
     traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
-               if shape == SHAPE else None)
+               if default else None)
     step_achieved = (k2_b + k1_b) * n / (t_max / args.steps) / 1e9
 
     if rank == 0:
@@ -347,11 +363,13 @@ def run_gpu(args, rank, world):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
                "config": gpu_config(shape, world,
-                                    "g_eq (tau_g = 1): A, u per node" if g_eq else "populations"),
+                                    "g_eq (tau_g = 1): A, u per node" if g_eq else "populations",
+                                    lattice, args.rho3, args.tau3),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic,
-                            "kernel": "node_kernel<D3Q19,f32,stage2,step,%s>" %
-                                      ("g_eq" if g_eq else "populations"),
+                            "kernel": "node_kernel<%s,f32,stage2,step,%s%s>" %
+                                      (lattice, "g_eq" if g_eq else "populations",
+                                       ",density contrast" if args.rho3 != 1.0 else ""),
                             "bytes_per_lu": k2_b, "peak_source": peak_kind,
                             "k2_ms": t_k2 * 1e3, "step_bytes_per_lu": k1_b + k2_b,
                             "step_achieved": step_achieved, "step_frac": step_achieved / peak},
@@ -619,6 +637,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="dsm", choices=["dsm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", default="D3Q19", choices=["D3Q19", "D2Q9"],
+                    help="D2Q9: a 2D pillar row (default 4096x4096 unless --shape has two sizes)")
+    ap.add_argument("--rho3", type=float, default=1.0, help="gas density (liquid 1)")
+    ap.add_argument("--tau3", type=float, default=1.0, help="gas relaxation time (liquid 1)")
     ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],
                     help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),

@@ -402,11 +402,15 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       mu = K_.k2 * bwell(C) + K_.k3 * bwell(c1 + C) - K_.a2k2 * lapC - K_.a2k3 * lapS;
       // density map rho = rho3 + (rho2 - rho3) C2/(C2 + C3), the ratio clamped
       // to [0, 1] and 0 where C2 + C3 = 1 - C1 <= 1e-6 (inside the solid)
+      // (FP32: the volume fraction, clamped to [0, 1] right after, needs no
+      // correctly rounded quotient -- the fast reciprocal-and-multiply division,
+      // within 2 ulp, replaces a full IEEE division at every neighbour)
       auto rho_of = [&](T cc, T s1) -> T {
         const T den = T(1) - s1;
         T ph = T(0);
         if (den > T(1e-6)) {
-          ph = cc / den;
+          if constexpr (sizeof(T) == 4) ph = __fdividef(cc, den);
+          else ph = cc / den;
           ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
         }
         return K_.rho3 + K_.drho * ph;
@@ -681,7 +685,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 }
 
 template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ && !RC ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;

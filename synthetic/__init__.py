@@ -246,6 +246,24 @@ def pillar_slab_3d(nx=256, ny=256, nz=192, seed=0, pitch=32, width=10, height=30
                 extra={"f_max": f_max, "ramp_steps": 10000, "seed": seed})
 
 
+def pillar_row_2d(nx=4096, ny=4096, seed=0, pitch=32, width=10, height=30, base=8,
+                  liquid=(38, 98), theta=None, g=2.5e-3, width_10_90=3.0) -> Case:
+    """The 2D analogue of pillar_slab_3d (D2Q9): base plate y < base, a row of
+    rectangular pillars width x height at the given pitch along x, a liquid layer
+    y in [liquid) on the pillar tops, theta drawn in [90, 150] from the seed when
+    not given, +-1e-3 noise."""
+    rng = np.random.default_rng(seed)
+    if theta is None:
+        theta = float(rng.uniform(90.0, 150.0))
+    shape = (nx, ny)
+    sd = pillars_sd(shape, base, width, pitch, height)
+    a_s = width_to_alpha(width_10_90)
+    c2 = layer_c2(shape, 1, liquid[0], liquid[1], 1.0, sd, a_s).ravel()
+    c2 = c2 + perturbation(seed, c2.size) * fluid_fraction(sd, a_s).ravel()
+    return Case("pillar_row_2d", "D2Q9", shape, sd.ravel(), c2, theta_deg=theta, g23=g, g12=g,
+                alpha_s=a_s)
+
+
 def plates_rise_3d(nx=384, ny=384, nz=256, gap=40, thick=8, theta=45.0, g=1e-2,
                    target_rise=120.0, x0=40, x1=340, reservoir=60, lid=8,
                    steps=50000) -> Case:

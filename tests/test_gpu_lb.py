@@ -143,6 +143,21 @@ def test_density_viscosity_contrast_fp64():
     assert max(errs.values()) < 1e-12, errs
 
 
+@pytest.mark.parametrize("form", ["auto", "populations"])
+def test_density_viscosity_contrast_fp32(form):
+    # FP32 arithmetic (the density map's volume fraction by the fast division)
+    # against the FP64 oracle: the FP32 tolerances of test_d3q19_fp32_parity
+    case = _small_3d(shape=(20, 18, 16), body=(0.0, 0.0, -1e-5))
+    case.rho2, case.rho3, case.tau2, case.tau3 = 1.0, 0.2, 1.0, 0.7
+    lat = gpu_lattice(case, "f32", g_storage=form)
+    p, c1, f, g = _oracle_case(case, O.D3Q19)
+    lat.step(30)
+    f, g = O.lb_run(p, 2, c1, f, g, 30)
+    e = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    assert e["C"] < 1e-5 and e["pt"] < 1e-5 and e["mu"] < 1e-4 and e["rho"] < 1e-5, e
+    assert max(e["ux"], e["uy"], e["uz"]) < 2e-4, e
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (3, 1), (1, 5), (5, 4)])
 def test_tiny_2d_lattices_fp64(shape):
     # degenerate periodic sizes: every neighbour may be the node itself
