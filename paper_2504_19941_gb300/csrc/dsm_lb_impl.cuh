@@ -988,6 +988,41 @@ LBArgs<T, S> typed(const LBRaw &r) {
   return a;
 }
 
+// The same pass for D2Q9, tiled: a 32 x 8 block stages (A, C, u_x, u_y) of its
+// tile and a one-node halo in shared memory once, then each node sums its nine
+// points from there (the per-node arithmetic is moments_eq_node, as above).
+template <class T, class S>
+__global__ void __launch_bounds__(MT_X * MT_Y) moments_eq_tiled2d_kernel(LBArgs<T, S> a) {
+  using L = Lat<0>;
+  constexpr int NH = MT_HX * MT_HY;
+  __shared__ T sA[NH], sC[NH], sU[NH], sV[NH];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + MT_X * ty;
+  const int nx = a.nx, ny = a.ny;
+  const int x0 = blockIdx.x * MT_X, y0 = blockIdx.y * MT_Y;
+  auto wrap = [](int v, int n) { v %= n; return v < 0 ? v + n : v; };
+  for (int k = tid; k < NH; k += MT_X * MT_Y) {
+    const int g = wrap(x0 - 1 + k % MT_HX, nx) + nx * wrap(y0 - 1 + k / MT_HX, ny);
+    sA[k] = __ldg(a.Mp[0] + g);
+    sC[k] = __ldg(a.Cprev + g);
+    sU[k] = __ldg(a.Mp[1] + g);
+    sV[k] = __ldg(a.Mp[2] + g);
+  }
+  __syncthreads();
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= nx || y >= ny) return;
+  T Ay[L::Q], Cy[L::Q], uy[L::Q][3];
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    const int k = (tx + 1 - L::cx(i)) + MT_HX * (ty + 1 - L::cy(i));  // x - c_i
+    Ay[i] = sA[k];
+    Cy[i] = sC[k];
+    uy[i][0] = (i == 0 || L::cx(i)) ? sU[k] : T(0);
+    uy[i][1] = (i == 0 || L::cy(i)) ? sV[k] : T(0);
+    uy[i][2] = T(0);
+  }
+  a.C[x + (long long)nx * y] = moments_eq_node<L, T>(Ay, Cy, uy);
+}
+
 template <class T>
 constexpr size_t moments_eq_smem() {
   return sizeof(T) * 5 * MT_RING * MT_HX * MT_HY;
@@ -1016,6 +1051,9 @@ struct LBOps {
       moments_eq_tiled_kernel<T, S><<<dim3((r.nx + MT_X - 1) / MT_X, (r.ny + MT_Y - 1) / MT_Y,
                                            (r.nz + zrun - 1) / zrun),
                                       dim3(MT_X, MT_Y, 1), moments_eq_smem<T>(), st>>>(typed<T, S>(r), zrun);
+    } else if (r.implicit && K == 0 && (long long)r.nx * r.ny >= 2ll * 152 * 256) {
+      moments_eq_tiled2d_kernel<T, S><<<dim3((r.nx + MT_X - 1) / MT_X, (r.ny + MT_Y - 1) / MT_Y),
+                                        dim3(MT_X, MT_Y, 1), 0, st>>>(typed<T, S>(r));
     } else if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     else moments_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();

@@ -158,6 +158,21 @@ def test_density_viscosity_contrast_fp32(form):
     assert max(e["ux"], e["uy"], e["uz"]) < 2e-4, e
 
 
+@pytest.mark.parametrize("prec,tol,tol_mu", [("f64", 1e-12, 1e-12), ("f32", 1e-5, 1e-4)])
+def test_d2q9_tiled_moments_parity(prec, tol, tol_mu):
+    # a 2D lattice large enough (>= 2 x 152 x 256 nodes) for the tiled D2Q9
+    # moments pass of the g_eq form, ragged against its 32 x 8 tiles
+    case = S.pillar_row_2d(333, 250, pitch=40, width=12, height=20, base=6, liquid=(30, 90),
+                           theta=110.0, g=0.01)
+    lat = gpu_lattice(case, prec)
+    p, c1, f, g = _oracle_case(case, O.D2Q9)
+    lat.step(12)
+    assert lat.g_implicit
+    f, g = O.lb_run(p, 2, c1, f, g, 12)
+    e = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g), ("C", "mu", "pt"))
+    assert e["C"] < tol and e["pt"] < tol and e["mu"] < tol_mu, e
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (3, 1), (1, 5), (5, 4)])
 def test_tiny_2d_lattices_fp64(shape):
     # degenerate periodic sizes: every neighbour may be the node itself
