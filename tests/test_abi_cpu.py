@@ -137,3 +137,45 @@ def test_null_arguments_rejected(lib):
     assert L.dsm_get_observables(None, None) == lib.DSM_E_INVAL
     assert L.dsm_batch_step(None, 1, None, None, 0) == lib.DSM_E_INVAL
     assert L.dsm_batch_scratch_bytes(None, 1, None) == lib.DSM_E_INVAL
+
+
+def test_vector_and_minimiser_arguments_rejected(lib):
+    # argument checks of the batched vector kernels and the native L-BFGS loop:
+    # each refuses before any device work, so fake addresses are never touched
+    import ctypes as C
+    import paper_2504_19941_gb300 as P
+    L = lib.load()
+    fake = 1 << 20
+    assert L.dsm_vec_dots(-1, 2, fake, 10, fake, fake, fake, 1 << 20, None) == lib.DSM_E_INVAL
+    assert L.dsm_vec_dots(10, 2, fake, 5, fake, fake, fake, 1 << 20, None) == lib.DSM_E_INVAL  # stride < n
+    sb = lib.dsm_vec_dots_scratch_bytes(1000, 4)
+    assert sb >= 4 * 8
+    assert L.dsm_vec_dots(1000, 4, fake, 1000, fake, fake, fake, sb - 1, None) == lib.DSM_E_WORKSPACE
+    coef = (C.c_double * 65)()
+    assert L.dsm_vec_lincomb(10, 65, fake, 10, coef, fake, 1.0, fake, None) == lib.DSM_E_INVAL
+    assert L.dsm_vec_lincomb(10, 2, None, 10, coef, fake, 1.0, fake, None) == lib.DSM_E_INVAL
+    p = P.make_params("D3Q19", (16, 16, 16), "f32", theta_deg=90)
+    nb = lib.dsm_lbfgs_workspace_bytes(p, 10)
+    # the history holds 2m vectors: the workspace grows with m
+    assert nb > 20 * 16 ** 3 * 4 and lib.dsm_lbfgs_workspace_bytes(p, 5) < nb
+    with pytest.raises(P.DSMError):
+        lib.dsm_lbfgs_workspace_bytes(p, 33)  # 2m above the combination limit
+    info = lib.dsm_lbfgs_info()
+    args = dict(fixed=fake, mask=None, active=2, dP=0.0, kcs=0.0, V0=0.0, fg=0.0, x=fake, m=10,
+                tol=1e-6, max_iter=10, work=fake * 256, work_bytes=nb)
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return L.dsm_lbfgs_minimize(C.byref(p), a["fixed"], a["mask"], a["active"], a["dP"],
+                                    a["kcs"], a["V0"], a["fg"], a["x"], a["m"], a["tol"],
+                                    a["max_iter"], a["work"], a["work_bytes"], C.byref(info), None)
+    assert call(active=3) == lib.DSM_E_INVAL
+    assert call(active=1) == lib.DSM_E_INVAL          # stage 1 needs the solid mask
+    assert call(kcs=-1.0) == lib.DSM_E_INVAL
+    assert call(m=0) == lib.DSM_E_INVAL
+    assert call(x=None) == lib.DSM_E_INVAL
+    assert call(work_bytes=nb - 1) == lib.DSM_E_WORKSPACE
+    assert call(work=fake * 256 + 16) == lib.DSM_E_WORKSPACE   # misaligned
+    cx = C.c_double()
+    one = (C.c_double * 1)(0.0)
+    assert L.dsm_lbfgs_compact(1, one, one, one, one, 1.0, C.byref(cx), one, one) == lib.DSM_E_INVAL
