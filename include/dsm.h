@@ -9,7 +9,9 @@
  * prescribed geometry.
  *
  * Conventions (all entry points)
- *   - Node index n = x + nx*(y + ny*z); every axis periodic; nz = 1 for D2Q9.
+ *   - Node index n = x + nx*(y + ny*z); nz = 1 for D2Q9.  Every axis is
+ *     periodic, except that the energy functions take mirror axes too
+ *     (dsm_params.mirror).
  *   - "real" is double for DSM_F64 lattices and float for every other precision.
  *   - Device pointers (d_*) must point to memory of the current CUDA device and
  *     stay valid for the call (and, for the workspace, until dsm_destroy).
@@ -75,6 +77,13 @@ typedef struct dsm_params {
   double tau_g;            /* Cahn-Hilliard relaxation time; M = (tau_g - 1/2)/3 */
   double body_force[3];    /* body force per unit liquid concentration */
   double beta, omega;      /* solid confinement and range penalty, LB stage 1 */
+  int mirror[3];           /* per axis x, y, z: 0 periodic, 1 mirror (symmetry plane
+                            * half a node beyond the first and last node, so the
+                            * step out of the edge node lands on the edge node).
+                            * Taken by the energy functions (dsm_fe_energy_grad,
+                            * dsm_fe_energy_grad_noalloc, dsm_lbfgs_minimize); the
+                            * lattice Boltzmann functions return DSM_E_UNSUPPORTED
+                            * for a mirror axis.  Other values: DSM_E_INVAL. */
 } dsm_params;
 
 typedef struct dsm_observables {

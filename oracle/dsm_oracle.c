@@ -37,6 +37,7 @@ typedef struct {
   double rho2, rho3, tau2, tau3, tau_g;
   double bx, by, bz;        /* body force per unit liquid concentration */
   double beta, omega;       /* solid confinement and range penalty (stage 1) */
+  int mirror[3];            /* per axis: 0 periodic, 1 mirror (energy only, see neighbour) */
 } or_params;
 
 typedef struct {
@@ -140,11 +141,25 @@ void or_solid_profile(long n, const double *sd, double alpha_s, double *c1) {
 /* ------------------------------------------------------------------------ */
 static long nnodes(const or_params *p) { return (long)p->nx * p->ny * p->nz; }
 
+/* Neighbour index along one axis: periodic, or a mirror (symmetry plane) half
+ * a node outside the first and last node, so that the node beyond the edge is
+ * the image of the edge node itself (-1 -> 0, n -> n - 1).  The energy
+ * minimisations of Sec. III use symmetry boundaries on some axes.           */
+static long axis_step(long v, int dv, long n, int mirror) {
+  long w = v + dv;
+  if (mirror) {
+    if (w < 0) w = -w - 1;
+    if (w >= n) w = 2 * n - w - 1;
+    return w;
+  }
+  return ((w % n) + n) % n;
+}
+
 static long neighbour(const or_params *p, long n, int dx, int dy, int dz) {
   long x = n % p->nx, y = (n / p->nx) % p->ny, z = n / ((long)p->nx * p->ny);
-  x = ((x + dx) % p->nx + p->nx) % p->nx;
-  y = ((y + dy) % p->ny + p->ny) % p->ny;
-  z = ((z + dz) % p->nz + p->nz) % p->nz;
+  x = axis_step(x, dx, p->nx, p->mirror[0]);
+  y = axis_step(y, dy, p->ny, p->mirror[1]);
+  z = axis_step(z, dz, p->nz, p->mirror[2]);
   return x + p->nx * (y + (long)p->ny * z);
 }
 

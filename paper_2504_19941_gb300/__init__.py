@@ -26,9 +26,11 @@ FIELDS = {"C1": DSM_FIELD_C1, "C2": DSM_FIELD_C2, "C3": DSM_FIELD_C3, "mu": DSM_
 
 def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, g12=2.5e-3,
                 g13=None, g23=2.5e-3, alpha=1.0, alpha_s=0.0, rho2=1.0, rho3=1.0, tau2=1.0,
-                tau3=1.0, tau_g=1.0, body=(0.0, 0.0, 0.0), beta=0.0, omega=0.0) -> dsm_params:
+                tau3=1.0, tau_g=1.0, body=(0.0, 0.0, 0.0), beta=0.0, omega=0.0,
+                mirror=(0, 0, 0)) -> dsm_params:
     """dsm_params from keyword arguments.  Give either theta_deg (with g23, g12)
-    or the three tensions g12, g13, g23."""
+    or the three tensions g12, g13, g23.  mirror: per axis, 1 for a symmetry
+    plane (taken by the energy functions; a Lattice needs periodic axes)."""
     p = dsm_params()
     p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -45,6 +47,8 @@ def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, 
     for a in range(3):
         p.body_force[a] = float(body[a])
     p.beta, p.omega = beta, omega
+    for a in range(3):
+        p.mirror[a] = int(mirror[a])
     return p
 
 

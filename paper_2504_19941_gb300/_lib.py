@@ -48,7 +48,7 @@ class dsm_params(C.Structure):
                 ("g23", C.c_double), ("theta_deg", C.c_double), ("rho2", C.c_double),
                 ("rho3", C.c_double), ("tau2", C.c_double), ("tau3", C.c_double),
                 ("tau_g", C.c_double), ("body_force", C.c_double * 3), ("beta", C.c_double),
-                ("omega", C.c_double)]
+                ("omega", C.c_double), ("mirror", C.c_int * 3)]
 
 
 class dsm_lbfgs_info(C.Structure):

@@ -79,8 +79,17 @@ dsm_status check_params(const dsm_params *p) {
   if (!(p->tau2 > 0.5) || !(p->tau3 > 0.5) || !(p->tau_g > 0.5)) return DSM_E_INVAL;
   if (!(p->rho2 > 0.0) || !(p->rho3 > 0.0)) return DSM_E_INVAL;
   if (p->alpha_s < 0.0) return DSM_E_INVAL;
+  for (int i = 0; i < 3; i++) {
+    if (p->mirror[i] != 0 && p->mirror[i] != 1) return DSM_E_INVAL;
+  }
   double k[3];
-  return kappa_of(p, k);
+  dsm_status s = kappa_of(p, k);
+  if (s != DSM_OK) return s;
+  // the lattice Boltzmann step streams across periodic faces only
+  for (int i = 0; i < 3; i++) {
+    if (p->mirror[i]) return DSM_E_UNSUPPORTED;
+  }
+  return DSM_OK;
 }
 
 struct Layout {
@@ -636,16 +645,8 @@ dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const floa
       ((uintptr_t)d_scratch & 255u))
     return DSM_E_WORKSPACE;
   FEArgs a;
-  memset(&a, 0, sizeof(a));
-  a.nx = p->nx;
-  a.ny = p->ny;
-  a.nz = p->nz;
-  a.d = p->lattice == DSM_D2Q9 ? 2 : 3;
-  for (int i = 0; i < 3; i++) a.kappa[i] = (float)k[i];
-  a.a2 = (float)(p->alpha * p->alpha);
-  a.beta = (float)p->beta;
-  a.fg = (float)fg;
-  a.active = active;
+  s = fe_args_of(p, k, active, fg, &a);
+  if (s != DSM_OK) return s;
   a.c1 = d_c1;
   a.c2 = d_c2;
   a.mask = d_mask;

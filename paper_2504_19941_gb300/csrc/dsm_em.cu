@@ -1,6 +1,8 @@
 // dsm_em.cu -- free energy + gradient kernel of the phase-field energy
 // minimisation (Sec. II.A of the paper) and the FP64-accumulating vector
 // kernels of its L-BFGS driver.
+#include <string.h>
+
 #include "dsm_em.cuh"
 #include "dsm_reduce.cuh"
 
@@ -54,9 +56,9 @@ __global__ void __launch_bounds__(256) fe_kernel(FEArgs a, int gx, int gy, int n
     const int y = by * blockDim.y + threadIdx.y;
     const int z = bz * blockDim.z + threadIdx.z;
     if (!(x < a.nx && y < a.ny && z < a.nz)) continue;
-    const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x + 1 == a.nx ? 0 : x + 1;
-    const int ym = y == 0 ? a.ny - 1 : y - 1, yp = y + 1 == a.ny ? 0 : y + 1;
-    const int zm = z == 0 ? a.nz - 1 : z - 1, zp = z + 1 == a.nz ? 0 : z + 1;
+    const int xm = x == 0 ? a.lo[0] : x - 1, xp = x + 1 == a.nx ? a.hi[0] : x + 1;
+    const int ym = y == 0 ? a.lo[1] : y - 1, yp = y + 1 == a.ny ? a.hi[1] : y + 1;
+    const int zm = z == 0 ? a.lo[2] : z - 1, zp = z + 1 == a.nz ? a.hi[2] : z + 1;
     const int s = a.nx * a.ny;
     const int ox[3] = {xm, x, xp}, oy[3] = {ym * a.nx, y * a.nx, yp * a.nx},
               oz[3] = {zm * s, z * s, zp * s};
@@ -141,6 +143,29 @@ __global__ void add_dev_scalar_kernel(long long n, const double *c, float *g) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x)
     g[k] += v;
+}
+
+dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, double fg,
+                      FEArgs *a) {
+  memset(a, 0, sizeof(*a));
+  a->nx = p->nx;
+  a->ny = p->ny;
+  a->nz = p->nz;
+  a->d = p->lattice == DSM_D2Q9 ? 2 : 3;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int i = 0; i < 3; i++) {
+    if (p->mirror[i] != 0 && p->mirror[i] != 1) return DSM_E_INVAL;
+    // a mirror plane half a node outside the edge reflects the step back onto
+    // the edge node: the lattice is half of a mirror-symmetric periodic one
+    a->lo[i] = p->mirror[i] ? 0 : n[i] - 1;
+    a->hi[i] = p->mirror[i] ? n[i] - 1 : 0;
+    a->kappa[i] = (float)kappa[i];
+  }
+  a->a2 = (float)(p->alpha * p->alpha);
+  a->beta = (float)p->beta;
+  a->fg = (float)fg;
+  a->active = active;
+  return DSM_OK;
 }
 
 static dim3 fe_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }

@@ -11,6 +11,7 @@ constexpr int VEC_BLOCKS = 152 * 4;  // fixed reduction grid of the vector kerne
 
 struct FEArgs {
   int nx, ny, nz, d;
+  int lo[3], hi[3];  // per axis, the coordinate one step below 0 and above n - 1
   float kappa[3];
   float a2;        // alpha^2
   float beta;      // confinement strength (active = 1)
@@ -22,6 +23,12 @@ struct FEArgs {
   float *grad;
   double *partials;
 };
+
+// FEArgs for the energy of a problem: sizes, kappa, alpha, beta, and the
+// neighbour of the edge nodes per axis (periodic: the far edge; mirror: the
+// edge node itself).  DSM_E_INVAL for a mirror flag other than 0 or 1.
+dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, double fg,
+                      FEArgs *a);
 
 long long fe_blocks(int kind, int nx, int ny, int nz);
 size_t fe_scratch_bytes(int kind, int nx, int ny, int nz);

@@ -181,16 +181,8 @@ dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
   M.n = (long long)p->nx * p->ny * p->nz;
   M.m = m;
   M.st = (cudaStream_t)cuda_stream;
-  memset(&M.fa, 0, sizeof(M.fa));
-  M.fa.nx = p->nx;
-  M.fa.ny = p->ny;
-  M.fa.nz = p->nz;
-  M.fa.d = p->lattice == DSM_D2Q9 ? 2 : 3;
-  for (int i = 0; i < 3; i++) M.fa.kappa[i] = (float)kap[i];
-  M.fa.a2 = (float)(p->alpha * p->alpha);
-  M.fa.beta = (float)p->beta;
-  M.fa.fg = (float)fg;
-  M.fa.active = active;
+  s = fe_args_of(p, kap, active, fg, &M.fa);
+  if (s != DSM_OK) return s;
   M.fa.mask = d_mask;
   M.kind = p->lattice;
   M.dP = dP;

@@ -73,19 +73,11 @@ extern "C" dsm_status dsm_fe_energy_grad_noalloc(const dsm_params *p, const floa
   if (s != DSM_OK) return s;
   // lattices whose reduction needs more than the fixed array are refused
   if (fe_scratch_bytes(p->lattice, p->nx, p->ny, p->nz) > kScratchBytes) return DSM_E_WORKSPACE;
+  FEArgs a;
+  s = fe_args_of(p, k, active, fg, &a);
+  if (s != DSM_OK) return s;
   void *scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return DSM_E_CUDA;
-  FEArgs a;
-  memset(&a, 0, sizeof(a));
-  a.nx = p->nx;
-  a.ny = p->ny;
-  a.nz = p->nz;
-  a.d = p->lattice == DSM_D2Q9 ? 2 : 3;
-  for (int i = 0; i < 3; i++) a.kappa[i] = (float)k[i];
-  a.a2 = (float)(p->alpha * p->alpha);
-  a.beta = (float)p->beta;
-  a.fg = (float)fg;
-  a.active = active;
   a.c1 = d_c1;
   a.c2 = d_c2;
   a.mask = d_mask;

@@ -95,6 +95,33 @@ def test_invalid_parameters_rejected(lib, bad):
     assert e.value.status == lib.DSM_E_INVAL
 
 
+def test_mirror_axes(lib):
+    # the lattice Boltzmann step takes periodic axes only; the energy functions
+    # take mirror faces; flags other than 0/1 are invalid everywhere.  Each call
+    # refuses before any device work, so the fake addresses are never touched.
+    import ctypes as C
+    import paper_2504_19941_gb300 as P
+    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, mirror=(0, 1, 0))
+    with pytest.raises(P.DSMError) as e:
+        lib.dsm_workspace_bytes(p)
+    assert e.value.status == lib.DSM_E_UNSUPPORTED
+    L = lib.load()
+    fake = 1 << 20
+    sb = lib.dsm_fe_scratch_bytes(p.lattice, 8, 8, 8)
+    bad = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, mirror=(0, 2, 0))
+    with pytest.raises(P.DSMError) as e:
+        lib.dsm_workspace_bytes(bad)
+    assert e.value.status == lib.DSM_E_INVAL
+    assert L.dsm_fe_energy_grad(C.byref(bad), fake, fake, None, 2, 0.0, 0.0, 0.0, 0.0, fake,
+                                fake, fake, fake * 256, sb, None) == lib.DSM_E_INVAL
+    assert L.dsm_fe_energy_grad_noalloc(C.byref(bad), fake, fake, None, 2, 0.0, 0.0, 0.0, 0.0,
+                                        fake, fake, fake, None) == lib.DSM_E_INVAL
+    nb = lib.dsm_lbfgs_workspace_bytes(bad, 5)
+    info = lib.dsm_lbfgs_info()
+    assert L.dsm_lbfgs_minimize(C.byref(bad), fake, None, 2, 0.0, 0.0, 0.0, 0.0, fake, 5, 1e-6,
+                                10, fake * 256, nb, C.byref(info), None) == lib.DSM_E_INVAL
+
+
 @pytest.mark.parametrize("prec,sb,extra", [("f64", 8, 0), ("f32", 4, 0), ("bf16", 2, 1),
                                            ("f16", 2, 1)])
 def test_workspace_size(lib, prec, sb, extra):

@@ -63,6 +63,69 @@ def test_energy_grad_parity(lat, shape, active, constraint):
     np.testing.assert_allclose(terms, to, rtol=1e-5, atol=1e-6)
 
 
+MIRROR_CASES = [("D2Q9", (23, 17), (1, 1, 0)), ("D3Q19", (13, 9, 7), (1, 0, 1)),
+                ("D3Q19", (16, 16, 16), (0, 1, 0))]
+
+
+@pytest.mark.parametrize("lat,shape,mirror", MIRROR_CASES)
+@pytest.mark.parametrize("active", [1, 2])
+def test_energy_grad_mirror_parity(lat, shape, mirror, active):
+    # symmetry planes on some axes: dsm_fe_energy_grad and the allocation-free
+    # entry point against the oracle with the same mirror faces
+    n = int(np.prod(shape))
+    c1, c2 = S.random_fields(n, seed=17)
+    c1 = 0.6 * c1
+    mask = (np.arange(n) % 4 == 1).astype(np.uint8)
+    kw = dict(kcs=0.0, V0=0.0, dP=0.015)
+    p = P.make_params(lat, shape, "f32", theta_deg=65.0, g23=0.9, g12=1.0, alpha=1.1, beta=8.0,
+                      mirror=mirror)
+    k = _lib.dsm_kappa(p)
+    kind = O.D2Q9 if lat == "D2Q9" else O.D3Q19
+    po = O.make_params(kind, shape, k, alpha=1.1, beta=8.0, mirror=mirror)
+    c1f, c2f, mf = _t(c1), _t(c2), _t(mask, torch.uint8)
+    fe = FreeEnergy(p)
+    E, g = fe(c1f, c2f, active=active, mask=mf, fg=0.01, **kw)
+    c1r, c2r = c1f.double().cpu().numpy(), c2f.double().cpu().numpy()
+    Eo, go, to = O.energy_grad(po, c1r, c2r, active=active, S=mask, fg=0.01, **kw)
+    assert abs(E.item() - Eo) / abs(Eo) < 1e-6
+    assert rel_err(g.double().cpu().numpy(), go) < 1e-5
+    np.testing.assert_allclose(fe.terms.cpu().numpy(), to, rtol=1e-5, atol=1e-6)
+    E2 = torch.empty(1, dtype=torch.float64, device=DEV)
+    g2 = torch.empty(n, dtype=torch.float32, device=DEV)
+    t2 = torch.empty(6, dtype=torch.float64, device=DEV)
+    _lib.dsm_fe_energy_grad_noalloc(p, c1f, c2f, mf, active, kw["dP"], 0.0, 0.0, 0.01, E2, g2, t2)
+    torch.cuda.synchronize()
+    assert abs(E2.item() - Eo) / abs(Eo) < 1e-6
+    assert rel_err(g2.double().cpu().numpy(), go) < 1e-5
+
+
+def test_lbfgs_mirror_half_domain_matches_symmetric_full_domain():
+    # a drop on a flat wall, symmetric about x = -1/2: the half lattice with a
+    # mirror face at x = 0 reaches the full periodic lattice's minimum on its
+    # nodes, with half its energy (volume constraint halved too)
+    nx, ny, wall = 48, 40, 8
+    full = (2 * nx, ny)
+    pf = P.make_params("D2Q9", full, "f32", theta_deg=70.0, g23=math.sqrt(8 / 9), g12=1.0)
+    ph = P.make_params("D2Q9", (nx, ny), "f32", theta_deg=70.0, g23=math.sqrt(8 / 9), g12=1.0,
+                       mirror=(1, 0, 0))
+    sd = S.slab_sd(full, 1, 0, wall)
+    c1 = O.solid_profile(sd.ravel(), 1.0).reshape(ny, 2 * nx)
+    c2 = S.cap_c2(full, wall - 0.5, 14.0, 90.0, 1.0, sd, 1.0).reshape(ny, 2 * nx)
+    # centre the drop on the plane between node 2nx-1 and node 0
+    c2 = np.roll(c2, nx, axis=1)
+    np.testing.assert_allclose(c2, c2[:, ::-1], atol=1e-12)
+    V0 = float(_t(c2).double().sum())
+    xf, Ef, inf_f = lbfgs(FreeEnergy(pf), _t(c2.ravel()), _t(c1.ravel()), active=2, kcs=0.05,
+                          V0=V0, tol=1e-5, max_iter=5000)
+    xh, Eh, inf_h = lbfgs(FreeEnergy(ph), _t(c2[:, :nx].ravel()), _t(c1[:, :nx].ravel()),
+                          active=2, kcs=0.05 * 2, V0=V0 / 2, tol=1e-5, max_iter=5000)
+    assert inf_f["rms_grad"] < 1e-5 and inf_h["rms_grad"] < 1e-5
+    # kcs doubles with V0 halved: 0.5 (2 kcs) (V/2 - V0/2)^2 is half the full term
+    assert abs(Eh - Ef / 2) / abs(Ef) < 1e-5, (Eh, Ef)
+    xf2 = xf.double().cpu().numpy().reshape(ny, 2 * nx)
+    assert np.max(np.abs(xh.double().cpu().numpy().reshape(ny, nx) - xf2[:, :nx])) < 2e-3
+
+
 def test_energy_grad_large_grid():
     shape = (128, 128, 128)
     case = S.em_sphere_interface()

@@ -13,6 +13,8 @@ term, a wrong sign or index, a transposed operand -- fails at least one:
   isotropic G and L ................ test_stencils_exact_on_quadratics
   equilibria and forcing ........... test_equilibrium_moments
   mu (stage 2) and energy .......... test_energy_gradient_fd, test_mu_equals_energy_gradient
+  mirror faces of the energy ....... test_mirror_energy_is_half_the_symmetric_domain,
+                                     test_mirror_energy_gradient_fd
   mu (stage 1) and confinement ..... test_stage1_mu_is_energy_gradient, test_solid_relaxation_keeps_shape
   streaming + collision ............ test_quiescent_fixed_point, test_mass_conservation,
                                      test_mirror_symmetry_2d, test_axis_swap_symmetry_3d
@@ -191,6 +193,66 @@ def test_energy_gradient_fd(kind, shape, active):
     fd = _fd_grad(lambda x: O.energy_grad(p, c1, x, want_grad=False, **kw2)[0], c2)
     assert np.max(np.abs(fd - g)) / np.max(np.abs(g)) < 1e-7
     assert abs(t[3] + 0.02 * c2.sum()) < 1e-12
+
+
+def _mirror_extend(a, shape, mirror):
+    """The periodic field twice as long along each mirror axis: the lattice
+    followed by its reflection (node x' >= n holds node 2n - 1 - x')."""
+    v = np.asarray(a).reshape(tuple(reversed(shape)))
+    for axis, m in enumerate(mirror[:len(shape)]):
+        if m:
+            ax = v.ndim - 1 - axis
+            v = np.concatenate([v, np.flip(v, axis=ax)], axis=ax)
+    return v
+
+
+@pytest.mark.parametrize("kind,shape,mirror", [(O.D2Q9, (7, 6), (1, 1, 0)),
+                                               (O.D2Q9, (5, 4), (0, 1, 0)),
+                                               (O.D3Q19, (4, 5, 3), (1, 0, 1))])
+@pytest.mark.parametrize("active", [1, 2])
+def test_mirror_energy_is_half_the_symmetric_domain(kind, shape, mirror, active):
+    """A lattice with mirror faces is half of the periodic lattice doubled by
+    reflection across them: its energy is that lattice's energy over 2^k, and
+    its gradient is the doubled lattice's gradient on the original nodes."""
+    n = int(np.prod(shape))
+    c1, c2 = S.random_fields(n, seed=11)
+    c1 = 0.6 * c1
+    Smask = (np.arange(n) % 3 == 0).astype(np.uint8)
+    kw = dict(active=active, dP=0.013, fg=0.0)
+    p = O.make_params(kind, shape, (0.7, 1.3, 0.9), alpha=1.2, beta=10.0, mirror=mirror)
+    E, g, t = O.energy_grad(p, c1, c2, S=Smask, **kw)
+    full = [_mirror_extend(v, shape, mirror) for v in (c1, c2, Smask)]
+    fshape = tuple(reversed(full[0].shape))
+    pf = O.make_params(kind, fshape, (0.7, 1.3, 0.9), alpha=1.2, beta=10.0)
+    Ef, gf, tf = O.energy_grad(pf, full[0].ravel(), full[1].ravel(),
+                               S=full[2].ravel().astype(np.uint8), **kw)
+    k = sum(mirror[:len(shape)])
+    assert E == pytest.approx(Ef / 2 ** k, rel=1e-13, abs=1e-13)
+    np.testing.assert_allclose(t, tf / 2 ** k, rtol=1e-12, atol=1e-13)
+    gfull = gf.reshape(full[0].shape)
+    sl = tuple(slice(0, m) for m in reversed(shape))
+    np.testing.assert_allclose(g, gfull[sl].ravel(), rtol=1e-12, atol=1e-13)
+    # and the periodic lattice of the same size differs (the faces matter)
+    p0 = O.make_params(kind, shape, (0.7, 1.3, 0.9), alpha=1.2, beta=10.0)
+    assert abs(O.energy_grad(p0, c1, c2, S=Smask, **kw)[0] - E) > 1e-6
+
+
+@pytest.mark.parametrize("kind,shape,mirror", [(O.D2Q9, (6, 5), (1, 0, 0)),
+                                               (O.D3Q19, (4, 3, 4), (0, 1, 1))])
+def test_mirror_energy_gradient_fd(kind, shape, mirror):
+    n = int(np.prod(shape))
+    c1, c2 = S.random_fields(n, seed=13)
+    p = O.make_params(kind, shape, (0.8, 1.1, 0.9), alpha=1.0, mirror=mirror)
+    kw = dict(active=2, kcs=0.2, V0=0.5 * n, fg=0.03)
+    E, g, _ = O.energy_grad(p, 0.5 * c1, c2, **kw)
+    fd = _fd_grad(lambda x: O.energy_grad(p, 0.5 * c1, x, want_grad=False, **kw)[0], c2)
+    assert np.max(np.abs(fd - g)) / np.max(np.abs(g)) < 1e-7
+
+
+def test_lb_functions_refuse_mirror_axes():
+    p = O.make_params(O.D2Q9, (6, 5), (0.8, 1.1, 0.9), mirror=(1, 0, 0))
+    with pytest.raises(ValueError):
+        O.lb_init(p, 2, None, np.full(30, 0.5))
 
 
 @pytest.mark.parametrize("kind,shape", [(O.D2Q9, (16, 16)), (O.D3Q19, (16, 16, 16))])
