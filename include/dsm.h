@@ -9,9 +9,8 @@
  * prescribed geometry.
  *
  * Conventions (all entry points)
- *   - Node index n = x + nx*(y + ny*z); nz = 1 for D2Q9.  Every axis is
- *     periodic, except that the energy functions take mirror axes too
- *     (dsm_params.mirror).
+ *   - Node index n = x + nx*(y + ny*z); nz = 1 for D2Q9.  Each face of the
+ *     lattice is periodic, a mirror or a wall (dsm_params.face).
  *   - "real" is double for DSM_F64 lattices and float for every other precision.
  *   - Device pointers (d_*) must point to memory of the current CUDA device and
  *     stay valid for the call (and, for the workspace, until dsm_destroy).
@@ -77,14 +76,26 @@ typedef struct dsm_params {
   double tau_g;            /* Cahn-Hilliard relaxation time; M = (tau_g - 1/2)/3 */
   double body_force[3];    /* body force per unit liquid concentration */
   double beta, omega;      /* solid confinement and range penalty, LB stage 1 */
-  int mirror[3];           /* per axis x, y, z: 0 periodic, 1 mirror (symmetry plane
-                            * half a node beyond the first and last node, so the
-                            * step out of the edge node lands on the edge node).
-                            * Taken by the energy functions (dsm_fe_energy_grad,
-                            * dsm_fe_energy_grad_noalloc, dsm_lbfgs_minimize); the
-                            * lattice Boltzmann functions return DSM_E_UNSUPPORTED
-                            * for a mirror axis.  Other values: DSM_E_INVAL. */
+  int face[6];             /* dsm_face of the faces x-, x+, y-, y+, z-, z+ */
 } dsm_params;
+
+/* Domain faces (the symmetry and halfway bounce-back boundaries the paper uses
+ * besides periodic ones, Sec. III).  A mirror or wall plane lies half a node
+ * beyond the edge node.  Both faces of an axis are periodic, or neither; the
+ * z faces of a D2Q9 lattice are periodic.  Other values: DSM_E_INVAL.
+ *   Stencils (G, L, the energy's pair sums): beyond a mirror or wall face they
+ *   see the edge node itself (zero normal gradient; a wall is neutral, the
+ *   method wets through the diffuse solid).
+ *   Streaming: a population crossing a mirror is reflected specularly (read at
+ *   the image node with the normal components of its velocity reversed); one
+ *   crossing a wall is bounced back at the node (f and g alike: no slip, no
+ *   flux).  A link crossing a wall takes the wall rule whatever lies beyond;
+ *   across a mirror the image node counts as the upstream node, so a solid
+ *   image takes the interpolated bounce-back.
+ *   Lattices with a mirror or wall face keep g as populations (the g_eq form
+ *   of dsm_set_g_storage is periodic only) and are refused by dsm_batch_step
+ *   with DSM_E_UNSUPPORTED. */
+typedef enum { DSM_FACE_PERIODIC = 0, DSM_FACE_MIRROR = 1, DSM_FACE_WALL = 2 } dsm_face;
 
 typedef struct dsm_observables {
   double mass_c2;   /* sum over nodes of C2 (current time level) */

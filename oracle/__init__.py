@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("rho2", C.c_double), ("rho3", C.c_double), ("tau2", C.c_double),
                 ("tau3", C.c_double), ("tau_g", C.c_double),
                 ("bx", C.c_double), ("by", C.c_double), ("bz", C.c_double),
-                ("beta", C.c_double), ("omega", C.c_double), ("mirror", C.c_int * 3)]
+                ("beta", C.c_double), ("omega", C.c_double), ("face", C.c_int * 6)]
 
 
 def _load():
@@ -126,14 +126,31 @@ def kappa_from_angle(theta_deg, g23, g12, alpha=1.0):
 
 def make_params(kind, shape, kappa, *, alpha=1.0, alpha_s=None, rho2=1.0, rho3=1.0,
                 tau2=1.0, tau3=1.0, tau_g=1.0, body=(0.0, 0.0, 0.0), beta=0.0,
-                omega=0.0, mirror=(0, 0, 0)) -> Params:
-    """mirror: per axis, 1 for a symmetry plane (energy functions only; the
-    lattice Boltzmann functions take periodic axes)."""
+                omega=0.0, faces=None) -> Params:
+    """faces: the boundary of the faces x-, x+, y-, y+, z-, z+, each "periodic",
+    "mirror" (symmetry plane) or "wall" (halfway bounce-back), or 0, 1, 2;
+    None: all periodic."""
     nx, ny = shape[0], shape[1]
     nz = shape[2] if len(shape) > 2 else 1
     return Params(kind, nx, ny, nz, alpha, alpha if alpha_s is None else alpha_s,
                   kappa[0], kappa[1], kappa[2], rho2, rho3, tau2, tau3, tau_g,
-                  body[0], body[1], body[2], beta, omega, (C.c_int * 3)(*mirror))
+                  body[0], body[1], body[2], beta, omega, (C.c_int * 6)(*face_codes(faces)))
+
+
+FACE_CODES = {"periodic": 0, "mirror": 1, "wall": 2}
+
+
+def face_codes(faces):
+    if faces is None:
+        return (0,) * 6
+    if len(faces) != 6:
+        raise ValueError("faces: six entries, x-, x+, y-, y+, z-, z+")
+    codes = tuple(FACE_CODES[f] if isinstance(f, str) else int(f) for f in faces)
+    for a in range(3):
+        if (codes[2 * a] == 0) != (codes[2 * a + 1] == 0) or not 0 <= codes[2 * a] <= 2 \
+                or not 0 <= codes[2 * a + 1] <= 2:
+            raise ValueError("faces: an axis is periodic on both faces or on neither")
+    return codes
 
 
 def _n(p: Params) -> int:
@@ -194,14 +211,8 @@ def link_q(kind, alpha_s, c1x, gc1, i):
     return _load().or_link_q(kind, alpha_s, c1x, _d(gc1), i)
 
 
-def _periodic(p: Params):
-    if any(p.mirror):
-        raise ValueError("the lattice Boltzmann functions take periodic axes only")
-
-
 def lb_init(p: Params, stage: int, c1, cfield, S=None):
     """Quiescent initial post-collision state (f, g), each q x N."""
-    _periodic(p)
     n, q = _n(p), _q(p)
     f = np.empty(q * n)
     g = np.empty(q * n)
@@ -217,7 +228,6 @@ FIELD_NAMES = ("C", "mu", "ux", "uy", "uz", "pt", "rho", "tau")
 
 def lb_run(p: Params, stage: int, c1, f, g, nsteps: int, S=None, want_fields=False):
     """Advance the post-collision state (f, g) by nsteps (copies, returns new)."""
-    _periodic(p)
     n = _n(p)
     f = _f64(f).copy()
     g = _f64(g).copy()
@@ -233,7 +243,6 @@ def lb_run(p: Params, stage: int, c1, f, g, nsteps: int, S=None, want_fields=Fal
 
 def lb_fields(p: Params, stage: int, c1, f, g, S=None):
     """Macroscopic fields at the current time level (dict of N-vectors)."""
-    _periodic(p)
     n = _n(p)
     f, g = _f64(f), _f64(g)
     c1a = _f64(c1 if c1 is not None else np.zeros(n)).ravel()
@@ -258,7 +267,6 @@ def energy_grad(p: Params, c1, c2, *, active=2, S=None, dP=0.0, kcs=0.0, V0=0.0,
 
 
 def observables(p: Params, c1, f, g):
-    _periodic(p)
     out = np.zeros(6)
     _load().or_observables(C.byref(p), _d(_f64(c1).ravel()), _d(_f64(f)), _d(_f64(g)), _d(out))
     return dict(mass_c2=out[0], mass_c1=out[1], kinetic=out[2], max_u=out[3],

@@ -13,7 +13,9 @@
  * taken serially in node order, so results do not depend on the thread count.
  *
  * Conventions
- *   node index  n = x + nx*(y + ny*z), all axes periodic (nz = 1 for D2Q9);
+ *   node index  n = x + nx*(y + ny*z) (nz = 1 for D2Q9);
+ *   each face is periodic, a mirror (symmetry plane) or a halfway
+ *   bounce-back wall, both of the latter half a node beyond the edge node;
  *   populations are q-major: f[i*N + n];
  *   the stored state is the POST-COLLISION population f*, g*; a step pulls
  *   (streams) first, then forms moments, forces and collides (Sec. II.B,
@@ -37,7 +39,8 @@ typedef struct {
   double rho2, rho3, tau2, tau3, tau_g;
   double bx, by, bz;        /* body force per unit liquid concentration */
   double beta, omega;       /* solid confinement and range penalty (stage 1) */
-  int mirror[3];            /* per axis: 0 periodic, 1 mirror (energy only, see neighbour) */
+  int face[6];              /* faces x-, x+, y-, y+, z-, z+: 0 periodic, 1 mirror,
+                               2 halfway bounce-back wall (see neighbour, pull) */
 } or_params;
 
 typedef struct {
@@ -141,26 +144,63 @@ void or_solid_profile(long n, const double *sd, double alpha_s, double *c1) {
 /* ------------------------------------------------------------------------ */
 static long nnodes(const or_params *p) { return (long)p->nx * p->ny * p->nz; }
 
-/* Neighbour index along one axis: periodic, or a mirror (symmetry plane) half
- * a node outside the first and last node, so that the node beyond the edge is
- * the image of the edge node itself (-1 -> 0, n -> n - 1).  The energy
- * minimisations of Sec. III use symmetry boundaries on some axes.           */
-static long axis_step(long v, int dv, long n, int mirror) {
+/* Neighbour index along one axis for the stencils (G, L, the pair sums of the
+ * energy): periodic, or, beyond a mirror or wall face, the image of the node
+ * across the plane half a node beyond the edge (-1 -> 0, n -> n - 1).  The
+ * energy minimisations of Sec. III use symmetry boundaries on some axes.
+ * reading: a bounce-back wall sees the same image, i.e. zero normal gradient
+ * of every concentration (a neutral wall; the method wets through the diffuse
+ * solid, not through the domain faces).                                     */
+static long axis_step(long v, int dv, long n, int lo, int hi) {
   long w = v + dv;
-  if (mirror) {
-    if (w < 0) w = -w - 1;
-    if (w >= n) w = 2 * n - w - 1;
-    return w;
-  }
+  if (w < 0 && lo) return -w - 1;
+  if (w >= n && hi) return 2 * n - w - 1;
   return ((w % n) + n) % n;
 }
 
 static long neighbour(const or_params *p, long n, int dx, int dy, int dz) {
   long x = n % p->nx, y = (n / p->nx) % p->ny, z = n / ((long)p->nx * p->ny);
-  x = axis_step(x, dx, p->nx, p->mirror[0]);
-  y = axis_step(y, dy, p->ny, p->mirror[1]);
-  z = axis_step(z, dz, p->nz, p->mirror[2]);
+  x = axis_step(x, dx, p->nx, p->face[0], p->face[1]);
+  y = axis_step(y, dy, p->ny, p->face[2], p->face[3]);
+  z = axis_step(z, dz, p->nz, p->face[4], p->face[5]);
   return x + p->nx * (y + (long)p->ny * z);
+}
+
+/* Streaming source of the population f_j (or g_j) at node n: the node and the
+ * direction whose post-collision value moves into direction j at n.  *cross
+ * tells which faces the link x - c_j -> x crosses: 0 none, 1 mirrors only,
+ * 2 a wall.
+ *   inside the lattice: x - c_j, direction j (f_j(x) = f*_j(x - c_j));
+ *   across a wall face: halfway bounce-back, n itself, direction opp(j);
+ *   across mirror faces only: specular reflection, the image node of x - c_j
+ *   and the direction j with its components normal to the crossed faces
+ *   reversed (the lattice is half of its reflected periodic double, so the
+ *   image node stands for the node beyond the plane).                       */
+static long pull(const or_params *p, const lattice *L, long n, int j, int *k, int *cross) {
+  long v[3] = {n % p->nx, (n / p->nx) % p->ny, n / ((long)p->nx * p->ny)};
+  long e[3] = {p->nx, p->ny, p->nz};
+  int c[3] = {L->c[j][0], L->c[j][1], L->c[j][2]};
+  int crossed = 0, wall = 0;
+  for (int a = 0; a < 3; a++) {
+    int t = 0;
+    if (v[a] - c[a] < 0) t = p->face[2 * a];
+    else if (v[a] - c[a] >= e[a]) t = p->face[2 * a + 1];
+    if (t) {
+      crossed = 1;
+      c[a] = -c[a];
+      if (t == 2) wall = 1;
+    }
+  }
+  *k = j;
+  *cross = wall ? 2 : crossed;
+  if (!crossed) return neighbour(p, n, -L->c[j][0], -L->c[j][1], -L->c[j][2]);
+  if (wall) {
+    *k = L->opp[j];
+    return n;
+  }
+  for (int i = 0; i < L->q; i++)
+    if (L->c[i][0] == c[0] && L->c[i][1] == c[1] && L->c[i][2] == c[2]) *k = i;
+  return neighbour(p, n, -L->c[j][0], -L->c[j][1], -L->c[j][2]);
 }
 
 /* Isotropic central differences (Sec. II.B says only "second order isotropic
@@ -368,9 +408,14 @@ static void work_free(work *w) {
 }
 
 /* Streaming (pull).  g streams everywhere (reading: the order parameter gets
- * no wall rule, so sum_x C is conserved exactly).  f at a fluid node pulls
- * from fluid neighbours; a link whose upstream node is solid takes the linear
- * interpolated bounce-back value.  Solid nodes carry f_i = w_i.             */
+ * no rule at the diffuse solid, so sum_x C is conserved exactly).  f at a
+ * fluid node pulls from fluid neighbours; a link whose upstream node is solid
+ * takes the linear interpolated bounce-back value.  Solid nodes carry
+ * f_i = w_i.  Links across a mirror or wall face follow pull() for f and g
+ * alike (a wall bounces g back too: no flux through it).  reading: a wall
+ * face comes before anything beyond it; across a mirror the image node is the
+ * upstream node, solid or not, and the interpolation's second node x + c_j is
+ * taken by pull() too (a second node beyond a wall counts as missing).      */
 static void stream(const or_params *p, const lattice *L, int stage,
                    const double *c1, const double *gc1, const double *f,
                    const double *g, work *w) {
@@ -378,8 +423,9 @@ static void stream(const or_params *p, const lattice *L, int stage,
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < N; n++) {
     for (int j = 0; j < L->q; j++) {
-      long y = neighbour(p, n, -L->c[j][0], -L->c[j][1], -L->c[j][2]);
-      w->gs[j * N + n] = g[j * N + y];
+      int k, cr;
+      long y = pull(p, L, n, j, &k, &cr);
+      w->gs[j * N + n] = g[k * N + y];
     }
     int solid_n = (stage == 2) && is_solid(c1[n]);
     if (solid_n) {
@@ -387,17 +433,19 @@ static void stream(const or_params *p, const lattice *L, int stage,
       continue;
     }
     for (int j = 0; j < L->q; j++) {
-      long y = neighbour(p, n, -L->c[j][0], -L->c[j][1], -L->c[j][2]);
-      if (stage == 1 || !is_solid(c1[y])) {
-        w->fs[j * N + n] = f[j * N + y];
+      int k, cr;
+      long y = pull(p, L, n, j, &k, &cr);
+      if (cr == 2 || stage == 1 || !is_solid(c1[y])) {
+        w->fs[j * N + n] = f[k * N + y];
         continue;
       }
       int i = L->opp[j]; /* link from n toward the wall node y = n + c_i */
       double gl[3] = {gc1[n], gc1[N + n], gc1[2 * N + n]};
       double q = link_q(L, p->alpha_s, c1[n], gl, i);
-      long z = neighbour(p, n, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
-      if (q < 0.5 && !is_solid(c1[z]))
-        w->fs[j * N + n] = 2.0 * q * f[i * N + n] + (1.0 - 2.0 * q) * f[i * N + z];
+      int kz, crz;
+      long z = pull(p, L, n, i, &kz, &crz); /* f_i one node away from the wall */
+      if (q < 0.5 && crz != 2 && !is_solid(c1[z]))
+        w->fs[j * N + n] = 2.0 * q * f[i * N + n] + (1.0 - 2.0 * q) * f[kz * N + z];
       else if (q < 0.5) /* reading: no second fluid node -> halfway rule */
         w->fs[j * N + n] = f[i * N + n];
       else

@@ -13,12 +13,13 @@ from . import _lib
 from ._lib import (DSM_BF16_STORE, DSM_D2Q9, DSM_D3Q19, DSM_F16_STORE, DSM_F32, DSM_F64,  # noqa
                    DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_PT,
                    DSM_FIELD_RHO, DSM_FIELD_TAU, DSM_FIELD_UX, DSM_FIELD_UY, DSM_FIELD_UZ,
-                   DSMError, dsm_params)
+                   DSM_FACE_MIRROR, DSM_FACE_PERIODIC, DSM_FACE_WALL, DSMError, dsm_params)
 
 _lib.load()
 
 PRECISIONS = {"f64": DSM_F64, "f32": DSM_F32, "bf16": DSM_BF16_STORE, "f16": DSM_F16_STORE}
 LATTICES = {"D2Q9": DSM_D2Q9, "D3Q19": DSM_D3Q19}
+FACES = {"periodic": DSM_FACE_PERIODIC, "mirror": DSM_FACE_MIRROR, "wall": DSM_FACE_WALL}
 FIELDS = {"C1": DSM_FIELD_C1, "C2": DSM_FIELD_C2, "C3": DSM_FIELD_C3, "mu": DSM_FIELD_MU,
           "ux": DSM_FIELD_UX, "uy": DSM_FIELD_UY, "uz": DSM_FIELD_UZ, "pt": DSM_FIELD_PT,
           "rho": DSM_FIELD_RHO, "tau": DSM_FIELD_TAU}
@@ -27,10 +28,11 @@ FIELDS = {"C1": DSM_FIELD_C1, "C2": DSM_FIELD_C2, "C3": DSM_FIELD_C3, "mu": DSM_
 def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, g12=2.5e-3,
                 g13=None, g23=2.5e-3, alpha=1.0, alpha_s=0.0, rho2=1.0, rho3=1.0, tau2=1.0,
                 tau3=1.0, tau_g=1.0, body=(0.0, 0.0, 0.0), beta=0.0, omega=0.0,
-                mirror=(0, 0, 0)) -> dsm_params:
+                faces=None) -> dsm_params:
     """dsm_params from keyword arguments.  Give either theta_deg (with g23, g12)
-    or the three tensions g12, g13, g23.  mirror: per axis, 1 for a symmetry
-    plane (taken by the energy functions; a Lattice needs periodic axes)."""
+    or the three tensions g12, g13, g23.  faces: the boundary of the faces x-,
+    x+, y-, y+, z-, z+, each "periodic", "mirror" (symmetry plane) or "wall"
+    (halfway bounce-back); None: all periodic."""
     p = dsm_params()
     p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -47,8 +49,11 @@ def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, 
     for a in range(3):
         p.body_force[a] = float(body[a])
     p.beta, p.omega = beta, omega
-    for a in range(3):
-        p.mirror[a] = int(mirror[a])
+    if faces is not None:
+        if len(faces) != 6:
+            raise ValueError("faces: six entries, x-, x+, y-, y+, z-, z+")
+        for k, f in enumerate(faces):
+            p.face[k] = FACES[f] if isinstance(f, str) else int(f)
     return p
 
 

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdsm.so")
 DSM_OK, DSM_E_INVAL, DSM_E_WORKSPACE, DSM_E_CUDA, DSM_E_NONFINITE, DSM_E_TIMEOUT, \
     DSM_E_STATE, DSM_E_UNSUPPORTED = range(8)
 DSM_D2Q9, DSM_D3Q19 = 0, 1
+DSM_FACE_PERIODIC, DSM_FACE_MIRROR, DSM_FACE_WALL = 0, 1, 2
 DSM_F64, DSM_F32, DSM_BF16_STORE, DSM_F16_STORE = 0, 1, 2, 3
 DSM_G_AUTO, DSM_G_POPULATIONS = 0, 1
 (DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_UX, DSM_FIELD_UY,
@@ -48,7 +49,7 @@ class dsm_params(C.Structure):
                 ("g23", C.c_double), ("theta_deg", C.c_double), ("rho2", C.c_double),
                 ("rho3", C.c_double), ("tau2", C.c_double), ("tau3", C.c_double),
                 ("tau_g", C.c_double), ("body_force", C.c_double * 3), ("beta", C.c_double),
-                ("omega", C.c_double), ("mirror", C.c_int * 3)]
+                ("omega", C.c_double), ("face", C.c_int * 6)]
 
 
 class dsm_lbfgs_info(C.Structure):

@@ -79,17 +79,9 @@ dsm_status check_params(const dsm_params *p) {
   if (!(p->tau2 > 0.5) || !(p->tau3 > 0.5) || !(p->tau_g > 0.5)) return DSM_E_INVAL;
   if (!(p->rho2 > 0.0) || !(p->rho3 > 0.0)) return DSM_E_INVAL;
   if (p->alpha_s < 0.0) return DSM_E_INVAL;
-  for (int i = 0; i < 3; i++) {
-    if (p->mirror[i] != 0 && p->mirror[i] != 1) return DSM_E_INVAL;
-  }
+  if (!faces_valid(p)) return DSM_E_INVAL;
   double k[3];
-  dsm_status s = kappa_of(p, k);
-  if (s != DSM_OK) return s;
-  // the lattice Boltzmann step streams across periodic faces only
-  for (int i = 0; i < 3; i++) {
-    if (p->mirror[i]) return DSM_E_UNSUPPORTED;
-  }
-  return DSM_OK;
+  return kappa_of(p, k);
 }
 
 struct Layout {
@@ -146,6 +138,11 @@ StepParams step_params(const dsm_params *p, const double k[3]) {
   s.beta = p->beta;
   s.omega = p->omega;
   s.rho_contrast = p->rho2 != p->rho3;
+  s.walls = 0;
+  for (int f = 0; f < 6; f++) {
+    s.face[f] = p->face[f];
+    s.walls |= p->face[f] != DSM_FACE_PERIODIC;
+  }
   return s;
 }
 
@@ -307,7 +304,7 @@ dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void
   h->stream = (cudaStream_t)cuda_stream;
   h->sp = step_params(p, h->kappa);
   h->g_form = DSM_G_AUTO;
-  h->eq = p->tau_g == 1.0;
+  h->eq = p->tau_g == 1.0 && !has_walls(p);
   // no solid yet: C1 = 0 everywhere; clear the error word and the mask
   cudaError_t e = cudaMemsetAsync(h->C1, 0, pitch * t.real_bytes, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->mask, 0, pitch, h->stream);
@@ -489,7 +486,7 @@ dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g)
 
 dsm_status dsm_set_g_storage(dsm_lattice *h, int form) {
   if (!h || (form != DSM_G_AUTO && form != DSM_G_POPULATIONS)) return DSM_E_INVAL;
-  const bool eq = form == DSM_G_AUTO && h->prm.tau_g == 1.0;
+  const bool eq = form == DSM_G_AUTO && h->prm.tau_g == 1.0 && !has_walls(&h->prm);
   if (h->g_implicit && !eq) {
     // write the current g_eq out as populations of the current buffer
     LBRaw a = raw_of(h, h->cur ^ 1);  // g_out = current buffer
@@ -728,6 +725,7 @@ static dsm_status batch_items(dsm_lattice *const *hs, int n, const long long *ns
   for (int i = 0; i < n; i++) {
     const dsm_lattice *h = hs[i];
     if (!h) return DSM_E_INVAL;
+    if (has_walls(&h->prm)) return DSM_E_UNSUPPORTED;  // the batched step is periodic
     if (h->kind != h0->kind || h->prm.precision != h0->prm.precision ||
         h->stream != h0->stream || h->sp.rho_contrast != h0->sp.rho_contrast || h->eq != h0->eq)
       return DSM_E_INVAL;

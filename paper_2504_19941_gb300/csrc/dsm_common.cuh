@@ -66,6 +66,15 @@ struct Lat<1> {
   }
 };
 
+// Index of the direction (cx, cy, cz) in lattice L (0 if absent).
+template <class L>
+__host__ __device__ constexpr int lat_index(int cx, int cy, int cz) {
+  int k = 0;
+  for (int i = 1; i < L::Q; i++)
+    if (L::cx(i) == cx && L::cy(i) == cy && L::cz(i) == cz) k = i;
+  return k;
+}
+
 // --------------------------------------------------------------------------
 // Population storage.  For the 16-bit precisions the hydrodynamic population is
 // stored as its offset from the rest weight, f_i - w_i, and the order-parameter
@@ -113,6 +122,8 @@ struct StepParams {
   double body[3];
   double beta, omega;
   int rho_contrast;         // rho2 != rho3
+  int face[6];              // x-, x+, y-, y+, z-, z+: 0 periodic, 1 mirror, 2 wall
+  int walls;                // some face is not periodic
 };
 
 // The same constants in the arithmetic type T, with every product and
@@ -222,6 +233,22 @@ LBTable lb_table_f64(int kind);
 LBTable lb_table_f32(int kind);
 LBTable lb_table_bf16(int kind);
 LBTable lb_table_f16(int kind);
+
+// Faces of dsm_params: each 0..2, an axis periodic on both faces or neither,
+// the z faces of a D2Q9 lattice periodic.
+inline bool faces_valid(const dsm_params *p) {
+  for (int a = 0; a < 3; a++) {
+    const int lo = p->face[2 * a], hi = p->face[2 * a + 1];
+    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return false;
+    if ((lo == 0) != (hi == 0)) return false;
+  }
+  return !(p->lattice == DSM_D2Q9 && (p->face[4] || p->face[5]));
+}
+inline bool has_walls(const dsm_params *p) {
+  for (int f = 0; f < 6; f++)
+    if (p->face[f]) return true;
+  return false;
+}
 
 __host__ __device__ inline long long round_up(long long v, long long m) {
   return (v + m - 1) / m * m;

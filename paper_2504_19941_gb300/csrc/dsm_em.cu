@@ -152,13 +152,13 @@ dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, do
   a->ny = p->ny;
   a->nz = p->nz;
   a->d = p->lattice == DSM_D2Q9 ? 2 : 3;
+  if (!faces_valid(p)) return DSM_E_INVAL;
   const int n[3] = {p->nx, p->ny, p->nz};
   for (int i = 0; i < 3; i++) {
-    if (p->mirror[i] != 0 && p->mirror[i] != 1) return DSM_E_INVAL;
-    // a mirror plane half a node outside the edge reflects the step back onto
-    // the edge node: the lattice is half of a mirror-symmetric periodic one
-    a->lo[i] = p->mirror[i] ? 0 : n[i] - 1;
-    a->hi[i] = p->mirror[i] ? n[i] - 1 : 0;
+    // a mirror or wall plane half a node outside the edge maps the step back
+    // onto the edge node: the lattice is half of a mirror-symmetric periodic one
+    a->lo[i] = p->face[2 * i] ? 0 : n[i] - 1;
+    a->hi[i] = p->face[2 * i + 1] ? n[i] - 1 : 0;
     a->kappa[i] = (float)kappa[i];
   }
   a->a2 = (float)(p->alpha * p->alpha);

@@ -25,8 +25,8 @@ struct FEArgs {
 };
 
 // FEArgs for the energy of a problem: sizes, kappa, alpha, beta, and the
-// neighbour of the edge nodes per axis (periodic: the far edge; mirror: the
-// edge node itself).  DSM_E_INVAL for a mirror flag other than 0 or 1.
+// neighbour of the edge nodes per axis (periodic: the far edge; mirror or
+// wall: the edge node itself).  DSM_E_INVAL for invalid faces.
 dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, double fg,
                       FEArgs *a);
 

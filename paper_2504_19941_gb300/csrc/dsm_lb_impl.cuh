@@ -53,6 +53,19 @@ struct Hood {
     oz[1] = z * s;
     oz[2] = zp * s;
   }
+  // The same with the lattice's faces: beyond a mirror or wall face the
+  // stencils see the edge node itself, the image of the node across the plane
+  // half a node out (zero normal gradient).
+  __device__ __forceinline__ void init_faces(int x, int y, int z, int nx, int ny, int nz,
+                                             const int (&face)[6]) {
+    init(x, y, z, nx, ny, nz);
+    if (x == 0 && face[0]) ox[0] = 0;
+    if (x + 1 == nx && face[1]) ox[2] = nx - 1;
+    if (y == 0 && face[2]) oy[0] = 0;
+    if (y + 1 == ny && face[3]) oy[2] = (ny - 1) * nx;
+    if (z == 0 && face[4]) oz[0] = 0;
+    if (z + 1 == nz && face[5]) oz[2] = (nz - 1) * nx * ny;
+  }
   template <class L>
   __device__ __forceinline__ int plus(int i) const {  // x + c_i
     return ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
@@ -70,6 +83,37 @@ struct Hood {
            (cz < 0 ? oz[0] : cz > 0 ? oz[2] : oz[1]);
   }
 };
+
+// Streaming across the lattice's faces, for the population pulled into
+// direction j at node (x, y, z).  Returns 0 when x - c_j lies inside (or across
+// a periodic face); 2 across a wall face: halfway bounce-back, direction
+// opp(j) read at the node itself; 1 across mirror faces only: specular
+// reflection, the direction with its components normal to the crossed faces
+// reversed, read at the image node (Hood::init_faces' x - c_j).  *k is the
+// direction to read.
+template <class L>
+__device__ __forceinline__ int face_cross(const int (&face)[6], int x, int y, int z, int nx,
+                                          int ny, int nz, int j, int *k) {
+  const int cx = L::cx(j), cy = L::cy(j), cz = L::cz(j);
+  const int tx = (cx > 0 && x == 0) ? face[0] : ((cx < 0 && x == nx - 1) ? face[1] : 0);
+  const int ty = (cy > 0 && y == 0) ? face[2] : ((cy < 0 && y == ny - 1) ? face[3] : 0);
+  const int tz = (cz > 0 && z == 0) ? face[4] : ((cz < 0 && z == nz - 1) ? face[5] : 0);
+  *k = j;
+  if (!(tx | ty | tz)) return 0;
+  if (tx == 2 || ty == 2 || tz == 2) {
+    *k = L::opp(j);
+    return 2;
+  }
+  *k = lat_index<L>(tx ? -cx : cx, ty ? -cy : cy, tz ? -cz : cz);
+  return 1;
+}
+
+// Node on a face that is not periodic.
+__device__ __forceinline__ bool on_wall_face(const int (&face)[6], int x, int y, int z, int nx,
+                                             int ny, int nz) {
+  return (face[0] && (x == 0 || x == nx - 1)) || (face[2] && (y == 0 || y == ny - 1)) ||
+         (face[4] && (z == 0 || z == nz - 1));
+}
 
 template <class T, class S>
 __device__ __forceinline__ T load_f(const S *base, int off, int i, double w) {
@@ -123,9 +167,22 @@ __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y
   using L = Lat<K>;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
-  h.init(x, y, z, a.nx, a.ny, a.nz);
+  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   T s = T(0);
+  if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
+    // a node on a mirror or wall face: the pulled g follow the face rules
+#pragma unroll 1
+    for (int i = 0; i < L::Q; i++) {
+      int k;
+      const int cr = face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &k);
+      const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(i));
+      if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
+      else s += load_g<T, S>(a.gin[k], src);
+    }
+    a.C[n] = s;
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < L::Q; i++) {
     if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
@@ -351,7 +408,9 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   if (MODE != MODE_OBS && !valid) return;
   if (!valid) x = y = z = 0;
   Hood h;
-  h.init(x, y, z, a.nx, a.ny, a.nz);
+  // (g held as g_eq implies periodic faces)
+  if constexpr (EQ) h.init(x, y, z, a.nx, a.ny, a.nz);
+  else h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   const ConstT<T> &K_ = a.c;
 
@@ -483,9 +542,17 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
       const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
       T v;
-      if (q < T(0.5) && !((nb_solid >> j) & 1u)) {
-        const int z2 = h.plus_rt<L>(j);  // x - c_i, the next fluid node away from the wall
-        const T fi_z = load_f<T, S>(a.fin[i], z2, i, L::w(i));
+      // x - c_i, the next fluid node away from the wall: with mirror or wall
+      // faces it is pulled like any population (none beyond a wall)
+      int ki = i;
+      bool second = !((nb_solid >> j) & 1u);
+      if constexpr (!EQ) {
+        if (a.p.walls && face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2)
+          second = false;
+      }
+      if (q < T(0.5) && second) {
+        const int z2 = h.plus_rt<L>(j);
+        const T fi_z = load_f<T, S>(a.fin[ki], z2, ki, L::w(ki));
         v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
       } else if (q < T(0.5)) {
         v = fi_x;  // no second fluid node: halfway rule
@@ -496,6 +563,31 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
 #pragma unroll
       for (int k = 1; k < Q; k++)
         if (k == j) f[k] = v;
+    }
+  }
+
+  // ---- mirror and wall faces -------------------------------------------------
+  // Links across a face take its rule (specular reflection at a mirror,
+  // halfway bounce-back at a wall) for f and g, except that a mirror link whose
+  // image upstream node is solid keeps the interpolated value set above.
+  if constexpr (!EQ) {
+    if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
+#pragma unroll 1
+      for (int j = 1; j < Q; j++) {
+        int k;
+        const int cr = face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
+        if (cr == 0) continue;
+        const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
+        const bool interp = STAGE == 2 && cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
+        const T fv = interp ? T(0) : load_f<T, S>(a.fin[k], src, k, L::w(k));
+        const T gv = LOAD_G ? load_g<T, S>(a.gin[k], src) : T(0);
+#pragma unroll
+        for (int kk = 1; kk < Q; kk++)
+          if (kk == j) {
+            if (!interp) f[kk] = fv;
+            if (LOAD_G) g[kk] = gv;
+          }
+      }
     }
   }
 
@@ -794,7 +886,7 @@ __global__ void __launch_bounds__(256) init_kernel(LBArgs<T, S> a, const T *cfie
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
-  h.init(x, y, z, a.nx, a.ny, a.nz);
+  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   const ConstT<T> &K_ = a.c;
   const T C = cfield[n];

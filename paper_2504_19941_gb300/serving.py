@@ -223,7 +223,7 @@ class GpuExecutor:
         return make_params(case.lattice, case.shape, self.precision, theta_deg=case.theta_deg,
                            g12=case.g12, g23=case.g23, alpha=case.alpha, alpha_s=case.alpha_s,
                            rho2=case.rho2, rho3=case.rho3, tau2=case.tau2, tau3=case.tau3,
-                           tau_g=case.tau_g, body=case.body)
+                           tau_g=case.tau_g, body=case.body, faces=case.faces)
 
     def is_large(self, req) -> bool:
         return req.n > self.small_nodes
@@ -238,11 +238,15 @@ class GpuExecutor:
         torch = self.torch
         case = getattr(req, "payload", None) or req.case()
         main = torch.cuda.current_stream(self.device)
-        # large lattices get a stream of their own (their steps overlap on the
-        # device); small ones share the current stream, which the batched
-        # launch requires
-        stream = main if req.n <= self.small_nodes else torch.cuda.Stream(self.device)
+        # large lattices, and lattices with mirror or wall faces (which the
+        # batched step does not take), get a stream of their own (their steps
+        # overlap on the device); small ones share the current stream, which
+        # the batched launch requires
+        solo = req.n > self.small_nodes or any(f not in (None, 0, "periodic")
+                                                for f in (case.faces or ()))
+        stream = torch.cuda.Stream(self.device) if solo else main
         lat = Lattice(self._params(case), device=self.device, stream=stream)
+        lat.solo = solo
         sd = torch.as_tensor(case.solid_sd, dtype=lat.real, device=self.device)
         c2 = torch.as_tensor(case.c2, dtype=lat.real, device=self.device)
         stream.wait_stream(main)
@@ -255,8 +259,8 @@ class GpuExecutor:
     def advance(self, work):
         from . import _lib
         torch = self.torch
-        small = [(h, k) for h, k in work if h.n <= self.small_nodes and k > 0]
-        large = [(h, k) for h, k in work if h.n > self.small_nodes and k > 0]
+        small = [(h, k) for h, k in work if not h.solo and k > 0]
+        large = [(h, k) for h, k in work if h.solo and k > 0]
         for h, k in large:  # queued on each lattice's own stream
             _lib.dsm_step(h.h, k)
         # one batched launch per lattice kind (a batch shares kind and precision)

@@ -202,6 +202,7 @@ class Case:
     body: tuple = (0.0, 0.0, 0.0)
     steps: int = 0
     extra: dict = field(default_factory=dict)
+    faces: tuple = None          # x-, x+, y-, y+, z-, z+ ("periodic", "mirror", "wall")
 
     @property
     def n(self) -> int:

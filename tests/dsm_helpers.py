@@ -36,7 +36,7 @@ def oracle_params(case: S.Case, kind: int):
     assert rc == 0
     return O.make_params(kind, case.shape, k, alpha=case.alpha, alpha_s=case.alpha_s,
                          rho2=case.rho2, rho3=case.rho3, tau2=case.tau2, tau3=case.tau3,
-                         tau_g=case.tau_g, body=case.body)
+                         tau_g=case.tau_g, body=case.body, faces=case.faces)
 
 
 def gpu_lattice(case: S.Case, precision: str, device="cuda", g_storage="auto"):
@@ -45,7 +45,7 @@ def gpu_lattice(case: S.Case, precision: str, device="cuda", g_storage="auto"):
     p = P.make_params(case.lattice, case.shape, precision, theta_deg=case.theta_deg, g12=case.g12,
                       g23=case.g23, alpha=case.alpha, alpha_s=case.alpha_s, rho2=case.rho2,
                       rho3=case.rho3, tau2=case.tau2, tau3=case.tau3, tau_g=case.tau_g,
-                      body=case.body)
+                      body=case.body, faces=case.faces)
     lat = P.Lattice(p, device=device)
     lat.set_g_storage(g_storage)
     real = lat.real

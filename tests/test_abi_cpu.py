@@ -95,23 +95,36 @@ def test_invalid_parameters_rejected(lib, bad):
     assert e.value.status == lib.DSM_E_INVAL
 
 
-def test_mirror_axes(lib):
-    # the lattice Boltzmann step takes periodic axes only; the energy functions
-    # take mirror faces; flags other than 0/1 are invalid everywhere.  Each call
-    # refuses before any device work, so the fake addresses are never touched.
+@pytest.mark.parametrize("faces,ok", [
+    (("mirror", "mirror", "wall", "wall", "periodic", "periodic"), True),
+    (("wall", "mirror", "periodic", "periodic", "mirror", "wall"), True),
+    (("mirror", "periodic", "periodic", "periodic", "periodic", "periodic"), False),
+    ((3, 3, 0, 0, 0, 0), False), ((-1, 1, 0, 0, 0, 0), False)])
+def test_face_validation(lib, faces, ok):
+    import paper_2504_19941_gb300 as P
+    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, faces=faces)
+    if ok:
+        assert lib.dsm_workspace_bytes(p) > 0
+    else:
+        with pytest.raises(P.DSMError) as e:
+            lib.dsm_workspace_bytes(p)
+        assert e.value.status == lib.DSM_E_INVAL
+    # the z faces of a D2Q9 lattice are periodic
+    p2 = P.make_params("D2Q9", (8, 8), "f32", theta_deg=90.0,
+                       faces=("periodic", "periodic", "wall", "wall", "mirror", "mirror"))
+    with pytest.raises(P.DSMError):
+        lib.dsm_workspace_bytes(p2)
+
+
+def test_invalid_faces_refused_by_energy_functions(lib):
+    # each call refuses before any device work, so the fake addresses are
+    # never touched
     import ctypes as C
     import paper_2504_19941_gb300 as P
-    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, mirror=(0, 1, 0))
-    with pytest.raises(P.DSMError) as e:
-        lib.dsm_workspace_bytes(p)
-    assert e.value.status == lib.DSM_E_UNSUPPORTED
     L = lib.load()
     fake = 1 << 20
-    sb = lib.dsm_fe_scratch_bytes(p.lattice, 8, 8, 8)
-    bad = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, mirror=(0, 2, 0))
-    with pytest.raises(P.DSMError) as e:
-        lib.dsm_workspace_bytes(bad)
-    assert e.value.status == lib.DSM_E_INVAL
+    sb = lib.dsm_fe_scratch_bytes(1, 8, 8, 8)
+    bad = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0, faces=(0, 0, 1, 0, 0, 0))
     assert L.dsm_fe_energy_grad(C.byref(bad), fake, fake, None, 2, 0.0, 0.0, 0.0, 0.0, fake,
                                 fake, fake, fake * 256, sb, None) == lib.DSM_E_INVAL
     assert L.dsm_fe_energy_grad_noalloc(C.byref(bad), fake, fake, None, 2, 0.0, 0.0, 0.0, 0.0,

@@ -63,25 +63,27 @@ def test_energy_grad_parity(lat, shape, active, constraint):
     np.testing.assert_allclose(terms, to, rtol=1e-5, atol=1e-6)
 
 
-MIRROR_CASES = [("D2Q9", (23, 17), (1, 1, 0)), ("D3Q19", (13, 9, 7), (1, 0, 1)),
-                ("D3Q19", (16, 16, 16), (0, 1, 0))]
+MIRROR_CASES = [("D2Q9", (23, 17), ("mirror", "mirror", "wall", "wall", "periodic", "periodic")),
+                ("D3Q19", (13, 9, 7), ("mirror", "mirror", "periodic", "periodic", "wall", "mirror")),
+                ("D3Q19", (16, 16, 16), ("periodic", "periodic", "mirror", "mirror", "periodic",
+                                         "periodic"))]
 
 
-@pytest.mark.parametrize("lat,shape,mirror", MIRROR_CASES)
+@pytest.mark.parametrize("lat,shape,faces", MIRROR_CASES)
 @pytest.mark.parametrize("active", [1, 2])
-def test_energy_grad_mirror_parity(lat, shape, mirror, active):
-    # symmetry planes on some axes: dsm_fe_energy_grad and the allocation-free
-    # entry point against the oracle with the same mirror faces
+def test_energy_grad_mirror_parity(lat, shape, faces, active):
+    # symmetry planes and walls on some axes: dsm_fe_energy_grad and the
+    # allocation-free entry point against the oracle with the same faces
     n = int(np.prod(shape))
     c1, c2 = S.random_fields(n, seed=17)
     c1 = 0.6 * c1
     mask = (np.arange(n) % 4 == 1).astype(np.uint8)
     kw = dict(kcs=0.0, V0=0.0, dP=0.015)
     p = P.make_params(lat, shape, "f32", theta_deg=65.0, g23=0.9, g12=1.0, alpha=1.1, beta=8.0,
-                      mirror=mirror)
+                      faces=faces)
     k = _lib.dsm_kappa(p)
     kind = O.D2Q9 if lat == "D2Q9" else O.D3Q19
-    po = O.make_params(kind, shape, k, alpha=1.1, beta=8.0, mirror=mirror)
+    po = O.make_params(kind, shape, k, alpha=1.1, beta=8.0, faces=faces)
     c1f, c2f, mf = _t(c1), _t(c2), _t(mask, torch.uint8)
     fe = FreeEnergy(p)
     E, g = fe(c1f, c2f, active=active, mask=mf, fg=0.01, **kw)
@@ -107,7 +109,7 @@ def test_lbfgs_mirror_half_domain_matches_symmetric_full_domain():
     full = (2 * nx, ny)
     pf = P.make_params("D2Q9", full, "f32", theta_deg=70.0, g23=math.sqrt(8 / 9), g12=1.0)
     ph = P.make_params("D2Q9", (nx, ny), "f32", theta_deg=70.0, g23=math.sqrt(8 / 9), g12=1.0,
-                       mirror=(1, 0, 0))
+                       faces=("mirror", "mirror", "periodic", "periodic", "periodic", "periodic"))
     sd = S.slab_sd(full, 1, 0, wall)
     c1 = O.solid_profile(sd.ravel(), 1.0).reshape(ny, 2 * nx)
     c2 = S.cap_c2(full, wall - 0.5, 14.0, 90.0, 1.0, sd, 1.0).reshape(ny, 2 * nx)

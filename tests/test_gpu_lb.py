@@ -207,6 +207,108 @@ def test_no_solid_and_pure_gas():
         assert rel_err(gf, f) < 1e-12 and rel_err(gg, g) < 1e-12
 
 
+# ---------------------------------------------------------------- domain faces
+def _faces_2d():
+    # a drop on a diffuse slab whose contact line meets the mirror face x = -1/2,
+    # a wall above; the body force drives the liquid into both
+    nx, ny = 40, 30
+    sd = S.slab_sd((nx, ny), 1, 0, 6)
+    a_s = S.width_to_alpha(3.0)
+    c2 = S.cap_c2((nx, ny), 5.5, 10.0, 80.0, 1.0, sd, a_s, centre_x=0.0).ravel()
+    c2 = c2 + S.perturbation(5, nx * ny)
+    return S.Case("faces2d", "D2Q9", (nx, ny), sd.ravel(), c2, theta_deg=60.0, g23=0.01,
+                  g12=0.01, alpha_s=a_s, body=(-2e-5, 1e-5, 0.0),
+                  faces=("mirror", "mirror", "wall", "wall", "periodic", "periodic"))
+
+
+def _faces_3d():
+    # pillars cut by the faces; x mirror, y wall, z mirror below and wall above
+    case = _small_3d(shape=(21, 17, 15), body=(-3e-6, 2e-6, 4e-6))
+    case.faces = ("mirror", "mirror", "wall", "wall", "mirror", "wall")
+    return case
+
+
+@pytest.mark.parametrize("make,kind,steps", [(_faces_2d, O.D2Q9, 60), (_faces_3d, O.D3Q19, 20)])
+def test_faces_fp64_parity(make, kind, steps):
+    case = make()
+    perm = direction_map(kind)
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, kind)
+    lat.step(steps)
+    assert not lat.g_implicit  # lattices with mirror or wall faces keep populations
+    f, g = O.lb_run(p, 2, c1, f, g, steps)
+    errs = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    gf, gg = gpu_pops(lat, perm)
+    errs["f"], errs["g"] = rel_err(gf, f), rel_err(gg, g)
+    assert max(errs.values()) < 1e-12, errs
+    ob = lat.observables()
+    ob_or = O.observables(p, c1, f, g)
+    assert abs(ob["mass_c2"] - ob_or["mass_c2"]) / ob_or["mass_c2"] < 1e-12
+
+
+@pytest.mark.parametrize("make,kind,steps", [(_faces_2d, O.D2Q9, 60), (_faces_3d, O.D3Q19, 40)])
+def test_faces_fp32_parity(make, kind, steps):
+    case = make()
+    perm = direction_map(kind)
+    lat = gpu_lattice(case, "f32")
+    p, c1, f, g = _oracle_case(case, kind)
+    lat.step(steps)
+    f, g = O.lb_run(p, 2, c1, f, g, steps)
+    e = compare(gpu_fields(lat), _oracle_fields(p, c1, f, g))
+    gf, gg = gpu_pops(lat, perm)
+    assert e["C"] < 1e-5 and e["pt"] < 1e-5 and e["mu"] < 1e-4, e
+    assert max(e["ux"], e["uy"], e["uz"]) < 2e-4, e
+    assert rel_err(gf, f) < 1e-5 and rel_err(gg, g) < 1e-5
+
+
+def test_faces_solid_relaxation_fp64():
+    shape = (24, 20)
+    faces = ("mirror", "mirror", "wall", "wall", "periodic", "periodic")
+    sd = S.slab_sd(shape, 1, 0, 5) + 0.0
+    Smask = (sd.ravel() > 0).astype(np.uint8)
+    Smask[:60] = 1  # a block in the corner at the mirror face
+    k, _ = O.kappa_from_angle(60.0, 0.01, 0.01)
+    po = O.make_params(O.D2Q9, shape, k, beta=1e-3, omega=2e-4, faces=faces)
+    f, g = O.lb_init(po, 1, None, Smask.astype(float), S=Smask)
+    f, g = O.lb_run(po, 1, None, f, g, 200, S=Smask)
+    c1_o = O.lb_fields(po, 1, None, f, g, S=Smask)["C"]
+    pp = P.make_params("D2Q9", shape, "f64", theta_deg=60.0, g12=0.01, g23=0.01, faces=faces)
+    lat = P.Lattice(pp)
+    lat.set_solid_c1(torch.as_tensor(Smask.astype(float), device="cuda"))
+    lat.relax_solid(torch.as_tensor(Smask, device="cuda"), 200, 1e-3, 2e-4)
+    assert rel_err(lat.field("C1").cpu().numpy(), c1_o) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+def test_wall_poiseuille_closed_form_gpu(prec, tol):
+    # halfway bounce-back between two walls at tau = 1/2 + sqrt(3/16): the
+    # steady profile is the parabola with the walls half a node out (the BGK
+    # slip (16 tau^2 - 16 tau + 1)/12 vanishes), at a size the oracle is not run
+    nx, ny, nz = 4, 6, 40
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    b = 1e-6
+    n = nx * ny * nz
+    case = S.Case("poiseuille", "D3Q19", (nx, ny, nz), np.full(n, -50.0), np.ones(n),
+                  theta_deg=90.0, g23=0.01, g12=0.01, tau2=tau, tau3=tau, body=(b, 0.0, 0.0),
+                  faces=("periodic", "periodic", "mirror", "mirror", "wall", "wall"))
+    lat = gpu_lattice(case, prec)
+    nu = (tau - 0.5) / 3.0
+    lat.step(int(30.0 * nz * nz / nu / math.pi ** 2))  # e^-30 of the slowest mode
+    ux = lat.field("ux").double().cpu().numpy().reshape(nz, ny, nx)
+    zc = np.arange(nz) + 0.5
+    exact = b / (2 * nu) * zc * (nz - zc)
+    assert np.max(np.abs(ux - exact[:, None, None])) < tol * exact.max()
+    assert np.abs(lat.field("uz").double().cpu().numpy()).max() < tol * exact.max()
+
+
+def test_faces_refused_by_batch():
+    case = _faces_2d()
+    lats = [gpu_lattice(case, "f32") for _ in range(2)]
+    with pytest.raises(P.DSMError) as e:
+        P._lib.dsm_batch_scratch_bytes([lat.h for lat in lats])
+    assert e.value.status == P._lib.DSM_E_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- stage 1
 @pytest.mark.parametrize("kind,shape", [(O.D2Q9, (24, 20)), (O.D3Q19, (14, 12, 10))])
 def test_solid_relaxation_fp64_parity(kind, shape):

@@ -195,6 +195,11 @@ def test_energy_gradient_fd(kind, shape, active):
     assert abs(t[3] + 0.02 * c2.sum()) < 1e-12
 
 
+def _mirror_faces(mirror):
+    """faces argument with both faces of each flagged axis a mirror."""
+    return tuple(f for m in mirror for f in (("mirror",) * 2 if m else ("periodic",) * 2))
+
+
 def _mirror_extend(a, shape, mirror):
     """The periodic field twice as long along each mirror axis: the lattice
     followed by its reflection (node x' >= n holds node 2n - 1 - x')."""
@@ -219,7 +224,8 @@ def test_mirror_energy_is_half_the_symmetric_domain(kind, shape, mirror, active)
     c1 = 0.6 * c1
     Smask = (np.arange(n) % 3 == 0).astype(np.uint8)
     kw = dict(active=active, dP=0.013, fg=0.0)
-    p = O.make_params(kind, shape, (0.7, 1.3, 0.9), alpha=1.2, beta=10.0, mirror=mirror)
+    p = O.make_params(kind, shape, (0.7, 1.3, 0.9), alpha=1.2, beta=10.0,
+                      faces=_mirror_faces(mirror))
     E, g, t = O.energy_grad(p, c1, c2, S=Smask, **kw)
     full = [_mirror_extend(v, shape, mirror) for v in (c1, c2, Smask)]
     fshape = tuple(reversed(full[0].shape))
@@ -242,17 +248,28 @@ def test_mirror_energy_is_half_the_symmetric_domain(kind, shape, mirror, active)
 def test_mirror_energy_gradient_fd(kind, shape, mirror):
     n = int(np.prod(shape))
     c1, c2 = S.random_fields(n, seed=13)
-    p = O.make_params(kind, shape, (0.8, 1.1, 0.9), alpha=1.0, mirror=mirror)
+    p = O.make_params(kind, shape, (0.8, 1.1, 0.9), alpha=1.0, faces=_mirror_faces(mirror))
     kw = dict(active=2, kcs=0.2, V0=0.5 * n, fg=0.03)
     E, g, _ = O.energy_grad(p, 0.5 * c1, c2, **kw)
     fd = _fd_grad(lambda x: O.energy_grad(p, 0.5 * c1, x, want_grad=False, **kw)[0], c2)
     assert np.max(np.abs(fd - g)) / np.max(np.abs(g)) < 1e-7
 
 
-def test_lb_functions_refuse_mirror_axes():
-    p = O.make_params(O.D2Q9, (6, 5), (0.8, 1.1, 0.9), mirror=(1, 0, 0))
-    with pytest.raises(ValueError):
-        O.lb_init(p, 2, None, np.full(30, 0.5))
+def test_wall_face_energy_is_the_mirror_energy():
+    # a bounce-back wall is neutral: its stencil sees the edge node's image,
+    # as a mirror face does, so the energy cannot tell them apart
+    shape = (6, 5)
+    c1, c2 = S.random_fields(30, seed=3)
+    pm = O.make_params(O.D2Q9, shape, (0.8, 1.1, 0.9), faces=_mirror_faces((0, 1, 0)))
+    pw = O.make_params(O.D2Q9, shape, (0.8, 1.1, 0.9),
+                       faces=("periodic", "periodic", "wall", "wall", "periodic", "periodic"))
+    Em, gm, _ = O.energy_grad(pm, 0.5 * c1, c2)
+    Ew, gw, _ = O.energy_grad(pw, 0.5 * c1, c2)
+    assert Em == Ew
+    np.testing.assert_array_equal(gm, gw)
+    with pytest.raises(ValueError):  # one face periodic, the other not
+        O.make_params(O.D2Q9, shape, (0.8, 1.1, 0.9),
+                      faces=("mirror", "periodic", "periodic", "periodic", "periodic", "periodic"))
 
 
 @pytest.mark.parametrize("kind,shape", [(O.D2Q9, (16, 16)), (O.D3Q19, (16, 16, 16))])
@@ -378,6 +395,110 @@ def test_axis_swap_symmetry_3d():
     uy = F["uy"].reshape(n, n, n)
     np.testing.assert_allclose(C, np.swapaxes(C, 1, 2), atol=1e-13)
     np.testing.assert_allclose(ux, np.swapaxes(uy, 1, 2), atol=1e-13)
+
+
+def _disc_sd(shape, centre, R):
+    """Signed distance to a disc, sphere or cylinder (positive inside); a
+    centre coordinate of None leaves that axis out."""
+    axes = np.meshgrid(*[np.arange(m, dtype=float) for m in reversed(shape)], indexing="ij")
+    r2 = sum((ax - c) ** 2 for ax, c in zip(reversed(axes), centre) if c is not None)
+    return R - np.sqrt(r2)
+
+
+@pytest.mark.parametrize("kind,half,mirror,steps", [(O.D2Q9, (14, 12), (1, 1, 0), 150),
+                                                    (O.D3Q19, (7, 6, 5), (1, 1, 0), 25)])
+def test_lb_mirror_faces_match_reflected_periodic(kind, half, mirror, steps):
+    """Specular reflection at mirror faces: a lattice with mirror faces evolves
+    exactly as its reflected periodic double does on the original nodes
+    (corner links that cross two faces included)."""
+    dim = len(half)
+    full = tuple(2 * m if mirror[a] else m for a, m in enumerate(half))
+    a_s = S.width_to_alpha(3.0)
+    # a solid disc / sphere about the corner (-1/2, -1/2) and a drop about the
+    # opposite corner: both symmetric under the reflections of the double
+    import itertools
+    hi = tuple(h - 0.5 if mirror[a] else None for a, h in enumerate(half))
+    R = min(half[a] for a in range(dim) if mirror[a]) / 2.0
+    # the corner (-1/2, -1/2) of the periodic double, with its periodic images
+    corners = itertools.product(*[(-0.5, f - 0.5) if mirror[a] else (None,)
+                                  for a, f in enumerate(full)])
+    sd = np.max([_disc_sd(full, c, R) for c in corners], axis=0)
+    c1f = O.solid_profile(sd.ravel(), a_s).reshape(sd.shape)
+    dsd = _disc_sd(full, hi, R - 0.5)
+    c2f = (0.5 + 0.5 * np.tanh(dsd / 2.0)) * (1.0 - c1f)
+    # the double is symmetric under each reflection x -> 2n - 1 - x
+    for a in range(dim):
+        if mirror[a]:
+            ax = dim - 1 - a
+            np.testing.assert_allclose(c1f, np.flip(c1f, axis=ax), atol=1e-15)
+            np.testing.assert_allclose(c2f, np.flip(c2f, axis=ax), atol=1e-15)
+    k, _ = O.kappa_from_angle(70.0, 0.01, 0.01)
+    body = (0.0, 0.0, 1e-5)[:3] if dim == 3 else (0.0, 0.0, 0.0)
+    pf = O.make_params(kind, full, k, alpha_s=a_s, body=body)
+    ph = O.make_params(kind, half, k, alpha_s=a_s, body=body, faces=_mirror_faces(mirror))
+    sl = tuple(slice(0, m) for m in reversed(half))
+    f, g = O.lb_init(pf, 2, c1f.ravel(), c2f.ravel())
+    _, _, Ff = O.lb_run(pf, 2, c1f.ravel(), f, g, steps, want_fields=True)
+    f, g = O.lb_init(ph, 2, c1f[sl].ravel(), c2f[sl].ravel())
+    _, _, Fh = O.lb_run(ph, 2, c1f[sl].ravel(), f, g, steps, want_fields=True)
+    assert np.abs(Fh["ux"]).max() > 1e-6
+    for name in ("C", "mu", "ux", "uy", "uz", "pt"):
+        np.testing.assert_allclose(Fh[name], Ff[name].reshape(sd.shape)[sl].ravel(),
+                                   rtol=0, atol=1e-13, err_msg=name)
+
+
+@pytest.mark.parametrize("kind,shape,faces,body", [
+    (O.D2Q9, (3, 12), ("periodic", "periodic", "wall", "wall", "periodic", "periodic"),
+     (1e-6, 0.0, 0.0)),
+    (O.D3Q19, (2, 3, 10), ("mirror", "mirror", "periodic", "periodic", "wall", "wall"),
+     (0.0, 1e-6, 0.0))])
+@pytest.mark.parametrize("tau", [0.8, 0.5 + math.sqrt(3.0 / 16.0), 1.5])
+def test_wall_poiseuille_closed_form(kind, shape, faces, body, tau):
+    """Halfway bounce-back walls: body-force Poiseuille flow of the BGK scheme.
+    The steady discrete solution is the parabola with walls half a node beyond
+    the edge nodes plus a constant slip b/(2 nu) (16 tau^2 - 16 tau + 1)/12,
+    which vanishes at tau = 1/2 + sqrt(3/16) (the known viscosity-dependent
+    slip of bounce-back with BGK, He, Zou, Luo & Dembo, J. Stat. Phys. 87,
+    1997)."""
+    n = int(np.prod(shape))
+    p = O.make_params(kind, shape, (0.01, 0.004, 0.007), tau2=tau, tau3=tau, body=body,
+                      faces=faces)
+    c1, c2 = np.zeros(n), np.ones(n)  # all liquid, no solid: mu = 0, F = b
+    f, g = O.lb_init(p, 2, c1, c2)
+    f, g, F = O.lb_run(p, 2, c1, f, g, int(8000 / math.sqrt(tau - 0.5)), want_fields=True)
+    H = shape[-1]
+    b = body[0] if kind == O.D2Q9 else body[1]
+    u = (F["ux"] if kind == O.D2Q9 else F["uy"]).reshape(tuple(reversed(shape)))
+    s = np.arange(H)
+    nu = (tau - 0.5) / 3.0
+    exact = b / (2 * nu) * ((s + 0.5) * (H - 0.5 - s) + (16 * tau * tau - 16 * tau + 1) / 12.0)
+    exact = exact.reshape((H,) + (1,) * (u.ndim - 1))
+    assert np.max(np.abs(u - exact)) < 1e-9 * np.max(exact)
+    other = F["uy"] if kind == O.D2Q9 else F["ux"]
+    assert np.abs(other).max() < 1e-14
+
+
+def test_faces_conserve_mass():
+    """Mirror and wall faces pass no mass: sum f and sum g are kept exactly
+    while a drop is driven into a wall and along a mirror plane (equal
+    densities: with a density contrast the pressure moment's u.G[rho]/2 term
+    moves sum f by itself)."""
+    nx, ny = 20, 16
+    n = nx * ny
+    dsd = _disc_sd((nx, ny), (4.0, 9.0), 5.0)
+    c2 = (0.5 + 0.5 * np.tanh(dsd / 2.0)).ravel()
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    for faces in [("mirror", "wall", "wall", "mirror", "periodic", "periodic"),
+                  ("wall", "wall", "wall", "wall", "periodic", "periodic")]:
+        p = O.make_params(O.D2Q9, (nx, ny), k, body=(-2e-5, 1e-5, 0.0), faces=faces,
+                          tau2=0.8, tau3=1.0)
+        c1 = np.zeros(n)
+        f, g = O.lb_init(p, 2, c1, c2)
+        f1, g1 = O.lb_run(p, 2, c1, f, g, 300)
+        assert abs(f1.sum() - f.sum()) < 1e-12 * f.sum()
+        assert abs(g1.sum() - g.sum()) < 1e-12 * g.sum()
+        ob = O.observables(p, c1, f1, g1)
+        assert ob["nonfinite"] == 0 and ob["kinetic"] > 0
 
 
 def test_link_q_planar():
