@@ -93,3 +93,63 @@ def width_10_90(profile: np.ndarray) -> float:
                 return k + (level - p[k]) / (p[k + 1] - p[k])
         raise ValueError("level not crossed")
     return cross(0.9) - cross(0.1)
+
+
+def sample_bilinear(field: np.ndarray, px: np.ndarray, py: np.ndarray) -> np.ndarray:
+    """Bilinear interpolation of a (ny, nx) field at points (px, py), node
+    coordinates, clamped to the lattice."""
+    ny, nx = field.shape
+    px = np.clip(px, 0.0, nx - 1.0)
+    py = np.clip(py, 0.0, ny - 1.0)
+    x0 = np.minimum(np.floor(px).astype(int), nx - 2)
+    y0 = np.minimum(np.floor(py).astype(int), ny - 2)
+    fx, fy = px - x0, py - y0
+    f00, f10 = field[y0, x0], field[y0, x0 + 1]
+    f01, f11 = field[y0 + 1, x0], field[y0 + 1, x0 + 1]
+    return (1 - fy) * ((1 - fx) * f00 + fx * f10) + fy * ((1 - fx) * f01 + fx * f11)
+
+
+def meniscus_position(c2: np.ndarray, entrance, direction, length: float, ds: float = 0.25,
+                      start: float = -5.0) -> float:
+    """Distance along a channel's axis, from its entrance, of the liquid front:
+    the first point past `start` where C2 along the axis drops below 1/2
+    (bilinear interpolation of the field, linear between samples).  Returns
+    `length` when the channel is full, `start` when it is empty."""
+    s = np.arange(start, length + ds / 2, ds)
+    v = sample_bilinear(c2, entrance[0] + s * direction[0], entrance[1] + s * direction[1])
+    below = np.flatnonzero(v < 0.5)
+    if below.size == 0:
+        return float(length)
+    k = below[0]
+    if k == 0:
+        return float(start)
+    return float(s[k - 1] + ds * (v[k - 1] - 0.5) / (v[k - 1] - v[k]))
+
+
+def lucas_washburn_fit(t: np.ndarray, L: np.ndarray):
+    """Least-squares fit of L = L0 + k sqrt(t - t0) (Sec. IV, Eq. [eqn:cfilling],
+    t0 and L0 the constants of the initial entry).  For each t0 the model is
+    linear in (L0, k); t0 is found by a bounded scalar search below the first
+    sample.  Returns (k, L0, t0, rms residual)."""
+    from scipy.optimize import minimize_scalar
+    t = np.asarray(t, dtype=np.float64)
+    L = np.asarray(L, dtype=np.float64)
+
+    def solve(t0):
+        A = np.stack([np.ones_like(t), np.sqrt(t - t0)], axis=1)
+        coef, *_ = np.linalg.lstsq(A, L, rcond=None)
+        r = A @ coef - L
+        return coef, float(np.sqrt(np.mean(r * r)))
+
+    span = t[-1] - t[0]
+    res = minimize_scalar(lambda t0: solve(t0)[1], bounds=(t[0] - 10.0 * span, t[0] - 1e-9),
+                          method="bounded", options={"xatol": 1e-6 * span})
+    (L0, k), rms = solve(res.x)
+    return float(k), float(L0), float(res.x), rms
+
+
+def washburn_angle(k: float, gamma: float, H: float, eta: float) -> float:
+    """Contact angle (degrees) that makes the Lucas-Washburn prefactor
+    sqrt(gamma H cos(theta) / (3 eta)) equal to k."""
+    c = 3.0 * eta * k * k / (gamma * H)
+    return math.degrees(math.acos(max(-1.0, min(1.0, c))))

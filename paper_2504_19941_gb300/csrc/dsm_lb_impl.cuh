@@ -169,26 +169,26 @@ __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y
   Hood h;
   h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  // the moving populations are small next to the rest one (g_0 ~ C): summing
+  // them first and adding g_0 last rounds once at the scale of C instead of
+  // Q - 1 times, which keeps FP32 from drifting the liquid mass
+  const T g0 = Store<S>::k16 ? T(a.g0_in[n]) : load_g<T, S>(a.gin[0], n);
   T s = T(0);
   if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
     // a node on a mirror or wall face: the pulled g follow the face rules
 #pragma unroll 1
-    for (int i = 0; i < L::Q; i++) {
+    for (int i = 1; i < L::Q; i++) {
       int k;
       const int cr = face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &k);
       const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(i));
-      if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
-      else s += load_g<T, S>(a.gin[k], src);
+      s += load_g<T, S>(a.gin[k], src);
     }
-    a.C[n] = s;
+    a.C[n] = g0 + s;
     return;
   }
 #pragma unroll
-  for (int i = 0; i < L::Q; i++) {
-    if (Store<S>::k16 && i == 0) s += T(a.g0_in[n]);
-    else s += load_g<T, S>(a.gin[i], h.minus<L>(i));
-  }
-  a.C[n] = s;
+  for (int i = 1; i < L::Q; i++) s += load_g<T, S>(a.gin[i], h.minus<L>(i));
+  a.C[n] = g0 + s;
 }
 
 template <int K, class T, class S>

@@ -337,6 +337,42 @@ def pillar_gap_2d(period=64, height=120, width=24, pillar=40, base=6, theta=112.
                 alpha_s=solid_width, extra={"gap": np.flatnonzero(gap), "s": s})
 
 
+def capillary_channel_2d(nx=1750, ny=450, length=900.0, width=40.0, angle_deg=20.0,
+                         entrance=(300.0, 71.0), reservoir=120.0, theta=60.0, g=2.5e-3,
+                         seed=0) -> Case:
+    """Lattice Boltzmann capillary filling (Sec. IV, "Capillary Filling
+    Dynamics"): a solid slab crossed by a straight channel of the given length
+    and width, its axis inclined by angle_deg to the x axis so that the solid
+    does not align to the grid; a finite liquid reservoir against the slab's
+    entrance face, gas elsewhere.  Periodic left/right, mirror top/bottom.
+    Liquid viscosity 1/6, gas 2/300, equal densities, M = 1/6 (tau = 1,
+    0.52 and tau_g = 1).
+
+    Channel coordinates: s along the axis from the entrance point, t across
+    it.  The solid is {0 <= s <= length} minus {|t| < width/2}; solid_sd is its
+    signed distance (positive inside) as the smaller of the two constraints'
+    distances, extra['mask'] the sharp region S from which the paper relaxes
+    the solid first.  The reservoir is {-reservoir <= s < 0}: c2 is its tanh
+    profile in s (the caller multiplies it by 1 - C1 once the solid is set).
+    extra holds the axis (entrance, direction), the channel length and width."""
+    shape = (nx, ny)
+    x, y = _coords(shape)
+    a = math.radians(angle_deg)
+    d = (math.cos(a), math.sin(a))
+    xe, ye = entrance
+    sx = (x - xe) * d[0] + (y - ye) * d[1]
+    tx = -(x - xe) * d[1] + (y - ye) * d[0]
+    sd = np.minimum(np.minimum(sx, length - sx), np.abs(tx) - width / 2.0)
+    c2 = 0.25 * (1.0 + np.tanh((sx + reservoir) / 2.0)) * (1.0 - np.tanh(sx / 2.0))
+    c2 = c2.ravel() + perturbation(seed, nx * ny)
+    return Case("capillary_channel_2d", "D2Q9", shape, sd.ravel(), c2, theta_deg=theta, g23=g,
+                g12=g, alpha_s=1.0, tau2=1.0, tau3=0.5 + 3.0 * 2.0 / 300.0, tau_g=1.0,
+                faces=("periodic", "periodic", "mirror", "mirror", "periodic", "periodic"),
+                extra={"mask": (sd.ravel() > 0).astype(np.uint8), "entrance": (xe, ye),
+                       "direction": d, "length": length, "width": width,
+                       "beta": 1e-3, "omega": 2e-4, "solid_steps": 5000})
+
+
 def random_fields(n, seed=0, lo=0.05, hi=0.95):
     """Independent uniform fields in [lo, hi) for finite-difference checks."""
     rng = np.random.default_rng(seed)

@@ -279,14 +279,17 @@ def test_faces_solid_relaxation_fp64():
     assert rel_err(lat.field("C1").cpu().numpy(), c1_o) < 1e-12
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-4)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 2e-3)])
 def test_wall_poiseuille_closed_form_gpu(prec, tol):
     # halfway bounce-back between two walls at tau = 1/2 + sqrt(3/16): the
     # steady profile is the parabola with the walls half a node out (the BGK
-    # slip (16 tau^2 - 16 tau + 1)/12 vanishes), at a size the oracle is not run
+    # slip (16 tau^2 - 16 tau + 1)/12 vanishes), at a size the oracle is not run.
+    # FP32: the per-step forcing increment 3 w_i b is about 900 ulps of w_i
+    # here, and its rounding biases u by about 1/900 (at b = 1e-6 it was 45
+    # ulps and 1 %)
     nx, ny, nz = 4, 6, 40
     tau = 0.5 + math.sqrt(3.0 / 16.0)
-    b = 1e-6
+    b = 2e-5
     n = nx * ny * nz
     case = S.Case("poiseuille", "D3Q19", (nx, ny, nz), np.full(n, -50.0), np.ones(n),
                   theta_deg=90.0, g23=0.01, g12=0.01, tau2=tau, tau3=tau, body=(b, 0.0, 0.0),

@@ -22,6 +22,10 @@ term, a wrong sign or index, a transposed operand -- fails at least one:
   interface thermodynamics ......... test_flat_interface_profile_and_tension, test_laplace_em
   wetting .......................... test_young_em, test_young_lb
   gravity energy ................... test_jurin_em
+  mirror and wall faces (LB) ....... test_lb_mirror_faces_match_reflected_periodic,
+                                     test_wall_poiseuille_closed_form, test_faces_conserve_mass
+  capillary filling analysis ....... test_lucas_washburn_fit_recovers_known_curve,
+                                     test_meniscus_position_on_an_inclined_axis
   pressure term, wetting transition  test_critical_pressure_em
 Parity unpinned: the L-BFGS iteration trajectory (only its converged results
 are used, through the pins above).
@@ -499,6 +503,30 @@ def test_faces_conserve_mass():
         assert abs(g1.sum() - g.sum()) < 1e-12 * g.sum()
         ob = O.observables(p, c1, f1, g1)
         assert ob["nonfinite"] == 0 and ob["kinetic"] > 0
+
+
+def test_lucas_washburn_fit_recovers_known_curve():
+    # the fit of Eq. [eqn:cfilling] on samples of L0 + k sqrt(t - t0), exact and
+    # with noise; and the angle that gives a prefactor back
+    t = np.linspace(2000.0, 300000.0, 60)
+    k, L0, t0, rms = A.lucas_washburn_fit(t, 3.0 + 0.3 * np.sqrt(t - 50.0))
+    assert abs(k - 0.3) < 1e-6 and abs(L0 - 3.0) < 1e-3 and rms < 1e-4
+    noisy = 3.0 + 0.3 * np.sqrt(t - 50.0) + np.random.default_rng(0).normal(0.0, 0.05, t.size)
+    assert abs(A.lucas_washburn_fit(t, noisy)[0] - 0.3) < 2e-3
+    kk = math.sqrt(2.5e-3 * 40.0 * math.cos(math.radians(60.0)) / (3.0 / 6.0))
+    assert abs(A.washburn_angle(kk, 2.5e-3, 40.0, 1.0 / 6.0) - 60.0) < 1e-9
+
+
+def test_meniscus_position_on_an_inclined_axis():
+    ny, nx = 120, 300
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    a = math.radians(20.0)
+    d, e = (math.cos(a), math.sin(a)), (40.0, 20.0)
+    s = (x - e[0]) * d[0] + (y - e[1]) * d[1]
+    for s0 in (12.3, 57.71, 100.0):
+        c2 = 0.5 * (1.0 - np.tanh((s - s0) / 2.0))
+        assert abs(A.meniscus_position(c2, e, d, 200.0) - s0) < 0.02
+    assert A.meniscus_position(np.ones((ny, nx)), e, d, 200.0) == 200.0
 
 
 def test_link_q_planar():
