@@ -155,6 +155,15 @@ dsm_status dsm_set_solid(dsm_lattice *h, const void *d_field, int kind);
 dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int steps,
                            double beta, double omega);
 
+/* The solid region of the current diffuse solid: d_mask[n] = 1 where
+ * C1 > 1/2, else 0 (nx*ny*nz bytes, device, caller-owned).  This is the
+ * redefinition step of the two-step solid initialisation for sharp corners
+ * (Sec. II.B, after Eq. [frozen:poly-quadratic_lbm]): a short dsm_relax_solid
+ * with larger beta and Omega, then S := {C1 > 1/2} by this call, then a
+ * further dsm_relax_solid with the new S.  DSM_E_STATE before any solid was
+ * set. */
+dsm_status dsm_solid_region(dsm_lattice *h, unsigned char *d_mask);
+
 /* Set the liquid field C2 (nx*ny*nz reals) and initialise the populations at
  * rest: f_i = w_i, g_i = g_eq_i(C2, mu(C2), u = 0).  Resets the step counter
  * and any latched error. */

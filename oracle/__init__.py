@@ -252,6 +252,28 @@ def lb_fields(p: Params, stage: int, c1, f, g, S=None):
     return dict(zip(FIELD_NAMES, fields.reshape(8, n)))
 
 
+def relax_solid(p: Params, S, c1, steps: int, beta: float, omega: float):
+    """Stage-1 relaxation (Sec. II.B, solid initialisation): from C1 at rest,
+    `steps` LB steps with confinement to the region S at strength beta and
+    range penalty omega; returns the relaxed C1."""
+    q = Params.from_buffer_copy(p)
+    q.beta, q.omega = beta, omega
+    S = np.ascontiguousarray(S, dtype=np.uint8).ravel()
+    f, g = lb_init(q, 1, None, c1, S=S)
+    f, g = lb_run(q, 1, None, f, g, steps, S=S)
+    return lb_fields(q, 1, None, f, g, S=S)["C"]
+
+
+def solid_two_step(p: Params, S, c1, steps1, beta1, omega1, steps2, beta2, omega2):
+    """Two-step solid initialisation for sharp corners (Sec. II.B, after
+    Eq. [frozen:poly-quadratic_lbm]): a short relaxation with larger beta and
+    Omega, the region redefined as S := {C1 > 1/2}, then a further relaxation
+    with the new S (from the relaxed C1, at rest).  Returns (C1, new S)."""
+    c1a = relax_solid(p, S, c1, steps1, beta1, omega1)
+    S2 = (c1a > 0.5).astype(np.uint8)
+    return relax_solid(p, S2, c1a, steps2, beta2, omega2), S2
+
+
 def energy_grad(p: Params, c1, c2, *, active=2, S=None, dP=0.0, kcs=0.0, V0=0.0, fg=0.0,
                 want_grad=True):
     """Discrete free energy E, its gradient w.r.t. the active field, and the terms

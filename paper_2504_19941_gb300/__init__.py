@@ -99,6 +99,24 @@ class Lattice:
         assert mask.dtype.itemsize == 1 and mask.numel() == self.n and mask.is_cuda
         _lib.dsm_relax_solid(self.h, mask, steps, beta, omega)
 
+    def solid_region(self, out=None):
+        """S = {C1 > 1/2} of the current diffuse solid, a uint8 device tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        _lib.dsm_solid_region(self.h, out)
+        return out
+
+    def relax_solid_two_step(self, mask, steps1: int, beta1: float, omega1: float, steps2: int,
+                             beta2: float, omega2: float):
+        """The two-step solid initialisation for sharp corners (Sec. II.B): a
+        short relaxation with larger beta and Omega, S := {C1 > 1/2}, then a
+        further relaxation with the new S.  Returns the new S."""
+        self.relax_solid(mask, steps1, beta1, omega1)
+        region = self.solid_region()
+        self.relax_solid(region, steps2, beta2, omega2)
+        return region
+
     def set_fluid(self, c2):
         _lib.dsm_set_fluid(self.h, self._field_arg(c2))
 

@@ -24,7 +24,7 @@ DSM_G_AUTO, DSM_G_POPULATIONS = 0, 1
 
 EXPORTED = (
     "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
-    "dsm_set_solid", "dsm_relax_solid", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
+    "dsm_set_solid", "dsm_relax_solid", "dsm_solid_region", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
     "dsm_step_collide", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
@@ -85,6 +85,7 @@ def load():
         "dsm_create": (st, [P, vp, C.c_size_t, vp, C.POINTER(vp)]),
         "dsm_set_solid": (st, [vp, vp, C.c_int]),
         "dsm_relax_solid": (st, [vp, vp, C.c_int, C.c_double, C.c_double]),
+        "dsm_solid_region": (st, [vp, vp]),
         "dsm_set_fluid": (st, [vp, vp]),
         "dsm_step": (st, [vp, C.c_longlong]),
         "dsm_step_moments": (st, [vp]),
@@ -197,6 +198,10 @@ def dsm_set_solid(h: int, field, kind: int):
 
 def dsm_relax_solid(h: int, mask, steps: int, beta: float, omega: float):
     _check(load().dsm_relax_solid(h, _ptr(mask), steps, beta, omega), "dsm_relax_solid")
+
+
+def dsm_solid_region(h: int, mask):
+    _check(load().dsm_solid_region(h, _ptr(mask)), "dsm_solid_region")
 
 
 def dsm_set_fluid(h: int, c2):

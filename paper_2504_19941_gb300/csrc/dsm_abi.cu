@@ -206,6 +206,15 @@ __global__ void obs_finalize_kernel(const double *partials, long long nb, double
   if (threadIdx.x < OBS_K) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// S = {C1 > 1/2} (dsm_solid_region)
+template <class T>
+__global__ void __launch_bounds__(256) solid_region_kernel(const T *c1, unsigned char *mask,
+                                                           long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    mask[k] = c1[k] > T(0.5) ? 1 : 0;
+}
+
 extern "C" {
 
 const char *dsm_status_string(dsm_status s) {
@@ -362,6 +371,20 @@ dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int step
   h->has_solid = true;
   h->has_fluid = false;
   return DSM_OK;
+}
+
+dsm_status dsm_solid_region(dsm_lattice *h, unsigned char *d_mask) {
+  if (!h || !d_mask) return DSM_E_INVAL;
+  if (!h->has_solid) return DSM_E_STATE;
+  long long blocks = (h->N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (h->tab.real_bytes == 8)
+    solid_region_kernel<double><<<(int)blocks, 256, 0, h->stream>>>((const double *)h->C1, d_mask,
+                                                                    h->N);
+  else
+    solid_region_kernel<float><<<(int)blocks, 256, 0, h->stream>>>((const float *)h->C1, d_mask,
+                                                                   h->N);
+  return cuda_status(cudaGetLastError());
 }
 
 dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2) {

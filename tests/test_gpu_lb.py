@@ -334,6 +334,25 @@ def test_solid_relaxation_fp64_parity(kind, shape):
     assert rel_err(c1_g, c1_o) < 1e-12
 
 
+@pytest.mark.parametrize("faces", [None, ("mirror", "mirror", "wall", "wall", "periodic",
+                                           "periodic")])
+def test_two_step_solid_fp64_parity(faces):
+    # short run with larger beta and Omega, S := {C1 > 1/2}, further run
+    n = 40
+    y, x = np.mgrid[0:n, 0:n]
+    S0 = ((abs(x - 19.5) < 8) & (abs(y - 13.5) < 8)).astype(np.uint8).ravel()
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    po = O.make_params(O.D2Q9, (n, n), k, faces=faces)
+    c1_o, S2_o = O.solid_two_step(po, S0, S0.astype(float), 300, 1e-2, 2e-3, 700, 1e-3, 2e-4)
+    pp = P.make_params("D2Q9", (n, n), "f64", theta_deg=90.0, g12=0.01, g23=0.01, faces=faces)
+    lat = P.Lattice(pp)
+    lat.set_solid_c1(torch.as_tensor(S0.astype(float), device="cuda"))
+    S2 = lat.relax_solid_two_step(torch.as_tensor(S0, device="cuda"), 300, 1e-2, 2e-3, 700,
+                                  1e-3, 2e-4)
+    np.testing.assert_array_equal(S2.cpu().numpy(), S2_o)
+    assert rel_err(lat.field("C1").cpu().numpy(), c1_o) < 1e-12
+
+
 # ---------------------------------------------------------------- full size
 def _block_indices(shape, centre, r=4):
     nx, ny, nz = shape

@@ -529,6 +529,49 @@ def test_meniscus_position_on_an_inclined_axis():
     assert A.meniscus_position(np.ones((ny, nx)), e, d, 200.0) == 200.0
 
 
+def _square(n=40, half=8):
+    y, x = np.mgrid[0:n, 0:n]
+    c = (n - 1) / 2.0
+    return ((abs(x - c) < half) & (abs(y - c) < half)).astype(np.uint8).ravel()
+
+
+def test_two_step_solid_rounds_the_corners():
+    """Two-step solid initialisation (Sec. II.B): a diffuse profile cannot
+    follow a square's corners, so a one-step relaxation leaves nodes where the
+    confinement still pulls; after the redefinition S := {C1 > 1/2} the final
+    C1 agrees with its region everywhere.  The redefined region has rounded
+    corners; the stage-1 dynamics conserve sum C1, so the mass taken from the
+    corners moves the middles of the edges out by a node; and it keeps the
+    square's symmetry."""
+    n = 40
+    S0 = _square(n)
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    p = O.make_params(O.D2Q9, (n, n), k)
+
+    def wrong_side(c1, S):
+        return int((((S == 1) & (c1 < 0.5)) | ((S == 0) & (c1 > 0.5))).sum())
+    c1_one = O.relax_solid(p, S0, S0.astype(float), 3000, 1e-3, 2e-4)
+    c1_two, S2 = O.solid_two_step(p, S0, S0.astype(float), 500, 1e-2, 2e-3, 2500, 1e-3, 2e-4)
+    assert wrong_side(c1_one, S0) > 20
+    assert wrong_side(c1_two, S2) == 0
+    c1a = O.relax_solid(p, S0, S0.astype(float), 500, 1e-2, 2e-3)
+    np.testing.assert_array_equal(S2, (c1a > 0.5).astype(np.uint8))
+    assert abs(c1a.sum() - S0.sum()) < 1e-10 * S0.sum()
+    c = (n - 1) / 2.0
+    d = S2.astype(int) - S0.astype(int)
+    for idx, corner in ((np.flatnonzero(d < 0), True), (np.flatnonzero(d > 0), False)):
+        assert idx.size > 0
+        y, x = np.divmod(idx, n)
+        ax, ay = abs(x - c), abs(y - c)
+        if corner:   # lost: near the corners (both offsets large)
+            assert np.all(np.minimum(ax, ay) >= 5.5)
+        else:        # gained: one row out, near the middle of an edge
+            assert np.all((np.maximum(ax, ay) == 8.5) & (np.minimum(ax, ay) <= 2.5))
+    sq = S2.reshape(n, n)
+    np.testing.assert_array_equal(sq, sq.T)
+    np.testing.assert_array_equal(sq, sq[::-1, :])
+
+
 def test_link_q_planar():
     # a planar tanh profile with its C1 = 1/2 surface a distance delta from the
     # node: the link fraction is delta / (n.d) / |c|
