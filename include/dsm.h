@@ -256,6 +256,34 @@ dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const floa
                               float *d_grad, double *d_terms, void *d_scratch,
                               size_t scratch_bytes, void *cuda_stream);
 
+/* Free energy of N = nfluid fluid components on a frozen solid (the N + 1
+ * component model of Sec. II.A, which the paper states for any N and
+ * demonstrates for N = 2).  Components: C_1 the solid (d_c1), the free fluids
+ * C_2 .. C_N (d_c: N - 1 planes of nx*ny*nz floats, plane f holding
+ * C_{2+f}), and C_{N+1} = 1 - C_1 - (C_2 + .. + C_N).  Each component k
+ * carries kappa_k/2 C_k^2 (1 - C_k)^2 and the lattice-weighted gradient term
+ * of dsm_fe_energy_grad with its own kappa_k (host array kappa, N + 1 values:
+ * kappa_1 .. kappa_{N+1}), so any two components meet with tension
+ * alpha (kappa_m + kappa_n) / 6.  Each free fluid f carries its own pressure
+ * term -dP[f] V_f (kcs[f] == 0) or volume constraint kcs[f]/2 (V_f - V0[f])^2
+ * (host arrays of N - 1 values; null for zeros), V_f = sum_x C_{2+f}.  No
+ * gravity or confinement term.  From p: lattice, sizes, alpha and faces (the
+ * tensions of p are not used).
+ *   d_grad: N - 1 planes, dE/dC_{2+f} = d_{2+f} - d_{N+1} + the constraint's
+ *   derivative, d_k = kappa_k b(C_k) - alpha^2 kappa_k L[C_k].
+ *   d_terms (optional, 3 + N - 1 doubles): bulk, gradient, constraint, V_2..V_N.
+ * 2 <= nfluid <= 4; every fluid kappa (k >= 2) > 0; kcs >= 0; otherwise
+ * DSM_E_INVAL.  With N = 2 this is the stage-2 energy of dsm_fe_energy_grad
+ * without gravity.  d_scratch: at least dsm_fe_multi_scratch_bytes() bytes,
+ * 256-byte aligned.  Asynchronous on the stream. */
+dsm_status dsm_fe_multi_scratch_bytes(int lattice, int nx, int ny, int nz, int nfluid,
+                                      size_t *bytes);
+dsm_status dsm_fe_energy_grad_multi(const dsm_params *p, int nfluid, const double *kappa,
+                                    const float *d_c1, const float *d_c, const double *dP,
+                                    const double *kcs, const double *V0, double *d_energy,
+                                    float *d_grad, double *d_terms, void *d_scratch,
+                                    size_t scratch_bytes, void *cuda_stream);
+
 /* Allocation-free variant of dsm_fe_energy_grad, for callers that cannot
  * allocate device memory at all (a host program that links only this library
  * and has no CUDA allocator of its own, or an application whose device memory
@@ -356,6 +384,18 @@ dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
                               dsm_lbfgs_info *info, void *cuda_stream);
 dsm_status dsm_lbfgs_compact(int k, const double *SY, const double *YY, const double *a,
                              const double *b, double gamma, double *cx, double *cs, double *cy);
+
+/* The same L-BFGS over the N - 1 free fluid fields of dsm_fe_energy_grad_multi
+ * together (d_x: N - 1 planes, overwritten with the final point; the solid
+ * d_c1 fixed).  The rms gradient is taken over all planes.  d_work: at least
+ * dsm_lbfgs_multi_workspace_bytes(p, nfluid, m) bytes, 256-byte aligned. */
+dsm_status dsm_lbfgs_multi_workspace_bytes(const dsm_params *p, int nfluid, int m,
+                                           size_t *bytes);
+dsm_status dsm_lbfgs_minimize_multi(const dsm_params *p, int nfluid, const double *kappa,
+                                    const float *d_c1, const double *dP, const double *kcs,
+                                    const double *V0, float *d_x, int m, double tol,
+                                    long long max_iter, void *d_work, size_t work_bytes,
+                                    dsm_lbfgs_info *info, void *cuda_stream);
 
 /* Batched step: advance handle i by nsteps[i] stage-2 steps, all handles in
  * ONE persistent cooperative launch.  Resident blocks walk a work list of

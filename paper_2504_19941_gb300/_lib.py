@@ -31,6 +31,8 @@ EXPORTED = (
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
     "dsm_vec_axpby", "dsm_lbfgs_direction", "dsm_vec_dots_scratch_bytes", "dsm_vec_dots",
     "dsm_vec_lincomb", "dsm_lbfgs_workspace_bytes", "dsm_lbfgs_minimize", "dsm_lbfgs_compact",
+    "dsm_fe_multi_scratch_bytes", "dsm_fe_energy_grad_multi", "dsm_lbfgs_multi_workspace_bytes",
+    "dsm_lbfgs_minimize_multi",
     "dsm_batch_scratch_bytes", "dsm_batch_step",
     "dsm_destroy",
 )
@@ -120,6 +122,14 @@ def load():
                                     C.c_double, fp, C.c_int, C.c_double, C.c_longlong, vp,
                                     C.c_size_t, C.POINTER(dsm_lbfgs_info), vp]),
         "dsm_lbfgs_compact": (st, [C.c_int, dp, dp, dp, dp, C.c_double, dp, dp, dp]),
+        "dsm_fe_multi_scratch_bytes": (st, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                            C.POINTER(C.c_size_t)]),
+        "dsm_fe_energy_grad_multi": (st, [P, C.c_int, dp, fp, fp, dp, dp, dp, vp, fp, vp, vp,
+                                          C.c_size_t, vp]),
+        "dsm_lbfgs_multi_workspace_bytes": (st, [P, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_lbfgs_minimize_multi": (st, [P, C.c_int, dp, fp, dp, dp, dp, fp, C.c_int,
+                                          C.c_double, C.c_longlong, vp, C.c_size_t,
+                                          C.POINTER(dsm_lbfgs_info), vp]),
         "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
         "dsm_destroy": (st, [vp]),
@@ -335,6 +345,56 @@ def dsm_vec_lincomb(n: int, nv: int, V, stride: int, coef, x, cx: float, y, stre
     arr = (C.c_double * max(nv, 1))(*[float(v) for v in coef[:nv]])
     _check(load().dsm_vec_lincomb(n, nv, _ptr(V), stride, arr, _ptr(x), float(cx), _ptr(y),
                                   _stream(stream)), "dsm_vec_lincomb")
+
+
+def _doubles(v, n):
+    """Host double array of n values (None -> None)."""
+    if v is None:
+        return None
+    vals = [float(x) for x in v]
+    if len(vals) != n:
+        raise ValueError(f"expected {n} values, got {len(vals)}")
+    return (C.c_double * n)(*vals)
+
+
+def dsm_fe_multi_scratch_bytes(lattice: int, nx: int, ny: int, nz: int, nfluid: int) -> int:
+    n = C.c_size_t()
+    _check(load().dsm_fe_multi_scratch_bytes(lattice, nx, ny, nz, nfluid, C.byref(n)),
+           "dsm_fe_multi_scratch_bytes")
+    return n.value
+
+
+def dsm_fe_energy_grad_multi(params: dsm_params, nfluid: int, kappa, c1, c, dP, kcs, V0, energy,
+                             grad, terms, scratch, scratch_bytes: int, stream=None):
+    nf = nfluid - 1
+    _check(load().dsm_fe_energy_grad_multi(C.byref(params), nfluid, _doubles(kappa, nfluid + 1),
+                                           _ptr(c1), _ptr(c), _doubles(dP, nf), _doubles(kcs, nf),
+                                           _doubles(V0, nf), _ptr(energy), _ptr(grad),
+                                           _ptr(terms), _ptr(scratch), scratch_bytes,
+                                           _stream(stream)),
+           "dsm_fe_energy_grad_multi")
+
+
+def dsm_lbfgs_multi_workspace_bytes(params: dsm_params, nfluid: int, m: int) -> int:
+    b = C.c_size_t()
+    _check(load().dsm_lbfgs_multi_workspace_bytes(C.byref(params), nfluid, m, C.byref(b)),
+           "dsm_lbfgs_multi_workspace_bytes")
+    return b.value
+
+
+def dsm_lbfgs_minimize_multi(params: dsm_params, nfluid: int, kappa, c1, dP, kcs, V0, x, m: int,
+                             tol: float, max_iter: int, work, work_bytes: int, stream=None,
+                             check=True) -> dict:
+    info = dsm_lbfgs_info()
+    nf = nfluid - 1
+    s = load().dsm_lbfgs_minimize_multi(C.byref(params), nfluid, _doubles(kappa, nfluid + 1),
+                                        _ptr(c1), _doubles(dP, nf), _doubles(kcs, nf),
+                                        _doubles(V0, nf), _ptr(x), m, tol, max_iter, _ptr(work),
+                                        work_bytes, C.byref(info), _stream(stream))
+    if check:
+        _check(s, "dsm_lbfgs_minimize_multi")
+    return dict(iterations=info.iterations, evaluations=info.evaluations, energy=info.energy,
+                rms_grad=info.rms_grad, converged=bool(info.converged), status=s)
 
 
 def dsm_lbfgs_workspace_bytes(params: dsm_params, m: int) -> int:

@@ -675,6 +675,35 @@ dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const floa
                                (cudaStream_t)cuda_stream));
 }
 
+dsm_status dsm_fe_multi_scratch_bytes(int lattice, int nx, int ny, int nz, int nfluid,
+                                      size_t *bytes) {
+  if (!bytes || (lattice != DSM_D2Q9 && lattice != DSM_D3Q19) || nx < 1 || ny < 1 || nz < 1)
+    return DSM_E_INVAL;
+  if (nfluid < 2 || nfluid > FEM_MAX_NF + 1) return DSM_E_INVAL;
+  *bytes = fe_multi_scratch_bytes(lattice, nx, ny, nz, nfluid - 1);
+  return DSM_OK;
+}
+
+dsm_status dsm_fe_energy_grad_multi(const dsm_params *p, int nfluid, const double *kappa,
+                                    const float *d_c1, const float *d_c, const double *dP,
+                                    const double *kcs, const double *V0, double *d_energy,
+                                    float *d_grad, double *d_terms, void *d_scratch,
+                                    size_t scratch_bytes, void *cuda_stream) {
+  if (!d_c1 || !d_c || !d_grad || !d_scratch) return DSM_E_INVAL;
+  FEMArgs a;
+  FEMCons cons;
+  dsm_status s = fem_args_of(p, nfluid, kappa, dP, kcs, V0, &a, &cons);
+  if (s != DSM_OK) return s;
+  if (scratch_bytes < fe_multi_scratch_bytes(p->lattice, p->nx, p->ny, p->nz, a.nf) ||
+      ((uintptr_t)d_scratch & 255u))
+    return DSM_E_WORKSPACE;
+  a.c1 = d_c1;
+  a.c = d_c;
+  a.grad = d_grad;
+  return cuda_status(fe_multi_launch(p->lattice, a, cons, d_energy, d_terms, d_scratch,
+                                     (cudaStream_t)cuda_stream));
+}
+
 dsm_status dsm_vec_scratch_bytes(long long n, size_t *bytes) {
   if (!bytes || n < 0) return DSM_E_INVAL;
   *bytes = vec_scratch_bytes(n);

@@ -1,6 +1,7 @@
 // dsm_em.cu -- free energy + gradient kernel of the phase-field energy
 // minimisation (Sec. II.A of the paper) and the FP64-accumulating vector
 // kernels of its L-BFGS driver.
+#include <math.h>
 #include <string.h>
 
 #include "dsm_em.cuh"
@@ -145,6 +146,42 @@ __global__ void add_dev_scalar_kernel(long long n, const double *c, float *g) {
     g[k] += v;
 }
 
+dsm_status fem_args_of(const dsm_params *p, int nfluid, const double *kappa, const double *dP,
+                       const double *kcs, const double *V0, FEMArgs *a, FEMCons *cons) {
+  if (!p || !kappa || !a || !cons) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == DSM_D2Q9 && p->nz != 1))
+    return DSM_E_INVAL;
+  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
+  if (nfluid < 2 || nfluid > FEM_MAX_NF + 1 || !(p->alpha > 0.0)) return DSM_E_INVAL;
+  if (!faces_valid(p)) return DSM_E_INVAL;
+  memset(a, 0, sizeof(*a));
+  memset(cons, 0, sizeof(*cons));
+  a->nx = p->nx;
+  a->ny = p->ny;
+  a->nz = p->nz;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int i = 0; i < 3; i++) {
+    a->lo[i] = p->face[2 * i] ? 0 : n[i] - 1;
+    a->hi[i] = p->face[2 * i + 1] ? n[i] - 1 : 0;
+  }
+  a->nf = nfluid - 1;
+  for (int k = 0; k <= nfluid; k++) {
+    if (k > 0 && !(kappa[k] > 0.0)) return DSM_E_INVAL;  // every fluid needs its bulk term
+    if (!isfinite(kappa[k])) return DSM_E_INVAL;
+    a->kappa[k] = (float)kappa[k];
+  }
+  for (int f = 0; f < a->nf; f++) {
+    cons->dP[f] = dP ? dP[f] : 0.0;
+    cons->kcs[f] = kcs ? kcs[f] : 0.0;
+    cons->V0[f] = V0 ? V0[f] : 0.0;
+    if (cons->kcs[f] < 0.0) return DSM_E_INVAL;
+  }
+  a->a2 = (float)(p->alpha * p->alpha);
+  a->plane = (long long)p->nx * p->ny * p->nz;
+  return DSM_OK;
+}
+
 dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, double fg,
                       FEArgs *a) {
   memset(a, 0, sizeof(*a));
@@ -205,6 +242,177 @@ cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, doub
     add_dev_scalar_kernel<<<(int)blocks, 256, 0, st>>>(N, dEcs, a.grad);
   }
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K4 for N fluid components (N = NF + 1 fluids, NF free fields): the same
+// per-component terms with C_{N+1} = 1 - C_1 - sum_f C_f, whose differences are
+// minus the sum of the others'.  dE/dC_f = d_f - d_{N+1} (+ the constraint),
+// d_k = kappa_k b(C_k) - a^2 kappa_k L[C_k].  Per-block FP64 partials: bulk,
+// gradient, then V_f of each free fluid.
+// ---------------------------------------------------------------------------
+template <int K, int NF>
+__global__ void __launch_bounds__(256) fe_multi_kernel(FEMArgs a, int gx, int gy, int nbricks) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  constexpr int NC = NF + 2;  // components: solid, free fluids, dependent fluid
+  constexpr int NA = 2 + NF;
+  FF acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; k++) acc[k] = FF{0.0f, 0.0f};
+  const int G = gridDim.x;
+  const int sx = G % gx, sy = (G / gx) % gy, sz = G / (gx * gy);
+  int bx = blockIdx.x % gx, by = (blockIdx.x / gx) % gy, bz = blockIdx.x / (gx * gy);
+  for (int b = blockIdx.x; b < nbricks; b += G) {
+    if (b != blockIdx.x) {
+      bx += sx;
+      by += sy;
+      bz += sz;
+      if (bx >= gx) {
+        bx -= gx;
+        by++;
+      }
+      if (by >= gy) {
+        by -= gy;
+        bz++;
+      }
+    }
+    const int x = bx * blockDim.x + threadIdx.x;
+    const int y = by * blockDim.y + threadIdx.y;
+    const int z = bz * blockDim.z + threadIdx.z;
+    if (!(x < a.nx && y < a.ny && z < a.nz)) continue;
+    const int xm = x == 0 ? a.lo[0] : x - 1, xp = x + 1 == a.nx ? a.hi[0] : x + 1;
+    const int ym = y == 0 ? a.lo[1] : y - 1, yp = y + 1 == a.ny ? a.hi[1] : y + 1;
+    const int zm = z == 0 ? a.lo[2] : z - 1, zp = z + 1 == a.nz ? a.hi[2] : z + 1;
+    const int s = a.nx * a.ny;
+    const int ox[3] = {xm, x, xp}, oy[3] = {ym * a.nx, y * a.nx, yp * a.nx},
+              oz[3] = {zm * s, z * s, zp * s};
+    const int n = x + y * a.nx + z * s;
+    float cv[NC];
+    cv[0] = a.c1[n];
+    float last = 1.0f - cv[0];
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      cv[1 + f] = a.c[f * a.plane + n];
+      last -= cv[1 + f];
+    }
+    cv[NC - 1] = last;
+    float l[NC], p[NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) l[k] = p[k] = 0.0f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+      const int m = ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
+      const float w = float(L::w(i));
+      float dsum = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NC - 1; k++) {
+        const float v = k == 0 ? __ldg(a.c1 + m) : __ldg(a.c + (k - 1) * a.plane + m);
+        const float d = v - cv[k];
+        const float t = w * d;
+        l[k] += t;
+        p[k] = fmaf(t, d, p[k]);
+        dsum += d;
+      }
+      // the dependent fluid's difference is -dsum
+      l[NC - 1] -= w * dsum;
+      p[NC - 1] = fmaf(w * dsum, dsum, p[NC - 1]);
+    }
+    float bulk = 0.0f, grd = 0.0f, dd[NC];
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+      const float q = cv[k] * (1.0f - cv[k]);
+      bulk += 0.5f * a.kappa[k] * q * q;
+      grd += a.kappa[k] * p[k];
+      dd[k] = a.kappa[k] * bw(cv[k]) - a.a2 * a.kappa[k] * (6.0f * l[k]);
+    }
+    acc[0] = ff_add(acc[0], FF{bulk, 0.0f});
+    acc[1] = ff_add(acc[1], FF{1.5f * a.a2 * grd, 0.0f});
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      acc[2 + f] = ff_add(acc[2 + f], FF{cv[1 + f], 0.0f});
+      a.grad[f * a.plane + n] = dd[1 + f] - dd[NC - 1] + a.const_grad[f];
+    }
+  }
+  int sums[NA];
+#pragma unroll
+  for (int k = 0; k < NA; k++) sums[k] = 0;
+  block_reduce_ff<NA>(acc, sums, a.partials + (long long)blockIdx.x * NA);
+}
+
+// Sum the per-block partials in block order; assemble E, the terms (bulk,
+// gradient, constraint, V_f) and each free fluid's constraint derivative.
+template <int NF>
+__global__ void fe_multi_finalize_kernel(const double *partials, long long nb, FEMCons cons,
+                                         double *energy, double *terms, double *dEcs) {
+  constexpr int NA = 2 + NF;
+  __shared__ double sh[NA][256];
+  double s[NA];
+  for (int k = 0; k < NA; k++) s[k] = 0.0;
+  for (long long b = threadIdx.x; b < nb; b += blockDim.x)
+    for (int k = 0; k < NA; k++) s[k] += partials[b * NA + k];
+  for (int k = 0; k < NA; k++) sh[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < NA; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double Ecs = 0.0;
+    for (int f = 0; f < NF; f++) {
+      const double V = sh[2 + f][0];
+      const bool press = cons.kcs[f] == 0.0;
+      Ecs += press ? -cons.dP[f] * V : 0.5 * cons.kcs[f] * (V - cons.V0[f]) * (V - cons.V0[f]);
+      dEcs[f] = press ? -cons.dP[f] : cons.kcs[f] * (V - cons.V0[f]);
+      if (terms) terms[3 + f] = V;
+    }
+    const double E = sh[0][0] + sh[1][0] + Ecs;
+    if (energy) energy[0] = E;
+    if (terms) {
+      terms[0] = sh[0][0];
+      terms[1] = sh[1][0];
+      terms[2] = Ecs;
+    }
+  }
+}
+
+size_t fe_multi_scratch_bytes(int kind, int nx, int ny, int nz, int nf) {
+  return (size_t)round_up(fe_blocks(kind, nx, ny, nz) * (2 + nf) * sizeof(double), 256) + 256;
+}
+
+template <int K, int NF>
+static cudaError_t fe_multi_run(FEMArgs a, const FEMCons &cons, double *energy, double *terms,
+                                void *scratch, cudaStream_t st) {
+  const long long nb = fe_blocks(K, a.nx, a.ny, a.nz);
+  double *partials = (double *)scratch;
+  double *dEcs = (double *)((char *)scratch + round_up(nb * (2 + NF) * sizeof(double), 256));
+  a.partials = partials;
+  for (int f = 0; f < NF; f++) a.const_grad[f] = cons.kcs[f] == 0.0 ? (float)(-cons.dP[f]) : 0.0f;
+  const dim3 g = fe_bricks(K, a.nx, a.ny, a.nz);
+  const int nbricks = (int)((long long)g.x * g.y * g.z);
+  fe_multi_kernel<K, NF><<<(unsigned)nb, fe_block(K), 0, st>>>(a, g.x, g.y, nbricks);
+  fe_multi_finalize_kernel<NF><<<1, 256, 0, st>>>(partials, nb, cons, energy, terms, dEcs);
+  const long long N = (long long)a.nx * a.ny * a.nz;
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  for (int f = 0; f < NF; f++)
+    if (cons.kcs[f] != 0.0)
+      add_dev_scalar_kernel<<<(int)blocks, 256, 0, st>>>(N, dEcs + f, a.grad + f * a.plane);
+  return cudaGetLastError();
+}
+
+cudaError_t fe_multi_launch(int kind, FEMArgs a, const FEMCons &cons, double *energy,
+                            double *terms, void *scratch, cudaStream_t st) {
+  switch (kind * 4 + a.nf) {
+    case 1: return fe_multi_run<0, 1>(a, cons, energy, terms, scratch, st);
+    case 2: return fe_multi_run<0, 2>(a, cons, energy, terms, scratch, st);
+    case 3: return fe_multi_run<0, 3>(a, cons, energy, terms, scratch, st);
+    case 5: return fe_multi_run<1, 1>(a, cons, energy, terms, scratch, st);
+    case 6: return fe_multi_run<1, 2>(a, cons, energy, terms, scratch, st);
+    case 7: return fe_multi_run<1, 3>(a, cons, energy, terms, scratch, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -30,6 +30,36 @@ struct FEArgs {
 dsm_status fe_args_of(const dsm_params *p, const double kappa[3], int active, double fg,
                       FEArgs *a);
 
+// Energy of N fluid components on a frozen solid (N = nf + 1, nf free fluid
+// fields C_2 .. C_N stored as nf planes; C_{N+1} = 1 - C_1 - sum of them).
+constexpr int FEM_MAX_NF = 3;
+struct FEMArgs {
+  int nx, ny, nz;
+  int lo[3], hi[3];
+  int nf;                          // free fluid fields, 1 .. FEM_MAX_NF
+  float kappa[FEM_MAX_NF + 2];     // kappa_1, the free fluids', the dependent fluid's
+  float a2;                        // alpha^2
+  float const_grad[FEM_MAX_NF];    // constant added to each free gradient (pressure form)
+  long long plane;                 // nodes per field plane
+  const float *c1, *c;             // solid; free fluid planes
+  float *grad;                     // nf planes
+  double *partials;
+};
+// Per free fluid: pressure dP (kcs = 0) or volume constraint kcs (V - V0)^2 / 2.
+struct FEMCons {
+  double dP[FEM_MAX_NF], kcs[FEM_MAX_NF], V0[FEM_MAX_NF];
+};
+size_t fe_multi_scratch_bytes(int kind, int nx, int ny, int nz, int nf);
+// FEMArgs and FEMCons of an N-fluid energy (nfluid = N): lattice, sizes, alpha
+// and faces from p, kappa_1 .. kappa_{N+1} from kappa, the constraints from
+// the host arrays dP, kcs, V0 (N - 1 each, or null for zeros).  DSM_E_INVAL
+// for a bad size, nfluid outside 2 .. FEM_MAX_NF + 1, a fluid kappa <= 0,
+// kcs < 0 or invalid faces.
+dsm_status fem_args_of(const dsm_params *p, int nfluid, const double *kappa, const double *dP,
+                       const double *kcs, const double *V0, FEMArgs *a, FEMCons *cons);
+cudaError_t fe_multi_launch(int kind, FEMArgs a, const FEMCons &cons, double *energy,
+                            double *terms, void *scratch, cudaStream_t st);
+
 long long fe_blocks(int kind, int nx, int ny, int nz);
 size_t fe_scratch_bytes(int kind, int nx, int ny, int nz);
 cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, double *energy,

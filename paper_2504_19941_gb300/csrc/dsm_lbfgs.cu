@@ -75,7 +75,7 @@ double cubic_step(double a, double fa, double da, double b, double fb, double db
 }
 
 struct Minimiser {
-  long long n;
+  long long n;  // vector length: nodes, or nodes x free fluids
   int m;
   cudaStream_t st;
   FEArgs fa;
@@ -83,12 +83,21 @@ struct Minimiser {
   double dP, kcs, V0;
   const float *fixed;
   int active;
+  bool multi = false;  // N fluids: x holds the free fluid planes
+  FEMArgs fm;
+  FEMCons fcons;
   // device buffers (carved from the caller's workspace)
   float *xb[2], *gb[2], *d, *hist;
   double *E[2], *dots, *vout;
   void *fe_scr, *vec_scr, *dots_scr;
 
   cudaError_t evaluate(const float *x, double *e_out, float *g_out) {
+    if (multi) {
+      FEMArgs b = fm;
+      b.c = x;
+      b.grad = g_out;
+      return fe_multi_launch(kind, b, fcons, e_out, nullptr, fe_scr, st);
+    }
     FEArgs a = fa;
     a.c1 = active == 2 ? fixed : x;
     a.c2 = active == 2 ? x : fixed;
@@ -118,79 +127,11 @@ struct Minimiser {
 
 }  // namespace
 
-extern "C" {
-
-dsm_status dsm_lbfgs_compact(int k, const double *SY, const double *YY, const double *a,
-                             const double *b, double gamma, double *cx, double *cs, double *cy) {
-  if (k < 1 || !SY || !YY || !a || !b || !cx || !cs || !cy) return DSM_E_INVAL;
-  return compact(k, SY, YY, a, b, gamma, cx, cs, cy) ? DSM_OK : DSM_E_INVAL;
-}
-
-static size_t lbfgs_layout(const dsm_params *p, int m, size_t off[12]) {
-  const long long n = (long long)p->nx * p->ny * p->nz;
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    size_t at = o;
-    o += (size_t)round_up((long long)bytes, 256);
-    return at;
-  };
-  off[0] = take(n * sizeof(float));               // second x buffer
-  off[1] = take(n * sizeof(float));               // g
-  off[2] = take(n * sizeof(float));               // gt
-  off[3] = take(n * sizeof(float));               // d
-  off[4] = take((size_t)2 * m * n * sizeof(float));  // s_0..s_{m-1}, y_0..y_{m-1}
-  off[5] = take(2 * sizeof(double));              // E, Et
-  off[6] = take((size_t)(4 * m + 2) * sizeof(double));  // batched dots, then s.s and g.g
-  off[7] = take(4 * sizeof(double));              // single dots
-  off[8] = take(fe_scratch_bytes(p->lattice, p->nx, p->ny, p->nz));
-  off[9] = take(vec_scratch_bytes(n));
-  off[10] = take(vec_dots_scratch_bytes(n, 2 * m));
-  return o;
-}
-
-dsm_status dsm_lbfgs_workspace_bytes(const dsm_params *p, int m, size_t *bytes) {
-  if (!p || !bytes || m < 1 || 2 * m > LINCOMB_MAX) return DSM_E_INVAL;
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DSM_E_INVAL;
-  size_t off[12];
-  *bytes = lbfgs_layout(p, m, off);
-  return DSM_OK;
-}
-
-dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
-                              const unsigned char *d_mask, int active, double dP, double kcs,
-                              double V0, double fg, float *d_x, int m, double tol,
-                              long long max_iter, void *d_work, size_t work_bytes,
-                              dsm_lbfgs_info *info, void *cuda_stream) {
-  if (!p || !d_fixed || !d_x || !d_work || !info) return DSM_E_INVAL;
-  if (active != 1 && active != 2) return DSM_E_INVAL;
-  if (active == 1 && !d_mask) return DSM_E_INVAL;
-  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == DSM_D2Q9 && p->nz != 1))
-    return DSM_E_INVAL;
-  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
-  if (m < 1 || 2 * m > LINCOMB_MAX || max_iter < 0 || !(tol >= 0.0) || kcs < 0.0)
-    return DSM_E_INVAL;
-  double kap[3];
-  dsm_status s = dsm_kappa(p, kap);
-  if (s != DSM_OK) return s;
-  size_t off[12];
-  if (work_bytes < lbfgs_layout(p, m, off) || ((uintptr_t)d_work & 255u)) return DSM_E_WORKSPACE;
-  memset(info, 0, sizeof(*info));
-
-  Minimiser M;
-  M.n = (long long)p->nx * p->ny * p->nz;
-  M.m = m;
-  M.st = (cudaStream_t)cuda_stream;
-  s = fe_args_of(p, kap, active, fg, &M.fa);
-  if (s != DSM_OK) return s;
-  M.fa.mask = d_mask;
-  M.kind = p->lattice;
-  M.dP = dP;
-  M.kcs = kcs;
-  M.V0 = V0;
-  M.fixed = d_fixed;
-  M.active = active;
-  char *w = (char *)d_work;
+// The L-BFGS loop over M.n-vectors (x in d_x, overwritten), workspace w laid
+// out by lbfgs_layout_n.
+static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *d_x, double tol,
+                     long long max_iter, dsm_lbfgs_info *info) {
+  const int m = M.m;
   M.xb[0] = d_x;
   M.xb[1] = (float *)(w + off[0]);
   M.gb[0] = (float *)(w + off[1]);
@@ -392,6 +333,129 @@ dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
   info->rms_grad = sqrt(gg / n);
   info->converged = converged;
   return DSM_OK;
+}
+
+extern "C" {
+
+dsm_status dsm_lbfgs_compact(int k, const double *SY, const double *YY, const double *a,
+                             const double *b, double gamma, double *cx, double *cs, double *cy) {
+  if (k < 1 || !SY || !YY || !a || !b || !cx || !cs || !cy) return DSM_E_INVAL;
+  return compact(k, SY, YY, a, b, gamma, cx, cs, cy) ? DSM_OK : DSM_E_INVAL;
+}
+
+// Workspace of an L-BFGS run over n-vectors whose energy needs fe_bytes of
+// scratch.
+static size_t lbfgs_layout_n(long long n, int m, size_t fe_bytes, size_t off[12]) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += (size_t)round_up((long long)bytes, 256);
+    return at;
+  };
+  off[0] = take(n * sizeof(float));               // second x buffer
+  off[1] = take(n * sizeof(float));               // g
+  off[2] = take(n * sizeof(float));               // gt
+  off[3] = take(n * sizeof(float));               // d
+  off[4] = take((size_t)2 * m * n * sizeof(float));  // s_0..s_{m-1}, y_0..y_{m-1}
+  off[5] = take(2 * sizeof(double));              // E, Et
+  off[6] = take((size_t)(4 * m + 2) * sizeof(double));  // batched dots, then s.s and g.g
+  off[7] = take(4 * sizeof(double));              // single dots
+  off[8] = take(fe_bytes);
+  off[9] = take(vec_scratch_bytes(n));
+  off[10] = take(vec_dots_scratch_bytes(n, 2 * m));
+  return o;
+}
+
+static size_t lbfgs_layout(const dsm_params *p, int m, size_t off[12]) {
+  return lbfgs_layout_n((long long)p->nx * p->ny * p->nz, m,
+                        fe_scratch_bytes(p->lattice, p->nx, p->ny, p->nz), off);
+}
+
+dsm_status dsm_lbfgs_workspace_bytes(const dsm_params *p, int m, size_t *bytes) {
+  if (!p || !bytes || m < 1 || 2 * m > LINCOMB_MAX) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DSM_E_INVAL;
+  size_t off[12];
+  *bytes = lbfgs_layout(p, m, off);
+  return DSM_OK;
+}
+
+dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
+                              const unsigned char *d_mask, int active, double dP, double kcs,
+                              double V0, double fg, float *d_x, int m, double tol,
+                              long long max_iter, void *d_work, size_t work_bytes,
+                              dsm_lbfgs_info *info, void *cuda_stream) {
+  if (!p || !d_fixed || !d_x || !d_work || !info) return DSM_E_INVAL;
+  if (active != 1 && active != 2) return DSM_E_INVAL;
+  if (active == 1 && !d_mask) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == DSM_D2Q9 && p->nz != 1))
+    return DSM_E_INVAL;
+  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
+  if (m < 1 || 2 * m > LINCOMB_MAX || max_iter < 0 || !(tol >= 0.0) || kcs < 0.0)
+    return DSM_E_INVAL;
+  double kap[3];
+  dsm_status s = dsm_kappa(p, kap);
+  if (s != DSM_OK) return s;
+  size_t off[12];
+  if (work_bytes < lbfgs_layout(p, m, off) || ((uintptr_t)d_work & 255u)) return DSM_E_WORKSPACE;
+  memset(info, 0, sizeof(*info));
+
+  Minimiser M;
+  M.n = (long long)p->nx * p->ny * p->nz;
+  M.m = m;
+  M.st = (cudaStream_t)cuda_stream;
+  s = fe_args_of(p, kap, active, fg, &M.fa);
+  if (s != DSM_OK) return s;
+  M.fa.mask = d_mask;
+  M.kind = p->lattice;
+  M.dP = dP;
+  M.kcs = kcs;
+  M.V0 = V0;
+  M.fixed = d_fixed;
+  M.active = active;
+  return run_lbfgs(M, (char *)d_work, off, d_x, tol, max_iter, info);
+}
+
+dsm_status dsm_lbfgs_multi_workspace_bytes(const dsm_params *p, int nfluid, int m,
+                                           size_t *bytes) {
+  if (!p || !bytes || m < 1 || 2 * m > LINCOMB_MAX) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (nfluid < 2 || nfluid > FEM_MAX_NF + 1) return DSM_E_INVAL;
+  size_t off[12];
+  const long long nodes = (long long)p->nx * p->ny * p->nz;
+  *bytes = lbfgs_layout_n(nodes * (nfluid - 1), m,
+                          fe_multi_scratch_bytes(p->lattice, p->nx, p->ny, p->nz, nfluid - 1),
+                          off);
+  return DSM_OK;
+}
+
+dsm_status dsm_lbfgs_minimize_multi(const dsm_params *p, int nfluid, const double *kappa,
+                                    const float *d_c1, const double *dP, const double *kcs,
+                                    const double *V0, float *d_x, int m, double tol,
+                                    long long max_iter, void *d_work, size_t work_bytes,
+                                    dsm_lbfgs_info *info, void *cuda_stream) {
+  if (!d_c1 || !d_x || !d_work || !info) return DSM_E_INVAL;
+  if (m < 1 || 2 * m > LINCOMB_MAX || max_iter < 0 || !(tol >= 0.0)) return DSM_E_INVAL;
+  Minimiser M;
+  dsm_status s = fem_args_of(p, nfluid, kappa, dP, kcs, V0, &M.fm, &M.fcons);
+  if (s != DSM_OK) return s;
+  const long long nodes = (long long)p->nx * p->ny * p->nz;
+  size_t off[12];
+  const size_t need = lbfgs_layout_n(
+      nodes * (nfluid - 1), m, fe_multi_scratch_bytes(p->lattice, p->nx, p->ny, p->nz, nfluid - 1),
+      off);
+  if (work_bytes < need || ((uintptr_t)d_work & 255u)) return DSM_E_WORKSPACE;
+  memset(info, 0, sizeof(*info));
+  M.multi = true;
+  M.fm.c1 = d_c1;
+  M.n = nodes * (nfluid - 1);
+  M.m = m;
+  M.st = (cudaStream_t)cuda_stream;
+  M.kind = p->lattice;
+  M.fixed = d_c1;
+  M.active = 2;
+  return run_lbfgs(M, (char *)d_work, off, d_x, tol, max_iter, info);
 }
 
 }  // extern "C"

@@ -95,3 +95,45 @@ def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0
     info = _lib.dsm_lbfgs_minimize(fe.params, other, mask, active, dP, kcs, V0, fg, x, m, tol,
                                    max_iter, work, nb, fe.stream)
     return x, info["energy"], info
+
+
+class FreeEnergyMulti:
+    """Energy + gradients of N fluid components on a frozen solid
+    (dsm_fe_energy_grad_multi): kappa holds kappa_1 .. kappa_{N+1}; the free
+    fluids C_2 .. C_N are the N - 1 planes of one (N - 1, nodes) FP32 tensor."""
+
+    def __init__(self, params: dsm_params, nfluid: int, kappa, device="cuda", stream=None):
+        self.params = params
+        self.nfluid = int(nfluid)
+        self.kappa = [float(k) for k in kappa]
+        self.device = torch.device(device)
+        self.stream = stream
+        self.n = params.nx * params.ny * params.nz
+        self.sb = _lib.dsm_fe_multi_scratch_bytes(params.lattice, params.nx, params.ny,
+                                                  params.nz, self.nfluid)
+        self.scratch = torch.empty(self.sb, dtype=torch.uint8, device=self.device)
+        self.terms = torch.zeros(2 + self.nfluid, dtype=torch.float64, device=self.device)
+
+    def __call__(self, c1, c, *, dP=None, kcs=None, V0=None, energy=None, grad=None):
+        """Returns (E as a 1-element float64 device tensor, gradients as an
+        (N - 1, nodes) float32 device tensor)."""
+        if energy is None:
+            energy = torch.empty(1, dtype=torch.float64, device=self.device)
+        if grad is None:
+            grad = torch.empty((self.nfluid - 1, self.n), dtype=torch.float32, device=self.device)
+        _lib.dsm_fe_energy_grad_multi(self.params, self.nfluid, self.kappa, c1, c, dP, kcs, V0,
+                                      energy, grad, self.terms, self.scratch, self.sb,
+                                      self.stream)
+        return energy, grad
+
+
+def lbfgs_multi(fe: FreeEnergyMulti, x0, c1, *, dP=None, kcs=None, V0=None, m=10, tol=1e-6,
+                max_iter=10000):
+    """Minimise the N-fluid energy over the free fluid planes from x0 ((N - 1,
+    nodes) FP32, not modified) with the native L-BFGS loop.  Returns (x, E, info)."""
+    x = x0.detach().clone().contiguous()
+    nb = _lib.dsm_lbfgs_multi_workspace_bytes(fe.params, fe.nfluid, m)
+    work = torch.empty(nb, dtype=torch.uint8, device=x.device)
+    info = _lib.dsm_lbfgs_minimize_multi(fe.params, fe.nfluid, fe.kappa, c1, dP, kcs, V0, x, m,
+                                         tol, max_iter, work, nb, fe.stream)
+    return x, info["energy"], info

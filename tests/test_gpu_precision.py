@@ -80,12 +80,15 @@ def test_storage_forms_against_fp64():
         assert abs(ob["mass_c2"] - m0[prec]) / m0[prec] < t["mass"], prec
 
 
+@pytest.mark.parametrize("faces", [None, ("mirror", "mirror", "wall", "wall", "mirror", "wall")])
 @pytest.mark.parametrize("prec,bits", [("bf16", 8), ("f16", 11)])
-def test_one_step_within_encoding_rounding(prec, bits):
+def test_one_step_within_encoding_rounding(prec, bits, faces):
     # from a state representable in the storage, one step in FP32 arithmetic
     # differs from the FP64 oracle's step only by the rounding of the stored
-    # result (and FP32 arithmetic, far smaller)
+    # result (and FP32 arithmetic, far smaller); with mirror and wall faces too
+    # (whose lattices keep g as 16-bit populations with an FP32 g_0)
     case = _plates()
+    case.faces = faces
     case.shape = (24, 20, 16)
     n = 24 * 20 * 16
     sd = S.box_sd(case.shape, (4, 5, 0), (20, 9, 16))
