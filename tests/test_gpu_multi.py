@@ -75,21 +75,25 @@ def test_two_fluids_equal_the_two_fluid_entry_point():
 
 
 def test_lbfgs_multi_lens_matches_oracle():
-    # a lens of fluid 2 at the flat interface between fluid 3 (below) and the
-    # dependent fluid 4 (above), no solid; fluids 2 and 3 volume-constrained.
-    # Tensions (kappa_m + kappa_n)/6: 0.30, 0.317, 0.283, so the lens stays a
-    # lens (the spreading coefficient is negative)
-    nx, ny = 48, 40
+    # half a lens of fluid 2 at the flat interface between fluid 3 (below) and
+    # the dependent fluid 4 (above), centred on the mirror face x = -1/2 (mirror
+    # faces all round: a lens in a periodic box could slide freely, and the
+    # minimum would not be unique); no solid; fluids 2 and 3
+    # volume-constrained.  Tensions (kappa_m + kappa_n)/6: 0.30, 0.317, 0.283,
+    # so the lens stays a lens (the spreading coefficient is negative).  Two
+    # different oracle starts reach the same minimum (checked to 1e-6).
+    nx, ny = 32, 40
     n = nx * ny
+    faces = ("mirror", "mirror", "mirror", "mirror", "periodic", "periodic")
     y, x = np.mgrid[0:ny, 0:nx].astype(float)
-    lens = 0.5 * (1.0 + np.tanh((8.0 - np.hypot(x - 23.5, y - 20.0)) / 2.0))
+    lens = 0.5 * (1.0 + np.tanh((8.0 - np.hypot(x + 0.5, y - 20.0)) / 2.0))
     below = 0.5 * (1.0 - np.tanh((y - 20.0) / 2.0)) * (1.0 - lens)
     C0 = np.stack([lens.ravel(), below.ravel()])
     kappa = (0.5, 1.0, 0.8, 0.9)
     V0 = C0.sum(axis=1)
     kcs = (0.05, 0.05)
-    p = P.make_params("D2Q9", (nx, ny), "f32", theta_deg=90.0)
-    po = O.make_params(O.D2Q9, (nx, ny), (1.0, 1.0, 1.0))
+    p = P.make_params("D2Q9", (nx, ny), "f32", theta_deg=90.0, faces=faces)
+    po = O.make_params(O.D2Q9, (nx, ny), (1.0, 1.0, 1.0), faces=faces)
     c1 = np.zeros(n)
     fe = FreeEnergyMulti(p, 3, kappa)
     X, E, info = lbfgs_multi(fe, _t(C0), _t(c1), kcs=kcs, V0=V0, tol=1e-5, max_iter=6000)
