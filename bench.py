@@ -680,6 +680,32 @@ def run_em(args, rank, world):
                           max_iter=args.em_iters)
     torch.cuda.synchronize()
     t_lb = time.perf_counter() - t0
+    # N fluid components: the same lattice with the liquid split into N - 1
+    # free fluids; algorithmic bytes per node 4 (2 (N - 1) + 1): read C1 and the
+    # free planes, write their gradients
+    from paper_2504_19941_gb300.energy import FreeEnergyMulti
+    multi = {}
+    for nfluid in (2, 3, 4):
+        nf = nfluid - 1
+        C = (c2 / nf).repeat(nf, 1).contiguous()
+        kap = [0.0] + [float(k) for k in P._lib.dsm_kappa(p)[1:]] + [0.9] * (nfluid - 2)
+        kap[0] = float(P._lib.dsm_kappa(p)[0])
+        fm = FreeEnergyMulti(p, nfluid, kap, device=dev)
+        Em = torch.empty(1, dtype=torch.float64, device=dev)
+        gm = torch.empty((nf, n), dtype=torch.float32, device=dev)
+        for _ in range(5):
+            fm(c1, C, energy=Em, grad=gm)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fm(c1, C, energy=Em, grad=gm)
+        e1.record()
+        torch.cuda.synchronize()
+        t_m = e0.elapsed_time(e1) / 1e3 / reps
+        b = 4 * (2 * nf + 1)
+        multi[f"N={nfluid}"] = {"eval_ms": t_m * 1e3, "bytes_per_node": b,
+                                "achieved_gbs": b * n / t_m / 1e9,
+                                "frac": b * n / t_m / 1e9 / peak}
     if rank == 0:
         print(json.dumps({"metric": "EM energy+gradient evaluations/s (128^3, D3Q19 stencil)",
                           "value": 1.0 / t_eval, "unit": "evals/s", "n_gpus": 1,
@@ -694,7 +720,8 @@ def run_em(args, rank, world):
                                     "evaluations": info["evaluations"],
                                     "rms_grad": info["rms_grad"], "energy": Emin,
                                     "seconds": t_lb, "iters_per_s": info["iterations"] / t_lb,
-                                    "tol": 1e-6}}), flush=True)
+                                    "tol": 1e-6},
+                          "multi_fluid": multi}), flush=True)
     return 0
 
 
