@@ -420,6 +420,42 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
 /* Release the handle (host memory only; the workspace stays the caller's). */
 dsm_status dsm_destroy(dsm_lattice *h);
 
+/* ---- N fluid components, lattice Boltzmann ------------------------------
+ * The stage-2 step for N = nfluid fluids (2 <= N <= 4) on a frozen diffuse
+ * solid: the N + 1-component model of Sec. II.B, which the paper states for
+ * any N and demonstrates for N = 2.  Fluids C_2 .. C_N are free, each with its
+ * own Cahn-Hilliard populations; C_{N+1} = 1 - C_1 - (C_2 + .. + C_N).
+ * Host arrays: kappa (N + 1 values, kappa_1 .. kappa_{N+1}: the tension of
+ * components m, n is alpha (kappa_m + kappa_n) / 6), rho and tau (N values,
+ * fluids 2 .. N + 1).  From p: lattice, sizes, precision (DSM_F64 or DSM_F32;
+ * others DSM_E_UNSUPPORTED), alpha, alpha_s, tau_g, body_force (on fluid 2),
+ * faces.  Population form; one step = the moments pass and the fused pass:
+ *   mu_f = d_f - d_{N+1},  d_k = kappa_k b(C_k) - alpha^2 kappa_k L[C_k];
+ *   F = sum_f mu_f G[C_f] + C_2 b;
+ *   rho = rho_{N+1} + sum_f (rho_f - rho_{N+1}) phi_f, phi_f = C_f / (1 - C_1)
+ *   clamped to [0, 1]; tau = the tau of the locally largest fluid (ties to the
+ *   later fluid); interpolated bounce-back and the face rules as for N = 2.
+ * With N = 2 this is dsm_step's population form.  The workspace (at least
+ * dsm_ml_workspace_bytes, 256-byte aligned) is the caller's.  dsm_ml_set_solid
+ * takes a signed distance (kind 0) or C1 itself (kind 1); dsm_ml_set_fluids
+ * the free fluids (N - 1 planes of nx*ny*nz reals) and writes the rest state.
+ * dsm_ml_get_field: DSM_FIELD_C2 with index f gives C_{2+f} (index N - 1: the
+ * dependent fluid), DSM_FIELD_MU with index f gives mu_{2+f}, DSM_FIELD_C1,
+ * UX, UY, UZ, PT, RHO, TAU as for dsm_get_field; DSM_FIELD_C3 is DSM_E_INVAL.
+ * dsm_ml_get_populations: f (Q planes) and g (N - 1 blocks of Q planes), dense
+ * nx*ny*nz rows.  No error latching: the caller checks fields for NaN. */
+typedef struct dsm_mlattice dsm_mlattice;
+dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes);
+dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa,
+                         const double *rho, const double *tau, void *d_workspace,
+                         size_t bytes, void *cuda_stream, dsm_mlattice **out);
+dsm_status dsm_ml_set_solid(dsm_mlattice *h, const void *d_field, int kind);
+dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c);
+dsm_status dsm_ml_step(dsm_mlattice *h, long long nsteps);
+dsm_status dsm_ml_get_field(dsm_mlattice *h, int field, int index, void *d_dst);
+dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g);
+dsm_status dsm_ml_destroy(dsm_mlattice *h);
+
 #ifdef __cplusplus
 }
 #endif

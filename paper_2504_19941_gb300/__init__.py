@@ -165,3 +165,64 @@ class Lattice:
 
     def set_state(self, buf):
         _lib.dsm_set_state(self.h, buf, buf.numel())
+
+
+class MultiLattice:
+    """A lattice of N = nfluid fluid components (dsm_ml_*): kappa holds
+    kappa_1 .. kappa_{N+1}, rho and tau the N fluids' densities and relaxation
+    times (fluids 2 .. N + 1).  The workspace is a torch tensor it owns."""
+
+    def __init__(self, params: dsm_params, nfluid: int, kappa, rho, tau, device="cuda",
+                 stream=None):
+        import torch
+        self.params = params
+        self.nfluid = int(nfluid)
+        self.n = params.nx * params.ny * params.nz
+        self.q = 9 if params.lattice == DSM_D2Q9 else 19
+        self.real = torch.float64 if params.precision == DSM_F64 else torch.float32
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.nbytes = _lib.dsm_ml_workspace_bytes(params, self.nfluid)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.h = _lib.dsm_ml_create(params, self.nfluid, kappa, rho, tau, self.workspace,
+                                    self.nbytes, self.stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            _lib.dsm_ml_destroy(h)
+            self.h = None
+
+    def _arg(self, t, count):
+        assert t.dtype == self.real and t.numel() == count and t.is_cuda
+        return t.contiguous()
+
+    def set_solid_distance(self, sd):
+        _lib.dsm_ml_set_solid(self.h, self._arg(sd, self.n), 0)
+
+    def set_solid_c1(self, c1):
+        _lib.dsm_ml_set_solid(self.h, self._arg(c1, self.n), 1)
+
+    def set_fluids(self, c):
+        """The free fluids C_2 .. C_N, an (N - 1, nodes) tensor."""
+        _lib.dsm_ml_set_fluids(self.h, self._arg(c, (self.nfluid - 1) * self.n))
+
+    def step(self, nsteps: int = 1):
+        _lib.dsm_ml_step(self.h, int(nsteps))
+
+    def field(self, name: str, index: int = 0, out=None):
+        """name as for Lattice.field; "C" with index f is C_{2+f} (index N - 1:
+        the dependent fluid), "mu" with index f is mu_{2+f}."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=self.real, device=self.device)
+        code = DSM_FIELD_C2 if name == "C" else FIELDS[name]
+        _lib.dsm_ml_get_field(self.h, code, index, out)
+        return out
+
+    def populations(self):
+        import torch
+        f = torch.empty(self.q * self.n, dtype=self.real, device=self.device)
+        g = torch.empty((self.nfluid - 1) * self.q * self.n, dtype=self.real, device=self.device)
+        _lib.dsm_ml_get_populations(self.h, f, g)
+        return f, g

@@ -34,7 +34,9 @@ EXPORTED = (
     "dsm_fe_multi_scratch_bytes", "dsm_fe_energy_grad_multi", "dsm_lbfgs_multi_workspace_bytes",
     "dsm_lbfgs_minimize_multi",
     "dsm_batch_scratch_bytes", "dsm_batch_step",
-    "dsm_destroy",
+    "dsm_destroy", "dsm_ml_workspace_bytes", "dsm_ml_create", "dsm_ml_set_solid",
+    "dsm_ml_set_fluids", "dsm_ml_step", "dsm_ml_get_field", "dsm_ml_get_populations",
+    "dsm_ml_destroy",
 )
 
 
@@ -133,6 +135,14 @@ def load():
         "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
         "dsm_destroy": (st, [vp]),
+        "dsm_ml_workspace_bytes": (st, [P, C.c_int, C.POINTER(C.c_size_t)]),
+        "dsm_ml_create": (st, [P, C.c_int, dp, dp, dp, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "dsm_ml_set_solid": (st, [vp, vp, C.c_int]),
+        "dsm_ml_set_fluids": (st, [vp, vp]),
+        "dsm_ml_step": (st, [vp, C.c_longlong]),
+        "dsm_ml_get_field": (st, [vp, C.c_int, C.c_int, vp]),
+        "dsm_ml_get_populations": (st, [vp, vp, vp]),
+        "dsm_ml_destroy": (st, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -446,3 +456,43 @@ def dsm_batch_step(handles, nsteps, scratch, scratch_bytes: int):
 
 def dsm_destroy(h: int):
     _check(load().dsm_destroy(h), "dsm_destroy")
+
+
+def dsm_ml_workspace_bytes(params: dsm_params, nfluid: int) -> int:
+    n = C.c_size_t()
+    _check(load().dsm_ml_workspace_bytes(C.byref(params), nfluid, C.byref(n)),
+           "dsm_ml_workspace_bytes")
+    return n.value
+
+
+def dsm_ml_create(params: dsm_params, nfluid: int, kappa, rho, tau, workspace, nbytes: int,
+                  stream=None) -> int:
+    h = C.c_void_p()
+    _check(load().dsm_ml_create(C.byref(params), nfluid, _doubles(kappa, nfluid + 1),
+                                _doubles(rho, nfluid), _doubles(tau, nfluid), _ptr(workspace),
+                                nbytes, _stream(stream), C.byref(h)), "dsm_ml_create")
+    return h.value
+
+
+def dsm_ml_set_solid(h: int, field, kind: int):
+    _check(load().dsm_ml_set_solid(h, _ptr(field), kind), "dsm_ml_set_solid")
+
+
+def dsm_ml_set_fluids(h: int, c):
+    _check(load().dsm_ml_set_fluids(h, _ptr(c)), "dsm_ml_set_fluids")
+
+
+def dsm_ml_step(h: int, nsteps: int):
+    _check(load().dsm_ml_step(h, nsteps), "dsm_ml_step")
+
+
+def dsm_ml_get_field(h: int, field: int, index: int, out):
+    _check(load().dsm_ml_get_field(h, field, index, _ptr(out)), "dsm_ml_get_field")
+
+
+def dsm_ml_get_populations(h: int, f, g):
+    _check(load().dsm_ml_get_populations(h, _ptr(f), _ptr(g)), "dsm_ml_get_populations")
+
+
+def dsm_ml_destroy(h: int):
+    _check(load().dsm_ml_destroy(h), "dsm_ml_destroy")

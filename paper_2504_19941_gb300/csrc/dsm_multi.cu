@@ -1,0 +1,630 @@
+// dsm_multi.cu -- the lattice Boltzmann step for N fluid components on a frozen
+// diffuse solid (Sec. II.B states the method for the N + 1-component model and
+// demonstrates N = 2; here N = 2 .. 4).  Population form, FP64 or FP32
+// storage and arithmetic; every free fluid C_2 .. C_N has its own
+// Cahn-Hilliard populations g_f, and C_{N+1} = 1 - C_1 - sum_f C_f.
+//
+// Per step, as for two fluids: a moments pass (C_f = sum_i g_f,i after the
+// pull) and a fused pass (pull f and g with interpolated bounce-back and the
+// face rules; chemical potentials, density and relaxation maps, forces,
+// moments; BGK collision of f and of every g_f).  Readings for N > 2, each
+// reducing to the two-fluid one:
+//   mu_f = d_f - d_{N+1},  d_k = kappa_k b(C_k) - alpha^2 kappa_k L[C_k]
+//     (the exact derivative of the N-fluid free energy);
+//   F = sum_f mu_f G[C_f] + C_2 b (the potential form for every fluid, the
+//     body force on fluid 2);
+//   rho = rho_{N+1} + sum_f (rho_f - rho_{N+1}) phi_f, phi_f = C_f / (1 - C_1)
+//     clamped to [0, 1] (0 where 1 - C_1 <= 1e-6);
+//   tau = the relaxation time of the locally largest fluid concentration,
+//     ties to the later fluid.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "dsm_lb_impl.cuh"
+
+namespace dsm {
+
+constexpr int ML_MAX_NF = 3;  // free fluids (N - 1)
+
+template <class T>
+struct MLArgs {
+  int nx, ny, nz;
+  long long N, pitch;
+  int face[6];
+  int walls;
+  T kappa[ML_MAX_NF + 2];            // kappa_1, the free fluids', the dependent fluid's
+  T rho[ML_MAX_NF + 1], om[ML_MAX_NF + 1];  // per fluid: density, 1 / tau
+  T omg, a2, alpha_s;
+  T body[3];
+  const T *f_in, *g_in;  // Q planes; NF x Q planes (fluid-major)
+  T *f_out, *g_out;
+  T *C;                  // NF planes: the moments pass output
+  const T *C1;
+  T *out;                // fields mode: one plane
+  int field, index;
+};
+
+template <class T>
+__device__ __forceinline__ const T *plane(const T *base, long long pitch, int k) {
+  return base + (long long)k * pitch;
+}
+template <class T>
+__device__ __forceinline__ T *plane(T *base, long long pitch, int k) {
+  return base + (long long)k * pitch;
+}
+
+// moments pass: C_f(x) = sum_i g_f,i pulled into x (face rules on the faces)
+template <int K, class T, int NF>
+__global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  const bool edge = a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    const T *g = a.g_in + (long long)f * Q * a.pitch;
+    T s = T(0);
+    for (int i = 1; i < Q; i++) {
+      int k = i, src = h.plus_rt<L>(L::opp(i));
+      if (edge && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &k) == 2) src = n;
+      s += plane(g, a.pitch, k)[src];
+    }
+    a.C[f * a.pitch + n] = plane(g, a.pitch, 0)[n] + s;
+  }
+}
+
+// rho of the volume fractions at one point
+template <class T, int NF>
+__device__ __forceinline__ T ml_rho(const MLArgs<T> &a, const T (&c)[NF], T c1) {
+  const T den = T(1) - c1;
+  T r = a.rho[NF];
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    T ph = T(0);
+    if (den > T(1e-6)) {
+      ph = c[f] / den;
+      ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
+    }
+    r += (a.rho[f] - a.rho[NF]) * ph;
+  }
+  return r;
+}
+
+enum { ML_STEP = 0, ML_FIELDS = 1 };
+
+template <int K, class T, int NF, int MODE>
+__global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  constexpr int NC = NF + 2;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+
+  // ---- the neighbourhood: C1 and the free fluids, stencils of every component
+  T cv[NC], lap[NC], gC[NF][3], gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
+  unsigned nb_solid = 0;  // bit i: x + c_i is solid
+  cv[0] = a.C1[n];
+  T last = T(1) - cv[0];
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    cv[1 + f] = a.C[f * a.pitch + n];
+    last -= cv[1 + f];
+  }
+  cv[NC - 1] = last;
+#pragma unroll
+  for (int k = 0; k < NC; k++) lap[k] = T(0);
+#pragma unroll
+  for (int f = 0; f < NF; f++) gC[f][0] = gC[f][1] = gC[f][2] = T(0);
+  for (int i = 1; i < Q; i++) {
+    const int m = h.plus_rt<L>(i);
+    const T w = T(L::w(i));
+    const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
+    const T c1m = a.C1[m];
+    T cm[NF], lastm = T(1) - c1m;
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      cm[f] = a.C[f * a.pitch + m];
+      lastm -= cm[f];
+      lap[1 + f] += w * (cm[f] - cv[1 + f]);
+      gC[f][0] += w * cx * cm[f];
+      gC[f][1] += w * cy * cm[f];
+      gC[f][2] += w * cz * cm[f];
+    }
+    lap[0] += w * (c1m - cv[0]);
+    lap[NC - 1] += w * (lastm - cv[NC - 1]);
+    const T r = w * ml_rho<T, NF>(a, cm, c1m);
+    gR[0] += r * cx;
+    gR[1] += r * cy;
+    gR[2] += r * cz;
+    gc1[0] += w * cx * c1m;
+    gc1[1] += w * cy * c1m;
+    gc1[2] += w * cz * c1m;
+    if (c1m >= T(0.5)) nb_solid |= 1u << i;
+  }
+  T mu[NF], F[3] = {T(0), T(0), T(0)};
+  T d[NC];
+#pragma unroll
+  for (int k = 0; k < NC; k++)
+    d[k] = a.kappa[k] * bwell(cv[k]) - a.a2 * a.kappa[k] * (T(6) * lap[k]);
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    mu[f] = d[1 + f] - d[NC - 1];
+    for (int e = 0; e < 3; e++) F[e] += mu[f] * (T(3) * gC[f][e]);
+  }
+  for (int e = 0; e < 3; e++) {
+    F[e] += cv[1] * a.body[e];
+    gR[e] *= T(3);
+    gc1[e] *= T(3);
+  }
+  T cfree[NF];
+#pragma unroll
+  for (int f = 0; f < NF; f++) cfree[f] = cv[1 + f];
+  const T rho = ml_rho<T, NF>(a, cfree, cv[0]);
+  // relaxation of the locally largest fluid, ties to the later one
+  int big = NF;
+  T bigc = cv[NC - 1];
+#pragma unroll
+  for (int f = NF - 1; f >= 0; f--)
+    if (cv[1 + f] > bigc) {
+      bigc = cv[1 + f];
+      big = f;
+    }
+  const T om = a.om[big];
+  const bool solid_x = cv[0] >= T(0.5);
+
+  // ---- pull f and every g_f (face rules), interpolated bounce-back for f
+  const bool edge = a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
+  T fs[Q], gs[NF][Q];
+  for (int j = 0; j < Q; j++) {
+    int k = j, src = h.plus_rt<L>(L::opp(j)), cr = 0;
+    if (edge) {
+      cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
+      if (cr == 2) src = n;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+      gs[f][j] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
+    T v = plane(a.f_in, a.pitch, k)[src];
+    const int i = L::opp(j);
+    if (j > 0 && !solid_x && cr != 2 && ((nb_solid >> i) & 1u)) {
+      // the upstream node (or its image across a mirror) is solid
+      const T cc = cv[0] < T(1e-9) ? T(1e-9) : (cv[0] > T(0.5) ? T(0.5) : cv[0]);
+      const T xs = T(2) * a.alpha_s * atanh(T(2) * cc - T(1));
+      const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
+      const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
+      const T fi_x = plane(a.f_in, a.pitch, i)[n];
+      int ki = i;
+      bool second = !((nb_solid >> j) & 1u);
+      if (a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
+      if (q < T(0.5) && second) {
+        v = T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
+      } else if (q < T(0.5)) {
+        v = fi_x;
+      } else {
+        v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * plane(a.f_in, a.pitch, j)[n];
+      }
+    }
+    fs[j] = v;
+  }
+
+  // ---- moments: rho u = sum c f + F/2, pt = sum f + u.G[rho]/2
+  T u[3] = {T(0), T(0), T(0)}, pt = T(1);
+  if (!solid_x) {
+    T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
+    for (int j = 0; j < Q; j++) {
+      m0 += fs[j];
+      m1[0] += T(L::cx(j)) * fs[j];
+      m1[1] += T(L::cy(j)) * fs[j];
+      m1[2] += T(L::cz(j)) * fs[j];
+    }
+    for (int e = 0; e < 3; e++) u[e] = (m1[e] + T(0.5) * F[e]) / rho;
+    pt = m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]);
+  }
+  if constexpr (MODE == ML_FIELDS) {
+    T v;
+    switch (a.field) {
+      case DSM_FIELD_C1: v = cv[0]; break;
+      case DSM_FIELD_C2: v = cv[1 + (a.index < NF ? a.index : NF)]; break;
+      case DSM_FIELD_MU: v = mu[a.index < NF ? a.index : 0]; break;
+      case DSM_FIELD_UX: v = u[0]; break;
+      case DSM_FIELD_UY: v = u[1]; break;
+      case DSM_FIELD_UZ: v = u[2]; break;
+      case DSM_FIELD_PT: v = pt; break;
+      case DSM_FIELD_RHO: v = rho; break;
+      default: v = T(1) / om; break;
+    }
+    a.out[n] = v;
+    return;
+  }
+
+  // ---- BGK collision of f (Eq. [eqn:feq], Eq. [eqn:hydroforce]) and of g_f
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
+  const T kF = T(1) - T(0.5) * om;
+  for (int i = 0; i < Q; i++) {
+    const T w = T(L::w(i));
+    const T ci[3] = {T(L::cx(i)), T(L::cy(i)), T(L::cz(i))};
+    const T cu = ci[0] * u[0] + ci[1] * u[1] + ci[2] * u[2];
+    const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+    T fo = w;
+    if (!solid_x) {
+      const T cg = ci[0] * gR[0] + ci[1] * gR[1] + ci[2] * gR[2];
+      const T cF = ci[0] * F[0] + ci[1] * F[1] + ci[2] * F[2];
+      const T Fi = kF * w * ((cg - ug) * s + T(3) * cF);
+      fo = fs[i] + (w * (pt + rho * s) - fs[i]) * om + Fi;
+    }
+    plane(a.f_out, a.pitch, i)[n] = fo;
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      const T Cf = cv[1 + f];
+      const T geq = i == 0 ? Cf - (T(1) - w) * mu[f] + w * Cf * s : w * (mu[f] + Cf * s);
+      T *go = a.g_out + (long long)f * Q * a.pitch;
+      plane(go, a.pitch, i)[n] = gs[f][i] + (geq - gs[f][i]) * a.omg;
+    }
+  }
+}
+
+// initial state at rest: f_i = w_i, g_f,i = g_eq,i(C_f, mu_f(C), u = 0); C
+// (NF planes) is read from a.C
+template <int K, class T, int NF>
+__global__ void __launch_bounds__(256) ml_init_kernel(MLArgs<T> a) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  constexpr int NC = NF + 2;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  T cv[NC], lap[NC];
+  cv[0] = a.C1[n];
+  T last = T(1) - cv[0];
+  for (int f = 0; f < NF; f++) {
+    cv[1 + f] = a.C[f * a.pitch + n];
+    last -= cv[1 + f];
+  }
+  cv[NC - 1] = last;
+  for (int k = 0; k < NC; k++) lap[k] = T(0);
+  for (int i = 1; i < Q; i++) {
+    const int m = h.plus_rt<L>(i);
+    const T w = T(L::w(i));
+    const T c1m = a.C1[m];
+    T lastm = T(1) - c1m;
+    for (int f = 0; f < NF; f++) {
+      const T cm = a.C[f * a.pitch + m];
+      lastm -= cm;
+      lap[1 + f] += w * (cm - cv[1 + f]);
+    }
+    lap[0] += w * (c1m - cv[0]);
+    lap[NC - 1] += w * (lastm - cv[NC - 1]);
+  }
+  T d[NC];
+  for (int k = 0; k < NC; k++)
+    d[k] = a.kappa[k] * bwell(cv[k]) - a.a2 * a.kappa[k] * (T(6) * lap[k]);
+  for (int i = 0; i < Q; i++) {
+    const T w = T(L::w(i));
+    plane(a.f_out, a.pitch, i)[n] = w;
+    for (int f = 0; f < NF; f++) {
+      const T mu = d[1 + f] - d[NC - 1];
+      const T Cf = cv[1 + f];
+      T *go = a.g_out + (long long)f * Q * a.pitch;
+      plane(go, a.pitch, i)[n] = i == 0 ? Cf - (T(1) - w) * mu : w * mu;
+    }
+  }
+}
+
+}  // namespace dsm
+
+using namespace dsm;
+
+struct dsm_mlattice {
+  dsm_params prm;
+  int nf, q, real_bytes;
+  double kappa[ML_MAX_NF + 2], rho[ML_MAX_NF + 1], tau[ML_MAX_NF + 1];
+  long long N, pitch;
+  cudaStream_t stream;
+  char *f[2], *g[2], *C, *C1;
+  int cur;
+  bool has_solid, has_fluid;
+};
+
+namespace {
+
+struct MLLayout {
+  size_t f[2], g[2], C, C1, total;
+};
+
+MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch) {
+  MLLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (size_t)round_up((long long)bytes, 256);
+    return at;
+  };
+  for (int b = 0; b < 2; b++) L.f[b] = take((size_t)q * pitch * real_bytes);
+  for (int b = 0; b < 2; b++) L.g[b] = take((size_t)nf * q * pitch * real_bytes);
+  L.C = take((size_t)nf * pitch * real_bytes);
+  L.C1 = take((size_t)pitch * real_bytes);
+  L.total = o;
+  return L;
+}
+
+dsm_status ml_check(const dsm_params *p, int nfluid, const double *kappa, const double *rho,
+                    const double *tau) {
+  if (!p || !kappa || !rho || !tau) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == DSM_D2Q9 && p->nz != 1))
+    return DSM_E_INVAL;
+  if ((long long)p->nx * p->ny * p->nz >= (1ll << 31)) return DSM_E_INVAL;
+  if (nfluid < 2 || nfluid > ML_MAX_NF + 1) return DSM_E_INVAL;
+  if (!(p->alpha > 0.0) || p->alpha_s < 0.0 || !(p->tau_g > 0.5)) return DSM_E_INVAL;
+  if (!faces_valid(p)) return DSM_E_INVAL;
+  for (int k = 0; k <= nfluid; k++)
+    if (!isfinite(kappa[k]) || (k > 0 && !(kappa[k] > 0.0))) return DSM_E_INVAL;
+  for (int f = 0; f < nfluid; f++)
+    if (!(rho[f] > 0.0) || !(tau[f] > 0.5)) return DSM_E_INVAL;
+  if (p->precision != DSM_F64 && p->precision != DSM_F32) return DSM_E_UNSUPPORTED;
+  return DSM_OK;
+}
+
+template <class T>
+MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
+  MLArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.nx = h->prm.nx;
+  a.ny = h->prm.ny;
+  a.nz = h->prm.nz;
+  a.N = h->N;
+  a.pitch = h->pitch;
+  for (int k = 0; k < 6; k++) {
+    a.face[k] = h->prm.face[k];
+    a.walls |= h->prm.face[k] != 0;
+  }
+  for (int k = 0; k <= h->nf + 1; k++) a.kappa[k] = T(h->kappa[k]);
+  for (int f = 0; f <= h->nf; f++) {
+    a.rho[f] = T(h->rho[f]);
+    a.om[f] = T(1.0 / h->tau[f]);
+  }
+  a.omg = T(1.0 / h->prm.tau_g);
+  a.a2 = T(h->prm.alpha * h->prm.alpha);
+  a.alpha_s = T(h->prm.alpha_s > 0.0 ? h->prm.alpha_s : h->prm.alpha);
+  for (int e = 0; e < 3; e++) a.body[e] = T(h->prm.body_force[e]);
+  if (h->prm.lattice == DSM_D2Q9) a.body[2] = T(0);
+  a.f_in = (const T *)h->f[src];
+  a.g_in = (const T *)h->g[src];
+  a.f_out = (T *)h->f[src ^ 1];
+  a.g_out = (T *)h->g[src ^ 1];
+  a.C = (T *)h->C;
+  a.C1 = (const T *)h->C1;
+  return a;
+}
+
+dim3 ml_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+dim3 ml_grid(const dsm_mlattice *h) {
+  return lb_grid_of(ml_block(h->prm.lattice), h->prm.nx, h->prm.ny, h->prm.nz);
+}
+
+// kernel dispatch over (lattice, free fluids) for one arithmetic type
+template <class T, template <int, class, int> class Launch>
+cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a) {
+  const int key = h->prm.lattice * 4 + h->nf;
+  const dim3 g = ml_grid(h), b = ml_block(h->prm.lattice);
+  switch (key) {
+    case 1: Launch<0, T, 1>::go(g, b, a, h->stream); break;
+    case 2: Launch<0, T, 2>::go(g, b, a, h->stream); break;
+    case 3: Launch<0, T, 3>::go(g, b, a, h->stream); break;
+    case 5: Launch<1, T, 1>::go(g, b, a, h->stream); break;
+    case 6: Launch<1, T, 2>::go(g, b, a, h->stream); break;
+    case 7: Launch<1, T, 3>::go(g, b, a, h->stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int K, class T, int NF>
+struct MomentsL {
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
+    ml_moments_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+  }
+};
+template <int K, class T, int NF>
+struct StepL {
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
+    ml_node_kernel<K, T, NF, ML_STEP><<<g, b, 0, s>>>(a);
+  }
+};
+template <int K, class T, int NF>
+struct FieldsL {
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
+    ml_node_kernel<K, T, NF, ML_FIELDS><<<g, b, 0, s>>>(a);
+  }
+};
+template <int K, class T, int NF>
+struct InitL {
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
+    ml_init_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+  }
+};
+
+template <class T>
+cudaError_t ml_step(dsm_mlattice *h) {
+  MLArgs<T> a = ml_args<T>(h, h->cur);
+  cudaError_t e = ml_dispatch<T, MomentsL>(h, a);
+  if (e == cudaSuccess) e = ml_dispatch<T, StepL>(h, a);
+  if (e == cudaSuccess) h->cur ^= 1;
+  return e;
+}
+
+template <class T>
+cudaError_t ml_fields(dsm_mlattice *h, int field, int index, void *dst) {
+  MLArgs<T> a = ml_args<T>(h, h->cur);
+  a.field = field;
+  a.index = index;
+  a.out = (T *)dst;
+  cudaError_t e = ml_dispatch<T, MomentsL>(h, a);
+  if (e == cudaSuccess) e = ml_dispatch<T, FieldsL>(h, a);
+  return e;
+}
+
+dsm_status ml_status(cudaError_t e) { return e == cudaSuccess ? DSM_OK : DSM_E_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes) {
+  if (!p || !bytes) return DSM_E_INVAL;
+  if (p->lattice != DSM_D2Q9 && p->lattice != DSM_D3Q19) return DSM_E_INVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || nfluid < 2 || nfluid > ML_MAX_NF + 1)
+    return DSM_E_INVAL;
+  if (p->precision != DSM_F64 && p->precision != DSM_F32) return DSM_E_UNSUPPORTED;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
+  *bytes = ml_layout(q, nfluid - 1, p->precision == DSM_F64 ? 8 : 4, round_up(N, 64)).total;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, const double *rho,
+                         const double *tau, void *d_workspace, size_t bytes, void *cuda_stream,
+                         dsm_mlattice **out) {
+  if (!out) return DSM_E_INVAL;
+  *out = nullptr;
+  dsm_status s = ml_check(p, nfluid, kappa, rho, tau);
+  if (s != DSM_OK) return s;
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  const long long pitch = round_up(N, 64);
+  const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
+  const int rb = p->precision == DSM_F64 ? 8 : 4;
+  const MLLayout L = ml_layout(q, nfluid - 1, rb, pitch);
+  if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255u)) return DSM_E_WORKSPACE;
+  dsm_mlattice *h = new (std::nothrow) dsm_mlattice;
+  if (!h) return DSM_E_INVAL;
+  memset(h, 0, sizeof(*h));
+  h->prm = *p;
+  h->nf = nfluid - 1;
+  h->q = q;
+  h->real_bytes = rb;
+  for (int k = 0; k <= nfluid; k++) h->kappa[k] = kappa[k];
+  for (int f = 0; f < nfluid; f++) {
+    h->rho[f] = rho[f];
+    h->tau[f] = tau[f];
+  }
+  h->N = N;
+  h->pitch = pitch;
+  h->stream = (cudaStream_t)cuda_stream;
+  char *w = (char *)d_workspace;
+  for (int b = 0; b < 2; b++) {
+    h->f[b] = w + L.f[b];
+    h->g[b] = w + L.g[b];
+  }
+  h->C = w + L.C;
+  h->C1 = w + L.C1;
+  // no solid until one is set: C1 = 0
+  if (cudaMemsetAsync(h->C1, 0, (size_t)pitch * rb, h->stream) != cudaSuccess) {
+    delete h;
+    return DSM_E_CUDA;
+  }
+  *out = h;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_set_solid(dsm_mlattice *h, const void *d_field, int kind) {
+  if (!h || !d_field || (kind != 0 && kind != 1)) return DSM_E_INVAL;
+  cudaError_t e;
+  if (kind == 1) {
+    e = cudaMemcpyAsync(h->C1, d_field, (size_t)h->N * h->real_bytes, cudaMemcpyDeviceToDevice,
+                        h->stream);
+  } else {
+    long long blocks = (h->N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const double as = h->prm.alpha_s > 0.0 ? h->prm.alpha_s : h->prm.alpha;
+    if (h->real_bytes == 8)
+      solid_profile_kernel<double><<<(int)blocks, 256, 0, h->stream>>>(
+          (const double *)d_field, (double *)h->C1, h->N, as);
+    else
+      solid_profile_kernel<float><<<(int)blocks, 256, 0, h->stream>>>(
+          (const float *)d_field, (float *)h->C1, h->N, (float)as);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->has_solid = true;
+  h->has_fluid = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c) {
+  if (!h || !d_c) return DSM_E_INVAL;
+  // the free fluids into C (plane by plane), then the rest state into buffer 0
+  for (int f = 0; f < h->nf; f++) {
+    cudaError_t e = cudaMemcpyAsync(h->C + (size_t)f * h->pitch * h->real_bytes,
+                                    (const char *)d_c + (size_t)f * h->N * h->real_bytes,
+                                    (size_t)h->N * h->real_bytes, cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return DSM_E_CUDA;
+  }
+  h->cur = 0;
+  cudaError_t e;
+  if (h->real_bytes == 8) e = ml_dispatch<double, InitL>(h, ml_args<double>(h, 1));
+  else e = ml_dispatch<float, InitL>(h, ml_args<float>(h, 1));
+  if (e != cudaSuccess) return DSM_E_CUDA;
+  h->has_fluid = true;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_step(dsm_mlattice *h, long long nsteps) {
+  if (!h || nsteps < 0) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  for (long long t = 0; t < nsteps; t++) {
+    const cudaError_t e = h->real_bytes == 8 ? ml_step<double>(h) : ml_step<float>(h);
+    if (e != cudaSuccess) return DSM_E_CUDA;
+  }
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_get_field(dsm_mlattice *h, int field, int index, void *d_dst) {
+  if (!h || !d_dst || field < DSM_FIELD_C1 || field > DSM_FIELD_TAU) return DSM_E_INVAL;
+  if (field == DSM_FIELD_C3) return DSM_E_INVAL;
+  if (field == DSM_FIELD_C2 && (index < 0 || index > h->nf)) return DSM_E_INVAL;
+  if (field == DSM_FIELD_MU && (index < 0 || index >= h->nf)) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  return ml_status(h->real_bytes == 8 ? ml_fields<double>(h, field, index, d_dst)
+                                      : ml_fields<float>(h, field, index, d_dst));
+}
+
+dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g) {
+  if (!h || (!d_f && !d_g)) return DSM_E_INVAL;
+  if (!h->has_fluid) return DSM_E_STATE;
+  const size_t row = (size_t)h->N * h->real_bytes, pb = (size_t)h->pitch * h->real_bytes;
+  for (int i = 0; d_f && i < h->q; i++)
+    if (cudaMemcpyAsync((char *)d_f + i * row, h->f[h->cur] + i * pb, row,
+                        cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return DSM_E_CUDA;
+  for (int i = 0; d_g && i < h->nf * h->q; i++)
+    if (cudaMemcpyAsync((char *)d_g + i * row, h->g[h->cur] + i * pb, row,
+                        cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return DSM_E_CUDA;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_destroy(dsm_mlattice *h) {
+  delete h;
+  return DSM_OK;
+}
+
+}  // extern "C"

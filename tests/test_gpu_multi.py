@@ -107,3 +107,168 @@ def test_lbfgs_multi_lens_matches_oracle():
     assert info_o["rms_grad"] < 1e-8
     assert abs(E - Eo) / abs(Eo) < 1e-5, (E, Eo)
     assert np.max(np.abs(X.double().cpu().numpy().ravel() - xo)) < 2e-3
+
+
+# ---------------------------------------------------------------- LB, N fluids
+from oracle.multi_lb import MultiLB  # noqa: E402
+
+from dsm_helpers import direction_map  # noqa: E402
+
+
+def _ml_case_2d(nf):
+    # a drop of fluid 2 on a diffuse wall, a layer of fluid 3 (and fluid 4 in
+    # a second drop for N = 4) under the dependent fluid; mirror x faces
+    nx, ny = 24, 20
+    sd = S.slab_sd((nx, ny), 1, 0, 4)
+    c1 = O.solid_profile(sd.ravel(), 1.0)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    free = 1.0 - c1.reshape(ny, nx)
+    drop = 0.5 * (1 + np.tanh((5.0 - np.hypot(x - 6.0, y - 9.0)) / 2.0)) * free
+    layer = np.clip(0.5 * (1 - np.tanh((y - 13.0) / 2.0)) * free - drop, 0, 1)
+    C = [drop, layer]
+    if nf == 3:
+        d2 = 0.5 * (1 + np.tanh((3.0 - np.hypot(x - 17.0, y - 16.0)) / 2.0)) * free
+        C.append(d2)
+        C[1] = np.clip(C[1] - d2, 0, 1)
+    C = np.stack([c.ravel() for c in C])
+    kappa = (0.02, 0.03, 0.025, 0.035, 0.028)[:nf + 2]
+    rho = (1.0, 0.7, 0.5, 0.8)[:nf + 1]
+    tau = (0.8, 1.0, 0.7, 0.9)[:nf + 1]
+    faces = ("mirror", "mirror", "periodic", "periodic", "periodic", "periodic")
+    return (nx, ny), c1, C, kappa, rho, tau, faces, (1e-5, -1e-5, 0.0)
+
+
+def _ml_case_3d(nf):
+    shape = (14, 12, 10)
+    nx, ny, nz = shape
+    sd = S.pillars_sd(shape, 3, 4, 7, 5, offset=2)
+    c1 = O.solid_profile(sd.ravel(), 1.0)
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    free = 1.0 - c1.reshape(nz, ny, nx)
+    drop = 0.5 * (1 + np.tanh((3.5 - np.hypot(np.hypot(x - 7, y - 6), z - 6.0)) / 2.0)) * free
+    layer = np.clip(0.5 * (1 - np.tanh((z - 4.5) / 2.0)) * free - drop, 0, 1)
+    C = [drop, layer]
+    if nf == 3:
+        C.append(0.5 * (1 + np.tanh((z - 8.0) / 2.0)) * free * 0.8)
+    C = np.stack([c.ravel() for c in C])
+    kappa = (0.02, 0.03, 0.025, 0.035, 0.028)[:nf + 2]
+    rho = (1.0, 0.7, 0.5, 0.8)[:nf + 1]
+    tau = (0.8, 1.0, 0.7, 0.9)[:nf + 1]
+    faces = ("mirror", "mirror", "wall", "wall", "mirror", "wall")
+    return shape, c1, C, kappa, rho, tau, faces, (0.0, 1e-5, -1e-5)
+
+
+def _ml_run(case, prec, steps, tau_g=0.9):
+    shape, c1, C, kappa, rho, tau, faces, body = case
+    nf = C.shape[0]
+    lat = "D2Q9" if len(shape) == 2 else "D3Q19"
+    kind = O.D2Q9 if lat == "D2Q9" else O.D3Q19
+    real = torch.float64 if prec == "f64" else torch.float32
+    p = P.make_params(lat, shape, prec, theta_deg=90.0, tau_g=tau_g, body=body, faces=faces,
+                      alpha_s=1.0)
+    ml = P.MultiLattice(p, nf + 1, kappa, rho, tau)
+    ml.set_solid_c1(_t(c1, real))
+    ml.set_fluids(_t(C, real))
+    ml.step(steps)
+    po = O.make_params(kind, shape, kappa[:3], tau_g=tau_g, body=body, faces=faces, alpha_s=1.0)
+    c1r = _t(c1, real).double().cpu().numpy()
+    m = MultiLB(po, kappa, rho, tau, c1r)
+    f, g = m.init(_t(C, real).double().cpu().numpy())
+    f, g = m.run(f, g, steps)
+    return ml, m, f, g, kind
+
+
+def _ml_compare(ml, m, f, g, kind):
+    perm = direction_map(kind)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    fg_, gg_ = ml.populations()
+    q, n, nf = ml.q, ml.n, ml.nfluid - 1
+    gf = fg_.double().cpu().numpy().reshape(q, n)[inv]
+    gg = gg_.double().cpu().numpy().reshape(nf, q, n)[:, inv]
+    errs = {"f": rel_err(gf, f), "g": rel_err(gg, g)}
+    F = m.fields(f, g)
+    for k in range(nf):
+        errs[f"C{k}"] = rel_err(ml.field("C", k).double().cpu().numpy(), F["C"][k])
+        errs[f"mu{k}"] = rel_err(ml.field("mu", k).double().cpu().numpy(), F["mu"][k])
+    for a, name in enumerate(("ux", "uy", "uz")):
+        if np.abs(F["u"][a]).max() > 0:
+            errs[name] = rel_err(ml.field(name).double().cpu().numpy(), F["u"][a])
+    errs["pt"] = rel_err(ml.field("pt").double().cpu().numpy(), F["pt"])
+    errs["rho"] = rel_err(ml.field("rho").double().cpu().numpy(), F["rho"])
+    errs["tau"] = rel_err(ml.field("tau").double().cpu().numpy(), F["tau"])
+    return errs
+
+
+@pytest.mark.parametrize("make", [_ml_case_2d, _ml_case_3d])
+@pytest.mark.parametrize("nf", [2, 3])
+def test_ml_fp64_parity(make, nf):
+    ml, m, f, g, kind = _ml_run(make(nf), "f64", 20)
+    errs = _ml_compare(ml, m, f, g, kind)
+    assert max(errs.values()) < 1e-12, errs
+
+
+@pytest.mark.parametrize("make", [_ml_case_2d, _ml_case_3d])
+def test_ml_fp32_parity(make):
+    ml, m, f, g, kind = _ml_run(make(2), "f32", 40)
+    e = _ml_compare(ml, m, f, g, kind)
+    assert e["f"] < 1e-5 and e["g"] < 1e-5 and e["C0"] < 1e-5 and e["C1"] < 1e-5, e
+    assert e["pt"] < 1e-5 and e["rho"] < 1e-5 and e["mu0"] < 1e-4 and e["mu1"] < 1e-4, e
+    assert max(v for k_, v in e.items() if k_ in ("ux", "uy", "uz")) < 2e-4, e
+    assert e["tau"] == 0.0, e
+
+
+def test_ml_two_fluids_equal_the_lattice():
+    # N = 2 through the N-fluid path equals the two-fluid step (population form)
+    case = _ml_case_2d(2)
+    shape, c1, C, kappa, rho, tau, faces, body = case
+    p = P.make_params("D2Q9", shape, "f64", theta_deg=90.0, tau_g=0.9, body=body, faces=faces,
+                      alpha_s=1.0, rho2=rho[0], rho3=rho[2], tau2=tau[0], tau3=tau[2])
+    k3 = (kappa[0], kappa[1], kappa[3])
+    # the two-fluid lattice takes its kappa from the tensions: find them
+    g12 = (k3[0] + k3[1]) / 6.0
+    g13 = (k3[0] + k3[2]) / 6.0
+    g23 = (k3[1] + k3[2]) / 6.0
+    p.tension_mode, p.g12, p.g13, p.g23 = 0, g12, g13, g23
+    np.testing.assert_allclose(_lib.dsm_kappa(p), k3, rtol=1e-12)
+    lat = P.Lattice(p)
+    lat.set_g_storage("populations")
+    lat.set_solid_c1(_t(c1, torch.float64))
+    lat.set_fluid(_t(C[0], torch.float64))
+    lat.step(30)
+    ml = P.MultiLattice(p, 2, k3, (rho[0], rho[2]), (tau[0], tau[2]))
+    ml.set_solid_c1(_t(c1, torch.float64))
+    ml.set_fluids(_t(C[:1], torch.float64))
+    ml.step(30)
+    f1, g1 = lat.populations()
+    f2, g2 = ml.populations()
+    assert rel_err(f2.cpu().numpy(), f1.cpu().numpy()) < 1e-12
+    assert rel_err(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-12
+
+
+def test_ml_three_layers_relax_to_the_energy_minimum():
+    # fluid 2 | fluid 3 | fluid 4 between walls: the stationary LB state is the
+    # N-fluid energy minimum at the same volumes (the CPU pin stops at 6000
+    # steps and 1e-4)
+    nx = 48
+    x = np.arange(nx, dtype=float)
+    C = np.stack([0.5 * (1.0 - np.tanh((x - 16.0) / 2.0)),
+                  0.5 * (np.tanh((x - 16.0) / 2.0) - np.tanh((x - 32.0) / 2.0))])
+    kappa = (0.0, 0.1, 0.12, 0.11)
+    faces = ("wall", "wall", "periodic", "periodic", "periodic", "periodic")
+    p = P.make_params("D2Q9", (nx, 1), "f64", theta_deg=90.0, faces=faces)
+    ml = P.MultiLattice(p, 3, kappa, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0))
+    ml.set_solid_c1(torch.zeros(nx, dtype=torch.float64, device=DEV))
+    ml.set_fluids(_t(C, torch.float64))
+    ml.step(200000)
+    got = np.stack([ml.field("C", k).cpu().numpy() for k in range(2)])
+    po = O.make_params(O.D2Q9, (nx, 1), kappa[:3], faces=faces)
+    V0 = C.sum(axis=1)
+
+    def fg(v):
+        e, gr, _ = M.energy_grad_multi(po, kappa, np.zeros(nx), v.reshape(2, nx), kcs=(1.0, 1.0),
+                                       V0=V0)
+        return e, gr.ravel()
+    v, E, gr, info = olbfgs.minimize(fg, C.ravel(), tol=1e-11, max_iter=20000)
+    assert np.max(np.abs(got - v.reshape(2, nx))) < 1e-6
+    assert np.abs(ml.field("ux").cpu().numpy()).max() < 1e-9
