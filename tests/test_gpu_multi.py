@@ -214,8 +214,12 @@ def test_ml_fp32_parity(make):
     e = _ml_compare(ml, m, f, g, kind)
     assert e["f"] < 1e-5 and e["g"] < 1e-5 and e["C0"] < 1e-5 and e["C1"] < 1e-5, e
     assert e["pt"] < 1e-5 and e["rho"] < 1e-5 and e["mu0"] < 1e-4 and e["mu1"] < 1e-4, e
-    assert max(v for k_, v in e.items() if k_ in ("ux", "uy", "uz")) < 2e-4, e
-    assert e["tau"] == 0.0, e
+    # the velocity is a cancelling sum of O(0.1) populations: its FP32 rounding
+    # relative to max |u| is larger here, where three fluids' forces partly
+    # cancel, than in the two-fluid case (2e-4)
+    assert max(v for k_, v in e.items() if k_ in ("ux", "uy", "uz")) < 5e-4, e
+    # the same fluid rules every node; tau comes back as 1 / (1 / tau) in FP32
+    assert e["tau"] < 1e-7, e
 
 
 def test_ml_two_fluids_equal_the_lattice():
