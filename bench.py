@@ -606,6 +606,59 @@ def run_capillary(args, rank, world):
     return 0
 
 
+def run_multi(args, rank, world):
+    """N fluid components (dsm_ml_*): three fluids on the D3Q19 FP32 pillar
+    slab 256x256x192, the liquid split into two fluids (x below and above the
+    middle), population form.  Algorithmic bytes per lattice update: read and
+    write f and both fluids' g (2 x 19 x 4 x 3) and read C1 in the fused pass
+    (460 B); read both g and write both C in the moments pass (160 B)."""
+    import torch
+    import paper_2504_19941_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    case = make_case(SHAPE)
+    nx = SHAPE[0]
+    c2 = torch.as_tensor(case.c2, dtype=torch.float32, device=dev)
+    xs = torch.arange(c2.numel(), device=dev) % nx
+    C = torch.stack([c2 * (xs < nx // 2), c2 * (xs >= nx // 2)]).contiguous()
+    p = P.make_params("D3Q19", SHAPE, "f32", theta_deg=case.theta_deg, g12=case.g12,
+                      g23=case.g23, alpha_s=case.alpha_s)
+    k = P._lib.dsm_kappa(p)
+    kappa = [k[0], k[1], k[1], k[2]]        # both liquids alike, the gas third
+    ml = P.MultiLattice(p, 3, kappa, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), device=dev)
+    ml.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
+    ml.set_fluids(C)
+    for _ in range(args.warmup):
+        ml.step(1)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        ml.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    ux = ml.field("ux")
+    assert torch.isfinite(ux).all(), "non-finite velocity after the timed steps"
+    peak, peak_kind = _peaks()
+    b = 460 + 160
+    if rank == 0:
+        print(json.dumps({
+            "metric": "D3Q19 three-fluid LB MLUPS (256x256x192 pillar slab)", "unit": "MLUPS",
+            "value": ml.n / t / 1e6, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "D3Q19 FP32 pillar slab 256x256x192, three fluids",
+                       "nodes": ml.n, "l2": "f and g 2.9 GB per buffer, larger than L2; no flush"},
+            "roofline": {"bound": "hbm", "step_bytes_per_lu": b,
+                         "achieved": b * ml.n / t / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": b * ml.n / t / 1e9 / peak, "peak_source": peak_kind},
+            "clocks": clk.summary(), "gpu_launches": 2 * args.steps}), flush=True)
+    return 0
+
+
 def run_critical(args, rank, world):
     """Critical pressure of the Cassie-Baxter to Wenzel transition on 2D pillars
     (Sec. III) by bisection over GPU energy minimisations, for a sweep of five
@@ -741,7 +794,8 @@ def main():
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
     ap.add_argument("--workload", default="lb",
-                    choices=["lb", "serve", "precision", "fp64", "em", "critical", "capillary"])
+                    choices=["lb", "serve", "precision", "fp64", "em", "critical", "capillary",
+                             "multi"])
     ap.add_argument("--em-iters", type=int, default=3000)
     # default: a saturating burst (every request at once, full step budgets)
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -766,6 +820,8 @@ def main():
         return run_plain_fp64(args, rank, world)
     if args.workload == "em":
         return run_em(args, rank, world)
+    if args.workload == "multi":
+        return run_multi(args, rank, world)
     if args.workload == "capillary":
         return run_capillary(args, rank, world)
     if args.workload == "critical":

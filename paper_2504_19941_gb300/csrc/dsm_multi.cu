@@ -72,10 +72,15 @@ __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   for (int f = 0; f < NF; f++) {
     const T *g = a.g_in + (long long)f * Q * a.pitch;
     T s = T(0);
-    for (int i = 1; i < Q; i++) {
-      int k = i, src = h.plus_rt<L>(L::opp(i));
-      if (edge && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &k) == 2) src = n;
-      s += plane(g, a.pitch, k)[src];
+    if (edge) {
+      for (int i = 1; i < Q; i++) {
+        int k = i, src = h.plus_rt<L>(L::opp(i));
+        if (face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &k) == 2) src = n;
+        s += plane(g, a.pitch, k)[src];
+      }
+    } else {
+#pragma unroll
+      for (int i = 1; i < Q; i++) s += __ldg(plane(g, a.pitch, i) + h.minus<L>(i));
     }
     a.C[f * a.pitch + n] = plane(g, a.pitch, 0)[n] + s;
   }
@@ -128,15 +133,16 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   for (int k = 0; k < NC; k++) lap[k] = T(0);
 #pragma unroll
   for (int f = 0; f < NF; f++) gC[f][0] = gC[f][1] = gC[f][2] = T(0);
+#pragma unroll
   for (int i = 1; i < Q; i++) {
-    const int m = h.plus_rt<L>(i);
+    const int m = h.plus<L>(i);
     const T w = T(L::w(i));
     const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
-    const T c1m = a.C1[m];
+    const T c1m = __ldg(a.C1 + m);
     T cm[NF], lastm = T(1) - c1m;
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-      cm[f] = a.C[f * a.pitch + m];
+      cm[f] = __ldg(a.C + f * a.pitch + m);
       lastm -= cm[f];
       lap[1 + f] += w * (cm[f] - cv[1 + f]);
       gC[f][0] += w * cx * cm[f];
@@ -185,30 +191,32 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   const T om = a.om[big];
   const bool solid_x = cv[0] >= T(0.5);
 
-  // ---- pull f and every g_f (face rules), interpolated bounce-back for f
-  const bool edge = a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
+  // ---- pull f and every g_f from x - c_j, all loads issued up front; the
+  // rare links (a solid upstream node, a domain face) are corrected below
   T fs[Q], gs[NF][Q];
+#pragma unroll
   for (int j = 0; j < Q; j++) {
-    int k = j, src = h.plus_rt<L>(L::opp(j)), cr = 0;
-    if (edge) {
-      cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
-      if (cr == 2) src = n;
-    }
+    const int src = h.minus<L>(j);
+    fs[j] = __ldg(plane(a.f_in, a.pitch, j) + src);
 #pragma unroll
     for (int f = 0; f < NF; f++)
-      gs[f][j] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
-    T v = plane(a.f_in, a.pitch, k)[src];
-    const int i = L::opp(j);
-    if (j > 0 && !solid_x && cr != 2 && ((nb_solid >> i) & 1u)) {
-      // the upstream node (or its image across a mirror) is solid
-      const T cc = cv[0] < T(1e-9) ? T(1e-9) : (cv[0] > T(0.5) ? T(0.5) : cv[0]);
-      const T xs = T(2) * a.alpha_s * atanh(T(2) * cc - T(1));
-      const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
+      gs[f][j] = __ldg(plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, j) + src);
+  }
+  // interpolated bounce-back where the upstream node (or its image across a
+  // mirror) is solid
+  if (!solid_x && (nb_solid & ~1u)) {
+    const T cc = cv[0] < T(1e-9) ? T(1e-9) : (cv[0] > T(0.5) ? T(0.5) : cv[0]);
+    const T xs = T(2) * a.alpha_s * atanh(T(2) * cc - T(1));
+    const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
+    for (int j = 1; j < Q; j++) {
+      const int i = L::opp(j);
+      if (!((nb_solid >> i) & 1u)) continue;
       const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
       const T fi_x = plane(a.f_in, a.pitch, i)[n];
       int ki = i;
       bool second = !((nb_solid >> j) & 1u);
       if (a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
+      T v;
       if (q < T(0.5) && second) {
         v = T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
       } else if (q < T(0.5)) {
@@ -216,14 +224,40 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
       } else {
         v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * plane(a.f_in, a.pitch, j)[n];
       }
+#pragma unroll
+      for (int k = 1; k < Q; k++)
+        if (k == j) fs[k] = v;
     }
-    fs[j] = v;
+  }
+  // mirror and wall faces: specular reflection or halfway bounce-back for f
+  // and every g_f (a mirror link with a solid image keeps the value above)
+  if (a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz)) {
+    for (int j = 1; j < Q; j++) {
+      int k;
+      const int cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
+      if (cr == 0) continue;
+      const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
+      const bool interp = cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
+      const T fv = plane(a.f_in, a.pitch, k)[src];
+      T gv[NF];
+#pragma unroll
+      for (int f = 0; f < NF; f++)
+        gv[f] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
+#pragma unroll
+      for (int kk = 1; kk < Q; kk++)
+        if (kk == j) {
+          if (!interp) fs[kk] = fv;
+#pragma unroll
+          for (int f = 0; f < NF; f++) gs[f][kk] = gv[f];
+        }
+    }
   }
 
   // ---- moments: rho u = sum c f + F/2, pt = sum f + u.G[rho]/2
   T u[3] = {T(0), T(0), T(0)}, pt = T(1);
   if (!solid_x) {
     T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
+#pragma unroll
     for (int j = 0; j < Q; j++) {
       m0 += fs[j];
       m1[0] += T(L::cx(j)) * fs[j];
@@ -254,6 +288,7 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
   const T kF = T(1) - T(0.5) * om;
+#pragma unroll
   for (int i = 0; i < Q; i++) {
     const T w = T(L::w(i));
     const T ci[3] = {T(L::cx(i)), T(L::cy(i)), T(L::cz(i))};
@@ -415,16 +450,18 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
   return a;
 }
 
-dim3 ml_block(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
+dim3 ml_block(const dsm_mlattice *h) {
+  return lb_block(h->prm.lattice, h->prm.nx, h->prm.ny, h->prm.nz);
+}
 dim3 ml_grid(const dsm_mlattice *h) {
-  return lb_grid_of(ml_block(h->prm.lattice), h->prm.nx, h->prm.ny, h->prm.nz);
+  return lb_grid_of(ml_block(h), h->prm.nx, h->prm.ny, h->prm.nz);
 }
 
 // kernel dispatch over (lattice, free fluids) for one arithmetic type
 template <class T, template <int, class, int> class Launch>
 cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a) {
   const int key = h->prm.lattice * 4 + h->nf;
-  const dim3 g = ml_grid(h), b = ml_block(h->prm.lattice);
+  const dim3 g = ml_grid(h), b = ml_block(h);
   switch (key) {
     case 1: Launch<0, T, 1>::go(g, b, a, h->stream); break;
     case 2: Launch<0, T, 2>::go(g, b, a, h->stream); break;
