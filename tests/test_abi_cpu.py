@@ -219,3 +219,53 @@ def test_vector_and_minimiser_arguments_rejected(lib):
     cx = C.c_double()
     one = (C.c_double * 1)(0.0)
     assert L.dsm_lbfgs_compact(1, one, one, one, one, 1.0, C.byref(cx), one, one) == lib.DSM_E_INVAL
+
+
+def test_multi_fluid_arguments_rejected(lib):
+    # the N-fluid energy, its L-BFGS and the N-fluid lattice refuse bad
+    # arguments before any device work, so the fake addresses are never touched
+    import ctypes as C
+    import paper_2504_19941_gb300 as P
+    L = lib.load()
+    fake = 1 << 20
+    p = P.make_params("D3Q19", (8, 8, 8), "f32", theta_deg=90.0)
+    d = lambda *v: (C.c_double * len(v))(*v)  # noqa: E731
+    sb = lib.dsm_fe_multi_scratch_bytes(1, 8, 8, 8, 3)
+    assert sb > 0
+
+    def fe(nfluid, kappa, kcs=None, scratch_bytes=sb, c=fake):
+        return L.dsm_fe_energy_grad_multi(C.byref(p), nfluid, kappa, fake, c, None, kcs, None,
+                                          fake, fake, None, fake * 256, scratch_bytes, None)
+    assert fe(5, d(1, 1, 1, 1, 1, 1)) == lib.DSM_E_INVAL            # N above 4
+    assert fe(1, d(1, 1)) == lib.DSM_E_INVAL                        # N below 2
+    assert fe(3, d(1, 1, 0.0, 1)) == lib.DSM_E_INVAL                # a fluid kappa <= 0
+    assert fe(3, None) == lib.DSM_E_INVAL
+    assert fe(3, d(1, 1, 1, 1), kcs=d(-1.0, 0.0)) == lib.DSM_E_INVAL
+    assert fe(3, d(1, 1, 1, 1), c=None) == lib.DSM_E_INVAL
+    assert fe(3, d(-0.5, 1, 1, 1), scratch_bytes=16) == lib.DSM_E_WORKSPACE  # kappa_1 < 0 is valid
+    with pytest.raises(P.DSMError):
+        lib.dsm_lbfgs_multi_workspace_bytes(p, 5, 10)
+    nb = lib.dsm_lbfgs_multi_workspace_bytes(p, 3, 10)
+    assert nb > lib.dsm_lbfgs_workspace_bytes(p, 10)                # two planes per vector
+    info = lib.dsm_lbfgs_info()
+    assert L.dsm_lbfgs_minimize_multi(C.byref(p), 3, d(1, 1, 1, 1), fake, None, None, None,
+                                      fake, 10, 1e-6, 10, fake * 256, nb - 1, C.byref(info),
+                                      None) == lib.DSM_E_WORKSPACE
+    # the N-fluid lattice
+    assert lib.dsm_ml_workspace_bytes(p, 3) > lib.dsm_ml_workspace_bytes(p, 2)
+    with pytest.raises(P.DSMError) as e:
+        lib.dsm_ml_workspace_bytes(P.make_params("D3Q19", (8, 8, 8), "bf16", theta_deg=90.0), 3)
+    assert e.value.status == lib.DSM_E_UNSUPPORTED
+    h = C.c_void_p()
+    nbm = lib.dsm_ml_workspace_bytes(p, 3)
+
+    def create(nfluid, kappa, rho, tau, ws=fake * 256, nbytes=nbm):
+        return L.dsm_ml_create(C.byref(p), nfluid, kappa, rho, tau, ws, nbytes, None,
+                               C.byref(h))
+    assert create(5, d(1, 1, 1, 1, 1, 1), d(1, 1, 1, 1, 1), d(1, 1, 1, 1, 1)) == lib.DSM_E_INVAL
+    assert create(3, d(1, 1, 1, 1), d(1, 0.0, 1), d(1, 1, 1)) == lib.DSM_E_INVAL   # rho <= 0
+    assert create(3, d(1, 1, 1, 1), d(1, 1, 1), d(1, 0.5, 1)) == lib.DSM_E_INVAL   # tau <= 1/2
+    assert create(3, d(1, 1, 1, 1), d(1, 1, 1), d(1, 1, 1), ws=None) == lib.DSM_E_WORKSPACE
+    assert create(3, d(1, 1, 1, 1), d(1, 1, 1), d(1, 1, 1), nbytes=nbm - 1) == lib.DSM_E_WORKSPACE
+    assert L.dsm_ml_step(None, 1) == lib.DSM_E_INVAL
+    assert L.dsm_ml_get_field(None, 1, 0, fake) == lib.DSM_E_INVAL
