@@ -616,12 +616,13 @@ def run_multi(args, rank, world):
     import paper_2504_19941_gb300 as P
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    case = make_case(SHAPE)
-    nx = SHAPE[0]
+    shape = tuple(int(v) for v in args.shape.split(","))
+    case = make_case(shape)
+    nx = shape[0]
     c2 = torch.as_tensor(case.c2, dtype=torch.float32, device=dev)
     xs = torch.arange(c2.numel(), device=dev) % nx
     C = torch.stack([c2 * (xs < nx // 2), c2 * (xs >= nx // 2)]).contiguous()
-    p = P.make_params("D3Q19", SHAPE, "f32", theta_deg=case.theta_deg, g12=case.g12,
+    p = P.make_params("D3Q19", shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
                       g23=case.g23, alpha_s=case.alpha_s)
     k = P._lib.dsm_kappa(p)
     kappa = [k[0], k[1], k[1], k[2]]        # both liquids alike, the gas third
@@ -646,11 +647,11 @@ def run_multi(args, rank, world):
     b = 460 + 160
     if rank == 0:
         print(json.dumps({
-            "metric": "D3Q19 three-fluid LB MLUPS (256x256x192 pillar slab)", "unit": "MLUPS",
+            "metric": "D3Q19 three-fluid LB MLUPS (%dx%dx%d pillar slab)" % shape, "unit": "MLUPS",
             "value": ml.n / t / 1e6, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "D3Q19 FP32 pillar slab 256x256x192, three fluids",
+            "config": {"workload": "D3Q19 FP32 pillar slab %dx%dx%d, three fluids" % shape,
                        "nodes": ml.n, "l2": "f and g 2.9 GB per buffer, larger than L2; no flush"},
             "roofline": {"bound": "hbm", "step_bytes_per_lu": b,
                          "achieved": b * ml.n / t / 1e9, "peak": peak, "unit": "GB/s",

@@ -38,6 +38,7 @@ struct MLArgs {
   T rho[ML_MAX_NF + 1], om[ML_MAX_NF + 1];  // per fluid: density, 1 / tau
   T omg, a2, alpha_s;
   T body[3];
+  int rc;                // the fluids' densities differ (else rho is constant)
   const T *f_in, *g_in;  // Q planes; NF x Q planes (fluid-major)
   T *f_out, *g_out;
   T *C;                  // NF planes: the moments pass output
@@ -86,18 +87,21 @@ __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   }
 }
 
-// rho of the volume fractions at one point
+// rho of the volume fractions at one point.  One reciprocal of 1 - C1 per
+// point; in FP32 the fast reciprocal (within 2 ulp) serves, since every
+// fraction is clamped to [0, 1] right after.
 template <class T, int NF>
 __device__ __forceinline__ T ml_rho(const MLArgs<T> &a, const T (&c)[NF], T c1) {
   const T den = T(1) - c1;
   T r = a.rho[NF];
+  if (!(den > T(1e-6))) return r;
+  T inv;
+  if constexpr (sizeof(T) == 4) inv = __fdividef(1.0f, den);
+  else inv = T(1) / den;
 #pragma unroll
   for (int f = 0; f < NF; f++) {
-    T ph = T(0);
-    if (den > T(1e-6)) {
-      ph = c[f] / den;
-      ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
-    }
+    T ph = c[f] * inv;
+    ph = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
     r += (a.rho[f] - a.rho[NF]) * ph;
   }
   return r;
@@ -151,10 +155,12 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
     }
     lap[0] += w * (c1m - cv[0]);
     lap[NC - 1] += w * (lastm - cv[NC - 1]);
-    const T r = w * ml_rho<T, NF>(a, cm, c1m);
-    gR[0] += r * cx;
-    gR[1] += r * cy;
-    gR[2] += r * cz;
+    if (a.rc) {
+      const T r = w * ml_rho<T, NF>(a, cm, c1m);
+      gR[0] += r * cx;
+      gR[1] += r * cy;
+      gR[2] += r * cz;
+    }
     gc1[0] += w * cx * c1m;
     gc1[1] += w * cy * c1m;
     gc1[2] += w * cz * c1m;
@@ -437,6 +443,7 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
     a.om[f] = T(1.0 / h->tau[f]);
   }
   a.omg = T(1.0 / h->prm.tau_g);
+  for (int f = 0; f < h->nf; f++) a.rc |= h->rho[f] != h->rho[h->nf];
   a.a2 = T(h->prm.alpha * h->prm.alpha);
   a.alpha_s = T(h->prm.alpha_s > 0.0 ? h->prm.alpha_s : h->prm.alpha);
   for (int e = 0; e < 3; e++) a.body[e] = T(h->prm.body_force[e]);
