@@ -304,6 +304,27 @@ def test_wall_poiseuille_closed_form_gpu(prec, tol):
     assert np.abs(lat.field("uz").double().cpu().numpy()).max() < tol * exact.max()
 
 
+@pytest.mark.parametrize("shape", [(1, 1), (3, 1), (1, 5), (5, 4)])
+@pytest.mark.parametrize("faces", [("mirror", "mirror", "wall", "wall", "periodic", "periodic"),
+                                   ("wall", "wall", "mirror", "mirror", "periodic", "periodic")])
+def test_tiny_lattices_with_faces_fp64(shape, faces):
+    # degenerate sizes: beyond a face the neighbour is the node itself, and a
+    # one-node axis has both faces on the same node
+    n = shape[0] * shape[1]
+    sd = np.full(n, -3.0)
+    sd[0] = 1.0
+    c2 = 0.3 + S.perturbation(2, n, 0.2)
+    case = S.Case("tiny", "D2Q9", shape, sd, c2, theta_deg=70.0, g23=0.01, g12=0.01,
+                  alpha_s=1.0, body=(1e-4, -1e-4, 0.0), faces=faces)
+    lat = gpu_lattice(case, "f64")
+    p, c1, f, g = _oracle_case(case, O.D2Q9)
+    lat.step(7)
+    f, g = O.lb_run(p, 2, c1, f, g, 7)
+    perm = direction_map(O.D2Q9)
+    gf, gg = gpu_pops(lat, perm)
+    assert rel_err(gf, f) < 1e-12 and rel_err(gg, g) < 1e-12
+
+
 def test_faces_refused_by_batch():
     case = _faces_2d()
     lats = [gpu_lattice(case, "f32") for _ in range(2)]

@@ -276,3 +276,20 @@ def test_ml_three_layers_relax_to_the_energy_minimum():
     v, E, gr, info = olbfgs.minimize(fg, C.ravel(), tol=1e-11, max_iter=20000)
     assert np.max(np.abs(got - v.reshape(2, nx))) < 1e-6
     assert np.abs(ml.field("ux").cpu().numpy()).max() < 1e-9
+
+
+@pytest.mark.parametrize("shape,faces", [((13, 9, 7), ("mirror", "mirror", "periodic", "periodic",
+                                                      "wall", "wall")),
+                                         ((3, 1), ("wall", "wall", "mirror", "mirror", "periodic",
+                                                   "periodic"))])
+def test_ml_ragged_and_tiny_fp64(shape, faces):
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(n)
+    c1 = np.where(np.arange(n) % 5 == 0, 0.7, 0.02)
+    C = rng.uniform(0.1, 0.3, size=(2, n)) * (1 - c1)
+    case = (shape, c1, C, (0.02, 0.03, 0.025, 0.035), (1.0, 0.7, 0.5), (0.8, 1.0, 0.7), faces,
+            (1e-5, 0.0, -1e-5) if len(shape) == 3 else (1e-5, 0.0, 0.0))
+    ml, m, f, g, kind = _ml_run(case, "f64", 9)
+    errs = _ml_compare(ml, m, f, g, kind)
+    assert max(errs.values()) < 1e-12, errs
+
