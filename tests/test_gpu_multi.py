@@ -191,9 +191,13 @@ def _ml_compare(ml, m, f, g, kind):
     for k in range(nf):
         errs[f"C{k}"] = rel_err(ml.field("C", k).double().cpu().numpy(), F["C"][k])
         errs[f"mu{k}"] = rel_err(ml.field("mu", k).double().cpu().numpy(), F["mu"][k])
+    umax = np.abs(F["u"]).max()
     for a, name in enumerate(("ux", "uy", "uz")):
-        if np.abs(F["u"][a]).max() > 0:
-            errs[name] = rel_err(ml.field(name).double().cpu().numpy(), F["u"][a])
+        got = ml.field(name).double().cpu().numpy()
+        if np.abs(F["u"][a]).max() > 1e-9 * umax:
+            errs[name] = rel_err(got, F["u"][a])
+        else:  # zero by symmetry up to rounding: compare against max |u|
+            errs[name] = np.abs(got - F["u"][a]).max() / max(umax, 1e-300)
     errs["pt"] = rel_err(ml.field("pt").double().cpu().numpy(), F["pt"])
     errs["rho"] = rel_err(ml.field("rho").double().cpu().numpy(), F["rho"])
     errs["tau"] = rel_err(ml.field("tau").double().cpu().numpy(), F["tau"])
