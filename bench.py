@@ -208,6 +208,19 @@ def cpu_baseline(max_seconds=15.0):
             "sample": f"D3Q19 FP64 oracle, 64x64x48 pillar-slab slice, {steps} steps, {dt:.1f} s"}
 
 
+def oracle_single_core(max_seconds=5.0):
+    """The same oracle slice on one host core (a child process with one OpenMP
+    thread): the single-core figure next to the all-cores one."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core",
+                        str(max_seconds)], env=env, capture_output=True, text=True, timeout=300)
+    try:
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (ValueError, IndexError):
+        return {"error": (r.stderr or r.stdout)[-200:]}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle timed on the host cores.  Each of the K
     timed steps (after W untimed ones) is a bounded sample of the workload --
@@ -237,7 +250,8 @@ def run_reference(args, rank, world):
                                       f"pillar-slab slice for {per_step:.2f} s ({steps_done} oracle "
                                       f"steps in {secs:.1f} s timed)"},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
+                   "d2h_bytes_per_step": 0},
+           "cpu_single_core": oracle_single_core()}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -530,11 +544,23 @@ def run_plain_fp64(args, rank, world):
             key = ("g_eq" if form == "auto" else "populations") + "/" + mode
             res[key] = {"us_per_step": dt / case.steps * 1e6, "MLUPS": lat.n * case.steps / dt / 1e6}
     best = min(res, key=lambda k: res[k]["us_per_step"])
+    # the oracle on the same case, on the host cores (200 steps)
+    import oracle as O
+    k, _ = O.kappa_from_angle(case.theta_deg, case.g23, case.g12)
+    po = O.make_params(O.D2Q9, case.shape, k, alpha_s=case.alpha_s)
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+    f, g = O.lb_init(po, 2, c1, case.c2)
+    t0 = time.perf_counter()
+    O.lb_run(po, 2, c1, f, g, 200)
+    t_or = (time.perf_counter() - t0) / 200
+    oracle = {"us_per_step": t_or * 1e6, "MLUPS": case.n / t_or / 1e6,
+              "cores": OracleSlice.cores(), "kind": "oracle", "sample": "200 steps of the same case"}
     if rank == 0:
         print(json.dumps({"metric": "D2Q9 FP64 128x64 wall drop, 2000 steps", "unit": "us/step",
                           "value": res[best]["us_per_step"], "best": best,
                           "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
-                          "data": "synthetic", "modes": res}), flush=True)
+                          "data": "synthetic", "modes": res, "cpu_baseline": oracle}),
+              flush=True)
     return 0
 
 
@@ -780,6 +806,14 @@ def run_em(args, rank, world):
 
 
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-one-core":
+        sl = OracleSlice()
+        sl.run(0.0)
+        steps, dt = sl.run(float(sys.argv[2]))
+        print(json.dumps({"value": sl.n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1,
+                          "kind": "oracle",
+                          "sample": f"64x64x48 slice, {steps} steps, {dt:.1f} s, one thread"}))
+        return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
