@@ -1040,15 +1040,18 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
 // that their work spreads over four times as many SMs.  Larger lattices: shapes
 // measured on the fused pass (D3Q19 FP32, g held as g_eq), best kept --
 //   256x256x192:  32x4x2 0.510 ms, 64x4x1 0.494, 128x2x1 0.486, 256x1x1 0.484;
+//                 later, on the current kernel: 256x1x1 0.4742, 128x1x1 0.4678,
+//                 64x1x1 0.4710 (128x1x1 also best for the population form and
+//                 for D2Q9 at 4096^2);
 //   384x384x256:  32x4x2 1.784 ms, 64x4x1 1.784, 64x2x2 1.772, 128x2x1 2.025,
 //                 128x1x2 2.017.
-// Whole 256-node rows where nx allows, else 64x2x2, else 32-wide bricks.  The
+// 128-node rows where nx is a multiple of 256, else 64x2x2, else 32-wide bricks.  The
 // batched launch keeps 32-wide bricks for every lattice (lb_block_batch), which
 // suits its small lattices.
 inline dim3 lb_block_batch(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
 inline dim3 lb_block(int kind, int nx, int ny, int nz) {
   if ((long long)nx * ny * nz < 2ll * 152 * 256) return kind == 0 ? dim3(32, 2, 1) : dim3(32, 1, 2);
-  if (nx % 256 == 0) return dim3(256, 1, 1);
+  if (nx % 256 == 0) return dim3(128, 1, 1);  // rows of 128: more, smaller blocks per SM
   if (nx % 64 == 0) return kind == 0 ? dim3(64, 4, 1) : dim3(64, 2, 2);
   return lb_block_batch(kind);
 }
