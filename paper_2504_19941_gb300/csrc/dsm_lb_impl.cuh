@@ -259,14 +259,14 @@ __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, in
   a.C[n] = moments_eq_node<L, T>(Ay, Cy, uy);
 }
 
-// The same pass for D3Q19, tiled: a 32 x 8 block walks a run of zrun z planes.
+// The same pass for D3Q19, tiled: a 32 x 4 block walks a run of zrun z planes.
 // Each plane of (A, C, u) over the tile and a one-node halo is copied once into
 // a five-plane shared ring by asynchronous copies (cp.async), three planes
 // ahead of the plane being summed, and the five in-plane "cross" points (0,0),
 // (+-1,0), (0,+-1) a node needs from planes z-1, z, z+1 stay in registers from
 // one z to the next: per node 37 shared reads instead of 71 scattered loads.
 // One barrier per plane.
-constexpr int MT_X = 32, MT_Y = 8, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_RING = 5;
+constexpr int MT_X = 32, MT_Y = 4, MT_HX = MT_X + 2, MT_HY = MT_Y + 2, MT_RING = 5;
 
 template <class T>
 struct EqPt {
@@ -290,7 +290,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <class T, class S>
-__global__ void __launch_bounds__(MT_X * MT_Y, sizeof(T) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(MT_X * MT_Y, sizeof(T) == 8 ? 1 : 6)
     moments_eq_tiled_kernel(LBArgs<T, S> a, int zrun) {
   using L = Lat<1>;
   constexpr int NH = MT_HX * MT_HY;          // nodes of one staged plane
@@ -1045,13 +1045,14 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
 //                 for D2Q9 at 4096^2);
 //   384x384x256:  32x4x2 1.784 ms, 64x4x1 1.784, 64x2x2 1.772, 128x2x1 2.025,
 //                 128x1x2 2.017.
-// 128-node rows where nx is a multiple of 256, else 64x2x2, else 32-wide bricks.  The
+//   384x384x256, later: 64x2x2 1.7357 ms, 128x1x1 1.7138.
+// 128-node rows where nx is a multiple of 128, else 64x2x2, else 32-wide bricks.  The
 // batched launch keeps 32-wide bricks for every lattice (lb_block_batch), which
 // suits its small lattices.
 inline dim3 lb_block_batch(int kind) { return kind == 0 ? dim3(32, 8, 1) : dim3(32, 4, 2); }
 inline dim3 lb_block(int kind, int nx, int ny, int nz) {
   if ((long long)nx * ny * nz < 2ll * 152 * 256) return kind == 0 ? dim3(32, 2, 1) : dim3(32, 1, 2);
-  if (nx % 256 == 0) return dim3(128, 1, 1);  // rows of 128: more, smaller blocks per SM
+  if (nx % 128 == 0) return dim3(128, 1, 1);  // rows of 128: more, smaller blocks per SM
   if (nx % 64 == 0) return kind == 0 ? dim3(64, 4, 1) : dim3(64, 2, 2);
   return lb_block_batch(kind);
 }
@@ -1083,7 +1084,7 @@ LBArgs<T, S> typed(const LBRaw &r) {
   return a;
 }
 
-// The same pass for D2Q9, tiled: a 32 x 8 block stages (A, C, u_x, u_y) of its
+// The same pass for D2Q9, tiled: a 32 x 4 block stages (A, C, u_x, u_y) of its
 // tile and a one-node halo in shared memory once, then each node sums its nine
 // points from there (the per-node arithmetic is moments_eq_node, as above).
 template <class T, class S>
@@ -1139,10 +1140,10 @@ struct LBOps {
     }
     if (r.implicit && K == 1) {
       // the longest run of z planes (fewer ring refills per plane) that still
-      // fills one wave of three 256-thread blocks per SM
+      // fills one wave of six 128-thread blocks per SM
       const int tiles = ((r.nx + MT_X - 1) / MT_X) * ((r.ny + MT_Y - 1) / MT_Y);
       int zrun = 32;
-      while (zrun > 4 && (long long)tiles * ((r.nz + zrun - 1) / zrun) < 3 * 152) zrun /= 2;
+      while (zrun > 4 && (long long)tiles * ((r.nz + zrun - 1) / zrun) < 6 * 152) zrun /= 2;
       moments_eq_tiled_kernel<T, S><<<dim3((r.nx + MT_X - 1) / MT_X, (r.ny + MT_Y - 1) / MT_Y,
                                            (r.nz + zrun - 1) / zrun),
                                       dim3(MT_X, MT_Y, 1), moments_eq_smem<T>(), st>>>(typed<T, S>(r), zrun);
