@@ -128,6 +128,53 @@ def test_lbfgs_mirror_half_domain_matches_symmetric_full_domain():
     assert np.max(np.abs(xh.double().cpu().numpy().reshape(ny, nx) - xf2[:, :nx])) < 2e-3
 
 
+def _sinusoid_problem(case):
+    p = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg, g23=case.g23,
+                      g12=case.g12)
+    c1 = O.solid_profile(case.solid_sd, case.alpha_s)
+    return p, _t(c1), _t(case.c2)
+
+
+def test_lbfgs_sinusoid_drop_full_size():
+    # the 128^3 energy-minimisation case of a drop on the sinusoidal wall
+    # z < 16 + 6 sin(2 pi x / 32), volume-constrained (k_cs = 1e-2): the native
+    # L-BFGS converges, lowers the energy and keeps the volume
+    case = S.em_sinusoid_drop()
+    p, c1f, c2f = _sinusoid_problem(case)
+    V0 = float(c2f.double().sum())
+    fe = FreeEnergy(p)
+    E0, _ = fe(c1f, c2f, active=2, kcs=case.extra["kcs"], V0=V0)
+    x, E, info = lbfgs(fe, c2f, c1f, active=2, kcs=case.extra["kcs"], V0=V0, tol=1e-5,
+                       max_iter=20000)
+    assert info["converged"] and info["rms_grad"] < 1e-5, info
+    assert E < E0.item()
+    assert abs(float(x.double().sum()) / V0 - 1.0) < 5e-3
+    assert float(x.min()) > -0.05 and float(x.max()) < 1.05
+
+
+def test_lbfgs_sinusoid_drop_matches_oracle():
+    # the same geometry scaled to 32^3: the GPU minimiser and the oracle's
+    # reach the same minimum
+    case = S.em_sinusoid_drop(n=32, amplitude=1.5, wavelength=8.0, base=4.0, radius=7.5)
+    p, c1f, c2f = _sinusoid_problem(case)
+    V0 = float(c2f.double().sum())
+    kcs = case.extra["kcs"]
+    x, E, info = lbfgs(FreeEnergy(p), c2f, c1f, active=2, kcs=kcs, V0=V0, tol=1e-5,
+                       max_iter=20000)
+    assert info["rms_grad"] < 1e-5
+    po = O.make_params(O.D3Q19, case.shape, _lib.dsm_kappa(p))
+    c1 = c1f.double().cpu().numpy()
+
+    def fg(v):
+        e, gr, _ = O.energy_grad(po, c1, v, active=2, kcs=kcs, V0=V0)
+        return e, gr
+    xo, Eo, _, info_o = olbfgs.minimize(fg, c2f.double().cpu().numpy(), tol=1e-7,
+                                        max_iter=20000)
+    assert info_o["rms_grad"] < 2e-7
+    assert abs(E - Eo) / abs(Eo) < 1e-5, (E, Eo)
+    assert np.max(np.abs(x.double().cpu().numpy() - xo)) < 2e-3
+
+
 def test_energy_grad_large_grid():
     shape = (128, 128, 128)
     case = S.em_sphere_interface()
