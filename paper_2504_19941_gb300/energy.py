@@ -41,6 +41,16 @@ class FreeEnergy:
         return energy, grad
 
 
+    def decomposition(self) -> dict:
+        """The last evaluation's energy by term (Sec. III.B reports the surface
+        and gravitational parts of capillary rise): surface = bulk + gradient
+        (the interfacial energy of every component pair), confinement,
+        constraint (pressure or volume term), gravity, and the liquid volume V."""
+        t = self.terms.cpu().tolist()
+        return {"surface": t[0] + t[1], "bulk": t[0], "gradient": t[1], "confinement": t[2],
+                "constraint": t[3], "gravity": t[4], "volume": t[5]}
+
+
 class Energy(torch.autograd.Function):
     """E(C) with the hand-written adjoint.  Differentiable in the active field."""
 

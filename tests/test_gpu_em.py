@@ -61,6 +61,10 @@ def test_energy_grad_parity(lat, shape, active, constraint):
     assert rel_err(g.double().cpu().numpy(), go) < 1e-5
     terms = fe.terms.cpu().numpy()
     np.testing.assert_allclose(terms, to, rtol=1e-5, atol=1e-6)
+    d = fe.decomposition()
+    assert abs(d["surface"] - (to[0] + to[1])) <= 1e-5 * abs(to[0] + to[1])
+    assert abs(d["surface"] + d["confinement"] + d["constraint"] + d["gravity"] - Eo) \
+        <= 1e-6 * abs(Eo)
 
 
 MIRROR_CASES = [("D2Q9", (23, 17), ("mirror", "mirror", "wall", "wall", "periodic", "periodic")),
