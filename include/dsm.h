@@ -435,7 +435,12 @@ dsm_status dsm_destroy(dsm_lattice *h);
  *   rho = rho_{N+1} + sum_f (rho_f - rho_{N+1}) phi_f, phi_f = C_f / (1 - C_1)
  *   clamped to [0, 1]; tau = the tau of the locally largest fluid (ties to the
  *   later fluid); interpolated bounce-back and the face rules as for N = 2.
- * With N = 2 this is dsm_step's population form.  The workspace (at least
+ * With tau_g = 1 and every face periodic each g_f is held as g_eq (the
+ * post-collision g_f is g_eq, fixed by A_f = mu_f - 3/2 C_f u.u, C_f and u):
+ * the fused pass stores A_f and u instead of Q populations per fluid and the
+ * moments pass rebuilds C_f from them, as dsm_set_g_storage's DSM_G_AUTO does
+ * for two fluids.  Otherwise g_f is stored as populations.  With N = 2 this is
+ * dsm_step in the same storage form.  The workspace (at least
  * dsm_ml_workspace_bytes, 256-byte aligned) is the caller's.  dsm_ml_set_solid
  * takes a signed distance (kind 0) or C1 itself (kind 1); dsm_ml_set_fluids
  * the free fluids (N - 1 planes of nx*ny*nz reals) and writes the rest state.
@@ -443,7 +448,7 @@ dsm_status dsm_destroy(dsm_lattice *h);
  * dependent fluid), DSM_FIELD_MU with index f gives mu_{2+f}, DSM_FIELD_C1,
  * UX, UY, UZ, PT, RHO, TAU as for dsm_get_field; DSM_FIELD_C3 is DSM_E_INVAL.
  * dsm_ml_get_populations: f (Q planes) and g (N - 1 blocks of Q planes), dense
- * nx*ny*nz rows.  No error latching: the caller checks fields for NaN. */
+ * nx*ny*nz rows (held as g_eq: rebuilt from (A_f, C_f, u)).  No error latching: the caller checks fields for NaN. */
 typedef struct dsm_mlattice dsm_mlattice;
 dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes);
 dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa,

@@ -17,6 +17,11 @@
 //     clamped to [0, 1] (0 where 1 - C_1 <= 1e-6);
 //   tau = the relaxation time of the locally largest fluid concentration,
 //     ties to the later fluid.
+// At tau_g = 1 with periodic faces every g_f is held as g_eq, as for two
+// fluids: the post-collision g_f is g_eq fixed by (A_f = mu_f - 3/2 C_f u.u,
+// C_f, u), so the fused pass stores A_f and the shared u instead of Q
+// populations per fluid, and the moments pass rebuilds each C_f from its
+// neighbours' (A_f, C_f, u) with the two-fluid form's arithmetic.
 #include <math.h>
 #include <string.h>
 
@@ -42,6 +47,9 @@ struct MLArgs {
   const T *f_in, *g_in;  // Q planes; NF x Q planes (fluid-major)
   T *f_out, *g_out;
   T *C;                  // NF planes: the moments pass output
+  const T *Cprev;        // g_eq form: NF planes, C of the state's last collision
+  T *A;                  // g_eq form: NF planes of A_f = mu_f - 3/2 C_f u.u
+  T *U;                  // g_eq form: u_x, u_y, u_z planes
   const T *C1;
   T *out;                // fields mode: one plane
   int field, index;
@@ -87,6 +95,40 @@ __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   }
 }
 
+// moments pass with g held as g_eq: C_f(x) = sum_i g_eq_i(x - c_i) from the
+// neighbours' (A_f, C_f, u), through the two-fluid form's per-node arithmetic
+template <int K, class T, int NF>
+__global__ void __launch_bounds__(256) ml_moments_eq_kernel(MLArgs<T> a) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z * blockDim.z + threadIdx.z;
+  if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+  Hood h;
+  h.init(x, y, z, a.nx, a.ny, a.nz);
+  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  T uy[Q][3];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const int m = i == 0 ? n : h.minus<L>(i);
+    uy[i][0] = (i == 0 || L::cx(i)) ? __ldg(a.U + m) : T(0);
+    uy[i][1] = (i == 0 || L::cy(i)) ? __ldg(a.U + a.pitch + m) : T(0);
+    uy[i][2] = (L::D == 3 && (i == 0 || L::cz(i))) ? __ldg(a.U + 2 * a.pitch + m) : T(0);
+  }
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    T Ay[Q], Cy[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const int m = i == 0 ? n : h.minus<L>(i);
+      Ay[i] = __ldg(a.A + f * a.pitch + m);
+      Cy[i] = __ldg(a.Cprev + f * a.pitch + m);
+    }
+    a.C[f * a.pitch + n] = moments_eq_node<L, T>(Ay, Cy, uy);
+  }
+}
+
 // rho of the volume fractions at one point.  One reciprocal of 1 - C1 per
 // point; in FP32 the fast reciprocal (within 2 ulp) serves, since every
 // fraction is clamped to [0, 1] right after.
@@ -109,7 +151,7 @@ __device__ __forceinline__ T ml_rho(const MLArgs<T> &a, const T (&c)[NF], T c1) 
 
 enum { ML_STEP = 0, ML_FIELDS = 1 };
 
-template <int K, class T, int NF, int MODE>
+template <int K, class T, int NF, int MODE, bool EQ>
 __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
@@ -199,14 +241,16 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
 
   // ---- pull f and every g_f from x - c_j, all loads issued up front; the
   // rare links (a solid upstream node, a domain face) are corrected below
-  T fs[Q], gs[NF][Q];
+  T fs[Q], gs[EQ ? 1 : NF][Q];
 #pragma unroll
   for (int j = 0; j < Q; j++) {
     const int src = h.minus<L>(j);
     fs[j] = __ldg(plane(a.f_in, a.pitch, j) + src);
+    if constexpr (!EQ) {
 #pragma unroll
-    for (int f = 0; f < NF; f++)
-      gs[f][j] = __ldg(plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, j) + src);
+      for (int f = 0; f < NF; f++)
+        gs[f][j] = __ldg(plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, j) + src);
+    }
   }
   // interpolated bounce-back where the upstream node (or its image across a
   // mirror) is solid
@@ -237,7 +281,8 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   }
   // mirror and wall faces: specular reflection or halfway bounce-back for f
   // and every g_f (a mirror link with a solid image keeps the value above)
-  if (a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz)) {
+  // (the g_eq form is periodic only)
+  if (!EQ && a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz)) {
     for (int j = 1; j < Q; j++) {
       int k;
       const int cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
@@ -253,8 +298,10 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
       for (int kk = 1; kk < Q; kk++)
         if (kk == j) {
           if (!interp) fs[kk] = fv;
+          if constexpr (!EQ) {
 #pragma unroll
-          for (int f = 0; f < NF; f++) gs[f][kk] = gv[f];
+            for (int f = 0; f < NF; f++) gs[f][kk] = gv[f];
+          }
         }
     }
   }
@@ -308,19 +355,29 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
       fo = fs[i] + (w * (pt + rho * s) - fs[i]) * om + Fi;
     }
     plane(a.f_out, a.pitch, i)[n] = fo;
+    if constexpr (!EQ) {
 #pragma unroll
-    for (int f = 0; f < NF; f++) {
-      const T Cf = cv[1 + f];
-      const T geq = i == 0 ? Cf - (T(1) - w) * mu[f] + w * Cf * s : w * (mu[f] + Cf * s);
-      T *go = a.g_out + (long long)f * Q * a.pitch;
-      plane(go, a.pitch, i)[n] = gs[f][i] + (geq - gs[f][i]) * a.omg;
+      for (int f = 0; f < NF; f++) {
+        const T Cf = cv[1 + f];
+        const T geq = i == 0 ? Cf - (T(1) - w) * mu[f] + w * Cf * s : w * (mu[f] + Cf * s);
+        T *go = a.g_out + (long long)f * Q * a.pitch;
+        plane(go, a.pitch, i)[n] = gs[f][i] + (geq - gs[f][i]) * a.omg;
+      }
     }
+  }
+  if constexpr (EQ) {
+    // g* = g_eq (tau_g = 1): store what fixes it
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.A[f * a.pitch + n] = mu[f] - T(1.5) * cv[1 + f] * uu;
+    a.U[n] = u[0];
+    a.U[a.pitch + n] = u[1];
+    if (L::D == 3) a.U[2 * a.pitch + n] = u[2];
   }
 }
 
 // initial state at rest: f_i = w_i, g_f,i = g_eq,i(C_f, mu_f(C), u = 0); C
 // (NF planes) is read from a.C
-template <int K, class T, int NF>
+template <int K, class T, int NF, bool EQ>
 __global__ void __launch_bounds__(256) ml_init_kernel(MLArgs<T> a) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
@@ -360,11 +417,39 @@ __global__ void __launch_bounds__(256) ml_init_kernel(MLArgs<T> a) {
   for (int i = 0; i < Q; i++) {
     const T w = T(L::w(i));
     plane(a.f_out, a.pitch, i)[n] = w;
+    if constexpr (!EQ) {
+      for (int f = 0; f < NF; f++) {
+        const T mu = d[1 + f] - d[NC - 1];
+        const T Cf = cv[1 + f];
+        T *go = a.g_out + (long long)f * Q * a.pitch;
+        plane(go, a.pitch, i)[n] = i == 0 ? Cf - (T(1) - w) * mu : w * mu;
+      }
+    }
+  }
+  if constexpr (EQ) {  // at rest: A_f = mu_f, u = 0
+    for (int f = 0; f < NF; f++) a.A[f * a.pitch + n] = d[1 + f] - d[NC - 1];
+    for (int e = 0; e < L::D; e++) a.U[e * a.pitch + n] = T(0);
+  }
+}
+
+// the populations of g held as g_eq, for reading the state: g_f,i(x) =
+// g_eq_i(A_f, C_f, u at x), C_f that of the state's last collision; dense
+// output, NF blocks of Q rows of N
+template <int K, class T, int NF>
+__global__ void __launch_bounds__(256) ml_g_of_eq_kernel(MLArgs<T> a, T *out) {
+  using L = Lat<K>;
+  constexpr int Q = L::Q;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const T ux = a.U[n], uy = a.U[a.pitch + n], uz = L::D == 3 ? a.U[2 * a.pitch + n] : T(0);
+    const T uu = ux * ux + uy * uy + uz * uz;
     for (int f = 0; f < NF; f++) {
-      const T mu = d[1 + f] - d[NC - 1];
-      const T Cf = cv[1 + f];
-      T *go = a.g_out + (long long)f * Q * a.pitch;
-      plane(go, a.pitch, i)[n] = i == 0 ? Cf - (T(1) - w) * mu : w * mu;
+      const T A = a.A[f * a.pitch + n], Cf = a.Cprev[f * a.pitch + n];
+      for (int i = 0; i < Q; i++) {
+        const T v = i == 0 ? Cf - T(1.0 - L::w(0)) * A - T(1.5) * Cf * uu
+                           : T(L::w(i)) * geq_core(A, Cf, cdot<L>(i, ux, uy, uz));
+        out[((long long)f * Q + i) * a.N + n] = v;
+      }
     }
   }
 }
@@ -379,18 +464,22 @@ struct dsm_mlattice {
   double kappa[ML_MAX_NF + 2], rho[ML_MAX_NF + 1], tau[ML_MAX_NF + 1];
   long long N, pitch;
   cudaStream_t stream;
-  char *f[2], *g[2], *C, *C1;
+  char *f[2], *g[2], *C[2], *C1, *M;  // C[cur]: C of the last collision; M: A_f and u
   int cur;
+  bool eq;  // g held as g_eq (tau_g = 1, periodic faces)
   bool has_solid, has_fluid;
 };
 
 namespace {
 
 struct MLLayout {
-  size_t f[2], g[2], C, C1, total;
+  size_t f[2], g[2], C[2], C1, M, total;
 };
 
-MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch) {
+// g held as g_eq: tau_g = 1 and every face periodic
+bool ml_eq(const dsm_params *p) { return p->tau_g == 1.0 && !has_walls(p); }
+
+MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq) {
   MLLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -399,9 +488,10 @@ MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch) {
     return at;
   };
   for (int b = 0; b < 2; b++) L.f[b] = take((size_t)q * pitch * real_bytes);
-  for (int b = 0; b < 2; b++) L.g[b] = take((size_t)nf * q * pitch * real_bytes);
-  L.C = take((size_t)nf * pitch * real_bytes);
+  for (int b = 0; b < 2; b++) L.g[b] = take(eq ? 0 : (size_t)nf * q * pitch * real_bytes);
+  for (int b = 0; b < 2; b++) L.C[b] = take((size_t)nf * pitch * real_bytes);
   L.C1 = take((size_t)pitch * real_bytes);
+  L.M = take(eq ? (size_t)(nf + 3) * pitch * real_bytes : 0);
   L.total = o;
   return L;
 }
@@ -452,7 +542,10 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
   a.g_in = (const T *)h->g[src];
   a.f_out = (T *)h->f[src ^ 1];
   a.g_out = (T *)h->g[src ^ 1];
-  a.C = (T *)h->C;
+  a.C = (T *)h->C[src ^ 1];
+  a.Cprev = (const T *)h->C[src];
+  a.A = (T *)h->M;
+  a.U = h->M ? (T *)h->M + (long long)h->nf * h->pitch : nullptr;
   a.C1 = (const T *)h->C1;
   return a;
 }
@@ -466,16 +559,17 @@ dim3 ml_grid(const dsm_mlattice *h) {
 
 // kernel dispatch over (lattice, free fluids) for one arithmetic type
 template <class T, template <int, class, int> class Launch>
-cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a) {
+cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a, void *extra = nullptr) {
   const int key = h->prm.lattice * 4 + h->nf;
   const dim3 g = ml_grid(h), b = ml_block(h);
+  const bool eq = h->eq;
   switch (key) {
-    case 1: Launch<0, T, 1>::go(g, b, a, h->stream); break;
-    case 2: Launch<0, T, 2>::go(g, b, a, h->stream); break;
-    case 3: Launch<0, T, 3>::go(g, b, a, h->stream); break;
-    case 5: Launch<1, T, 1>::go(g, b, a, h->stream); break;
-    case 6: Launch<1, T, 2>::go(g, b, a, h->stream); break;
-    case 7: Launch<1, T, 3>::go(g, b, a, h->stream); break;
+    case 1: Launch<0, T, 1>::go(g, b, a, h->stream, eq, extra); break;
+    case 2: Launch<0, T, 2>::go(g, b, a, h->stream, eq, extra); break;
+    case 3: Launch<0, T, 3>::go(g, b, a, h->stream, eq, extra); break;
+    case 5: Launch<1, T, 1>::go(g, b, a, h->stream, eq, extra); break;
+    case 6: Launch<1, T, 2>::go(g, b, a, h->stream, eq, extra); break;
+    case 7: Launch<1, T, 3>::go(g, b, a, h->stream, eq, extra); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -483,26 +577,38 @@ cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a) {
 
 template <int K, class T, int NF>
 struct MomentsL {
-  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
-    ml_moments_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
+    if (eq) ml_moments_eq_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+    else ml_moments_kernel<K, T, NF><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct StepL {
-  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
-    ml_node_kernel<K, T, NF, ML_STEP><<<g, b, 0, s>>>(a);
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
+    if (eq) ml_node_kernel<K, T, NF, ML_STEP, true><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_STEP, false><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct FieldsL {
-  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
-    ml_node_kernel<K, T, NF, ML_FIELDS><<<g, b, 0, s>>>(a);
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
+    if (eq) ml_node_kernel<K, T, NF, ML_FIELDS, true><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_FIELDS, false><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct InitL {
-  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s) {
-    ml_init_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+  static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
+    if (eq) ml_init_kernel<K, T, NF, true><<<g, b, 0, s>>>(a);
+    else ml_init_kernel<K, T, NF, false><<<g, b, 0, s>>>(a);
+  }
+};
+template <int K, class T, int NF>
+struct GofEqL {
+  static void go(dim3, dim3, const MLArgs<T> &a, cudaStream_t s, bool, void *out) {
+    long long blocks = (a.N + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    ml_g_of_eq_kernel<K, T, NF><<<(int)blocks, 256, 0, s>>>(a, (T *)out);
   }
 };
 
@@ -540,7 +646,8 @@ dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes
   if (p->precision != DSM_F64 && p->precision != DSM_F32) return DSM_E_UNSUPPORTED;
   const long long N = (long long)p->nx * p->ny * p->nz;
   const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
-  *bytes = ml_layout(q, nfluid - 1, p->precision == DSM_F64 ? 8 : 4, round_up(N, 64)).total;
+  *bytes = ml_layout(q, nfluid - 1, p->precision == DSM_F64 ? 8 : 4, round_up(N, 64), ml_eq(p))
+               .total;
   return DSM_OK;
 }
 
@@ -555,7 +662,7 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   const long long pitch = round_up(N, 64);
   const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
   const int rb = p->precision == DSM_F64 ? 8 : 4;
-  const MLLayout L = ml_layout(q, nfluid - 1, rb, pitch);
+  const MLLayout L = ml_layout(q, nfluid - 1, rb, pitch, ml_eq(p));
   if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255u)) return DSM_E_WORKSPACE;
   dsm_mlattice *h = new (std::nothrow) dsm_mlattice;
   if (!h) return DSM_E_INVAL;
@@ -572,13 +679,15 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   h->N = N;
   h->pitch = pitch;
   h->stream = (cudaStream_t)cuda_stream;
+  h->eq = ml_eq(p);
   char *w = (char *)d_workspace;
   for (int b = 0; b < 2; b++) {
     h->f[b] = w + L.f[b];
-    h->g[b] = w + L.g[b];
+    h->g[b] = h->eq ? nullptr : w + L.g[b];
+    h->C[b] = w + L.C[b];
   }
-  h->C = w + L.C;
   h->C1 = w + L.C1;
+  h->M = h->eq ? w + L.M : nullptr;
   // no solid until one is set: C1 = 0
   if (cudaMemsetAsync(h->C1, 0, (size_t)pitch * rb, h->stream) != cudaSuccess) {
     delete h;
@@ -614,9 +723,10 @@ dsm_status dsm_ml_set_solid(dsm_mlattice *h, const void *d_field, int kind) {
 
 dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c) {
   if (!h || !d_c) return DSM_E_INVAL;
-  // the free fluids into C (plane by plane), then the rest state into buffer 0
+  // the free fluids into C[0] (plane by plane), then the rest state into
+  // buffer 0 (with g held as g_eq, C[0] is then the C of the state)
   for (int f = 0; f < h->nf; f++) {
-    cudaError_t e = cudaMemcpyAsync(h->C + (size_t)f * h->pitch * h->real_bytes,
+    cudaError_t e = cudaMemcpyAsync(h->C[0] + (size_t)f * h->pitch * h->real_bytes,
                                     (const char *)d_c + (size_t)f * h->N * h->real_bytes,
                                     (size_t)h->N * h->real_bytes, cudaMemcpyDeviceToDevice,
                                     h->stream);
@@ -659,6 +769,12 @@ dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g) {
     if (cudaMemcpyAsync((char *)d_f + i * row, h->f[h->cur] + i * pb, row,
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       return DSM_E_CUDA;
+  if (d_g && h->eq) {  // rebuilt from (A_f, C_f, u)
+    const cudaError_t e = h->real_bytes == 8
+                              ? ml_dispatch<double, GofEqL>(h, ml_args<double>(h, h->cur), d_g)
+                              : ml_dispatch<float, GofEqL>(h, ml_args<float>(h, h->cur), d_g);
+    return e == cudaSuccess ? DSM_OK : DSM_E_CUDA;
+  }
   for (int i = 0; d_g && i < h->nf * h->q; i++)
     if (cudaMemcpyAsync((char *)d_g + i * row, h->g[h->cur] + i * pb, row,
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)

@@ -297,3 +297,51 @@ def test_ml_ragged_and_tiny_fp64(shape, faces):
     errs = _ml_compare(ml, m, f, g, kind)
     assert max(errs.values()) < 1e-12, errs
 
+
+def _periodic(case):
+    shape, c1, C, kappa, rho, tau, faces, body = case
+    return shape, c1, C, kappa, rho, tau, None, body
+
+
+@pytest.mark.parametrize("make", [_ml_case_2d, _ml_case_3d])
+@pytest.mark.parametrize("nf", [2, 3])
+def test_ml_geq_form_fp64_parity(make, nf):
+    # tau_g = 1 and periodic faces: g held as g_eq (A_f, u); the same step as
+    # the population-form oracle up to rounding
+    ml, m, f, g, kind = _ml_run(_periodic(make(nf)), "f64", 20, tau_g=1.0)
+    errs = _ml_compare(ml, m, f, g, kind)
+    assert max(errs.values()) < 1e-12, errs
+
+
+def test_ml_geq_form_fp32_parity():
+    ml, m, f, g, kind = _ml_run(_periodic(_ml_case_3d(2)), "f32", 40, tau_g=1.0)
+    e = _ml_compare(ml, m, f, g, kind)
+    assert e["f"] < 1e-5 and e["g"] < 1e-5 and e["C0"] < 1e-5 and e["C1"] < 1e-5, e
+    assert e["pt"] < 1e-5 and e["rho"] < 1e-5 and e["mu0"] < 1e-4 and e["mu1"] < 1e-4, e
+    assert max(v for k_, v in e.items() if k_ in ("ux", "uy", "uz")) < 5e-4, e
+
+
+def test_ml_geq_two_fluids_equal_the_lattice():
+    # N = 2 in the g_eq form equals the two-fluid lattice in its g_eq form
+    shape, c1, C, kappa, rho, tau, faces, body = _ml_case_2d(2)
+    p = P.make_params("D2Q9", shape, "f64", theta_deg=90.0, tau_g=1.0, body=body,
+                      alpha_s=1.0, rho2=rho[0], rho3=rho[2], tau2=tau[0], tau3=tau[2])
+    k3 = (kappa[0], kappa[1], kappa[3])
+    p.tension_mode = 0
+    p.g12, p.g13, p.g23 = (k3[0] + k3[1]) / 6.0, (k3[0] + k3[2]) / 6.0, (k3[1] + k3[2]) / 6.0
+    lat = P.Lattice(p)
+    lat.set_solid_c1(_t(c1, torch.float64))
+    lat.set_fluid(_t(C[0], torch.float64))
+    lat.step(30)
+    assert lat.g_implicit
+    ml = P.MultiLattice(p, 2, k3, (rho[0], rho[2]), (tau[0], tau[2]))
+    ml.set_solid_c1(_t(c1, torch.float64))
+    ml.set_fluids(_t(C[:1], torch.float64))
+    ml.step(30)
+    f1, g1 = lat.populations()
+    f2, g2 = ml.populations()
+    assert rel_err(f2.cpu().numpy(), f1.cpu().numpy()) < 1e-12
+    assert rel_err(g2.cpu().numpy(), g1.cpu().numpy()) < 1e-12
+    for name in ("mu", "ux", "pt"):
+        assert rel_err(ml.field(name).cpu().numpy(), lat.field(name).cpu().numpy()) < 1e-12
+
