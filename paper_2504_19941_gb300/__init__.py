@@ -187,6 +187,11 @@ class MultiLattice:
         self.h = _lib.dsm_ml_create(params, self.nfluid, kappa, rho, tau, self.workspace,
                                     self.nbytes, self.stream)
 
+    @property
+    def g_implicit(self) -> bool:
+        """g held as g_eq (tau_g = 1 and every face periodic)."""
+        return self.params.tau_g == 1.0 and not any(self.params.face)
+
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
