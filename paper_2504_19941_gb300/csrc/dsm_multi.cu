@@ -575,10 +575,49 @@ cudaError_t ml_dispatch(const dsm_mlattice *h, const MLArgs<T> &a, void *extra =
   return cudaGetLastError();
 }
 
+// D3Q19 with g held as g_eq: the two-fluid z-marching tiled moments pass,
+// once per free fluid, on that fluid's (A_f, C_f) planes and the shared u
+// (the same per-node arithmetic as ml_moments_eq_kernel)
+template <class T>
+void ml_moments_eq_tiled(const MLArgs<T> &a, int nf, cudaStream_t s) {
+  const size_t smem = moments_eq_smem<T>();
+  if (smem > 48 * 1024) {
+    static bool opted_in = false;
+    if (!opted_in) {
+      if (cudaFuncSetAttribute(moments_eq_tiled_kernel<T, T>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return;
+      opted_in = true;
+    }
+  }
+  const int tiles = ((a.nx + MT_X - 1) / MT_X) * ((a.ny + MT_Y - 1) / MT_Y);
+  int zrun = 32;
+  while (zrun > 4 && (long long)tiles * ((a.nz + zrun - 1) / zrun) < 6 * 152) zrun /= 2;
+  const dim3 grid((a.nx + MT_X - 1) / MT_X, (a.ny + MT_Y - 1) / MT_Y, (a.nz + zrun - 1) / zrun);
+  for (int f = 0; f < nf; f++) {
+    LBArgs<T, T> b;
+    memset(&b, 0, sizeof(b));
+    b.nx = a.nx;
+    b.ny = a.ny;
+    b.nz = a.nz;
+    b.N = a.N;
+    b.pitch = a.pitch;
+    b.Mp[0] = a.A + (long long)f * a.pitch;
+    b.Mp[1] = a.U;
+    b.Mp[2] = a.U + a.pitch;
+    b.Mp[3] = a.U + 2 * a.pitch;
+    b.Cprev = a.Cprev + (long long)f * a.pitch;
+    b.C = a.C + (long long)f * a.pitch;
+    moments_eq_tiled_kernel<T, T><<<grid, dim3(MT_X, MT_Y, 1), smem, s>>>(b, zrun);
+  }
+}
+
 template <int K, class T, int NF>
 struct MomentsL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
-    if (eq) ml_moments_eq_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+    if (eq && K == 1) ml_moments_eq_tiled<T>(a, NF, s);
+    else if (eq) ml_moments_eq_kernel<K, T, NF><<<g, b, 0, s>>>(a);
     else ml_moments_kernel<K, T, NF><<<g, b, 0, s>>>(a);
   }
 };
