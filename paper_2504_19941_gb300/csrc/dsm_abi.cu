@@ -10,6 +10,7 @@
 
 #include "dsm_em.cuh"
 #include "dsm_lb_impl.cuh"
+#include "dsm_trace.cuh"
 
 using namespace dsm;
 
@@ -341,6 +342,7 @@ dsm_status dsm_set_solid(dsm_lattice *h, const void *d_field, int kind) {
 
 dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int steps, double beta,
                            double omega) {
+  TraceRange trace_range("dsm_relax_solid (stage 1)");
   if (!h || !d_mask || steps < 0 || beta < 0.0 || omega < 0.0) return DSM_E_INVAL;
   cudaError_t e = cudaMemcpyAsync(h->mask, d_mask, h->N, cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return DSM_E_CUDA;
@@ -403,6 +405,7 @@ dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2) {
 }
 
 dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
+  TraceRange trace_range("dsm_step");
   if (!h || nsteps < 0) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched) return DSM_E_STATE;
   for (long long t = 0; t < nsteps; t++) {
@@ -419,6 +422,7 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
 }
 
 dsm_status dsm_step_moments(dsm_lattice *h) {
+  TraceRange trace_range("moments pass (K1)");
   if (!h) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched) return DSM_E_STATE;
   LBRaw a = raw_of(h, h->cur);
@@ -428,6 +432,7 @@ dsm_status dsm_step_moments(dsm_lattice *h) {
 }
 
 dsm_status dsm_step_collide(dsm_lattice *h) {
+  TraceRange trace_range("fused pass (K2)");
   if (!h) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched || !h->moments_ready) return DSM_E_STATE;
   LBRaw a = raw_of(h, h->cur);
@@ -650,6 +655,7 @@ dsm_status dsm_fe_energy_grad(const dsm_params *p, const float *d_c1, const floa
                               double V0, double fg, double *d_energy, float *d_grad,
                               double *d_terms, void *d_scratch, size_t scratch_bytes,
                               void *cuda_stream) {
+  TraceRange trace_range("energy and gradient (K4)");
   if (!p || !d_c1 || !d_c2 || !d_grad || !d_scratch) return DSM_E_INVAL;
   if (active != 1 && active != 2) return DSM_E_INVAL;
   if (active == 1 && !d_mask) return DSM_E_INVAL;
@@ -689,6 +695,7 @@ dsm_status dsm_fe_energy_grad_multi(const dsm_params *p, int nfluid, const doubl
                                     const double *kcs, const double *V0, double *d_energy,
                                     float *d_grad, double *d_terms, void *d_scratch,
                                     size_t scratch_bytes, void *cuda_stream) {
+  TraceRange trace_range("N-fluid energy and gradient");
   if (!d_c1 || !d_c || !d_grad || !d_scratch) return DSM_E_INVAL;
   FEMArgs a;
   FEMCons cons;
@@ -801,6 +808,7 @@ dsm_status dsm_batch_scratch_bytes(dsm_lattice *const *hs, int n, size_t *bytes)
 
 dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps, void *d_scratch,
                           size_t scratch_bytes) {
+  TraceRange trace_range("batched step (K9)");
   if (!nsteps || !d_scratch) return DSM_E_INVAL;
   std::vector<BatchRaw> items;
   dsm_status s = batch_items(hs, n, nsteps, items);

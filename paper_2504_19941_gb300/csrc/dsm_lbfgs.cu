@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "dsm_em.cuh"
+#include "dsm_trace.cuh"
 
 using namespace dsm;
 
@@ -384,6 +385,7 @@ dsm_status dsm_lbfgs_minimize(const dsm_params *p, const float *d_fixed,
                               double V0, double fg, float *d_x, int m, double tol,
                               long long max_iter, void *d_work, size_t work_bytes,
                               dsm_lbfgs_info *info, void *cuda_stream) {
+  TraceRange trace_range("L-BFGS");
   if (!p || !d_fixed || !d_x || !d_work || !info) return DSM_E_INVAL;
   if (active != 1 && active != 2) return DSM_E_INVAL;
   if (active == 1 && !d_mask) return DSM_E_INVAL;
@@ -435,6 +437,7 @@ dsm_status dsm_lbfgs_minimize_multi(const dsm_params *p, int nfluid, const doubl
                                     const double *V0, float *d_x, int m, double tol,
                                     long long max_iter, void *d_work, size_t work_bytes,
                                     dsm_lbfgs_info *info, void *cuda_stream) {
+  TraceRange trace_range("N-fluid L-BFGS");
   if (!d_c1 || !d_x || !d_work || !info) return DSM_E_INVAL;
   if (m < 1 || 2 * m > LINCOMB_MAX || max_iter < 0 || !(tol >= 0.0)) return DSM_E_INVAL;
   Minimiser M;

@@ -28,6 +28,7 @@
 #include <new>
 
 #include "dsm_lb_impl.cuh"
+#include "dsm_trace.cuh"
 
 namespace dsm {
 
@@ -781,6 +782,7 @@ dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c) {
 }
 
 dsm_status dsm_ml_step(dsm_mlattice *h, long long nsteps) {
+  TraceRange trace_range("N-fluid step");
   if (!h || nsteps < 0) return DSM_E_INVAL;
   if (!h->has_fluid) return DSM_E_STATE;
   for (long long t = 0; t < nsteps; t++) {

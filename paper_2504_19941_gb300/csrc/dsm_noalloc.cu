@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "dsm_em.cuh"
+#include "dsm_trace.cuh"
 
 using namespace dsm;
 
