@@ -448,7 +448,10 @@ dsm_status dsm_destroy(dsm_lattice *h);
  * dependent fluid), DSM_FIELD_MU with index f gives mu_{2+f}, DSM_FIELD_C1,
  * UX, UY, UZ, PT, RHO, TAU as for dsm_get_field; DSM_FIELD_C3 is DSM_E_INVAL.
  * dsm_ml_get_populations: f (Q planes) and g (N - 1 blocks of Q planes), dense
- * nx*ny*nz rows (held as g_eq: rebuilt from (A_f, C_f, u)).  No error latching: the caller checks fields for NaN. */
+ * nx*ny*nz rows (held as g_eq: rebuilt from (A_f, C_f, u)).  The fused pass
+ * latches a non-finite state in the workspace; dsm_ml_check synchronises the
+ * stream and returns DSM_E_NONFINITE once it is latched (dsm_ml_set_fluids
+ * clears it). */
 typedef struct dsm_mlattice dsm_mlattice;
 dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes);
 dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa,
@@ -459,6 +462,7 @@ dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c);
 dsm_status dsm_ml_step(dsm_mlattice *h, long long nsteps);
 dsm_status dsm_ml_get_field(dsm_mlattice *h, int field, int index, void *d_dst);
 dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g);
+dsm_status dsm_ml_check(dsm_mlattice *h);
 dsm_status dsm_ml_destroy(dsm_mlattice *h);
 
 #ifdef __cplusplus

@@ -225,6 +225,10 @@ class MultiLattice:
         _lib.dsm_ml_get_field(self.h, code, index, out)
         return out
 
+    def status(self) -> int:
+        """0, or the status latched by the fused pass (DSM_E_NONFINITE)."""
+        return _lib.dsm_ml_check(self.h, check=False)
+
     def populations(self):
         import torch
         f = torch.empty(self.q * self.n, dtype=self.real, device=self.device)

@@ -36,7 +36,7 @@ EXPORTED = (
     "dsm_batch_scratch_bytes", "dsm_batch_step",
     "dsm_destroy", "dsm_ml_workspace_bytes", "dsm_ml_create", "dsm_ml_set_solid",
     "dsm_ml_set_fluids", "dsm_ml_step", "dsm_ml_get_field", "dsm_ml_get_populations",
-    "dsm_ml_destroy",
+    "dsm_ml_check", "dsm_ml_destroy",
 )
 
 
@@ -142,6 +142,7 @@ def load():
         "dsm_ml_step": (st, [vp, C.c_longlong]),
         "dsm_ml_get_field": (st, [vp, C.c_int, C.c_int, vp]),
         "dsm_ml_get_populations": (st, [vp, vp, vp]),
+        "dsm_ml_check": (st, [vp]),
         "dsm_ml_destroy": (st, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -492,6 +493,13 @@ def dsm_ml_get_field(h: int, field: int, index: int, out):
 
 def dsm_ml_get_populations(h: int, f, g):
     _check(load().dsm_ml_get_populations(h, _ptr(f), _ptr(g)), "dsm_ml_get_populations")
+
+
+def dsm_ml_check(h: int, check=True) -> int:
+    s = load().dsm_ml_check(h)
+    if check:
+        _check(s, "dsm_ml_check")
+    return s
 
 
 def dsm_ml_destroy(h: int):

@@ -54,6 +54,7 @@ struct MLArgs {
   const T *C1;
   T *out;                // fields mode: one plane
   int field, index;
+  int *err;              // latched error word (bit ERR_NONFINITE)
 };
 
 template <class T>
@@ -339,6 +340,12 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   }
 
   // ---- BGK collision of f (Eq. [eqn:feq], Eq. [eqn:hydroforce]) and of g_f
+  {
+    T chk = pt + u[0] + u[1] + u[2];
+#pragma unroll
+    for (int f = 0; f < NF; f++) chk += mu[f] + cv[1 + f];
+    if (!isfinite(chk)) atomicOr(a.err, ERR_NONFINITE);
+  }
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
   const T kF = T(1) - T(0.5) * om;
@@ -466,6 +473,7 @@ struct dsm_mlattice {
   long long N, pitch;
   cudaStream_t stream;
   char *f[2], *g[2], *C[2], *C1, *M;  // C[cur]: C of the last collision; M: A_f and u
+  int *err;                            // latched error word in the workspace
   int cur;
   bool eq;  // g held as g_eq (tau_g = 1, periodic faces)
   bool has_solid, has_fluid;
@@ -474,7 +482,7 @@ struct dsm_mlattice {
 namespace {
 
 struct MLLayout {
-  size_t f[2], g[2], C[2], C1, M, total;
+  size_t f[2], g[2], C[2], C1, M, err, total;
 };
 
 // g held as g_eq: tau_g = 1 and every face periodic
@@ -493,6 +501,7 @@ MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq) {
   for (int b = 0; b < 2; b++) L.C[b] = take((size_t)nf * pitch * real_bytes);
   L.C1 = take((size_t)pitch * real_bytes);
   L.M = take(eq ? (size_t)(nf + 3) * pitch * real_bytes : 0);
+  L.err = take(sizeof(int));
   L.total = o;
   return L;
 }
@@ -548,6 +557,7 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
   a.A = (T *)h->M;
   a.U = h->M ? (T *)h->M + (long long)h->nf * h->pitch : nullptr;
   a.C1 = (const T *)h->C1;
+  a.err = h->err;
   return a;
 }
 
@@ -728,8 +738,10 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   }
   h->C1 = w + L.C1;
   h->M = h->eq ? w + L.M : nullptr;
-  // no solid until one is set: C1 = 0
-  if (cudaMemsetAsync(h->C1, 0, (size_t)pitch * rb, h->stream) != cudaSuccess) {
+  h->err = (int *)(w + L.err);
+  // no solid until one is set: C1 = 0; no error latched
+  if (cudaMemsetAsync(h->C1, 0, (size_t)pitch * rb, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) {
     delete h;
     return DSM_E_CUDA;
   }
@@ -773,6 +785,7 @@ dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c) {
     if (e != cudaSuccess) return DSM_E_CUDA;
   }
   h->cur = 0;
+  if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return DSM_E_CUDA;
   cudaError_t e;
   if (h->real_bytes == 8) e = ml_dispatch<double, InitL>(h, ml_args<double>(h, 1));
   else e = ml_dispatch<float, InitL>(h, ml_args<float>(h, 1));
@@ -821,6 +834,16 @@ dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g) {
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       return DSM_E_CUDA;
   return DSM_OK;
+}
+
+dsm_status dsm_ml_check(dsm_mlattice *h) {
+  if (!h) return DSM_E_INVAL;
+  int word = 0;
+  if (cudaMemcpyAsync(&word, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return DSM_E_CUDA;
+  return (word & ERR_NONFINITE) ? DSM_E_NONFINITE : DSM_OK;
 }
 
 dsm_status dsm_ml_destroy(dsm_mlattice *h) {

@@ -345,3 +345,22 @@ def test_ml_geq_two_fluids_equal_the_lattice():
     for name in ("mu", "ux", "pt"):
         assert rel_err(ml.field(name).cpu().numpy(), lat.field(name).cpu().numpy()) < 1e-12
 
+
+@pytest.mark.parametrize("tau_g", [0.9, 1.0])
+def test_ml_nonfinite_is_latched(tau_g):
+    # a NaN in the input fluids reaches the fused pass, which latches it;
+    # dsm_ml_set_fluids clears the word again
+    shape, c1, C, kappa, rho, tau, faces, body = _periodic(_ml_case_2d(2))
+    p = P.make_params("D2Q9", shape, "f64", theta_deg=90.0, tau_g=tau_g, alpha_s=1.0)
+    ml = P.MultiLattice(p, 3, kappa, rho, tau)
+    ml.set_solid_c1(_t(c1, torch.float64))
+    bad = C.copy()
+    bad[0, 17] = np.nan
+    ml.set_fluids(_t(bad, torch.float64))
+    ml.step(3)
+    assert ml.status() == _lib.DSM_E_NONFINITE
+    ml.set_fluids(_t(C, torch.float64))
+    assert ml.status() == 0
+    ml.step(3)
+    assert ml.status() == 0
+
