@@ -460,6 +460,39 @@ __global__ void __launch_bounds__(256) dots_kernel(long long n, const float *V, 
   block_reduce_ff<1>(s, sums, partials + (long long)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
+// the dots of every V_k against two vectors in one pass over V: partials
+// (k, block) hold the two sums side by side
+__global__ void __launch_bounds__(256) dots2_kernel(long long n, const float *V, long long stride,
+                                                    const float *x, const float *y,
+                                                    double *partials) {
+  const float *v = V + blockIdx.y * stride;
+  FF s[2] = {FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const float vk = v[k];
+    s[0] = ff_add(s[0], two_prod(vk, x[k]));
+    s[1] = ff_add(s[1], two_prod(vk, y[k]));
+  }
+  const int sums[2] = {0, 0};
+  block_reduce_ff<2>(s, sums, partials + 2 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// block (k, t): the partials of V_k against target t summed in block order,
+// as dots_finalize_kernel sums a single target's
+__global__ void dots2_finalize_kernel(const double *partials, int nb, int nv, double *out) {
+  __shared__ double sh[256];
+  const double *p = partials + 2 * (long long)blockIdx.x * nb + blockIdx.y;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[2 * b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.y * nv + blockIdx.x] = sh[0];
+}
+
 // one block per dot product: its block partials summed in block order
 __global__ void dots_finalize_kernel(const double *partials, int nb, double *out) {
   __shared__ double sh[256];
@@ -521,6 +554,16 @@ size_t vec_scratch_bytes(long long) { return VEC_BLOCKS * sizeof(double) + 256; 
 
 size_t vec_dots_scratch_bytes(long long n, int nv) {
   return (size_t)(nv > 0 ? nv : 1) * vec_grid(n) * sizeof(double) + 256;
+}
+
+cudaError_t vec_dots2(long long n, int nv, const float *V, long long stride, const float *x,
+                      const float *y, double *out, void *scratch, cudaStream_t st) {
+  if (nv <= 0 || n <= 0) return cudaSuccess;
+  const int g = vec_grid(n);
+  double *partials = (double *)scratch;
+  dots2_kernel<<<dim3(g, nv), 256, 0, st>>>(n, V, stride, x, y, partials);
+  dots2_finalize_kernel<<<dim3(nv, 2), 256, 0, st>>>(partials, g, nv, out);
+  return cudaGetLastError();
 }
 
 cudaError_t vec_dots(long long n, int nv, const float *V, long long stride, const float *x,

@@ -75,6 +75,10 @@ size_t vec_scratch_bytes(long long n);
 size_t vec_dots_scratch_bytes(long long n, int nv);
 cudaError_t vec_dots(long long n, int nv, const float *V, long long stride, const float *x,
                      double *out, void *scratch, cudaStream_t st);
+// out[0..nv) = V_k . x and out[nv..2nv) = V_k . y in one pass over V, each
+// bitwise equal to vec_dots' (scratch: vec_dots_scratch_bytes(n, 2 nv))
+cudaError_t vec_dots2(long long n, int nv, const float *V, long long stride, const float *x,
+                      const float *y, double *out, void *scratch, cudaStream_t st);
 cudaError_t vec_lincomb(long long n, int nv, const float *V, long long stride, const double *coef,
                         const float *x, double cx, float *y, cudaStream_t st);
 cudaError_t vec_dot(long long n, const float *x, const float *y, double *out, const double *scale,

@@ -296,9 +296,8 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
     const double minus1 = -1.0;
     CK(vec_axpby(n, step, M.d, 0.0, s_new, st));
     CK(vec_lincomb(n, 1, g, n, &minus1, gt, 1.0, y_new, st));
-    // every stored s, y against y_new and against g_new, in two batched passes
-    CK(vec_dots(n, 2 * m, M.hist, n, y_new, M.dots, M.dots_scr, st));
-    CK(vec_dots(n, 2 * m, M.hist, n, gt, M.dots + 2 * m, M.dots_scr, st));
+    // every stored s, y against y_new and against g_new, in one batched pass
+    CK(vec_dots2(n, 2 * m, M.hist, n, y_new, gt, M.dots, M.dots_scr, st));
     CK(vec_dot(n, s_new, s_new, M.dots + 4 * m, nullptr, M.vec_scr, st));
     CK(vec_dot(n, gt, gt, M.dots + 4 * m + 1, nullptr, M.vec_scr, st));
     CK(M.read(hv.data(), M.dots, 4 * m + 2));  // the iteration's one read after the step
@@ -363,7 +362,7 @@ static size_t lbfgs_layout_n(long long n, int m, size_t fe_bytes, size_t off[12]
   off[7] = take(4 * sizeof(double));              // single dots
   off[8] = take(fe_bytes);
   off[9] = take(vec_scratch_bytes(n));
-  off[10] = take(vec_dots_scratch_bytes(n, 2 * m));
+  off[10] = take(vec_dots_scratch_bytes(n, 4 * m));
   return o;
 }
 
