@@ -256,7 +256,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def gpu_config(shape, world, g_storage, lattice="D3Q19", rho3=1.0, tau3=1.0):
+def gpu_config(shape, world, g_storage, lattice="D3Q19", rho3=1.0, tau3=1.0, faces=None):
     nodes = 1
     for v in shape:
         nodes *= int(v)
@@ -268,6 +268,8 @@ def gpu_config(shape, world, g_storage, lattice="D3Q19", rho3=1.0, tau3=1.0):
         name = f"D3Q19 FP32 pillar-slab {shape[0]}x{shape[1]}x{shape[2]} (profiling size)"
     if rho3 != 1.0 or tau3 != 1.0:
         name += f", gas density {rho3}, gas tau {tau3} (liquid 1, 1)"
+    if faces:
+        name += ", faces " + "/".join(faces)
     return {"workload": name, "lattice": lattice, "nodes": nodes,
             "global_batch": world, "parallelism": f"replicas x{world}",
             "g_storage": g_storage,
@@ -293,8 +295,10 @@ def run_gpu(args, rank, world):
     if lattice == "D2Q9" and len(shape) != 2:
         shape = (4096, 4096)
     case = make_case(shape, lattice)
+    faces = tuple(args.faces.split(",")) if args.faces else None
     params = P.make_params(lattice, shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
-                           g23=case.g23, alpha_s=case.alpha_s, rho3=args.rho3, tau3=args.tau3)
+                           g23=case.g23, alpha_s=case.alpha_s, rho3=args.rho3, tau3=args.tau3,
+                           faces=faces)
     lat = P.Lattice(params, device=dev)
     lat.set_g_storage(args.g_storage)
     sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
@@ -365,7 +369,8 @@ def run_gpu(args, rank, world):
 
     peak, peak_kind = _peaks()
     achieved = k2_b * n / t_k2 / 1e9
-    default = shape == SHAPE and lattice == "D3Q19" and args.rho3 == 1.0 and args.tau3 == 1.0
+    default = (shape == SHAPE and lattice == "D3Q19" and args.rho3 == 1.0 and args.tau3 == 1.0
+               and not faces)
     traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
                if default else None)
     step_achieved = (k2_b + k1_b) * n / (t_max / args.steps) / 1e9
@@ -378,7 +383,7 @@ def run_gpu(args, rank, world):
                "data": "synthetic",
                "config": gpu_config(shape, world,
                                     "g_eq (tau_g = 1): A, u per node" if g_eq else "populations",
-                                    lattice, args.rho3, args.tau3),
+                                    lattice, args.rho3, args.tau3, faces),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic,
                             "kernel": "node_kernel<%s,f32,stage2,step,%s%s>" %
@@ -828,6 +833,8 @@ def main():
                     help="D2Q9: a 2D pillar row (default 4096x4096 unless --shape has two sizes)")
     ap.add_argument("--rho3", type=float, default=1.0, help="gas density (liquid 1)")
     ap.add_argument("--tau3", type=float, default=1.0, help="gas relaxation time (liquid 1)")
+    ap.add_argument("--faces", default="",
+                    help="six comma-separated faces x-,x+,y-,y+,z-,z+: periodic, mirror or wall")
     ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],
                     help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
