@@ -176,7 +176,7 @@ __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y
   T s = T(0);
   if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
     // a node on a mirror or wall face: the pulled g follow the face rules
-#pragma unroll 1
+#pragma unroll
     for (int i = 1; i < L::Q; i++) {
       int k;
       const int cr = face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &k);
@@ -570,23 +570,21 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   // Links across a face take its rule (specular reflection at a mirror,
   // halfway bounce-back at a wall) for f and g, except that a mirror link whose
   // image upstream node is solid keeps the interpolated value set above.
+  // (unrolled over the directions, so that only a face node's crossing links do
+  // work and every write is to a fixed register)
   if constexpr (!EQ) {
     if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
-#pragma unroll 1
+#pragma unroll
       for (int j = 1; j < Q; j++) {
         int k;
         const int cr = face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
-        if (cr == 0) continue;
-        const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
-        const bool interp = STAGE == 2 && cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
-        const T fv = interp ? T(0) : load_f<T, S>(a.fin[k], src, k, L::w(k));
-        const T gv = LOAD_G ? load_g<T, S>(a.gin[k], src) : T(0);
-#pragma unroll
-        for (int kk = 1; kk < Q; kk++)
-          if (kk == j) {
-            if (!interp) f[kk] = fv;
-            if (LOAD_G) g[kk] = gv;
-          }
+        if (cr != 0) {
+          const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
+          const bool interp =
+              STAGE == 2 && cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
+          if (!interp) f[j] = load_f<T, S>(a.fin[k], src, k, L::w(k));
+          if (LOAD_G) g[j] = load_g<T, S>(a.gin[k], src);
+        }
       }
     }
   }
