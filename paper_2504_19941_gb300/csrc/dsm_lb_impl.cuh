@@ -161,20 +161,24 @@ __device__ __noinline__ T link_fraction(T xs, T gn, T g0, T g1, T g2, int i) {
 
 // ---------------------------------------------------------------------------
 // K1: moments pass.  C(x) = sum_i g_i after streaming (Sec. II.B, C = sum g).
+// FC: the lattice has a mirror or wall face; without one the face code is
+// compiled out (here and in the fused pass), so periodic lattices keep their
+// register count.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S>
+template <int K, class T, class S, bool FC>
 __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y, int z) {
   using L = Lat<K>;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
-  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
+  if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
+  else h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   // the moving populations are small next to the rest one (g_0 ~ C): summing
   // them first and adding g_0 last rounds once at the scale of C instead of
   // Q - 1 times, which keeps FP32 from drifting the liquid mass
   const T g0 = Store<S>::k16 ? T(a.g0_in[n]) : load_g<T, S>(a.gin[0], n);
   T s = T(0);
-  if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
+  if (FC && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
     // a node on a mirror or wall face: the pulled g follow the face rules
 #pragma unroll
     for (int i = 1; i < L::Q; i++) {
@@ -191,9 +195,9 @@ __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y
   a.C[n] = g0 + s;
 }
 
-template <int K, class T, class S>
+template <int K, class T, class S, bool FC>
 __global__ void __launch_bounds__(256) moments_kernel(LBArgs<T, S> a) {
-  moments_body<K, T, S>(a, blockIdx.x * blockDim.x + threadIdx.x,
+  moments_body<K, T, S, FC>(a, blockIdx.x * blockDim.x + threadIdx.x,
                         blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z * blockDim.z + threadIdx.z);
 }
 
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(256) moments_eq_kernel(LBArgs<T, S> a) {
 // every node fluid).  MODE_STEP collides and writes the next state;
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ = false>
+template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ, bool FC>
 __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
                                           int field_sel) {
   using L = Lat<K>;
@@ -405,12 +409,12 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   // the pulled g enter only the g collision (C comes from the moments pass)
   constexpr bool LOAD_G = MODE == MODE_STEP && !EQ;
   static_assert(!EQ || STAGE == 2, "g as g_eq is a stage-2 form");
+  static_assert(!(EQ && FC), "g as g_eq implies periodic faces");
   if (MODE != MODE_OBS && !valid) return;
   if (!valid) x = y = z = 0;
   Hood h;
-  // (g held as g_eq implies periodic faces)
-  if constexpr (EQ) h.init(x, y, z, a.nx, a.ny, a.nz);
-  else h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
+  if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
+  else h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
   const ConstT<T> &K_ = a.c;
 
@@ -546,9 +550,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       // faces it is pulled like any population (none beyond a wall)
       int ki = i;
       bool second = !((nb_solid >> j) & 1u);
-      if constexpr (!EQ) {
-        if (a.p.walls && face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2)
-          second = false;
+      if constexpr (FC) {
+        if (face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
       }
       if (q < T(0.5) && second) {
         const int z2 = h.plus_rt<L>(j);
@@ -572,8 +575,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   // image upstream node is solid keeps the interpolated value set above.
   // (unrolled over the directions, so that only a face node's crossing links do
   // work and every write is to a fixed register)
-  if constexpr (!EQ) {
-    if (a.p.walls && on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
+  if constexpr (FC) {
+    if (on_wall_face(a.p.face, x, y, z, a.nx, a.ny, a.nz)) {
 #pragma unroll
       for (int j = 1; j < Q; j++) {
         int k;
@@ -774,12 +777,12 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   (void)gsum16;
 }
 
-template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ>
+template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ, bool FC>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ ? 3 : 2)) node_kernel(LBArgs<T, S> a, int field_sel) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
-  node_body<K, T, S, STAGE, MODE, RC, EQ>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
+  node_body<K, T, S, STAGE, MODE, RC, EQ, FC>(a, x, y, z, x < a.nx && y < a.ny && z < a.nz, field_sel);
 }
 
 // ---------------------------------------------------------------------------
@@ -861,9 +864,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
         const int z = bz * blockDim.z + threadIdx.z;
         if (phase == 0) {
           if (EQ && (t > 0 || it->implicit0)) moments_eq_body<K, T, S>(sa, x, y, z);
-          else moments_body<K, T, S>(sa, x, y, z);
+          else moments_body<K, T, S, false>(sa, x, y, z);
         } else {
-          node_body<K, T, S, 2, MODE_STEP, RC, EQ>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
+          node_body<K, T, S, 2, MODE_STEP, RC, EQ, false>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
         }
       }
       if (!grid_barrier<T, S>(bar, items, nitems)) return;
@@ -1151,16 +1154,23 @@ struct LBOps {
       moments_eq_tiled2d_kernel<T, S><<<dim3((r.nx + T2_X - 1) / T2_X, (r.ny + T2_Y - 1) / T2_Y),
                                         dim3(T2_X, T2_Y, 1), 0, st>>>(typed<T, S>(r));
     } else if (r.implicit) moments_eq_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
-    else moments_kernel<K, T, S><<<g, b, 0, st>>>(typed<T, S>(r));
+    else if (r.p.walls) moments_kernel<K, T, S, true><<<g, b, 0, st>>>(typed<T, S>(r));
+    else moments_kernel<K, T, S, false><<<g, b, 0, st>>>(typed<T, S>(r));
     return cudaGetLastError();
+  }
+  template <int STAGE, int MODE, bool EQ, bool FC>
+  static void node_launch_fc(const LBRaw &r, cudaStream_t st) {
+    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz), b = lb_block(K, r.nx, r.ny, r.nz);
+    if (STAGE == 2 && r.p.rho_contrast)
+      node_kernel<K, T, S, STAGE, MODE, STAGE == 2, EQ, FC><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
+    else
+      node_kernel<K, T, S, STAGE, MODE, false, EQ, FC><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
   }
   template <int STAGE, int MODE, bool EQ = false>
   static void node_launch(const LBRaw &r, cudaStream_t st) {
-    const dim3 g = lb_grid(K, r.nx, r.ny, r.nz), b = lb_block(K, r.nx, r.ny, r.nz);
-    if (STAGE == 2 && r.p.rho_contrast)
-      node_kernel<K, T, S, STAGE, MODE, STAGE == 2, EQ><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
-    else
-      node_kernel<K, T, S, STAGE, MODE, false, EQ><<<g, b, 0, st>>>(typed<T, S>(r), r.field_sel);
+    // (g held as g_eq implies periodic faces)
+    if (!EQ && r.p.walls) node_launch_fc<STAGE, MODE, false, true>(r, st);
+    else node_launch_fc<STAGE, MODE, EQ, false>(r, st);
   }
   static cudaError_t node(const LBRaw &r, int stage, int mode, cudaStream_t st) {
     if (stage == 2) {

@@ -66,8 +66,9 @@ __device__ __forceinline__ T *plane(T *base, long long pitch, int k) {
   return base + (long long)k * pitch;
 }
 
-// moments pass: C_f(x) = sum_i g_f,i pulled into x (face rules on the faces)
-template <int K, class T, int NF>
+// moments pass: C_f(x) = sum_i g_f,i pulled into x (face rules on the faces;
+// FC: the lattice has a mirror or wall face, else the face code is compiled out)
+template <int K, class T, int NF, bool FC>
 __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
@@ -76,14 +77,16 @@ __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
-  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  else h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
-  const bool edge = a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
+  const bool edge = FC && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
 #pragma unroll
   for (int f = 0; f < NF; f++) {
     const T *g = a.g_in + (long long)f * Q * a.pitch;
     T s = T(0);
     if (edge) {
+#pragma unroll
       for (int i = 1; i < Q; i++) {
         int k = i, src = h.plus_rt<L>(L::opp(i));
         if (face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &k) == 2) src = n;
@@ -153,8 +156,11 @@ __device__ __forceinline__ T ml_rho(const MLArgs<T> &a, const T (&c)[NF], T c1) 
 
 enum { ML_STEP = 0, ML_FIELDS = 1 };
 
-template <int K, class T, int NF, int MODE, bool EQ>
+// FC: the lattice has a mirror or wall face (populations only); without one the
+// face code is compiled out, which keeps the periodic step's register count
+template <int K, class T, int NF, int MODE, bool EQ, bool FC>
 __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
+  static_assert(!(EQ && FC), "the g_eq form is periodic only");
   using L = Lat<K>;
   constexpr int Q = L::Q;
   constexpr int NC = NF + 2;
@@ -163,7 +169,12 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
-  h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  // RTF: face offsets and the interpolated bounce-back's face check at run
+  // time.  The g_eq variant keeps them although its faces are periodic: with
+  // them compiled out its schedule changed and the step took 12 % longer.
+  constexpr bool RTF = FC || EQ;
+  if constexpr (RTF) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
+  else h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
 
   // ---- the neighbourhood: C1 and the free fluids, stencils of every component
@@ -267,7 +278,8 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
       const T fi_x = plane(a.f_in, a.pitch, i)[n];
       int ki = i;
       bool second = !((nb_solid >> j) & 1u);
-      if (a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
+      if (RTF && a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2)
+        second = false;
       T v;
       if (q < T(0.5) && second) {
         v = T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
@@ -284,27 +296,23 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
   // mirror and wall faces: specular reflection or halfway bounce-back for f
   // and every g_f (a mirror link with a solid image keeps the value above)
   // (the g_eq form is periodic only)
-  if (!EQ && a.walls && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz)) {
-    for (int j = 1; j < Q; j++) {
-      int k;
-      const int cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
-      if (cr == 0) continue;
-      const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
-      const bool interp = cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
-      const T fv = plane(a.f_in, a.pitch, k)[src];
-      T gv[NF];
+  // (unrolled over the directions: the crossing links' loads are in flight
+  // together and each lands in a fixed register)
+  if constexpr (FC) {
+    if (on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz)) {
 #pragma unroll
-      for (int f = 0; f < NF; f++)
-        gv[f] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
+      for (int j = 1; j < Q; j++) {
+        int k;
+        const int cr = face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, j, &k);
+        if (cr != 0) {
+          const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
+          const bool interp = cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
+          if (!interp) fs[j] = plane(a.f_in, a.pitch, k)[src];
 #pragma unroll
-      for (int kk = 1; kk < Q; kk++)
-        if (kk == j) {
-          if (!interp) fs[kk] = fv;
-          if constexpr (!EQ) {
-#pragma unroll
-            for (int f = 0; f < NF; f++) gs[f][kk] = gv[f];
-          }
+          for (int f = 0; f < NF; f++)
+            gs[f][j] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
         }
+      }
     }
   }
 
@@ -629,21 +637,24 @@ struct MomentsL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
     if (eq && K == 1) ml_moments_eq_tiled<T>(a, NF, s);
     else if (eq) ml_moments_eq_kernel<K, T, NF><<<g, b, 0, s>>>(a);
-    else ml_moments_kernel<K, T, NF><<<g, b, 0, s>>>(a);
+    else if (a.walls) ml_moments_kernel<K, T, NF, true><<<g, b, 0, s>>>(a);
+    else ml_moments_kernel<K, T, NF, false><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct StepL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
-    if (eq) ml_node_kernel<K, T, NF, ML_STEP, true><<<g, b, 0, s>>>(a);
-    else ml_node_kernel<K, T, NF, ML_STEP, false><<<g, b, 0, s>>>(a);
+    if (eq) ml_node_kernel<K, T, NF, ML_STEP, true, false><<<g, b, 0, s>>>(a);
+    else if (a.walls) ml_node_kernel<K, T, NF, ML_STEP, false, true><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_STEP, false, false><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct FieldsL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
-    if (eq) ml_node_kernel<K, T, NF, ML_FIELDS, true><<<g, b, 0, s>>>(a);
-    else ml_node_kernel<K, T, NF, ML_FIELDS, false><<<g, b, 0, s>>>(a);
+    if (eq) ml_node_kernel<K, T, NF, ML_FIELDS, true, false><<<g, b, 0, s>>>(a);
+    else if (a.walls) ml_node_kernel<K, T, NF, ML_FIELDS, false, true><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_FIELDS, false, false><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
