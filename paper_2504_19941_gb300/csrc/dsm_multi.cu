@@ -159,7 +159,7 @@ enum { ML_STEP = 0, ML_FIELDS = 1 };
 // FC: the lattice has a mirror or wall face (populations only); without one the
 // face code is compiled out, which keeps the periodic step's register count
 template <int K, class T, int NF, int MODE, bool EQ, bool FC>
-__global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
+__device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
   static_assert(!(EQ && FC), "the g_eq form is periodic only");
   using L = Lat<K>;
   constexpr int Q = L::Q;
@@ -389,6 +389,23 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
     a.U[a.pitch + n] = u[1];
     if (L::D == 3) a.U[2 * a.pitch + n] = u[2];
   }
+}
+
+template <int K, class T, int NF, int MODE, bool EQ, bool FC>
+__global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
+  ml_node_body<K, T, NF, MODE, EQ, FC>(a);
+}
+// D3Q19 FP32 with three free fluids and a mirror or wall face: the unrolled
+// face fix-ups raise the register count past one 256-thread block per SM, and
+// asking for two (128 registers, no spills) ran 12 % faster.  With fewer free
+// fluids the cap was slower, so those keep the plain kernel.
+template <int K, class T, int NF, int MODE>
+__global__ void __launch_bounds__(256, 2) ml_node_faces_kernel(MLArgs<T> a) {
+  ml_node_body<K, T, NF, MODE, false, true>(a);
+}
+template <int K, class T, int NF>
+constexpr bool ml_faces_capped() {
+  return K == 1 && sizeof(T) == 4 && NF >= 3;
 }
 
 // initial state at rest: f_i = w_i, g_f,i = g_eq,i(C_f, mu_f(C), u = 0); C
@@ -645,16 +662,18 @@ template <int K, class T, int NF>
 struct StepL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
     if (eq) ml_node_kernel<K, T, NF, ML_STEP, true, false><<<g, b, 0, s>>>(a);
-    else if (a.walls) ml_node_kernel<K, T, NF, ML_STEP, false, true><<<g, b, 0, s>>>(a);
-    else ml_node_kernel<K, T, NF, ML_STEP, false, false><<<g, b, 0, s>>>(a);
+    else if (!a.walls) ml_node_kernel<K, T, NF, ML_STEP, false, false><<<g, b, 0, s>>>(a);
+    else if constexpr (ml_faces_capped<K, T, NF>()) ml_node_faces_kernel<K, T, NF, ML_STEP><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_STEP, false, true><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
 struct FieldsL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
     if (eq) ml_node_kernel<K, T, NF, ML_FIELDS, true, false><<<g, b, 0, s>>>(a);
-    else if (a.walls) ml_node_kernel<K, T, NF, ML_FIELDS, false, true><<<g, b, 0, s>>>(a);
-    else ml_node_kernel<K, T, NF, ML_FIELDS, false, false><<<g, b, 0, s>>>(a);
+    else if (!a.walls) ml_node_kernel<K, T, NF, ML_FIELDS, false, false><<<g, b, 0, s>>>(a);
+    else if constexpr (ml_faces_capped<K, T, NF>()) ml_node_faces_kernel<K, T, NF, ML_FIELDS><<<g, b, 0, s>>>(a);
+    else ml_node_kernel<K, T, NF, ML_FIELDS, false, true><<<g, b, 0, s>>>(a);
   }
 };
 template <int K, class T, int NF>
