@@ -171,7 +171,7 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
   Hood h;
   // RTF: face offsets and the interpolated bounce-back's face check at run
   // time.  The g_eq variant keeps them although its faces are periodic: with
-  // them compiled out its schedule changed and the step took 12 % longer.
+  // them compiled out its schedule changed and the step took 13 % longer.
   constexpr bool RTF = FC || EQ;
   if constexpr (RTF) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
