@@ -698,32 +698,42 @@ def run_multi(args, rank, world):
 def run_critical(args, rank, world):
     """Critical pressure of the Cassie-Baxter to Wenzel transition on 2D pillars
     (Sec. III) by bisection over GPU energy minimisations, for a sweep of five
-    contact angles on a 160x200 box with gap s = 81: the value is sweep points
-    per second; each point reports dP_c against -2 gamma cos(theta) / s."""
+    contact angles on a 160x200 box with gap s = 81, served as concurrent
+    searches (one host thread and CUDA stream per angle): the value is sweep
+    points per second.  The same sweep one search at a time is timed beside it,
+    and the two must give identical results; each point reports dP_c against
+    -2 gamma cos(theta) / s."""
     import torch
     import synthetic as S
     from paper_2504_19941_gb300 import critical as C
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     thetas = (60.0, 80.0, 100.0, 112.0, 135.0)
-    C.critical_pressure(S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4))  # warm
+    warm = S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4)
+    C.critical_sweep([warm, warm])  # module, context and thread-pool warm-up
+    cases = [S.pillar_gap_2d(period=160, height=200, width=79, pillar=100, base=6, theta=t)
+             for t in thetas]
     t0 = time.perf_counter()
-    pts = []
-    for t in thetas:
-        case = S.pillar_gap_2d(period=160, height=200, width=79, pillar=100, base=6, theta=t)
-        r = C.critical_pressure(case, tol=1e-4)
-        pts.append({"theta": t, "dP_c": r["dP_c"], "theory": r["theory"], "ratio": r["ratio"],
-                    "probes": r["probes"], "lbfgs_iterations": r["iterations"],
-                    "seconds": r["seconds"], "ms_per_lbfgs_iteration": r["seconds"] / max(
-                        r["iterations"], 1) * 1e3})
-    wall = time.perf_counter() - t0
+    one = [C.critical_pressure(c, tol=1e-4) for c in cases]
+    wall_one = time.perf_counter() - t0
+    res, wall = C.critical_sweep(cases, tol=1e-4)
+    same = all(a["dP_c"] == b["dP_c"] and a["iterations"] == b["iterations"]
+               for a, b in zip(one, res))
+    pts = [{"theta": t, "dP_c": r["dP_c"], "theory": r["theory"], "ratio": r["ratio"],
+            "probes": r["probes"], "lbfgs_iterations": r["iterations"],
+            "seconds": r["seconds"], "ms_per_lbfgs_iteration": r["seconds"] / max(
+                r["iterations"], 1) * 1e3} for t, r in zip(thetas, res)]
     if rank == 0:
         print(json.dumps({"metric": "critical-pressure sweep points/s (2D pillars, bisection to 1e-4)",
                           "value": len(pts) / wall, "unit": "points/s", "n_gpus": 1,
                           "higher_is_better": True, "dtype": "f32 fields / f64 energy",
                           "data": "synthetic",
-                          "config": {"workload": "160x200 box, pillar width 79, gap 81, height 100"},
+                          "config": {"workload": "160x200 box, pillar width 79, gap 81, height 100",
+                                     "searches": "concurrent, one thread and stream per angle"},
+                          "one_at_a_time": {"value": len(pts) / wall_one, "unit": "points/s",
+                                            "wall_s": wall_one},
+                          "identical_to_one_at_a_time": same, "wall_s": wall,
                           "points": pts}), flush=True)
-    return 0
+    return 0 if same else 1
 
 
 def run_em(args, rank, world):

@@ -16,11 +16,18 @@ dP_c = -2 gamma_lg cos(theta) / s, s the gap width.
 All device work goes through libdsm: the solid profile (dsm_set_solid), the
 energy and gradient (dsm_fe_energy_grad), the L-BFGS kernels, and the gap mean
 (dsm_vec_dot against an indicator vector).
+
+A sweep over several cases (contact angles, gap widths) runs its searches
+concurrently (critical_sweep): one host thread and one CUDA stream per case.
+The native L-BFGS loop releases the interpreter lock and waits only on its own
+stream, so one search's host work (bisection, line search) overlaps the other
+searches' kernels.
 """
 from __future__ import annotations
 
 import math
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import torch
 
@@ -122,3 +129,26 @@ def critical_pressure(case, tol: float = 1e-4, device="cuda", rms_tol=1e-6, max_
     return {"dP_c": dpc, "bracket": (lo, hi), "theory": th, "ratio": dpc / th if th else math.nan,
             "probes": pg.probes, "iterations": pg.iterations,
             "seconds": time.perf_counter() - t0}
+
+
+def critical_sweep(cases, tol: float = 1e-4, device="cuda", rms_tol=1e-6, max_iter=20000,
+                   workers=None):
+    """Critical pressures of several cases at once, each search on its own host
+    thread and CUDA stream (at most `workers` at a time; default: all).  Every
+    search owns its workspace and runs the same kernels as critical_pressure
+    alone, so each result equals its one-at-a-time result.  Returns (results in
+    case order, wall seconds)."""
+    dev = torch.device(device)
+    cases = list(cases)
+    if not cases:
+        return [], 0.0
+    workers = len(cases) if workers is None else max(1, min(int(workers), len(cases)))
+    streams = [torch.cuda.Stream(device=dev) for _ in cases]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = [ex.submit(critical_pressure, c, tol, dev, rms_tol, max_iter, s)
+                for c, s in zip(cases, streams)]
+        res = [f.result() for f in futs]
+    torch.cuda.synchronize(dev)
+    return res, time.perf_counter() - t0

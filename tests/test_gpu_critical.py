@@ -49,3 +49,17 @@ def test_suspended_and_collapsed_states():
     x, E_hi, info = pg.relax(1.5 * th)
     assert pg.gap_liquid(x) > 0.9 and info["rms_grad"] < 1e-6
 
+
+
+def test_concurrent_sweep_equals_one_at_a_time():
+    # one thread and stream per case: each search owns its workspace, so its
+    # result is the same alone and in the mix
+    cases = [S.pillar_gap_2d(period=40, height=64, width=16, pillar=24, base=4, theta=t)
+             for t in (60.0, 112.0, 135.0)]
+    one = [C.critical_pressure(c, tol=1e-4) for c in cases]
+    res, wall = C.critical_sweep(cases, tol=1e-4)
+    assert wall > 0
+    for a, b in zip(one, res):
+        assert a["dP_c"] == b["dP_c"] and a["bracket"] == b["bracket"], (a, b)
+        assert a["iterations"] == b["iterations"] and a["probes"] == b["probes"]
+    assert C.critical_sweep([]) == ([], 0.0)
