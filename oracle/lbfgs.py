@@ -9,7 +9,10 @@ and zooming with cubic interpolation, at most 20 trials per iteration
 (Nocedal & Wright, Numerical Optimization, Algorithms 3.5 and 3.6).
 
 Parity unpinned: the iteration-by-iteration trajectory is not fixed by the
-paper; only converged energies and fields are compared.
+paper; only converged energies and fields are compared.  Its steps are pinned
+against independent definitions: the two-loop direction against explicit BFGS
+matrix updates, the line search against the strong Wolfe conditions, and the
+minimiser against closed-form minima.
 """
 from __future__ import annotations
 
@@ -92,6 +95,23 @@ def _zoom(phi, f0, dg0, lo, flo, dglo, hi, fhi, dghi, c1, c2, budget, trials, be
     return 0.0, x, f0, gx, trials
 
 
+def two_loop(g, S, Y, R, gamma):
+    """H g for the L-BFGS inverse Hessian H of the pairs (S[k], Y[k]), oldest
+    first, R[k] = 1 / (S[k].Y[k]), from H0 = gamma I: the two-loop recursion
+    (Nocedal & Wright, Algorithm 7.4)."""
+    q = np.array(g, dtype=np.float64, copy=True)
+    al = []
+    for s, y, r in zip(reversed(S), reversed(Y), reversed(R)):
+        a = r * float(np.dot(s, q))
+        al.append(a)
+        q -= a * y
+    r_ = gamma * q
+    for (s, y, rr), a in zip(zip(S, Y, R), reversed(al)):
+        b = rr * float(np.dot(y, r_))
+        r_ += (a - b) * s
+    return r_
+
+
 def minimize(fg, x0, *, m=10, tol=1e-6, max_iter=10000, callback=None):
     """Minimise f with gradient fg(x) -> (f, g).  Stops when sqrt(mean(g^2)) < tol
     or after max_iter iterations.  Returns (x, f, g, info)."""
@@ -105,22 +125,11 @@ def minimize(fg, x0, *, m=10, tol=1e-6, max_iter=10000, callback=None):
         rms = math.sqrt(float(np.dot(g, g)) / n)
         if rms < tol:
             break
-        # two-loop recursion
-        q = g.copy()
-        al = []
-        for s, y, r in zip(reversed(S), reversed(Y), reversed(R)):
-            a = r * float(np.dot(s, q))
-            al.append(a)
-            q -= a * y
         if S:
             gamma = float(np.dot(S[-1], Y[-1])) / float(np.dot(Y[-1], Y[-1]))
         else:
             gamma = 1.0 / max(math.sqrt(float(np.dot(g, g))), 1e-300)
-        r_ = gamma * q
-        for (s, y, rr), a in zip(zip(S, Y, R), reversed(al)):
-            b = rr * float(np.dot(y, r_))
-            r_ += (a - b) * s
-        d = -r_
+        d = -two_loop(g, S, Y, R, gamma)
         step, xn, fn, gn, tr = line_search(fg, x, f, g, d)
         evals += tr
         if step == 0.0:
