@@ -94,24 +94,31 @@ class ClockSampler:
     def summary(self):
         if not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [s.strip() for s in line.split(",")]
-                if len(parts) < 9 or not parts[1].split()[0].isdigit():
-                    continue
-                sm.append(float(parts[1].split()[0]))
-                mx = float(parts[2].split()[0])
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
+            lines = f.readlines()
         os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clocks(lines)
+
+
+def parse_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in the
+    CSV lines of the ClockSampler query (header and malformed lines skipped)."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [s.strip() for s in line.split(",")]
+        if len(parts) < 9 or not parts[1].split() or not parts[1].split()[0].isdigit():
+            continue
+        sm.append(float(parts[1].split()[0]))
+        mx = float(parts[2].split()[0])
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def aggregate(t_local: float, units_local: float, dist=None):
