@@ -69,7 +69,7 @@ class Lattice:
         self.n = params.nx * params.ny * params.nz
         self.q = 9 if params.lattice == DSM_D2Q9 else 19
         self.real = torch.float64 if params.precision == DSM_F64 else torch.float32
-        self.device = torch.device(device)
+        self.device = _lib.cuda_device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.nbytes = _lib.dsm_workspace_bytes(params)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
@@ -84,10 +84,9 @@ class Lattice:
                 pass
             self.h = None
 
-    def _field_arg(self, t):
-        assert t.is_cuda and t.is_contiguous() and t.numel() == self.n and t.dtype == self.real, \
-            "field must be a contiguous CUDA tensor of nx*ny*nz reals of the lattice's type"
-        return t
+    def _field_arg(self, t, what="field"):
+        """A contiguous tensor of nx*ny*nz reals of the lattice's type on its device."""
+        return _lib.tensor_arg(t, self.n, self.real, self.device, what)
 
     def set_solid_distance(self, sd):
         _lib.dsm_set_solid(self.h, self._field_arg(sd), 0)
@@ -96,7 +95,7 @@ class Lattice:
         _lib.dsm_set_solid(self.h, self._field_arg(c1), 1)
 
     def relax_solid(self, mask, steps: int, beta: float, omega: float):
-        assert mask.dtype.itemsize == 1 and mask.numel() == self.n and mask.is_cuda
+        mask = _lib.tensor_arg(mask, self.n, None, self.device, "mask", copy=True, itemsize=1)
         _lib.dsm_relax_solid(self.h, mask, steps, beta, omega)
 
     def solid_region(self, out=None):
@@ -104,6 +103,7 @@ class Lattice:
         import torch
         if out is None:
             out = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        out = _lib.tensor_arg(out, self.n, None, self.device, "out", itemsize=1)
         _lib.dsm_solid_region(self.h, out)
         return out
 
@@ -130,6 +130,7 @@ class Lattice:
         import torch
         if out is None:
             out = torch.empty(self.n, dtype=self.real, device=self.device)
+        out = self._field_arg(out, "out")
         _lib.dsm_get_field(self.h, FIELDS[name], out)
         return out
 
@@ -141,9 +142,9 @@ class Lattice:
         return f, g
 
     def set_populations(self, f, g):
-        assert f.dtype == self.real and g.dtype == self.real
-        assert f.numel() == self.q * self.n and g.numel() == self.q * self.n
-        _lib.dsm_set_populations(self.h, f.contiguous(), g.contiguous())
+        f = _lib.tensor_arg(f, self.q * self.n, self.real, self.device, "f", copy=True)
+        g = _lib.tensor_arg(g, self.q * self.n, self.real, self.device, "g", copy=True)
+        _lib.dsm_set_populations(self.h, f, g)
 
     def set_g_storage(self, form: str):
         """'auto' (g held as g_eq when tau_g = 1) or 'populations'."""
@@ -164,6 +165,8 @@ class Lattice:
         return buf
 
     def set_state(self, buf):
+        import torch
+        buf = _lib.tensor_arg(buf, buf.numel(), torch.uint8, self.device, "state")
         _lib.dsm_set_state(self.h, buf, buf.numel())
 
 
@@ -180,7 +183,7 @@ class MultiLattice:
         self.n = params.nx * params.ny * params.nz
         self.q = 9 if params.lattice == DSM_D2Q9 else 19
         self.real = torch.float64 if params.precision == DSM_F64 else torch.float32
-        self.device = torch.device(device)
+        self.device = _lib.cuda_device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.nbytes = _lib.dsm_ml_workspace_bytes(params, self.nfluid)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
@@ -198,9 +201,8 @@ class MultiLattice:
             _lib.dsm_ml_destroy(h)
             self.h = None
 
-    def _arg(self, t, count):
-        assert t.dtype == self.real and t.numel() == count and t.is_cuda
-        return t.contiguous()
+    def _arg(self, t, count, what="field"):
+        return _lib.tensor_arg(t, count, self.real, self.device, what, copy=True)
 
     def set_solid_distance(self, sd):
         _lib.dsm_ml_set_solid(self.h, self._arg(sd, self.n), 0)
@@ -221,6 +223,7 @@ class MultiLattice:
         import torch
         if out is None:
             out = torch.empty(self.n, dtype=self.real, device=self.device)
+        out = _lib.tensor_arg(out, self.n, self.real, self.device, "out")
         code = DSM_FIELD_C2 if name == "C" else FIELDS[name]
         _lib.dsm_ml_get_field(self.h, code, index, out)
         return out

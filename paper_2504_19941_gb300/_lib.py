@@ -174,6 +174,39 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def cuda_device(device):
+    """torch.device of a CUDA device with its index filled in."""
+    import torch
+    d = torch.device(device)
+    if d.type != "cuda":
+        raise ValueError(f"a CUDA device is required, not {d}")
+    return d if d.index is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+def tensor_arg(t, numel: int, dtype, device, what: str, copy: bool = False, itemsize=None):
+    """A device tensor handed to libdsm as a raw pointer: a torch tensor on
+    `device` with `numel` elements of `dtype` (or, with dtype None, of any type
+    of `itemsize` bytes), contiguous (with copy=True an input that is not is
+    copied instead).  Raises TypeError / ValueError otherwise, so that no launch
+    reads or writes past a buffer."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch tensor, got {type(t).__name__}")
+    if t.device != device:
+        raise ValueError(f"{what}: tensor on {t.device}, expected {device}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if itemsize is not None and t.element_size() != itemsize:
+        raise ValueError(f"{what}: {t.element_size()}-byte elements, expected {itemsize}")
+    if t.numel() != numel:
+        raise ValueError(f"{what}: {t.numel()} elements, expected {numel}")
+    if not t.is_contiguous():
+        if not copy:
+            raise ValueError(f"{what}: the tensor must be contiguous")
+        t = t.contiguous()
+    return t
+
+
 def _stream(stream):
     if stream is None:
         import torch

@@ -21,7 +21,7 @@ class FreeEnergy:
 
     def __init__(self, params: dsm_params, device="cuda", stream=None):
         self.params = params
-        self.device = torch.device(device)
+        self.device = _lib.cuda_device(device)
         self.stream = stream
         self.n = params.nx * params.ny * params.nz
         self.sb = _lib.dsm_fe_scratch_bytes(params.lattice, params.nx, params.ny, params.nz)
@@ -36,6 +36,13 @@ class FreeEnergy:
             energy = torch.empty(1, dtype=torch.float64, device=self.device)
         if grad is None:
             grad = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        arg = _lib.tensor_arg
+        c1 = arg(c1, self.n, torch.float32, self.device, "c1", copy=True)
+        c2 = arg(c2, self.n, torch.float32, self.device, "c2", copy=True)
+        if mask is not None:
+            mask = arg(mask, self.n, None, self.device, "mask", copy=True, itemsize=1)
+        energy = arg(energy, 1, torch.float64, self.device, "energy")
+        grad = arg(grad, self.n, torch.float32, self.device, "grad")
         _lib.dsm_fe_energy_grad(self.params, c1, c2, mask, active, dP, kcs, V0, fg, energy, grad,
                                 self.terms, self.scratch, self.sb, self.stream)
         return energy, grad
@@ -99,7 +106,11 @@ def lbfgs(fe: FreeEnergy, x0, other, *, active=2, mask=None, dP=0.0, kcs=0.0, V0
     """Minimise E over the active field from x0 (FP32 device vector, not
     modified) with the library's native L-BFGS loop (dsm_lbfgs_minimize).  Stops
     when sqrt(mean(grad^2)) < tol.  Returns (x, E, info)."""
-    x = x0.detach().clone().contiguous()
+    n = fe.n
+    x = _lib.tensor_arg(x0, n, torch.float32, fe.device, "x0", copy=True).detach().clone()
+    other = _lib.tensor_arg(other, n, torch.float32, fe.device, "other", copy=True)
+    if mask is not None:
+        mask = _lib.tensor_arg(mask, n, None, fe.device, "mask", copy=True, itemsize=1)
     nb = _lib.dsm_lbfgs_workspace_bytes(fe.params, m)
     work = torch.empty(nb, dtype=torch.uint8, device=x.device)
     info = _lib.dsm_lbfgs_minimize(fe.params, other, mask, active, dP, kcs, V0, fg, x, m, tol,
@@ -116,7 +127,7 @@ class FreeEnergyMulti:
         self.params = params
         self.nfluid = int(nfluid)
         self.kappa = [float(k) for k in kappa]
-        self.device = torch.device(device)
+        self.device = _lib.cuda_device(device)
         self.stream = stream
         self.n = params.nx * params.ny * params.nz
         self.sb = _lib.dsm_fe_multi_scratch_bytes(params.lattice, params.nx, params.ny,
@@ -131,6 +142,11 @@ class FreeEnergyMulti:
             energy = torch.empty(1, dtype=torch.float64, device=self.device)
         if grad is None:
             grad = torch.empty((self.nfluid - 1, self.n), dtype=torch.float32, device=self.device)
+        arg, nf = _lib.tensor_arg, self.nfluid - 1
+        c1 = arg(c1, self.n, torch.float32, self.device, "c1", copy=True)
+        c = arg(c, nf * self.n, torch.float32, self.device, "c", copy=True)
+        energy = arg(energy, 1, torch.float64, self.device, "energy")
+        grad = arg(grad, nf * self.n, torch.float32, self.device, "grad")
         _lib.dsm_fe_energy_grad_multi(self.params, self.nfluid, self.kappa, c1, c, dP, kcs, V0,
                                       energy, grad, self.terms, self.scratch, self.sb,
                                       self.stream)
@@ -141,7 +157,9 @@ def lbfgs_multi(fe: FreeEnergyMulti, x0, c1, *, dP=None, kcs=None, V0=None, m=10
                 max_iter=10000):
     """Minimise the N-fluid energy over the free fluid planes from x0 ((N - 1,
     nodes) FP32, not modified) with the native L-BFGS loop.  Returns (x, E, info)."""
-    x = x0.detach().clone().contiguous()
+    nf = fe.nfluid - 1
+    x = _lib.tensor_arg(x0, nf * fe.n, torch.float32, fe.device, "x0", copy=True).detach().clone()
+    c1 = _lib.tensor_arg(c1, fe.n, torch.float32, fe.device, "c1", copy=True)
     nb = _lib.dsm_lbfgs_multi_workspace_bytes(fe.params, fe.nfluid, m)
     work = torch.empty(nb, dtype=torch.uint8, device=x.device)
     info = _lib.dsm_lbfgs_minimize_multi(fe.params, fe.nfluid, fe.kappa, c1, dP, kcs, V0, x, m,

@@ -269,3 +269,33 @@ def test_multi_fluid_arguments_rejected(lib):
     assert create(3, d(1, 1, 1, 1), d(1, 1, 1), d(1, 1, 1), nbytes=nbm - 1) == lib.DSM_E_WORKSPACE
     assert L.dsm_ml_step(None, 1) == lib.DSM_E_INVAL
     assert L.dsm_ml_get_field(None, 1, 0, fake) == lib.DSM_E_INVAL
+
+
+def test_tensor_arguments_are_checked_before_any_launch():
+    # the Python layer hands raw pointers to libdsm, so it checks every tensor's
+    # device, type, size and layout first (here on CPU tensors and a CPU device)
+    torch = pytest.importorskip("torch")
+    from paper_2504_19941_gb300 import _lib as L
+    cpu = torch.device("cpu")
+    t = torch.zeros(12, dtype=torch.float32)
+    assert L.tensor_arg(t, 12, torch.float32, cpu, "x") is t
+    with pytest.raises(ValueError, match="elements"):
+        L.tensor_arg(t, 13, torch.float32, cpu, "x")
+    with pytest.raises(ValueError, match="dtype"):
+        L.tensor_arg(t, 12, torch.float64, cpu, "x")
+    with pytest.raises(ValueError, match="expected cuda"):
+        L.tensor_arg(t, 12, torch.float32, torch.device("cuda", 0), "x")
+    with pytest.raises(TypeError):
+        L.tensor_arg([0.0] * 12, 12, torch.float32, cpu, "x")
+    m = torch.zeros(12, dtype=torch.uint8)
+    assert L.tensor_arg(m, 12, None, cpu, "mask", itemsize=1) is m
+    with pytest.raises(ValueError, match="byte elements"):
+        L.tensor_arg(t, 12, None, cpu, "mask", itemsize=1)
+    nc = torch.zeros(4, 6, dtype=torch.float32)[:, ::2]       # 12 elements, strided
+    with pytest.raises(ValueError, match="contiguous"):
+        L.tensor_arg(nc, 12, torch.float32, cpu, "out")
+    c = L.tensor_arg(nc, 12, torch.float32, cpu, "x", copy=True)
+    assert c.is_contiguous() and torch.equal(c, nc)
+    with pytest.raises(ValueError, match="CUDA device"):
+        L.cuda_device("cpu")
+    assert L.cuda_device("cuda:1") == torch.device("cuda", 1)
