@@ -48,6 +48,15 @@ def lu_bytes(lattice: str, prec: str, g_eq: bool):
     if g_eq:
         return 2 * q * st + real + (1 + d) * real, (1 + d) * real + 2 * real
     return 2 * q * st + 2 * g_read + real, g_read + real
+
+
+def lu_bytes_single(prec: str):
+    """Algorithmic bytes per lattice update of the one-pass step (D3Q19, g held
+    as g_eq): read and write f, read and write (A, u) and C, read C1.  FP32:
+    152 + 40 + 4 = 196 B; 16-bit storage of f: 76 + 40 + 4 = 120 B."""
+    real = 8 if prec == "f64" else 4
+    st = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[prec]
+    return 2 * 19 * st + 2 * 5 * real + real
 SHAPE = (256, 256, 192)
 WORKLOAD = "D3Q19 FP32 pillar-slab 256x256x192 (12.58M nodes), plain method, stage-2 LB step"
 
@@ -143,7 +152,7 @@ def shard(items, rank: int, world: int):
     return [it for i, it in enumerate(items) if i % world == rank]
 
 
-def measured_traffic(name="node_kernel_d3q19_f32_geq"):
+def measured_traffic(name="zstep_kernel_d3q19_f32"):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     or None when the kernel source has changed since the counters were taken."""
     import hashlib
@@ -156,7 +165,7 @@ def measured_traffic(name="node_kernel_d3q19_f32_geq"):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("dsm_lb_impl.cuh", "dsm_common.cuh"):
+    for f in ("dsm_lb_impl.cuh", "dsm_common.cuh", "dsm_zstep.cuh"):
         with open(os.path.join(ROOT, "paper_2504_19941_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != rec.get("kernel_source_sha256_16"):
@@ -308,6 +317,7 @@ def run_gpu(args, rank, world):
                            faces=faces)
     lat = P.Lattice(params, device=dev)
     lat.set_g_storage(args.g_storage)
+    lat.set_step_form(args.step_form, args.zrun)
     sd_h = torch.as_tensor(case.solid_sd, dtype=torch.float32).pin_memory()
     c2_h = torch.as_tensor(case.c2, dtype=torch.float32).pin_memory()
     sd_d = sd_h.to(dev, non_blocking=True)
@@ -316,16 +326,25 @@ def run_gpu(args, rank, world):
     lat.set_fluid(c2_d)
     n = lat.n
     h = lat.h
+    # the one-pass step where the lattice allows it (one launch per step),
+    # else the moments pass and the fused pass (two launches)
+    single = lat.single_pass
 
     def one_step():
-        _lib.dsm_step_moments(h)
-        _lib.dsm_step_collide(h)
+        if single:
+            _lib.dsm_step(h, 1)
+        else:
+            _lib.dsm_step_moments(h)
+            _lib.dsm_step_collide(h)
 
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     g_eq = lat.g_implicit
-    k2_b, k1_b = lu_bytes(lattice, "f32", g_eq)
+    if single:
+        k2_b, k1_b = lu_bytes_single("f32"), 0
+    else:
+        k2_b, k1_b = lu_bytes(lattice, "f32", g_eq)
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -337,9 +356,13 @@ def run_gpu(args, rank, world):
         time.sleep(0.3)
         e0.record(stream)
         for k in range(args.steps):
-            _lib.dsm_step_moments(h)
-            ev[k][0].record(stream)
-            _lib.dsm_step_collide(h)
+            if single:
+                ev[k][0].record(stream)
+                _lib.dsm_step(h, 1)
+            else:
+                _lib.dsm_step_moments(h)
+                ev[k][0].record(stream)
+                _lib.dsm_step_collide(h)
             ev[k][1].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -378,8 +401,11 @@ def run_gpu(args, rank, world):
     achieved = k2_b * n / t_k2 / 1e9
     default = (shape == SHAPE and lattice == "D3Q19" and args.rho3 == 1.0 and args.tau3 == 1.0
                and not faces)
-    traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
-               if default else None)
+    if single:
+        traffic = measured_traffic("zstep_kernel_d3q19_f32") if default else None
+    else:
+        traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
+                   if default else None)
     step_achieved = (k2_b + k1_b) * n / (t_max / args.steps) / 1e9
 
     if rank == 0:
@@ -393,13 +419,18 @@ def run_gpu(args, rank, world):
                                     lattice, args.rho3, args.tau3, faces),
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic,
-                            "kernel": "node_kernel<%s,f32,stage2,step,%s%s>" %
+                            "kernel": ("zstep_kernel<f32,f32%s> (one pass per step, %d z planes "
+                                       "per block)" % (",density contrast" if args.rho3 != 1.0 else "",
+                                                       _lib.dsm_step_info(h)[1]))
+                                      if single else
+                                      "node_kernel<%s,f32,stage2,step,%s%s>" %
                                       (lattice, "g_eq" if g_eq else "populations",
                                        ",density contrast" if args.rho3 != 1.0 else ""),
                             "bytes_per_lu": k2_b, "peak_source": peak_kind,
                             "k2_ms": t_k2 * 1e3, "step_bytes_per_lu": k1_b + k2_b,
                             "step_achieved": step_achieved, "step_frac": step_achieved / peak},
-               "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
+               "clocks": clk.summary(), "e2e": e2e,
+               "gpu_launches": (1 if single else 2) * args.steps,
                "cpu_baseline": cb,
                "observables": {"mass_c2": obs["mass_c2"], "max_u": obs["max_u"]}}
         print(json.dumps(out), flush=True)
@@ -465,21 +496,27 @@ def run_serve(args, rank, world):
 
 
 def _time_steps(lat, steps, warmup):
-    """Per-step and fused-pass times (CUDA events) of `steps` steps."""
+    """Per-step and dominant-kernel times (CUDA events) of `steps` steps: the
+    one-pass step's launch, or the fused pass of the two-pass step."""
     import torch
     from paper_2504_19941_gb300 import _lib
     for _ in range(warmup):
         lat.step(1)
     torch.cuda.synchronize()
+    single = lat.single_pass
     stream = lat.stream
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(steps):
-        _lib.dsm_step_moments(lat.h)
-        ev[k][0].record(stream)
-        _lib.dsm_step_collide(lat.h)
+        if single:
+            ev[k][0].record(stream)
+            _lib.dsm_step(lat.h, 1)
+        else:
+            _lib.dsm_step_moments(lat.h)
+            ev[k][0].record(stream)
+            _lib.dsm_step_collide(lat.h)
         ev[k][1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -504,10 +541,13 @@ def run_precision(args, rank, world):
         lat.set_g_storage(args.g_storage)
         lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
         lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float32, device=dev))
+        lat.set_step_form(args.step_form, args.zrun)
         t_step, t_k2 = _time_steps(lat, args.steps, args.warmup)
-        bmin = lu_bytes("D3Q19", prec, lat.g_implicit)[0]
+        bmin = (lu_bytes_single(prec) if lat.single_pass
+                else lu_bytes("D3Q19", prec, lat.g_implicit)[0])
         ob = lat.observables()
         out[prec] = {"MLUPS": lat.n / t_step / 1e6, "ms_per_step": t_step * 1e3,
+                     "single_pass": lat.single_pass,
                      "k2_ms": t_k2 * 1e3, "bytes_per_lu": bmin,
                      "roofline_frac": bmin * lat.n / t_k2 / 1e9 / peak,
                      "nonfinite": ob["nonfinite"]}
@@ -852,6 +892,10 @@ def main():
     ap.add_argument("--tau3", type=float, default=1.0, help="gas relaxation time (liquid 1)")
     ap.add_argument("--faces", default="",
                     help="six comma-separated faces x-,x+,y-,y+,z-,z+: periodic, mirror or wall")
+    ap.add_argument("--step-form", default="auto", choices=["auto", "two_pass"],
+                    help="auto: one pass per step where the lattice allows it")
+    ap.add_argument("--zrun", type=int, default=0,
+                    help="z planes per block of the one-pass step (0: automatic)")
     ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],
                     help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),

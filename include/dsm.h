@@ -131,7 +131,9 @@ dsm_status dsm_kappa(const dsm_params *p, double kappa_out[3]);
 
 /* Workspace bytes a lattice of these parameters needs (populations, two
  * buffers each; C1; C, two buffers; the four g_eq planes; solid mask;
- * reduction scratch). */
+ * reduction scratch; for lattices the one-pass step applies to (see
+ * dsm_set_step_form), padded (A, u, C), two buffers, and padded C1:
+ * 11 reals per padded node, (nx + 8)(ny + 4) nz nodes). */
 dsm_status dsm_workspace_bytes(const dsm_params *p, size_t *bytes);
 
 /* Create a handle over a caller-owned device workspace (>= the size above,
@@ -183,6 +185,29 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps);
  * DSM_E_STATE. */
 dsm_status dsm_step_moments(dsm_lattice *h);
 dsm_status dsm_step_collide(dsm_lattice *h);
+
+/* How dsm_step advances a lattice.  The step of Sec. II.B needs C = sum_i g_i
+ * of the streamed populations on each node's neighbourhood before it can form
+ * mu, so dsm_step normally runs it as the two passes above.  For D3Q19 lattices
+ * with nx a multiple of 32, ny a multiple of 8, tau_g = 1 (g held as g_eq, see
+ * dsm_set_g_storage) and periodic faces, DSM_STEP_AUTO instead runs each step
+ * as ONE pass: blocks march 32 x 8 tiles up runs of z planes, rebuild the C of
+ * the step on chip from the staged (A, u, C) of the previous collision and
+ * collide.  The results are the same step (the same per-node arithmetic, so
+ * equal to the two-pass step up to nothing but FP32 contraction order); the
+ * state then lives in padded buffers of the workspace and is converted back
+ * before any call that reads it (fields, observables, populations, checkpoint,
+ * dsm_batch_step).  DSM_STEP_TWO_PASS always uses the two passes.
+ *   zrun: z planes per block of the one-pass step, 0 = chosen from the lattice
+ *   size and the GPU's resident blocks (a tuning knob; results do not depend on
+ *   it).  DSM_E_INVAL for an unknown form or zrun < 0. */
+enum { DSM_STEP_AUTO = 0, DSM_STEP_TWO_PASS = 1 };
+dsm_status dsm_set_step_form(dsm_lattice *h, int form, int zrun);
+
+/* Whether dsm_step currently runs the one-pass step (*single_pass = 1) and
+ * with how many z planes per block (*zrun; 0 for the two-pass step).  Either
+ * pointer may be NULL. */
+dsm_status dsm_step_info(dsm_lattice *h, int *single_pass, int *zrun);
 
 /* Observables of the current state; synchronises the stream.  Returns
  * DSM_E_NONFINITE (and sets out->nonfinite) when the state holds a NaN/Inf. */

@@ -151,6 +151,17 @@ class Lattice:
         _lib.dsm_set_g_storage(self.h, {"auto": _lib.DSM_G_AUTO,
                                         "populations": _lib.DSM_G_POPULATIONS}[form])
 
+    def set_step_form(self, form: str, zrun: int = 0):
+        """'auto' (one pass per step where the lattice allows it) or 'two_pass';
+        zrun: z planes per block of the one-pass step (0: automatic)."""
+        _lib.dsm_set_step_form(self.h, {"auto": _lib.DSM_STEP_AUTO,
+                                        "two_pass": _lib.DSM_STEP_TWO_PASS}[form], int(zrun))
+
+    @property
+    def single_pass(self) -> bool:
+        """True when dsm_step runs the one-pass step on this lattice."""
+        return _lib.dsm_step_info(self.h)[0]
+
     @property
     def g_implicit(self) -> bool:
         """True when the current state holds g as g_eq (A, u) rather than populations."""

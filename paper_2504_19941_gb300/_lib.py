@@ -19,13 +19,14 @@ DSM_D2Q9, DSM_D3Q19 = 0, 1
 DSM_FACE_PERIODIC, DSM_FACE_MIRROR, DSM_FACE_WALL = 0, 1, 2
 DSM_F64, DSM_F32, DSM_BF16_STORE, DSM_F16_STORE = 0, 1, 2, 3
 DSM_G_AUTO, DSM_G_POPULATIONS = 0, 1
+DSM_STEP_AUTO, DSM_STEP_TWO_PASS = 0, 1
 (DSM_FIELD_C1, DSM_FIELD_C2, DSM_FIELD_C3, DSM_FIELD_MU, DSM_FIELD_UX, DSM_FIELD_UY,
  DSM_FIELD_UZ, DSM_FIELD_PT, DSM_FIELD_RHO, DSM_FIELD_TAU) = range(10)
 
 EXPORTED = (
     "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
     "dsm_set_solid", "dsm_relax_solid", "dsm_solid_region", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
-    "dsm_step_collide", "dsm_get_observables",
+    "dsm_step_collide", "dsm_set_step_form", "dsm_step_info", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
@@ -94,6 +95,8 @@ def load():
         "dsm_step": (st, [vp, C.c_longlong]),
         "dsm_step_moments": (st, [vp]),
         "dsm_step_collide": (st, [vp]),
+        "dsm_set_step_form": (st, [vp, C.c_int, C.c_int]),
+        "dsm_step_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "dsm_get_observables": (st, [vp, C.POINTER(dsm_observables)]),
         "dsm_get_field": (st, [vp, C.c_int, vp]),
         "dsm_get_populations": (st, [vp, vp, vp]),
@@ -272,6 +275,17 @@ def dsm_step_moments(h: int):
 
 def dsm_step_collide(h: int):
     _check(load().dsm_step_collide(h), "dsm_step_collide")
+
+
+def dsm_set_step_form(h: int, form: int, zrun: int = 0):
+    _check(load().dsm_set_step_form(h, form, zrun), "dsm_set_step_form")
+
+
+def dsm_step_info(h: int):
+    """(single_pass, zrun) of dsm_step_info."""
+    sp, zr = C.c_int(0), C.c_int(0)
+    _check(load().dsm_step_info(h, C.byref(sp), C.byref(zr)), "dsm_step_info")
+    return bool(sp.value), zr.value
 
 
 def dsm_get_observables(h: int, check: bool = True) -> dict:

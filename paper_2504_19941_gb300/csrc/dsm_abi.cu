@@ -39,6 +39,18 @@ struct dsm_lattice {
   bool eq;         // the fused pass stores g as g_eq (tau_g = 1 and DSM_G_AUTO)
   bool g_implicit; // the current g are held as g_eq
   StepParams sp;
+  // single-pass step (dsm_zstep.cuh): padded quads (A, C, u_x, u_y) and u_z,
+  // two buffers, and padded C1; zc: the buffer holding the current state while
+  // zpacked
+  bool zok;        // the workspace has the padded buffers (D3Q19, nx % 32, ny % 8, tau_g = 1, periodic)
+  bool zpacked;    // the current g_eq state lives in the padded buffers
+  bool zmaps_ok;   // maps[] encoded
+  int zc, nxp, nyp;
+  void *Qz[2], *Uz[2], *C1z;
+  ZMaps maps[2];   // maps[b]: read the padded state of buffer b (and C1)
+  int step_form;   // DSM_STEP_AUTO or DSM_STEP_TWO_PASS
+  int zrun;        // planes per block of the single-pass step (0: automatic)
+  int zrun_auto;
 };
 
 namespace {
@@ -86,8 +98,18 @@ dsm_status check_params(const dsm_params *p) {
 }
 
 struct Layout {
-  size_t f[2], g[2], g0[2], C[2], M, C1, mask, partials, obs, err, total;
+  size_t f[2], g[2], g0[2], C[2], M, C1, mask, partials, obs, err, Qz[2], Uz[2], C1z, total;
 };
+
+// The single-pass step applies to D3Q19 lattices whose planes tile into 32 x 8
+// blocks, with tau_g = 1 (g held as g_eq) and periodic faces.
+bool z_eligible(const dsm_params *p) {
+  if (p->lattice != DSM_D3Q19 || p->tau_g != 1.0 || has_walls(p)) return false;
+  return p->nx % ZT_X == 0 && p->ny % ZT_Y == 0;
+}
+long long z_padded_nodes(const dsm_params *p) {
+  return (long long)(p->nx + 2 * ZPAD_X) * (p->ny + 2 * ZPAD_Y) * p->nz;
+}
 
 long long obs_blocks_of(int kind, int nx, int ny, int nz) {
   const dim3 g = lb_grid(kind, nx, ny, nz);
@@ -117,6 +139,12 @@ Layout layout_of(const dsm_params *p, const LBTable &t, long long N, long long p
   L.partials = take(obs_blocks_of(p->lattice, p->nx, p->ny, p->nz) * OBS_K * sizeof(double));
   L.obs = take(8 * sizeof(double));
   L.err = take(sizeof(int) * 4);
+  const long long P = z_eligible(p) ? z_padded_nodes(p) : 0;
+  L.Qz[0] = take(4 * P * t.real_bytes);
+  L.Qz[1] = take(4 * P * t.real_bytes);
+  L.Uz[0] = take(P * t.real_bytes);
+  L.Uz[1] = take(P * t.real_bytes);
+  L.C1z = take(P * t.real_bytes);
   L.total = o;
   (void)N;
   return L;
@@ -164,6 +192,8 @@ LBRaw raw_of(const dsm_lattice *h, int src) {
   r.C = h->Cb[src ^ 1];
   r.Cprev = h->Cb[src];
   r.M = h->M;
+  r.nxp = h->nxp;
+  r.nyp = h->nyp;
   r.eq = h->eq;
   r.implicit = h->g_implicit;
   r.C1 = h->C1;
@@ -172,6 +202,108 @@ LBRaw raw_of(const dsm_lattice *h, int src) {
   r.err = h->err;
   r.p = h->sp;
   return r;
+}
+
+// ---- single-pass step -------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return (EncodeTiledFn)f;
+  }();
+  return fn;
+}
+
+// A 3-D tensor map over padded planes of `comp` interleaved reals per node
+// (dims comp * nxp, nyp, nz) whose box is comp * ZB_X wide and `rows` high.
+bool encode_plane_map(CUtensorMap *m, void *base, int real_bytes, int comp, int nxp, int nyp,
+                      int nz, int rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)comp * nxp, (cuuint64_t)nyp, (cuuint64_t)nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)comp * nxp * real_bytes,
+                                (cuuint64_t)comp * nxp * nyp * real_bytes};
+  const cuuint32_t box[3] = {(cuuint32_t)(comp * ZB_X), (cuuint32_t)rows, 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return enc(m, real_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+             3, base, dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool z_maps(dsm_lattice *h) {
+  if (h->zmaps_ok) return true;
+  const int rb = h->tab.real_bytes, nz = h->prm.nz;
+  for (int b = 0; b < 2; b++) {
+    if (!encode_plane_map(&h->maps[b].Q, h->Qz[b], rb, 4, h->nxp, h->nyp, nz, ZB_Y) ||
+        !encode_plane_map(&h->maps[b].U, h->Uz[b], rb, 1, h->nxp, h->nyp, nz, ZB_Y) ||
+        !encode_plane_map(&h->maps[b].C1, h->C1z, rb, 1, h->nxp, h->nyp, nz, ZB1_Y))
+      return false;
+  }
+  h->zmaps_ok = true;
+  return true;
+}
+
+// The longest-lasting choice of planes per block: runs of zr planes give
+// tiles * ceil(nz / zr) blocks, which run in waves of the resident blocks; a
+// wave lasts about zr planes plus the run's prologue (this step's C of two
+// extra planes and the first staged planes, about 0.7 of a plane).
+int z_auto_run(dsm_lattice *h) {
+  if (h->zrun_auto) return h->zrun_auto;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long resident = (long long)(sms > 0 ? sms : 152) * (h->tab.zresident() > 0 ? h->tab.zresident() : 1);
+  const long long tiles = (long long)(h->prm.nx / ZT_X) * (h->prm.ny / ZT_Y);
+  const int nz = h->prm.nz;
+  double best = 1e300;
+  int run = nz;
+  for (int zr = 1; zr <= nz; zr++) {
+    const long long blocks = tiles * ((nz + zr - 1) / zr);
+    const double waves = (double)((blocks + resident - 1) / resident);
+    const double cost = waves * (zr + 0.7);
+    if (cost < best - 1e-9) {
+      best = cost;
+      run = zr;
+    }
+  }
+  h->zrun_auto = run;
+  return run;
+}
+
+bool z_active(const dsm_lattice *h) {
+  return h->zok && h->eq && h->step_form == DSM_STEP_AUTO;
+}
+
+// Canonical g_eq state -> padded buffers (buffer 0), and padded C1.
+cudaError_t z_pack(dsm_lattice *h) {
+  if (!z_maps(h)) return cudaErrorInvalidValue;
+  LBRaw a = raw_of(h, h->cur);
+  cudaError_t e = h->tab.zpack(a, h->Qz[0], h->Qz[1], h->Uz[0], h->Uz[1], h->C1z, h->stream);
+  if (e != cudaSuccess) return e;
+  h->zc = 0;
+  h->zpacked = true;
+  return cudaSuccess;
+}
+
+// Padded state -> canonical g_eq state (A, u planes and C of the last
+// collision), before any call that reads the state in its canonical layout.
+cudaError_t z_unpack(dsm_lattice *h) {
+  if (!h->zpacked) return cudaSuccess;
+  LBRaw a = raw_of(h, h->cur);
+  cudaError_t e = h->tab.zunpack(a, h->Qz[h->zc], h->Uz[h->zc], h->Cb[h->cur], h->stream);
+  if (e != cudaSuccess) return e;
+  h->zpacked = false;
+  return cudaSuccess;
 }
 
 // Read and clear nothing: report the latched device error word.
@@ -311,6 +443,15 @@ dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void
   h->obs = (double *)(h->ws + L.obs);
   h->err = (int *)(h->ws + L.err);
   h->obs_blocks = obs_blocks_of(p->lattice, p->nx, p->ny, p->nz);
+  h->zok = z_eligible(p);
+  h->nxp = p->nx + 2 * ZPAD_X;
+  h->nyp = p->ny + 2 * ZPAD_Y;
+  for (int b = 0; b < 2; b++) {
+    h->Qz[b] = h->zok ? h->ws + L.Qz[b] : nullptr;
+    h->Uz[b] = h->zok ? h->ws + L.Uz[b] : nullptr;
+  }
+  h->C1z = h->zok ? h->ws + L.C1z : nullptr;
+  h->step_form = DSM_STEP_AUTO;
   h->stream = (cudaStream_t)cuda_stream;
   h->sp = step_params(p, h->kappa);
   h->g_form = DSM_G_AUTO;
@@ -337,6 +478,7 @@ dsm_status dsm_set_solid(dsm_lattice *h, const void *d_field, int kind) {
   if (e != cudaSuccess) return DSM_E_CUDA;
   h->has_solid = true;
   h->has_fluid = false;
+  h->zpacked = false;
   return DSM_OK;
 }
 
@@ -353,6 +495,7 @@ dsm_status dsm_relax_solid(dsm_lattice *h, const unsigned char *d_mask, int step
   h->cur = 0;
   h->g_implicit = false;
   h->has_fluid = false;
+  h->zpacked = false;
   LBRaw r = raw_of(h, 1);  // out = buffer 0
   r.eq = 0;
   if ((e = h->tab.init(r, h->C1, 1, h->stream)) != cudaSuccess) return DSM_E_CUDA;
@@ -401,6 +544,7 @@ dsm_status dsm_set_fluid(dsm_lattice *h, const void *d_c2) {
   h->latched = false;
   h->moments_ready = false;
   h->g_implicit = false;  // the initial g are written as populations
+  h->zpacked = false;
   return DSM_OK;
 }
 
@@ -408,11 +552,27 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
   TraceRange trace_range("dsm_step");
   if (!h || nsteps < 0) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched) return DSM_E_STATE;
+  const bool single = z_active(h);
+  if (!single && z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   for (long long t = 0; t < nsteps; t++) {
-    LBRaw a = raw_of(h, h->cur);
-    cudaError_t e = h->tab.moments(a, h->stream);
-    if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_STEP, h->stream);
-    if (e != cudaSuccess) return DSM_E_CUDA;
+    cudaError_t e;
+    if (single && h->g_implicit) {
+      // one pass per step over the padded g_eq state
+      if (!h->zpacked && (e = z_pack(h)) != cudaSuccess) return DSM_E_CUDA;
+      LBRaw a = raw_of(h, h->cur);
+      a.Qz = h->Qz[h->zc ^ 1];
+      a.Uz = h->Uz[h->zc ^ 1];
+      e = h->tab.zstep(a, h->maps[h->zc], h->zrun > 0 ? h->zrun : z_auto_run(h), h->stream);
+      if (e != cudaSuccess) return DSM_E_CUDA;
+      h->zc ^= 1;
+    } else {
+      // moments pass, then the fused pass (also the first step after
+      // dsm_set_fluid, whose g are populations)
+      LBRaw a = raw_of(h, h->cur);
+      e = h->tab.moments(a, h->stream);
+      if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_STEP, h->stream);
+      if (e != cudaSuccess) return DSM_E_CUDA;
+    }
     h->cur ^= 1;
     h->step++;
     h->g_implicit = h->eq;
@@ -421,10 +581,27 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
   return DSM_OK;
 }
 
+dsm_status dsm_set_step_form(dsm_lattice *h, int form, int zrun) {
+  if (!h || (form != DSM_STEP_AUTO && form != DSM_STEP_TWO_PASS) || zrun < 0) return DSM_E_INVAL;
+  if (form == DSM_STEP_TWO_PASS && z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
+  h->step_form = form;
+  h->zrun = zrun;
+  return DSM_OK;
+}
+
+dsm_status dsm_step_info(dsm_lattice *h, int *single_pass, int *zrun) {
+  if (!h) return DSM_E_INVAL;
+  const bool single = z_active(h);
+  if (single_pass) *single_pass = single ? 1 : 0;
+  if (zrun) *zrun = single ? (h->zrun > 0 ? h->zrun : z_auto_run(h)) : 0;
+  return DSM_OK;
+}
+
 dsm_status dsm_step_moments(dsm_lattice *h) {
   TraceRange trace_range("moments pass (K1)");
   if (!h) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched) return DSM_E_STATE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   LBRaw a = raw_of(h, h->cur);
   if (h->tab.moments(a, h->stream) != cudaSuccess) return DSM_E_CUDA;
   h->moments_ready = true;
@@ -435,6 +612,7 @@ dsm_status dsm_step_collide(dsm_lattice *h) {
   TraceRange trace_range("fused pass (K2)");
   if (!h) return DSM_E_INVAL;
   if (!h->has_fluid || h->latched || !h->moments_ready) return DSM_E_STATE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   LBRaw a = raw_of(h, h->cur);
   if (h->tab.node(a, 2, MODE_STEP, h->stream) != cudaSuccess) return DSM_E_CUDA;
   h->cur ^= 1;
@@ -447,6 +625,7 @@ dsm_status dsm_step_collide(dsm_lattice *h) {
 dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out) {
   if (!h || !out) return DSM_E_INVAL;
   if (!h->has_fluid) return DSM_E_STATE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   LBRaw a = raw_of(h, h->cur);
   cudaError_t e = h->tab.moments(a, h->stream);
   if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_OBS, h->stream);
@@ -484,6 +663,7 @@ dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst) {
     return cuda_status(e);
   }
   if (!h->has_fluid) return DSM_E_STATE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   LBRaw a = raw_of(h, h->cur);
   a.out = d_dst;
   a.field_sel = field;
@@ -495,6 +675,7 @@ dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst) {
 dsm_status dsm_get_populations(dsm_lattice *h, void *d_f, void *d_g) {
   if (!h || !d_f || !d_g) return DSM_E_INVAL;
   if (!h->has_fluid) return DSM_E_STATE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   LBRaw a = raw_of(h, h->cur);
   return cuda_status(h->tab.get_pops(a, d_f, d_g, h->stream));
 }
@@ -509,12 +690,14 @@ dsm_status dsm_set_populations(dsm_lattice *h, const void *d_f, const void *d_g)
   h->latched = false;
   h->moments_ready = false;
   h->g_implicit = false;
+  h->zpacked = false;
   return DSM_OK;
 }
 
 dsm_status dsm_set_g_storage(dsm_lattice *h, int form) {
   if (!h || (form != DSM_G_AUTO && form != DSM_G_POPULATIONS)) return DSM_E_INVAL;
   const bool eq = form == DSM_G_AUTO && h->prm.tau_g == 1.0 && !has_walls(&h->prm);
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   if (h->g_implicit && !eq) {
     // write the current g_eq out as populations of the current buffer
     LBRaw a = raw_of(h, h->cur ^ 1);  // g_out = current buffer
@@ -578,6 +761,7 @@ dsm_status dsm_get_state(dsm_lattice *h, void *d_dst, size_t bytes) {
   if (!h->has_fluid) return DSM_E_STATE;
   const StateLayout L = state_layout(h);
   if (bytes < L.total || ((uintptr_t)d_dst & 255u)) return DSM_E_WORKSPACE;
+  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
   StateHeader hd;
   memset(&hd, 0, sizeof(hd));
   hd.magic = kStateMagic;
@@ -634,6 +818,7 @@ dsm_status dsm_set_state(dsm_lattice *h, const void *d_src, size_t bytes) {
   h->cur = 0;
   h->step = hd.step;
   h->g_implicit = hd.implicit != 0;
+  h->zpacked = false;
   h->has_fluid = true;
   h->latched = false;
   h->moments_ready = false;
@@ -815,6 +1000,8 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
   if (s != DSM_OK) return s;
   for (int i = 0; i < n; i++)
     if (!hs[i]->has_fluid || hs[i]->latched) return DSM_E_STATE;
+  for (int i = 0; i < n; i++)
+    if (z_unpack(hs[i]) != cudaSuccess) return DSM_E_CUDA;
   if (scratch_bytes < hs[0]->tab.batch_bytes(items.data(), n) || ((uintptr_t)d_scratch & 255u))
     return DSM_E_WORKSPACE;
   cudaError_t e = hs[0]->tab.batch(items.data(), n, d_scratch, scratch_bytes,

@@ -2,6 +2,7 @@
 // by the CUDA kernels of libdsm (sm_103a).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -178,6 +179,10 @@ struct LBArgs {
   S *fout[QMAX], *gout[QMAX];
   // g held as g_eq (tau_g = 1): planes A = mu - 3/2 C u.u, u_x, u_y, u_z
   T *Mp[4];
+  // single-pass step: padded quads (A, C, u_x, u_y) and u_z written by the
+  // step, and the padded plane sizes
+  T *Qz, *Uz;
+  int nxp, nyp;
 };
 
 // Error bits latched in the workspace error word.
@@ -197,6 +202,8 @@ struct LBRaw {
   const void *C1;
   const unsigned char *mask;
   void *M;          // 4 planes of pitch reals (see LBArgs::Mp)
+  void *Qz, *Uz;    // single-pass step outputs (see LBArgs::Qz)
+  int nxp, nyp;
   int eq;           // the fused pass stores g as g_eq (A, u) instead of populations
   int implicit;     // the current g are held as g_eq (A, u, Cprev)
   void *out;
@@ -213,6 +220,12 @@ struct BatchRaw {
   int cur0;
 };
 
+// Tensor maps of the single-pass step's staged boxes: the padded quads
+// (A, C, u_x, u_y) and u_z of the state it reads, and the padded C1.
+struct ZMaps {
+  CUtensorMap Q, U, C1;
+};
+
 struct LBTable {
   cudaError_t (*moments)(const LBRaw &, cudaStream_t);
   cudaError_t (*node)(const LBRaw &, int stage, int mode, cudaStream_t);
@@ -224,6 +237,14 @@ struct LBTable {
   cudaError_t (*batch)(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
                        bool eq, cudaStream_t);
   size_t (*batch_bytes)(const BatchRaw *items, int n);
+  // single-pass step (D3Q19, g held as g_eq, periodic; see dsm_zstep.cuh):
+  // one step from the padded state the maps describe into r.Qz / r.Uz;
+  // resident blocks per SM; canonical state <-> padded buffers
+  cudaError_t (*zstep)(const LBRaw &r, const ZMaps &m, int zrun, cudaStream_t);
+  int (*zresident)();
+  cudaError_t (*zpack)(const LBRaw &r, void *Qz0, void *Qz1, void *Uz0, void *Uz1, void *C1z,
+                       cudaStream_t);
+  cudaError_t (*zunpack)(const LBRaw &r, const void *Qz, const void *Uz, void *Cout, cudaStream_t);
   int q, real_bytes, store_bytes;
   bool k16;
 };

@@ -146,10 +146,23 @@ __device__ __forceinline__ T link_q(T c1x, const T (&gc1)[3], int i, T alpha_s) 
   return q > T(1) ? T(0.5) : q;
 }
 
-// The same link fraction from the node's precomputed x_s and |G[C1]|, for a
-// direction known only at run time (the wall-link loop is rolled).
+// The same link fraction from the node's precomputed x_s and |G[C1]|.
+// link_fraction_rt: for a direction known only at run time (a rolled wall-link
+// loop); link_fraction: for a direction known at compile time (an unrolled
+// loop: the length of c_i and its components are constants).  The same
+// arithmetic in the same order.
 template <class L, class T>
-__device__ __noinline__ T link_fraction(T xs, T gn, T g0, T g1, T g2, int i) {
+__device__ __noinline__ T link_fraction_rt(T xs, T gn, T g0, T g1, T g2, int i) {
+  if (!(gn >= T(1e-12))) return T(0.5);
+  const int l2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+  const T cl = l2 == 1 ? T(1) : sqrt(T(l2));
+  const T nd = (g0 * T(L::cx(i)) + g1 * T(L::cy(i)) + g2 * T(L::cz(i))) / (gn * cl);
+  if (!(nd > T(1e-6))) return T(0.5);
+  const T q = fabs(xs / nd) / cl;
+  return q > T(1) ? T(0.5) : q;
+}
+template <class L, class T>
+__device__ __forceinline__ T link_fraction(T xs, T gn, T g0, T g1, T g2, int i) {
   if (!(gn >= T(1e-12))) return T(0.5);
   const int l2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
   const T cl = l2 == 1 ? T(1) : sqrt(T(l2));
@@ -395,15 +408,45 @@ __global__ void __launch_bounds__(256) moments_eq_kernel(LBArgs<T, S> a) {
                            blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z * blockDim.z + threadIdx.z);
 }
 
+// Where the fused pass finds C and C1 on the node's 1-neighbourhood, and where
+// a collision of the g_eq form stores what fixes g (A = mu - 3/2 C u.u, u):
+// global memory, as the per-lattice and batched launches keep them.  The
+// single-pass step (dsm_zstep.cuh) reads both from shared memory instead.
+struct GlobalIO {
+  // wall links fixed in one rolled loop (fewer registers next to the
+  // neighbourhood loads in flight); the f pulls of a solid node are issued
+  // with the rest, before its C1 is known
+  static constexpr bool kUnrollWall = false;
+  static constexpr bool kSolidFirst = false;
+  template <class L, class T, class S>
+  __device__ __forceinline__ T C(const LBArgs<T, S> &a, const Hood &h, int i) const {
+    return __ldg(a.C + h.plus<L>(i));
+  }
+  template <class L, class T, class S>
+  __device__ __forceinline__ T C1(const LBArgs<T, S> &a, const Hood &h, int i) const {
+    return __ldg(a.C1 + h.plus<L>(i));
+  }
+  // (C of this collision is the moments pass's output already in a.C)
+  template <class L, class T, class S>
+  __device__ __forceinline__ void put_eq(const LBArgs<T, S> &a, int n, T, T A, T ux, T uy,
+                                         T uz) const {
+    a.Mp[0][n] = A;
+    a.Mp[1][n] = ux;
+    a.Mp[2][n] = uy;
+    if (L::D == 3) a.Mp[3][n] = uz;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // K2: fused pass.  STAGE 2: fluids on the frozen diffuse solid C1.
 // STAGE 1: relaxation of C1 itself (g carries C1; rho = 1, tau = tau_g = 1,
 // every node fluid).  MODE_STEP collides and writes the next state;
 // MODE_FIELDS writes one macroscopic field; MODE_OBS reduces observables.
 // ---------------------------------------------------------------------------
-template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ, bool FC>
+template <int K, class T, class S, int STAGE, int MODE, bool RC, bool EQ, bool FC,
+          class IO = GlobalIO>
 __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, int z, bool valid,
-                                          int field_sel) {
+                                          int field_sel, const IO &io = IO()) {
   using L = Lat<K>;
   constexpr int Q = L::Q;
   // the pulled g enter only the g collision (C comes from the moments pass)
@@ -430,9 +473,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     T Cn[Q], C1n[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      const int m = h.plus<L>(i);
-      Cn[i] = __ldg(a.C + m);
-      C1n[i] = (STAGE == 2) ? __ldg(a.C1 + m) : T(0);
+      Cn[i] = io.template C<L>(a, h, i);
+      C1n[i] = (STAGE == 2) ? io.template C1<L>(a, h, i) : T(0);
     }
 #pragma unroll
     for (int j = 0; j < Q; j++) {
@@ -440,7 +482,17 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
       if (!LOAD_G) g[j] = T(0);
       else if (Store<S>::k16 && j == 0) g[j] = T(a.g0_in[n]);
       else g[j] = load_g<T, S>(a.gin[j], src);
-      f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
+      if constexpr (IO::kSolidFirst) f[j] = T(L::w(j));
+      else f[j] = load_f<T, S>(a.fin[j], src, j, L::w(j));
+    }
+    // the pulled f of a solid node (C1 >= 1/2) are never used: its collision
+    // writes f* = w.  Where C1 of the node is at hand first (shared memory),
+    // a solid node skips the pulls, and a warp of solid nodes issues none.
+    if constexpr (IO::kSolidFirst) {
+      if (!(STAGE == 2 && C1n[0] >= T(0.5))) {
+#pragma unroll
+        for (int j = 0; j < Q; j++) f[j] = load_f<T, S>(a.fin[j], h.minus<L>(j), j, L::w(j));
+      }
     }
     C = Cn[0];
     c1 = C1n[0];
@@ -533,39 +585,72 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   const bool solid_x = (STAGE == 2) && c1 >= T(0.5);
 
   // ---- interpolated bounce-back at the diffuse solid ------------------------
-  // (rare: only fluid nodes with a solid neighbour) -- one rolled loop replaces
-  // the pulled value of every link whose upstream node x - c_j is solid.
+  // (only fluid nodes with a solid neighbour) -- replaces the pulled value of
+  // every link whose upstream node x - c_j is solid.  Two forms of the same
+  // arithmetic: one rolled loop over the directions, whose result goes to f[j]
+  // through a select over all directions (IO::kUnrollWall false: the fewest
+  // registers next to the neighbourhood loads of the global-memory pass), or
+  // unrolled, so that a warp executes the body of a direction only when one of
+  // its nodes has that wall link and each result lands in a fixed register.
   if (STAGE == 2 && !solid_x && (nb_solid & ~1u)) {
     // the node's distance to the C1 = 1/2 surface and the normal, once per node
     const T cc = c1 < T(1e-9) ? T(1e-9) : (c1 > T(0.5) ? T(0.5) : c1);
     const T xs = T(2) * K_.alpha_s * atanh(T(2) * cc - T(1));
     const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
-    for (int j = 1; j < Q; j++) {
-      const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
-      if (!((nb_solid >> i) & 1u)) continue;
-      const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
-      const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
-      T v;
-      // x - c_i, the next fluid node away from the wall: with mirror or wall
-      // faces it is pulled like any population (none beyond a wall)
-      int ki = i;
-      bool second = !((nb_solid >> j) & 1u);
-      if constexpr (FC) {
-        if (face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
-      }
-      if (q < T(0.5) && second) {
-        const int z2 = h.plus_rt<L>(j);
-        const T fi_z = load_f<T, S>(a.fin[ki], z2, ki, L::w(ki));
-        v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
-      } else if (q < T(0.5)) {
-        v = fi_x;  // no second fluid node: halfway rule
-      } else {
-        const T fj_x = load_f<T, S>(a.fin[j], n, j, L::w(j));
-        v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
-      }
+    if constexpr (IO::kUnrollWall) {
 #pragma unroll
-      for (int k = 1; k < Q; k++)
-        if (k == j) f[k] = v;
+      for (int j = 1; j < Q; j++) {
+        const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
+        if ((nb_solid >> i) & 1u) {
+          const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
+          const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
+          // x - c_i, the next fluid node away from the wall: with mirror or
+          // wall faces it is pulled like any population (none beyond a wall)
+          bool second = !((nb_solid >> j) & 1u);
+          int ki = i;
+          if constexpr (FC) {
+            if (face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
+          }
+          T v;
+          if (q < T(0.5) && second) {
+            const T fi_z = FC ? load_f<T, S>(a.fin[ki], h.plus<L>(j), ki, L::w(ki))
+                              : load_f<T, S>(a.fin[i], h.plus<L>(j), i, L::w(i));
+            v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
+          } else if (q < T(0.5)) {
+            v = fi_x;  // no second fluid node: halfway rule
+          } else {
+            const T fj_x = load_f<T, S>(a.fin[j], n, j, L::w(j));
+            v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
+          }
+          f[j] = v;
+        }
+      }
+    } else {
+      for (int j = 1; j < Q; j++) {
+        const int i = L::opp(j);  // link from x toward the wall node x + c_i = x - c_j
+        if (!((nb_solid >> i) & 1u)) continue;
+        const T q = link_fraction_rt<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
+        const T fi_x = load_f<T, S>(a.fin[i], n, i, L::w(i));
+        T v;
+        int ki = i;
+        bool second = !((nb_solid >> j) & 1u);
+        if constexpr (FC) {
+          if (face_cross<L>(a.p.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2) second = false;
+        }
+        if (q < T(0.5) && second) {
+          const int z2 = h.plus_rt<L>(j);
+          const T fi_z = load_f<T, S>(a.fin[ki], z2, ki, L::w(ki));
+          v = T(2) * q * fi_x + (T(1) - T(2) * q) * fi_z;
+        } else if (q < T(0.5)) {
+          v = fi_x;  // no second fluid node: halfway rule
+        } else {
+          const T fj_x = load_f<T, S>(a.fin[j], n, j, L::w(j));
+          v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * fj_x;
+        }
+#pragma unroll
+        for (int k = 1; k < Q; k++)
+          if (k == j) f[k] = v;
+      }
     }
   }
 
@@ -764,10 +849,7 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   if constexpr (EQ) {
     // g* = g_eq (tau_g = 1): store what fixes it.  The C of this collision is
     // this step's moments output a.C, which the next step reads as Cprev.
-    a.Mp[0][n] = mu - T(1.5) * C * uu;
-    a.Mp[1][n] = u[0];
-    a.Mp[2][n] = u[1];
-    if (L::D == 3) a.Mp[3][n] = u[2];
+    io.template put_eq<L>(a, n, C, mu - T(1.5) * C * uu, u[0], u[1], u[2]);
   } else if constexpr (Store<S>::k16) {
     // 16-bit storage: the rest population takes the rounding of the others so
     // that sum_i g*_i = C holds at every node (sum_i g_eq_i = C, so the exact
@@ -1033,6 +1115,12 @@ __global__ void __launch_bounds__(256) pops_set_kernel(LBArgs<T, S> a, const T *
   }
 }
 
+}  // namespace dsm
+
+#include "dsm_zstep.cuh"
+
+namespace dsm {
+
 // ---------------------------------------------------------------------------
 // Host side: typed launchers behind a type-erased table.
 // ---------------------------------------------------------------------------
@@ -1073,6 +1161,10 @@ LBArgs<T, S> typed(const LBRaw &r) {
   a.f_out = (S *)r.f_out; a.g_out = (S *)r.g_out; a.g0_out = r.g0_out;
   a.C = (T *)r.C; a.Cprev = (const T *)r.Cprev; a.C1 = (const T *)r.C1; a.mask = r.mask;
   for (int k = 0; k < 4; k++) a.Mp[k] = r.M ? (T *)r.M + (long long)k * r.pitch : nullptr;
+  a.Qz = (T *)r.Qz;
+  a.Uz = (T *)r.Uz;
+  a.nxp = r.nxp;
+  a.nyp = r.nyp;
   a.fields = (T *)r.out; a.partials = r.partials; a.err = r.err; a.p = r.p;
   a.c = ConstT<T>::make(r.p);
   for (int i = 0; i < QMAX; i++) {
@@ -1280,8 +1372,71 @@ struct LBOps {
     void *args[] = {(void *)&pi, (void *)&n, (void *)&po, (void *)&nb, (void *)&tmax, (void *)&bar};
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), blk, args, 0, st);
   }
+  // ---- single-pass step (D3Q19 only) ----
+  static bool zprepare() {  // opt in to its dynamic shared memory, once
+    if constexpr (K != 1) {
+      return false;
+    } else {
+      static const bool ok =
+          cudaFuncSetAttribute(zstep_kernel<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ZSmem<T>::total) == cudaSuccess &&
+          cudaFuncSetAttribute(zstep_kernel<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ZSmem<T>::total) == cudaSuccess;
+      return ok;
+    }
+  }
+  static int zresident() {
+    if constexpr (K != 1) {
+      return 0;
+    } else {
+      int per_sm = 0;
+      if (!zprepare() || cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &per_sm, zstep_kernel<T, S, false>, ZT_X * ZT_Y, ZSmem<T>::total) !=
+                             cudaSuccess)
+        return 0;
+      return per_sm;
+    }
+  }
+  static cudaError_t zstep(const LBRaw &r, const ZMaps &m, int zrun, cudaStream_t st) {
+    if constexpr (K != 1) {
+      return cudaErrorNotSupported;
+    } else {
+      if (!zprepare()) return cudaErrorInvalidValue;
+      if (zrun < 1 || r.nx % ZT_X || r.ny % ZT_Y) return cudaErrorInvalidValue;
+      const dim3 grid(r.nx / ZT_X, r.ny / ZT_Y, (r.nz + zrun - 1) / zrun), blk(ZT_X, ZT_Y, 1);
+      if (r.p.rho_contrast)
+        zstep_kernel<T, S, true><<<grid, blk, ZSmem<T>::total, st>>>(typed<T, S>(r), zrun, m.Q, m.U, m.C1);
+      else
+        zstep_kernel<T, S, false><<<grid, blk, ZSmem<T>::total, st>>>(typed<T, S>(r), zrun, m.Q, m.U, m.C1);
+      return cudaGetLastError();
+    }
+  }
+  static cudaError_t zpack(const LBRaw &r, void *Qz0, void *Qz1, void *Uz0, void *Uz1, void *C1z,
+                           cudaStream_t st) {
+    if constexpr (K != 1) {
+      return cudaErrorNotSupported;
+    } else {
+      zpack_kernel<T, S><<<152 * 8, 256, 0, st>>>(typed<T, S>(r), (T *)Qz0, (T *)Qz1, (T *)Uz0,
+                                                  (T *)Uz1, (T *)C1z, r.nxp, r.nyp);
+      return cudaGetLastError();
+    }
+  }
+  static cudaError_t zunpack(const LBRaw &r, const void *Qz, const void *Uz, void *Cout,
+                             cudaStream_t st) {
+    if constexpr (K != 1) {
+      return cudaErrorNotSupported;
+    } else {
+      zunpack_kernel<T, S><<<152 * 8, 256, 0, st>>>(typed<T, S>(r), (const T *)Qz, (const T *)Uz,
+                                                    (T *)Cout, r.nxp, r.nyp);
+      return cudaGetLastError();
+    }
+  }
   static LBTable table() {
     LBTable t;
+    t.zstep = &zstep;
+    t.zresident = &zresident;
+    t.zpack = &zpack;
+    t.zunpack = &zunpack;
     t.batch = &batch;
     t.batch_bytes = &batch_bytes;
     t.moments = &moments;
