@@ -27,6 +27,11 @@ term, a wrong sign or index, a transposed operand -- fails at least one:
   capillary filling analysis ....... test_lucas_washburn_fit_recovers_known_curve,
                                      test_meniscus_position_on_an_inclined_axis
   pressure term, wetting transition  test_critical_pressure_em
+  density and relaxation maps ...... test_density_map_uniform_acceleration,
+                                     test_viscosity_map_two_layer_channel,
+                                     test_translating_interface_density_contrast,
+                                     test_three_fluid_relaxation_map_three_layer_channel,
+                                     test_density_viscosity_pins_catch_planted_mistakes
 Parity unpinned: the L-BFGS iteration trajectory (only its converged results
 are used, through the pins above).
 """
@@ -822,3 +827,213 @@ def test_critical_pressure_em(theta):
                                th + 0.5 * abs(th) + 5e-3)
     # diffuse walls make the effective gap a little wider than s: within 4 %
     assert abs(dpc / th - 1) < 0.04, (dpc, th)
+
+
+# ------------------------------------------------------ density and viscosity
+# The density map rho = rho3 + (rho2 - rho3) C2/(C2 + C3) and the relaxation
+# map tau = tau3 + (tau2 - tau3) H(C2 - C3) (Sec. II.B, the hydrodynamic
+# equations for unequal densities and viscosities), pinned by closed forms of
+# the flow they produce; test_density_viscosity_pins_catch_planted_mistakes
+# shows that each pin fails for the plausible mistakes in these maps.
+def _accel_dev(c1v, c2v, rho2, rho3, b=1e-5, steps=(1, 5, 20)):
+    """Uniform composition under a uniform body force: every node is alike, so
+    each step adds exactly the force F = C2 b to sum_i c_i f_i (the forcing
+    term's first moment with u = (sum c f + F/2)/rho in the equilibrium), and
+    the velocity at step n is (n + 1/2) F / rho with rho from the volume
+    fraction phi = C2/(1 - C1), clamped to [0, 1].  Returns the largest
+    relative deviation over the given steps."""
+    shape, n = (4, 3), 12
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    p = O.make_params(O.D2Q9, shape, k, rho2=rho2, rho3=rho3, tau2=0.8, tau3=1.3,
+                      body=(b, 0.0, 0.0))
+    c1, c2 = np.full(n, c1v), np.full(n, c2v)
+    f, g = O.lb_init(p, 2, c1, c2)
+    phi = min(1.0, max(0.0, c2v / (1.0 - c1v)))
+    rho = rho3 + (rho2 - rho3) * phi
+    dev, done = 0.0, 0
+    for s in steps:
+        f, g = O.lb_run(p, 2, c1, f, g, s - done)
+        done = s
+        ux = O.lb_fields(p, 2, c1, f, g)["ux"]
+        exact = (s + 0.5) * c2v * b / rho
+        dev = max(dev, float(np.max(np.abs(ux - exact))) / exact)
+    return dev
+
+
+ACCEL_CASES = [(0.0, 1.0, 1.0, 0.4), (0.2, 0.4, 1.0, 0.4), (0.3, 0.8, 1.0, 0.4),
+               (0.1, 0.3, 0.25, 1.0)]
+
+
+@pytest.mark.parametrize("c1v,c2v,rho2,rho3", ACCEL_CASES)
+def test_density_map_uniform_acceleration(c1v, c2v, rho2, rho3):
+    # (0.3, 0.8): C2 + C3 = 0.7 < C2, the clamp phi = 1 applies
+    assert _accel_dev(c1v, c2v, rho2, rho3) < 1e-10
+
+
+def _channel_ode(nu_node, force):
+    """Steady unidirectional flow between no-slip walls half a node beyond the
+    edge nodes: d/dy(nu du/dy) = -force on the nodes, finite volumes with the
+    harmonic mean of the two nodes' viscosities on each link (continuous
+    shear stress at a viscosity jump)."""
+    H = nu_node.size
+    A = np.zeros((H, H))
+    for k in range(H):
+        for m in (k - 1, k + 1):
+            if 0 <= m < H:
+                nl = 2 * nu_node[k] * nu_node[m] / (nu_node[k] + nu_node[m])
+                A[k, k] -= nl
+                A[k, m] += nl
+            else:
+                A[k, k] -= 2 * nu_node[k]  # wall at distance 1/2
+    return np.linalg.solve(A, -force)
+
+
+def _two_layer_dev(tau2, tau3, H=32, b=2e-6):
+    """Liquid (y < H/2) under gas between two walls, the body force on the
+    liquid along the walls: returns (max deviation of u from the channel
+    solution with nu = (tau - 1/2)/3 of the locally larger fluid, over max u;
+    relative deviation of the liquid bulk's curvature from -b/nu_2)."""
+    faces = ("periodic", "periodic", "wall", "wall", "periodic", "periodic")
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    p = O.make_params(O.D2Q9, (2, H), k, tau2=tau2, tau3=tau3, body=(b, 0.0, 0.0), faces=faces)
+    y = np.arange(H)
+    c2 = np.repeat(0.5 * (1 - np.tanh((y - (H / 2 - 0.5)) / 2.0)), 2)
+    c1 = np.zeros(2 * H)
+    f, g = O.lb_init(p, 2, c1, c2)
+    steps = int(6 * H * H / ((min(tau2, tau3) - 0.5) / 3))
+    f, g, F = O.lb_run(p, 2, c1, f, g, steps, want_fields=True)
+    u = F["ux"].reshape(H, 2)[:, 0]
+    C = F["C"].reshape(H, 2)[:, 0]
+    nu = np.where(C - (1 - C) > 0, (tau2 - 0.5) / 3, (tau3 - 0.5) / 3)
+    ue = _channel_ode(nu, b * C)
+    kk = np.arange(3, H // 2 - 5)
+    curv = np.mean(u[kk + 1] - 2 * u[kk] + u[kk - 1])
+    return (float(np.max(np.abs(u - ue)) / np.max(np.abs(ue))),
+            abs(curv / (-b / ((tau2 - 0.5) / 3)) - 1.0))
+
+
+@pytest.mark.parametrize("tau2,tau3", [(1.7, 0.8), (0.8, 1.7)])
+def test_viscosity_map_two_layer_channel(tau2, tau3):
+    prof, curv = _two_layer_dev(tau2, tau3)
+    # discretisation and convergence error: profile 0.4-0.7 %, curvature
+    # 0.03-0.1 %; a liquid layer relaxing with the gas's tau misses the
+    # curvature by nu_3 / nu_2 - 1 (here -53 % or +112 %)
+    assert prof < 0.02 and curv < 0.01, (prof, curv)
+
+
+def _translate_dev(U=0.01, steps=300, rho3=0.3, nx=64):
+    """A liquid slab in gas (density ratio rho3) moving at uniform velocity U
+    normal to its interfaces: the continuum solution is a rigid translation
+    (density advected, u = U, uniform pressure), which the pressure moment's
+    u.G[rho]/2 term keeps in the discrete scheme.  Returns (max |u - U| / U,
+    max |pt - mean pt|) after `steps` steps."""
+    n = 2 * nx
+    k, _ = O.kappa_from_angle(90.0, 0.01, 0.01)
+    p = O.make_params(O.D2Q9, (nx, 2), k, rho2=1.0, rho3=rho3, tau2=0.9, tau3=0.7)
+    x = np.arange(nx)
+    c2 = np.tile(0.25 * (1 + np.tanh((x - 15.5) / 2.0)) * (1 + np.tanh((47.5 - x) / 2.0)), 2)
+    c1 = np.zeros(n)
+    mu = O.lb_fields(p, 2, c1, *O.lb_init(p, 2, c1, c2))["mu"]
+    rho = rho3 + (1.0 - rho3) * c2
+    f, g = np.zeros((9, n)), np.zeros((9, n))
+    for m in range(n):
+        f[:, m], g[:, m], _ = O.equilibria(O.D2Q9, 1.0, rho[m], [U, 0.0, 0.0], c2[m], mu[m],
+                                           1.0, [0.0, 0.0, 0.0], [0.0, 0.0, 0.0])
+    f, g = O.lb_run(p, 2, c1, f, g, steps)
+    F = O.lb_fields(p, 2, c1, f, g)
+    return (float(np.max(np.abs(F["ux"] - U)) / U),
+            float(np.max(np.abs(F["pt"] - F["pt"].mean()))))
+
+
+def test_translating_interface_density_contrast():
+    du, dp = _translate_dev()
+    # the scheme's own error on the diffuse interface: 8 % of U, 6e-4 in pt
+    # (without the u.G[rho]/2 term: 62 %, 3.2e-3)
+    assert du < 0.2 and dp < 1.5e-3, (du, dp)
+
+
+# mistakes a reader could make in the density and relaxation maps and in the
+# moments that use them, as edits of the C oracle
+PLANTED = [
+    ("densities swapped", "w->rho[n] = p->rho3 + (p->rho2 - p->rho3) * phi;",
+     "w->rho[n] = p->rho2 + (p->rho3 - p->rho2) * phi;"),
+    ("volume fraction without 1 - C1", "phi = C / den;", "phi = C;"),
+    ("no clamp of the volume fraction", "phi = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);",
+     "phi = phi;"),
+    ("relaxation map inverted", "w->tau[n] = (C - C3 > 0.0) ? p->tau2 : p->tau3;",
+     "w->tau[n] = (C - C3 > 0.0) ? p->tau3 : p->tau2;"),
+    ("u.G[rho]/2 dropped", "w->pt[n] = solid_n ? 1.0 : m0 + 0.5 * ug;",
+     "w->pt[n] = solid_n ? 1.0 : m0;"),
+    ("u.G[rho]/2 with the wrong sign", "w->pt[n] = solid_n ? 1.0 : m0 + 0.5 * ug;",
+     "w->pt[n] = solid_n ? 1.0 : m0 - 0.5 * ug;"),
+    ("no half-force in the velocity", "u[a] = (m1[a] + 0.5 * w->F[a * N + n]) / w->rho[n];",
+     "u[a] = m1[a] / w->rho[n];"),
+]
+
+
+def _oracle_variant(tmp_path, old, new):
+    src = open(os.path.join(os.path.dirname(O.__file__), "dsm_oracle.c")).read()
+    assert src.count(old) == 1, old
+    c = tmp_path / "variant.c"
+    so = tmp_path / "variant.so"
+    c.write_text(src.replace(old, new))
+    import subprocess
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", str(c), "-o", str(so), "-lm"])
+    return str(so)
+
+
+@pytest.mark.parametrize("name,old,new", PLANTED, ids=[p[0] for p in PLANTED])
+def test_density_viscosity_pins_catch_planted_mistakes(name, old, new, tmp_path, monkeypatch):
+    """Each planted mistake, compiled into a copy of the oracle, fails at
+    least one of the three pins above."""
+    so = _oracle_variant(tmp_path, old, new)
+    monkeypatch.setattr(O, "_lib", None)
+    monkeypatch.setattr(O, "_LIB", so)
+    monkeypatch.setattr(O, "build", lambda force=False: so)
+    fails = []
+    if max(_accel_dev(*c) for c in ACCEL_CASES) > 1e-10:
+        fails.append("acceleration")
+    du, dp = _translate_dev()
+    if du > 0.2 or dp > 1.5e-3:
+        fails.append("translation")
+    if not fails:
+        prof, curv = _two_layer_dev(1.7, 0.8)
+        if prof > 0.02 or curv > 0.01:
+            fails.append("two-layer channel")
+    assert fails, name
+    monkeypatch.setattr(O, "_lib", None)  # the real oracle again after the test
+
+
+def test_three_fluid_relaxation_map_three_layer_channel():
+    """N = 3 fluids (Sec. II.B for N + 1 components): three layers between two
+    walls, the body force on fluid 2, tau of the locally largest fluid.  The
+    N-fluid oracle's profile matches the channel solution with each node's
+    viscosity from that rule, and each layer's bulk curvature is -b C2 / nu."""
+    from oracle.multi_lb import MultiLB
+    H = 36
+    taus = (1.4, 0.8, 1.1)       # fluids 2, 3 (free) and 4 (dependent)
+    b = 2e-6
+    faces = ("periodic", "periodic", "wall", "wall", "periodic", "periodic")
+    kappa = (0.03, 0.02, 0.025, 0.03)
+    p = O.make_params(O.D2Q9, (2, H), kappa[:3], body=(b, 0.0, 0.0), faces=faces)
+    y = np.arange(H)
+    s = lambda a: 0.5 * (1 + np.tanh(a / 2.0))  # noqa: E731
+    c2 = s(11.5 - y)                   # fluid 2: y < 12
+    c3 = s(y - 11.5) * s(23.5 - y)     # fluid 3: 12 <= y < 24; fluid 4 above
+    Cm = np.stack([np.repeat(c2, 2), np.repeat(c3, 2)])
+    m = MultiLB(p, kappa, (1.0, 1.0, 1.0), taus, np.zeros(2 * H))
+    f, g = m.init(Cm)
+    steps = int(5 * H * H / ((min(taus) - 0.5) / 3))
+    f, g = m.run(f, g, steps)
+    M = m.fields(f, g)
+    u = M["u"][0].reshape(H, 2)[:, 0]
+    C = M["C"].reshape(2, H, 2)[:, :, 0]
+    allc = np.stack([C[0], C[1], 1.0 - C[0] - C[1]])
+    idx = 2 - np.argmax(allc[::-1], axis=0)  # the largest, ties to the later fluid
+    nu = (np.asarray(taus)[idx] - 0.5) / 3
+    ue = _channel_ode(nu, b * C[0])
+    assert np.max(np.abs(u - ue)) / np.max(np.abs(ue)) < 0.02
+    kk = np.arange(3, 8)
+    curv = np.mean(u[kk + 1] - 2 * u[kk] + u[kk - 1])
+    assert abs(curv / (-b / ((taus[0] - 0.5) / 3)) - 1.0) < 0.01
