@@ -322,9 +322,10 @@ dsm_status dsm_fe_energy_grad_multi(const dsm_params *p, int nfluid, const doubl
  * lattice the library accepts fits; a lattice whose reduction did not fit would
  * be refused with DSM_E_WORKSPACE.  Invalid sizes are refused with DSM_E_INVAL
  * before any device work.  No device memory is allocated or freed by this call.
- * The first call on a device resolves the array's device address (a one-time
- * set-up per device, with that device current); make that first call before
- * any stream capture.  All calls on a device share the array: calls whose work
+ * Each call looks up the array's device address in the current device's
+ * context (cudaGetSymbolAddress, host-side; no allocation); the first call on
+ * a device also loads the library's device image there, so make that first
+ * call before any stream capture.  All calls on a device share the array: calls whose work
  * overlaps on the GPU (different streams, or several host threads) race on it
  * and must be serialised by the caller.  Every scratch word a call reads is
  * written earlier in the same call, so nothing needs clearing between calls. */
@@ -443,6 +444,17 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
                           size_t scratch_bytes);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
+/* Polls a bounded device wait makes before it gives up: the grid barriers of
+ * dsm_batch_step poll a flag that the last block to arrive sets, and after
+ * this many polls (default 0: 2e7 polls, a few seconds) a block stops waiting,
+ * latches DSM_E_TIMEOUT in every lattice of the launch and returns, so the
+ * kernel always ends.  The next synchronising call (dsm_get_observables)
+ * reports DSM_E_TIMEOUT and the handles stay latched (DSM_E_STATE) until
+ * dsm_set_state, dsm_set_populations or dsm_set_fluid.  A small limit makes
+ * early blocks give up and exercises that path.  Process-wide; not
+ * thread-safe against concurrent dsm_batch_step calls. */
+dsm_status dsm_set_wait_limit(unsigned long long polls);
+
 dsm_status dsm_destroy(dsm_lattice *h);
 
 /* ---- N fluid components, lattice Boltzmann ------------------------------

@@ -34,7 +34,7 @@ EXPORTED = (
     "dsm_vec_lincomb", "dsm_lbfgs_workspace_bytes", "dsm_lbfgs_minimize", "dsm_lbfgs_compact",
     "dsm_fe_multi_scratch_bytes", "dsm_fe_energy_grad_multi", "dsm_lbfgs_multi_workspace_bytes",
     "dsm_lbfgs_minimize_multi",
-    "dsm_batch_scratch_bytes", "dsm_batch_step",
+    "dsm_batch_scratch_bytes", "dsm_batch_step", "dsm_set_wait_limit",
     "dsm_destroy", "dsm_ml_workspace_bytes", "dsm_ml_create", "dsm_ml_set_solid",
     "dsm_ml_set_fluids", "dsm_ml_step", "dsm_ml_get_field", "dsm_ml_get_populations",
     "dsm_ml_check", "dsm_ml_destroy",
@@ -137,6 +137,7 @@ def load():
                                           C.POINTER(dsm_lbfgs_info), vp]),
         "dsm_batch_scratch_bytes": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_batch_step": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.c_longlong), vp, C.c_size_t]),
+        "dsm_set_wait_limit": (st, [C.c_ulonglong]),
         "dsm_destroy": (st, [vp]),
         "dsm_ml_workspace_bytes": (st, [P, C.c_int, C.POINTER(C.c_size_t)]),
         "dsm_ml_create": (st, [P, C.c_int, dp, dp, dp, vp, C.c_size_t, vp, C.POINTER(vp)]),
@@ -500,6 +501,10 @@ def dsm_batch_step(handles, nsteps, scratch, scratch_bytes: int):
     hs = (C.c_void_p * max(n, 1))(*handles)
     ns = (C.c_longlong * max(n, 1))(*nsteps)
     _check(load().dsm_batch_step(hs, n, ns, _ptr(scratch), scratch_bytes), "dsm_batch_step")
+
+
+def dsm_set_wait_limit(polls: int):
+    _check(load().dsm_set_wait_limit(int(polls)), "dsm_set_wait_limit")
 
 
 def dsm_destroy(h: int):

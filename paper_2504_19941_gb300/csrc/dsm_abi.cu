@@ -58,6 +58,10 @@ namespace {
 
 dsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DSM_OK : DSM_E_CUDA; }
 
+// Polls of a bounded device wait before it gives up (dsm_set_wait_limit);
+// 0: each kernel's default.
+unsigned long long g_wait_limit = 0;
+
 bool lb_table_for(int kind, int precision, LBTable *t) {
   switch (precision) {
     case DSM_F64: *t = lb_table_f64(kind); return true;
@@ -1005,7 +1009,8 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
   if (scratch_bytes < hs[0]->tab.batch_bytes(items.data(), n) || ((uintptr_t)d_scratch & 255u))
     return DSM_E_WORKSPACE;
   cudaError_t e = hs[0]->tab.batch(items.data(), n, d_scratch, scratch_bytes,
-                                   hs[0]->sp.rho_contrast != 0, hs[0]->eq, hs[0]->stream);
+                                   hs[0]->sp.rho_contrast != 0, hs[0]->eq, g_wait_limit,
+                                   hs[0]->stream);
   if (e != cudaSuccess) return DSM_E_CUDA;
   for (int i = 0; i < n; i++) {
     hs[i]->cur ^= (int)(nsteps[i] & 1);
@@ -1013,6 +1018,11 @@ dsm_status dsm_batch_step(dsm_lattice *const *hs, int n, const long long *nsteps
     hs[i]->moments_ready = false;
     if (nsteps[i] > 0) hs[i]->g_implicit = hs[i]->eq;
   }
+  return DSM_OK;
+}
+
+dsm_status dsm_set_wait_limit(unsigned long long polls) {
+  g_wait_limit = polls;
   return DSM_OK;
 }
 

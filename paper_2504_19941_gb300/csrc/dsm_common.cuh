@@ -235,7 +235,7 @@ struct LBTable {
   cudaError_t (*set_pops)(const LBRaw &, const void *f, const void *g, cudaStream_t);
   cudaError_t (*materialize)(const LBRaw &, cudaStream_t);  // g_eq -> populations of g_out
   cudaError_t (*batch)(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
-                       bool eq, cudaStream_t);
+                       bool eq, unsigned long long spins, cudaStream_t);
   size_t (*batch_bytes)(const BatchRaw *items, int n);
   // single-pass step (D3Q19, g held as g_eq, periodic; see dsm_zstep.cuh):
   // one step from the padded state the maps describe into r.Qz / r.Uz;

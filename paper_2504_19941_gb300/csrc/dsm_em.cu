@@ -210,7 +210,6 @@ static dim3 fe_bricks(int kind, int nx, int ny, int nz) {
   const dim3 b = fe_block(kind);
   return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y, (nz + b.z - 1) / b.z);
 }
-constexpr long long FE_MAX_BLOCKS = 152 * 4;  // fixed grid: four blocks per SM
 
 // blocks (= partial sums) of one evaluation
 long long fe_blocks(int kind, int nx, int ny, int nz) {

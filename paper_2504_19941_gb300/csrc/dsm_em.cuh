@@ -7,6 +7,7 @@
 namespace dsm {
 
 constexpr int FE_K = 5;              // bulk, gradient, confinement, gravity, V
+constexpr long long FE_MAX_BLOCKS = 152 * 4;  // energy kernel's fixed grid: four blocks per SM
 constexpr int VEC_BLOCKS = 152 * 4;  // fixed reduction grid of the vector kernels
 
 struct FEArgs {

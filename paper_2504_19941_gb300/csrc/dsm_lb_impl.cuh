@@ -872,9 +872,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (EQ ? 3 : 2)) node_k
 // (same lattice kind and precision) by up to tmax steps: per step a moments
 // phase and a fused phase over the work list of (lattice, brick) pairs, each
 // phase followed by a grid-wide barrier.  Resident blocks walk the list in a
-// grid-stride loop.  Every barrier wait is bounded: after kBarrierSpins polls
-// the block latches ERR_TIMEOUT in every lattice's error word and returns, so
-// a lost block can never hang the GPU.  Per-node arithmetic is node_body /
+// grid-stride loop.  Every barrier wait is bounded: after `limit` polls
+// (kBarrierSpins unless the caller set dsm_set_wait_limit) the block latches
+// ERR_TIMEOUT in every lattice's error word and returns, so a lost block can
+// never hang the GPU.  Per-node arithmetic is node_body /
 // moments_body, the same code as the single-lattice step, so each lattice's
 // result equals its solo result bitwise.
 // ---------------------------------------------------------------------------
@@ -891,7 +892,8 @@ struct BatchItem {
 constexpr unsigned long long kBarrierSpins = 20000000ull;  // ~2-4 s of polling
 
 template <class T, class S>
-__device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int nitems) {
+__device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int nitems,
+                             unsigned long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
@@ -907,7 +909,7 @@ __device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int ni
       unsigned long long spins = 0;
       while (*gen == g) {
         __nanosleep(100);
-        if (++spins > kBarrierSpins) {
+        if (++spins > limit) {
           for (int i = 0; i < nitems; i++) atomicOr(items[i].a[0].err, ERR_TIMEOUT);
           ok = 0;
           break;
@@ -923,7 +925,7 @@ __device__ bool grid_barrier(unsigned *bar, const BatchItem<T, S> *items, int ni
 template <int K, class T, class S, bool RC, bool EQ>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
     batch_kernel(const BatchItem<T, S> *items, int nitems, const int *owner, int nbricks, int tmax,
-                 unsigned *bar) {
+                 unsigned *bar, unsigned long long spin_limit) {
   __shared__ LBArgs<T, S> sa;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
@@ -951,7 +953,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2)
           node_body<K, T, S, 2, MODE_STEP, RC, EQ, false>(sa, x, y, z, x < sa.nx && y < sa.ny && z < sa.nz, 0);
         }
       }
-      if (!grid_barrier<T, S>(bar, items, nitems)) return;
+      if (!grid_barrier<T, S>(bar, items, nitems, spin_limit)) return;
     }
   }
 }
@@ -1319,7 +1321,7 @@ struct LBOps {
            (size_t)round_up(bricks * (long long)sizeof(int), 256);
   }
   static cudaError_t batch(const BatchRaw *items, int n, void *scratch, size_t bytes, bool rc,
-                           bool eq, cudaStream_t st) {
+                           bool eq, unsigned long long spins, cudaStream_t st) {
     if (bytes < batch_bytes(items, n)) return cudaErrorInvalidValue;
     std::vector<BatchItem<T, S>> hi(n);
     std::vector<int> owner;
@@ -1369,7 +1371,9 @@ struct LBOps {
     int nb = (int)owner.size();
     const BatchItem<T, S> *pi = d_items;
     const int *po = d_owner;
-    void *args[] = {(void *)&pi, (void *)&n, (void *)&po, (void *)&nb, (void *)&tmax, (void *)&bar};
+    unsigned long long lim = spins ? spins : kBarrierSpins;
+    void *args[] = {(void *)&pi,   (void *)&n,   (void *)&po, (void *)&nb,
+                    (void *)&tmax, (void *)&bar, (void *)&lim};
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), blk, args, 0, st);
   }
   // ---- single-pass step (D3Q19 only) ----

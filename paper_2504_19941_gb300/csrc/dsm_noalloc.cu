@@ -16,8 +16,6 @@
 // term).
 #include <string.h>
 
-#include <mutex>
-
 #include "dsm_em.cuh"
 #include "dsm_trace.cuh"
 
@@ -32,26 +30,18 @@ constexpr size_t kScratchBytes = DSM_NOALLOC_SCRATCH_BYTES;
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices];  // device address of g_scratch, per device, once resolved
+// The energy kernel's reduction needs one partial sum per block of its fixed
+// grid plus the constraint slot: it must fit the array for every lattice.
+static_assert(((FE_MAX_BLOCKS * FE_K * sizeof(double) + 255) / 256) * 256 + 256 <= kScratchBytes,
+              "the fixed scratch array no longer holds the energy reduction");
 
-// Set-up, once per device, with that device current: resolve the device
-// address of the scratch array.
+// The array's device address in the current device's context.  Resolved on
+// every call: a host-side lookup once the library's device image is loaded
+// there (the first call on a device loads it), and always the address of the
+// context the kernels will run in, also after a device reset.
 cudaError_t scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return cudaSuccess;
+  *out = nullptr;
+  return cudaGetSymbolAddress(out, g_scratch);
 }
 
 }  // namespace
@@ -61,6 +51,7 @@ extern "C" dsm_status dsm_fe_energy_grad_noalloc(const dsm_params *p, const floa
                                                  int active, double dP, double kcs, double V0,
                                                  double fg, double *d_energy, float *d_grad,
                                                  double *d_terms, void *cuda_stream) {
+  TraceRange trace_range("energy and gradient (K4, no-alloc)");
   if (!p || !d_c1 || !d_c2 || !d_grad) return DSM_E_INVAL;
   if (active != 1 && active != 2) return DSM_E_INVAL;
   if (active == 1 && !d_mask) return DSM_E_INVAL;
@@ -83,8 +74,7 @@ extern "C" dsm_status dsm_fe_energy_grad_noalloc(const dsm_params *p, const floa
   a.c2 = d_c2;
   a.mask = d_mask;
   a.grad = d_grad;
-  return fe_launch(p->lattice, a, dP, kcs, V0, d_energy, d_terms, scratch,
-                   (cudaStream_t)cuda_stream) == cudaSuccess
-             ? DSM_OK
-             : DSM_E_CUDA;
+  const cudaError_t e = fe_launch(p->lattice, a, dP, kcs, V0, d_energy, d_terms, scratch,
+                                  (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? DSM_OK : DSM_E_CUDA;
 }
