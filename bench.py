@@ -563,6 +563,92 @@ def run_precision(args, rank, world):
     return 0
 
 
+def run_ramp(args, rank, world):
+    """The cfg2 physics run: the 256x256x192 pillar slab (gaps vented through
+    the base plate) under a body force on the liquid ramped linearly along -z
+    from 0 to twice the square-pillar critical-pressure estimate over
+    --ramp-steps steps, one run per seed (contact angle drawn in [90, 150]).
+    Reports per seed the critical pressure (the ramp's f H when the mean
+    C2 = 1/2 height next to the pillars falls 2 nodes below the pillar tops,
+    or None when the slab stays pinned through the ramp), the estimate, and
+    the MLUPS of the ramp's steps with the one-pass kernel's HBM fraction."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    import paper_2504_19941_gb300 as P
+    from paper_2504_19941_gb300.ramp import pillar_ring, pressure_ramp
+    from paper_2504_19941_gb300 import _lib
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    peak, peak_kind = _peaks()
+    seeds = shard(list(range(args.ramp_seeds)), rank, world)
+    runs = []
+    lu_total, t_total = 0.0, 0.0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for seed in seeds:
+            case = S.pillar_slab_3d(seed=seed, vent=10)
+            nx, ny, nz = case.shape
+            params = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg,
+                                   g12=case.g12, g23=case.g23, alpha_s=case.alpha_s)
+            lat = P.Lattice(params, device=dev)
+            lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
+            lat.set_fluid(torch.as_tensor(case.c2, dtype=torch.float32, device=dev))
+            c1 = lat.field("C1").double().cpu().numpy().reshape(nz, ny, nx)
+            ring = pillar_ring(c1[20])
+            thick = 98 - 38
+            f_max = case.extra["f_max"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(lat.stream)
+            r = pressure_ramp(lat, f_max, args.ramp_steps, c1, ring, 38, thick,
+                              check_every=100, stop_at_depinning=False)
+            e1.record(lat.stream)
+            torch.cuda.synchronize()
+            secs = e0.elapsed_time(e1) / 1e3
+            est = f_max * thick / 2.0
+            runs.append({"seed": seed, "theta_deg": case.theta_deg, "dp_estimate": est,
+                         "dp_crit": r["dp_crit"],
+                         "dp_crit_over_estimate": None if r["dp_crit"] is None
+                         else r["dp_crit"] / est,
+                         "dp_max": f_max * thick, "steps": r["steps"],
+                         "contact_line_start": r["history"][0][2],
+                         "contact_line_end": r["history"][-1][2],
+                         "single_pass": lat.single_pass,
+                         "seconds": secs, "MLUPS": lat.n * r["steps"] / secs / 1e6})
+            lu_total += lat.n * r["steps"]
+            t_total += secs
+            del lat
+            torch.cuda.empty_cache()
+    t_max, lups = aggregate(t_total, lu_total, dist)
+    value = lups / 1e6
+    achieved = lu_bytes_single("f32") * value * 1e6 / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": "cfg2 pressure ramp: critical pressure per contact angle; ramp MLUPS",
+            "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.ramp_steps,
+            "warmup": 0, "ms_per_step": t_total / max(1, sum(r["steps"] for r in runs)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "D3Q19 FP32 pillar slab 256x256x192, base plate vented under "
+                                   "each gap, body force on the liquid ramped 0 -> 2x the "
+                                   "square-pillar estimate along -z",
+                       "seeds": seeds, "check_every": 100,
+                       "timing": "CUDA events around each ramp: its steps, the force updates "
+                                 "and the field reads of the detector"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "zstep_kernel<f32,f32> (one pass per step)",
+                         "bytes_per_lu": lu_bytes_single("f32"), "peak_source": peak_kind},
+            "clocks": clk.summary(), "runs": runs}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_plain_fp64(args, rank, world):
     """The plain FP64 D2Q9 128x64 wall-drop case: per-step launches against one
     persistent batched launch of all its steps, in both storage forms of g."""
@@ -902,7 +988,9 @@ def main():
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
     ap.add_argument("--workload", default="lb",
                     choices=["lb", "serve", "precision", "fp64", "em", "critical", "capillary",
-                             "multi"])
+                             "multi", "ramp"])
+    ap.add_argument("--ramp-seeds", type=int, default=5)
+    ap.add_argument("--ramp-steps", type=int, default=10000)
     ap.add_argument("--em-iters", type=int, default=3000)
     # default: a saturating burst (every request at once, full step budgets)
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -933,6 +1021,8 @@ def main():
         return run_capillary(args, rank, world)
     if args.workload == "critical":
         return run_critical(args, rank, world)
+    if args.workload == "ramp":
+        return run_ramp(args, rank, world)
     return run_gpu(args, rank, world)
 
 

@@ -186,6 +186,13 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps);
 dsm_status dsm_step_moments(dsm_lattice *h);
 dsm_status dsm_step_collide(dsm_lattice *h);
 
+/* Change the body force on the liquid of a live lattice (body[3], per unit
+ * liquid concentration, F_g = C2 b: the gravity-like force of Sec. IV that
+ * drives the droplet on the sinusoidal surface, and the pressure of a
+ * critical-pressure ramp) for the steps enqueued after this call; the state
+ * is kept.  D2Q9 ignores body[2].  DSM_E_INVAL for a non-finite component. */
+dsm_status dsm_set_body_force(dsm_lattice *h, const double *body);
+
 /* How dsm_step advances a lattice.  The step of Sec. II.B needs C = sum_i g_i
  * of the streamed populations on each node's neighbourhood before it can form
  * mu, so dsm_step normally runs it as the two passes above.  For D3Q19 lattices

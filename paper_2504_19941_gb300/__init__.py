@@ -151,6 +151,10 @@ class Lattice:
         _lib.dsm_set_g_storage(self.h, {"auto": _lib.DSM_G_AUTO,
                                         "populations": _lib.DSM_G_POPULATIONS}[form])
 
+    def set_body_force(self, body):
+        """Body force on the liquid (3 components) for the following steps."""
+        _lib.dsm_set_body_force(self.h, body)
+
     def set_step_form(self, form: str, zrun: int = 0):
         """'auto' (one pass per step where the lattice allows it) or 'two_pass';
         zrun: z planes per block of the one-pass step (0: automatic)."""

@@ -26,7 +26,7 @@ DSM_STEP_AUTO, DSM_STEP_TWO_PASS = 0, 1
 EXPORTED = (
     "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
     "dsm_set_solid", "dsm_relax_solid", "dsm_solid_region", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
-    "dsm_step_collide", "dsm_set_step_form", "dsm_step_info", "dsm_get_observables",
+    "dsm_step_collide", "dsm_set_body_force", "dsm_set_step_form", "dsm_step_info", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
@@ -95,6 +95,7 @@ def load():
         "dsm_step": (st, [vp, C.c_longlong]),
         "dsm_step_moments": (st, [vp]),
         "dsm_step_collide": (st, [vp]),
+        "dsm_set_body_force": (st, [vp, C.POINTER(C.c_double)]),
         "dsm_set_step_form": (st, [vp, C.c_int, C.c_int]),
         "dsm_step_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "dsm_get_observables": (st, [vp, C.POINTER(dsm_observables)]),
@@ -276,6 +277,11 @@ def dsm_step_moments(h: int):
 
 def dsm_step_collide(h: int):
     _check(load().dsm_step_collide(h), "dsm_step_collide")
+
+
+def dsm_set_body_force(h: int, body):
+    b = (C.c_double * 3)(*[float(v) for v in body])
+    _check(load().dsm_set_body_force(h, b), "dsm_set_body_force")
 
 
 def dsm_set_step_form(h: int, form: int, zrun: int = 0):

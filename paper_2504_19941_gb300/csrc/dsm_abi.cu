@@ -585,6 +585,17 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
   return DSM_OK;
 }
 
+dsm_status dsm_set_body_force(dsm_lattice *h, const double *body) {
+  if (!h || !body) return DSM_E_INVAL;
+  for (int a = 0; a < 3; a++)
+    if (!isfinite(body[a])) return DSM_E_INVAL;
+  for (int a = 0; a < 3; a++) h->prm.body_force[a] = body[a];
+  h->sp.body[0] = body[0];
+  h->sp.body[1] = body[1];
+  h->sp.body[2] = h->kind == DSM_D2Q9 ? 0.0 : body[2];
+  return DSM_OK;
+}
+
 dsm_status dsm_set_step_form(dsm_lattice *h, int form, int zrun) {
   if (!h || (form != DSM_STEP_AUTO && form != DSM_STEP_TWO_PASS) || zrun < 0) return DSM_E_INVAL;
   if (form == DSM_STEP_TWO_PASS && z_unpack(h) != cudaSuccess) return DSM_E_CUDA;

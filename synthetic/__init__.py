@@ -110,14 +110,27 @@ def sinusoid_sd(shape, base: float, amplitude: float, wavelength: float,
 
 
 def pillars_sd(shape, base: int, width: int, pitch: int, height: int,
-               offset: int = 0) -> np.ndarray:
+               offset: int = 0, vent: int = 0) -> np.ndarray:
     """Base plate (nodes z < base) plus square pillars width x width, z in
     [base, base + height), on an x-y grid of the given pitch (3D), or a row of
-    rectangular pillars along x (2D, normal y)."""
+    rectangular pillars along x (2D, normal y).  vent > 0 (3D): the plate has a
+    square hole vent x vent under the middle of each gap cell (centred half a
+    pitch from the pillars), so gas below a liquid slab can leave through the
+    plate (and the periodic z boundary)."""
     d = len(shape)
     X = _coords(shape)
     normal = d - 1
     sd = slab_sd(shape, normal, 0, base)
+    if vent > 0 and d == 3:
+        # distance outside the vent's square prism: the plate minus the hole
+        hq = []
+        for a in range(2):
+            centre = offset + 0.5 * (width - 1) + 0.5 * pitch
+            da = X[a] - centre
+            da = da - pitch * np.round(da / pitch)
+            hq.append(np.abs(da) - 0.5 * vent)
+        inside_hole = np.maximum(hq[0], hq[1])   # < 0 inside the hole's footprint
+        sd = np.minimum(sd, inside_hole)
     # pillar cells: distance to the nearest pillar via the pitch-periodic image
     q = []
     for a in range(d - 1):
@@ -226,7 +239,7 @@ def wall_drop_2d(nx=128, ny=64, wall=8, radius=25.0, theta=60.0, width=4.0, seed
 
 def pillar_slab_3d(nx=256, ny=256, nz=192, seed=0, pitch=32, width=10, height=30,
                    base=8, liquid=(38, 98), diffuse_width=3.0, g=2.5e-3,
-                   steps=10000) -> Case:
+                   steps=10000, vent=0) -> Case:
     """Square micro-pillar array on a base plate with a liquid slab resting on the
     pillar tops (D3Q19).  Defaults: 256x256x192, pillars 10 wide and 30 high on an
     8-node base, 8 per axis at pitch 32 (the gap of 20 cannot tile 256 with
@@ -236,7 +249,7 @@ def pillar_slab_3d(nx=256, ny=256, nz=192, seed=0, pitch=32, width=10, height=30
     shape = (nx, ny, nz)
     rng = np.random.default_rng(seed)
     theta = float(rng.uniform(90.0, 150.0))
-    sd = pillars_sd(shape, base, width, pitch, height, offset=(pitch - width) // 2)
+    sd = pillars_sd(shape, base, width, pitch, height, offset=(pitch - width) // 2, vent=vent)
     a_s = width_to_alpha(diffuse_width)
     c2 = layer_c2(shape, 2, liquid[0], liquid[1], 1.0, sd, a_s).ravel()
     # square-pillar depinning estimate: dP ~ 4 a gamma |cos(theta)| / (p^2 - a^2)
