@@ -475,6 +475,8 @@ def run_serve(args, rank, world):
                          **policy).run(mine)
         wall = time.perf_counter() - t0
     s = summarize(recs, wall)
+    thetas = [r.result.get("theta_deg") for r in recs if r.status == "done"]
+    s["theta_deg_measured"] = sum(1 for t in thetas if t is not None and math.isfinite(t))
     base = None
     if not args.no_serial_baseline:
         t0 = time.perf_counter()
@@ -489,6 +491,9 @@ def run_serve(args, rank, world):
                "config": {"workload": f"{args.serve_requests} requests, Poisson {args.serve_rate}/s, "
                                       f"steps x{args.serve_scale}", "quantum": args.serve_quantum,
                           "max_large": policy["max_large"], "order": policy["order"],
+                          "executor": "asynchronous: per-lattice CUDA events, large lattices on "
+                                      "their own streams, small ones in one batched launch",
+                          "result": "observables and the apparent contact angle of the drop",
                           "parallelism": f"replicas x{world}"},
                "serving": s, "one_at_a_time": base, "clocks": clk.summary()}
         print(json.dumps(out), flush=True)
