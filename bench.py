@@ -654,6 +654,141 @@ def run_ramp(args, rank, world):
     return 0
 
 
+def meniscus_between_plates(c2_zyx, c1_zyx, yc, half_gap, x_lo, margin=3.0):
+    """Meniscus of a capillary rise between plates normal to y (rise along +x):
+    returns (height, theta_deg).  The z-averaged liquid field is taken in the
+    (x, y) plane; the height is where C2 crosses 1/2 along the gap's centre line
+    (first crossing above x_lo, linear interpolation); theta comes from a Kasa
+    circle fit of the C2 = 1/2 points in the gap at least `margin` nodes from
+    the plates (cos theta = w / R, w the half distance between the plates'
+    C1 = 1/2 planes)."""
+    import numpy as np
+    from paper_2504_19941_gb300.analysis import level_points, sphere_fit
+    c2 = c2_zyx.mean(axis=0)                  # (ny, nx)
+    col = c2[yc, x_lo:]
+    below = np.nonzero(col < 0.5)[0]
+    if below.size == 0 or below[0] == 0:
+        return math.nan, math.nan
+    k = below[0]
+    h = x_lo + (k - 1) + (col[k - 1] - 0.5) / (col[k - 1] - col[k])
+    # the plates' C1 = 1/2 planes on either side of the centre line
+    c1 = c1_zyx.mean(axis=0)[:, int(round(h))]
+    lo = yc
+    while lo > 0 and c1[lo - 1] < 0.5:
+        lo -= 1
+    hi = yc
+    while hi < c1.size - 1 and c1[hi + 1] < 0.5:
+        hi += 1
+    w = 0.5 * ((hi + (c1[hi] - 0.5) / (c1[hi] - c1[hi + 1]) if hi + 1 < c1.size else hi)
+               - (lo - (c1[lo] - 0.5) / (c1[lo] - c1[lo - 1]) if lo > 0 else lo))
+    pts, _ = level_points(c2[max(0, yc - half_gap):yc + half_gap + 1, :], 0.5)
+    pts[:, 1] += max(0, yc - half_gap)
+    keep = (np.abs(pts[:, 1] - yc) < w - margin) & (np.abs(pts[:, 0] - h) < 2 * half_gap)
+    pts = pts[keep]
+    if pts.shape[0] < 8:
+        return h, math.nan
+    _, R = sphere_fit(pts)
+    return h, math.degrees(math.acos(max(-1.0, min(1.0, w / R)))) if R > 0 else math.nan
+
+
+def run_cfg3(args, rank, world):
+    """Precision forms on the capillary rise between plates (384x384x256, gap
+    40, 45 degrees, gravity for a Jurin rise of 120 nodes): FP64, FP32 and BF16
+    / FP16 storage run the same steps (50k, or fewer when FP64's measured speed
+    would take longer than --cfg3-budget seconds); every --cfg3-check steps the
+    meniscus height and angle of each; at the end the errors of C2, rho, pt and
+    u against the FP64 run, and each form's MLUPS."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    import paper_2504_19941_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    shape = tuple(int(v) for v in args.cfg3_shape.split(","))
+    if shape == (384, 384, 256):
+        case = S.plates_rise_3d()
+    else:  # proportionally scaled geometry
+        sc = shape[0] / 384.0
+        case = S.plates_rise_3d(*shape, gap=int(round(40 * sc)), thick=max(3, int(round(8 * sc))),
+                                x0=int(round(40 * sc)), x1=int(round(340 * sc)),
+                                reservoir=int(round(60 * sc)), lid=max(3, int(round(8 * sc))),
+                                target_rise=120.0 * sc)
+    nx, ny, nz = case.shape
+    yc, half_gap = ny // 2, case.extra["gap"] // 2
+    x_lo = int(round(60 * nx / 384.0))
+
+    def make(prec):
+        p = P.make_params("D3Q19", case.shape, prec, theta_deg=case.theta_deg, g12=case.g12,
+                          g23=case.g23, alpha_s=case.alpha_s, body=case.body)
+        lat = P.Lattice(p, device=dev)
+        lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=lat.real, device=dev))
+        lat.set_fluid(torch.as_tensor(case.c2, dtype=lat.real, device=dev))
+        return lat
+
+    # FP64's speed decides how many steps every form runs
+    probe = make("f64")
+    probe.step(5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    probe.step(50)
+    torch.cuda.synchronize()
+    f64_step = (time.perf_counter() - t0) / 50
+    del probe
+    torch.cuda.empty_cache()
+    steps = min(args.cfg3_steps, int(args.cfg3_budget / f64_step) // args.cfg3_check * args.cfg3_check)
+    steps = max(steps, args.cfg3_check)
+    c1 = None
+    results, finals = {}, {}
+    for prec in ("f64", "f32", "bf16", "f16"):
+        lat = make(prec)
+        if c1 is None:
+            c1 = lat.field("C1").double().cpu().numpy().reshape(nz, ny, nx)
+        m0 = lat.observables()["mass_c2"]
+        hist = []
+        secs = 0.0
+        for done in range(args.cfg3_check, steps + 1, args.cfg3_check):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat.step(args.cfg3_check)
+            torch.cuda.synchronize()
+            secs += time.perf_counter() - t0
+            c2 = lat.field("C2").double().cpu().numpy().reshape(nz, ny, nx)
+            h, th = meniscus_between_plates(c2, c1, yc, half_gap, x_lo)
+            hist.append((done, h, th))
+        ob = lat.observables(check=False)
+        finals[prec] = {k: lat.field(k).double().cpu().numpy()
+                        for k in ("C2", "rho", "pt", "ux", "uy", "uz")}
+        results[prec] = {"MLUPS": lat.n * steps / secs / 1e6, "single_pass": lat.single_pass,
+                         "meniscus": hist, "mass_drift": (ob["mass_c2"] - m0) / m0,
+                         "nonfinite": ob["nonfinite"]}
+        del lat
+        torch.cuda.empty_cache()
+    ref = finals["f64"]
+    umax = max(np.abs(ref[k]).max() for k in ("ux", "uy", "uz"))
+    for prec in ("f32", "bf16", "f16"):
+        got = finals[prec]
+        err = {k: float(np.abs(got[k] - ref[k]).max() / np.abs(ref[k]).max())
+               for k in ("C2", "rho", "pt")}
+        err["u"] = float(max(np.abs(got[k] - ref[k]).max() for k in ("ux", "uy", "uz")) / umax)
+        h_ref, th_ref = results["f64"]["meniscus"][-1][1:]
+        h, th = results[prec]["meniscus"][-1][1:]
+        err["meniscus_height"] = h - h_ref
+        err["theta_deg"] = th - th_ref
+        results[prec]["error_vs_f64"] = err
+    if rank == 0:
+        print(json.dumps({
+            "metric": "cfg3 precision forms: errors against FP64 and MLUPS (capillary rise between plates)",
+            "value": results["bf16"]["MLUPS"], "unit": "MLUPS", "n_gpus": 1, "steps": steps,
+            "warmup": 0, "dtype": "bf16-storage/f32", "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"D3Q19 capillary rise between plates {nx}x{ny}x{nz}, gap "
+                                   f"{case.extra['gap']}, 45 deg, gamma 1e-2, Jurin rise 120 "
+                                   f"(scaled), {steps} steps (asked {args.cfg3_steps})",
+                       "f64_ms_per_step": f64_step * 1e3, "check_every": args.cfg3_check,
+                       "jurin_height": x_lo + 120.0 * nx / 384.0},
+            "forms": results}), flush=True)
+    return 0
+
+
 def run_plain_fp64(args, rank, world):
     """The plain FP64 D2Q9 128x64 wall-drop case: per-step launches against one
     persistent batched launch of all its steps, in both storage forms of g."""
@@ -874,10 +1009,22 @@ def run_critical(args, rank, world):
     return 0 if same else 1
 
 
+def lbfgs_bytes_per_node(m: int = 10) -> int:
+    """Algorithmic bytes per node of one L-BFGS iteration of the native loop
+    with m stored pairs and one line-search trial: the trial point, its energy
+    and gradient and g.d (12 + 12 + 8); the direction from the history and g
+    (2m + 1 vectors read, one written); the new pair (s: 8, y: 12); the dots
+    of every stored vector against y and g (2m + 2 vectors read); s.s and g.g
+    (4 + 4).  m = 10: 236 B."""
+    return 32 + (2 * m + 2) * 4 + 8 + 12 + (2 * m + 2) * 4 + 8
+
+
 def run_em(args, rank, world):
     """Energy-minimisation twin on a 128^3 grid (sphere of radius 20 at a flat
     liquid/gas interface): energy + gradient evaluations per second, and L-BFGS
-    iterations per second with the time to an rms gradient of 1e-6."""
+    iterations per second with the time to an rms gradient of 1e-6 for both
+    128^3 cases (the sphere at the interface and the drop on the sinusoidal
+    wall, each volume-constrained)."""
     import torch
     import synthetic as S
     import paper_2504_19941_gb300 as P
@@ -912,11 +1059,41 @@ def run_em(args, rank, world):
     torch.cuda.synchronize()
     t_eval = e0.elapsed_time(e1) / 1e3 / reps
     peak, peak_kind = _peaks()
-    t0 = time.perf_counter()
-    x, Emin, info = lbfgs(fe, c2, c1, active=2, kcs=1e-2, V0=V0, tol=1e-6,
-                          max_iter=args.em_iters)
-    torch.cuda.synchronize()
-    t_lb = time.perf_counter() - t0
+    minimisations = {}
+    for name in ("sphere_at_interface", "sinusoid_drop"):
+        if name == "sphere_at_interface":
+            xc, c1c, pc = c2, c1, p
+        else:
+            cs = S.em_sinusoid_drop()
+            pc = P.make_params("D3Q19", cs.shape, "f32", theta_deg=cs.theta_deg, g23=cs.g23,
+                               g12=cs.g12)
+            lat_s = P.Lattice(P.make_params("D3Q19", cs.shape, "f32", theta_deg=cs.theta_deg,
+                                            g23=cs.g23, g12=cs.g12, alpha_s=cs.alpha_s), device=dev)
+            lat_s.set_solid_distance(torch.as_tensor(cs.solid_sd, dtype=torch.float32, device=dev))
+            c1c = lat_s.field("C1")
+            del lat_s
+            xc = torch.as_tensor(cs.c2, dtype=torch.float32, device=dev)
+        fec = FreeEnergy(pc, device=dev)
+        V0c = float(xc.double().sum())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xm, Em, inf = lbfgs(fec, xc, c1c, active=2, kcs=1e-2, V0=V0c, tol=1e-6,
+                            max_iter=args.em_iters)
+        torch.cuda.synchronize()
+        t_m = time.perf_counter() - t0
+        it_s = inf["iterations"] / t_m
+        bpi = lbfgs_bytes_per_node() * n
+        minimisations[name] = {"iterations": inf["iterations"], "evaluations": inf["evaluations"],
+                               "rms_grad": inf["rms_grad"], "converged": bool(inf["converged"]),
+                               "energy": Em, "seconds_to_tol": t_m, "iters_per_s": it_s,
+                               "bytes_per_iteration": bpi,
+                               "achieved_gbs": bpi * it_s / 1e9,
+                               "frac": bpi * it_s / 1e9 / peak,
+                               "volume_drift": float(xm.double().sum()) / V0c - 1.0}
+    info = {k: minimisations["sphere_at_interface"][k] for k in ("iterations", "evaluations",
+                                                                  "rms_grad")}
+    Emin = minimisations["sphere_at_interface"]["energy"]
+    t_lb = minimisations["sphere_at_interface"]["seconds_to_tol"]
     # N fluid components: the same lattice with the liquid split into N - 1
     # free fluids; algorithmic bytes per node 4 (2 (N - 1) + 1): read C1 and the
     # free planes, write their gradients
@@ -957,7 +1134,9 @@ def run_em(args, rank, world):
                                     "evaluations": info["evaluations"],
                                     "rms_grad": info["rms_grad"], "energy": Emin,
                                     "seconds": t_lb, "iters_per_s": info["iterations"] / t_lb,
-                                    "tol": 1e-6},
+                                    "tol": 1e-6, "m": 10,
+                                    "bytes_per_node_per_iteration": lbfgs_bytes_per_node(),
+                                    "cases": minimisations},
                           "multi_fluid": multi}), flush=True)
     return 0
 
@@ -993,10 +1172,15 @@ def main():
                     help="lattice size nx,ny,nz (default: the benchmark workload)")
     ap.add_argument("--workload", default="lb",
                     choices=["lb", "serve", "precision", "fp64", "em", "critical", "capillary",
-                             "multi", "ramp"])
+                             "multi", "ramp", "cfg3"])
+    ap.add_argument("--cfg3-steps", type=int, default=50000)
+    ap.add_argument("--cfg3-check", type=int, default=5000)
+    ap.add_argument("--cfg3-budget", type=float, default=900.0,
+                    help="seconds the FP64 run may take; fewer steps if it would take longer")
+    ap.add_argument("--cfg3-shape", default="384,384,256")
     ap.add_argument("--ramp-seeds", type=int, default=5)
     ap.add_argument("--ramp-steps", type=int, default=10000)
-    ap.add_argument("--em-iters", type=int, default=3000)
+    ap.add_argument("--em-iters", type=int, default=20000)
     # default: a saturating burst (every request at once, full step budgets)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
@@ -1028,6 +1212,8 @@ def main():
         return run_critical(args, rank, world)
     if args.workload == "ramp":
         return run_ramp(args, rank, world)
+    if args.workload == "cfg3":
+        return run_cfg3(args, rank, world)
     return run_gpu(args, rank, world)
 
 

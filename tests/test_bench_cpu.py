@@ -72,3 +72,32 @@ def test_critical_sweep_order_and_worker_cap(monkeypatch):
     res, _ = C.critical_sweep(range(4), device="cpu")
     assert peak[0] == 4                                   # default: all at once
     assert C.critical_sweep([], device="cpu") == ([], 0.0)
+
+
+def test_meniscus_between_plates_recovers_height_and_angle():
+    """A circular meniscus between two plates (gap 2w along y, rise along +x)
+    with the liquid below it: the finder returns its height on the centre line
+    and the angle it makes with the plates (cos theta = w / R)."""
+    import math
+    import numpy as np
+    import synthetic as S
+    nx, ny, nz = 160, 64, 4
+    w, yc, theta = 14.0, 32, 45.0
+    shape = (nx, ny, nz)
+    # plates: y < yc - w and y >= yc + w (C1 = 1/2 planes at yc - w - 0.5, yc + w - 0.5)
+    sd = S.union_sd(S.slab_sd(shape, 1, 0, int(yc - w)), S.slab_sd(shape, 1, int(yc + w), ny))
+    c1 = (0.5 * (1 + np.tanh(sd / (2 * S.width_to_alpha(3.0))))).reshape(nz, ny, nx)
+    w_eff = w                                  # between the C1 = 1/2 planes
+    R = w_eff / math.cos(math.radians(theta))
+    h0 = 90.0
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    yc_eff = yc - 0.5
+    xc = h0 + R                                # centre above the meniscus (concave)
+    r = np.sqrt((X - xc) ** 2 + (Y - yc_eff) ** 2)
+    c2 = 0.5 * (1 + np.tanh((r - R) / 2.0))    # liquid outside the circle, below it
+    c2[X > xc] = 0.0
+    c2 = np.broadcast_to(c2, (nz, ny, nx)).copy()
+    h, th = bench.meniscus_between_plates(c2, c1, yc, int(w), 20)
+    # the centre line at y = yc is half a node off the circle's axis
+    assert abs(h - (xc - math.sqrt(R * R - 0.25))) < 0.02, h
+    assert abs(th - theta) < 1.0, th
