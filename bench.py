@@ -697,7 +697,9 @@ def run_cfg3(args, rank, world):
     / FP16 storage run the same steps (50k, or fewer when FP64's measured speed
     would take longer than --cfg3-budget seconds); every --cfg3-check steps the
     meniscus height and angle of each; at the end the errors of C2, rho, pt and
-    u against the FP64 run, and each form's MLUPS."""
+    u against the FP64 run, and each form's MLUPS.  --cfg3-reference f32
+    compares the 16-bit forms with FP32 instead and does not run FP64 (whose
+    steps cost 25 times FP32's on this GPU)."""
     import numpy as np
     import torch
     import synthetic as S
@@ -725,21 +727,27 @@ def run_cfg3(args, rank, world):
         lat.set_fluid(torch.as_tensor(case.c2, dtype=lat.real, device=dev))
         return lat
 
-    # FP64's speed decides how many steps every form runs
-    probe = make("f64")
-    probe.step(5)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    probe.step(50)
-    torch.cuda.synchronize()
-    f64_step = (time.perf_counter() - t0) / 50
-    del probe
-    torch.cuda.empty_cache()
-    steps = min(args.cfg3_steps, int(args.cfg3_budget / f64_step) // args.cfg3_check * args.cfg3_check)
-    steps = max(steps, args.cfg3_check)
+    ref_prec = args.cfg3_reference
+    f64_step = None
+    steps = args.cfg3_steps
+    if ref_prec == "f64":
+        # FP64's speed decides how many steps every form runs
+        probe = make("f64")
+        probe.step(5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        probe.step(50)
+        torch.cuda.synchronize()
+        f64_step = (time.perf_counter() - t0) / 50
+        del probe
+        torch.cuda.empty_cache()
+        steps = min(args.cfg3_steps,
+                    int(args.cfg3_budget / f64_step) // args.cfg3_check * args.cfg3_check)
+        steps = max(steps, args.cfg3_check)
     c1 = None
     results, finals = {}, {}
-    for prec in ("f64", "f32", "bf16", "f16"):
+    forms = ("f64", "f32", "bf16", "f16") if ref_prec == "f64" else ("f32", "bf16", "f16")
+    for prec in forms:
         lat = make(prec)
         if c1 is None:
             c1 = lat.field("C1").double().cpu().numpy().reshape(nz, ny, nx)
@@ -763,18 +771,18 @@ def run_cfg3(args, rank, world):
                          "nonfinite": ob["nonfinite"]}
         del lat
         torch.cuda.empty_cache()
-    ref = finals["f64"]
+    ref = finals[ref_prec]
     umax = max(np.abs(ref[k]).max() for k in ("ux", "uy", "uz"))
-    for prec in ("f32", "bf16", "f16"):
+    for prec in [f for f in forms if f != ref_prec]:
         got = finals[prec]
         err = {k: float(np.abs(got[k] - ref[k]).max() / np.abs(ref[k]).max())
                for k in ("C2", "rho", "pt")}
         err["u"] = float(max(np.abs(got[k] - ref[k]).max() for k in ("ux", "uy", "uz")) / umax)
-        h_ref, th_ref = results["f64"]["meniscus"][-1][1:]
+        h_ref, th_ref = results[ref_prec]["meniscus"][-1][1:]
         h, th = results[prec]["meniscus"][-1][1:]
         err["meniscus_height"] = h - h_ref
         err["theta_deg"] = th - th_ref
-        results[prec]["error_vs_f64"] = err
+        results[prec]["error_vs_" + ref_prec] = err
     if rank == 0:
         print(json.dumps({
             "metric": "cfg3 precision forms: errors against FP64 and MLUPS (capillary rise between plates)",
@@ -783,7 +791,9 @@ def run_cfg3(args, rank, world):
             "config": {"workload": f"D3Q19 capillary rise between plates {nx}x{ny}x{nz}, gap "
                                    f"{case.extra['gap']}, 45 deg, gamma 1e-2, Jurin rise 120 "
                                    f"(scaled), {steps} steps (asked {args.cfg3_steps})",
-                       "f64_ms_per_step": f64_step * 1e3, "check_every": args.cfg3_check,
+                       "reference": ref_prec,
+                       "f64_ms_per_step": None if f64_step is None else f64_step * 1e3,
+                       "check_every": args.cfg3_check,
                        "jurin_height": x_lo + 120.0 * nx / 384.0},
             "forms": results}), flush=True)
     return 0
@@ -1178,6 +1188,8 @@ def main():
     ap.add_argument("--cfg3-budget", type=float, default=900.0,
                     help="seconds the FP64 run may take; fewer steps if it would take longer")
     ap.add_argument("--cfg3-shape", default="384,384,256")
+    ap.add_argument("--cfg3-reference", default="f64", choices=["f64", "f32"],
+                    help="the form the others are compared with (f32: FP64 is not run)")
     ap.add_argument("--ramp-seeds", type=int, default=5)
     ap.add_argument("--ramp-steps", type=int, default=10000)
     ap.add_argument("--em-iters", type=int, default=20000)
