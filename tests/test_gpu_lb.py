@@ -559,3 +559,34 @@ def test_workspace_checks():
         P._lib.dsm_step(h, 1)  # no fluid yet
     assert e.value.status == P._lib.DSM_E_STATE
     P._lib.dsm_destroy(h)
+
+
+@pytest.mark.parametrize("theta", [15.0, 45.0, 90.0, 135.0, 165.0])
+def test_young_lb_paper_setup(theta):
+    """Supp. D's validation of the lattice Boltzmann contact angle: a drop of
+    radius 40 on a flat diffuse wall, gamma_23 = gamma_12 = 0.0025, tau = rho =
+    1, relaxes to Young's angle arccos((k3 - k2)/(k2 + k3)) within 1.5 degrees
+    over 15-165 degrees.  FP64 (the step tied to the oracle to 1e-12 above);
+    the run stops once the fitted angle moves less than 0.02 degrees in 10k
+    steps."""
+    nx, ny, wall, R = 360, 140, 8, 40.0
+    shape = (nx, ny)
+    sd = S.slab_sd(shape, 1, 0, wall)
+    a_s = S.width_to_alpha(4.0)
+    # start 5 degrees off (towards 90) with the same area as a half disc of radius 40
+    th0 = math.radians(theta + (5.0 if theta < 90 else -5.0))
+    Rc = math.sqrt(0.5 * math.pi * R * R / (th0 - math.sin(th0) * math.cos(th0)))
+    c2 = S.cap_c2(shape, wall - 0.5, Rc, math.degrees(th0), 1.0, sd, a_s).ravel()
+    case = S.Case("young", "D2Q9", shape, sd.ravel(), c2, theta_deg=theta, g23=0.0025,
+                  g12=0.0025, alpha_s=a_s)
+    lat = gpu_lattice(case, "f64")
+    c1 = lat.field("C1").cpu().numpy().reshape(ny, nx)
+    prev, th = None, None
+    for _ in range(40):
+        lat.step(10000)
+        th = A.contact_angle_flat(lat.field("C2").cpu().numpy().reshape(ny, nx), c1)
+        if prev is not None and abs(th - prev) < 0.02:
+            break
+        prev = th
+    assert lat.observables()["nonfinite"] == 0
+    assert abs(th - theta) < 1.5, (th, theta)

@@ -20,7 +20,7 @@ term, a wrong sign or index, a transposed operand -- fails at least one:
                                      test_mirror_symmetry_2d, test_axis_swap_symmetry_3d
   interpolated bounce-back ......... test_link_q_planar, test_bouzidi_poiseuille
   interface thermodynamics ......... test_flat_interface_profile_and_tension, test_laplace_em
-  wetting .......................... test_young_em, test_young_lb
+  wetting .......................... test_young_em, test_young_lb, test_laplace_lb
   gravity energy ................... test_jurin_em
   mirror and wall faces (LB) ....... test_lb_mirror_faces_match_reflected_periodic,
                                      test_wall_poiseuille_closed_form, test_faces_conserve_mass
@@ -737,10 +737,20 @@ def test_young_em(theta):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("theta", [90.0, 135.0])
-def test_young_lb(theta):
-    nx, ny, R, g = 64, 36, 12.0, 0.03
-    shape = (nx, ny)
+@pytest.mark.parametrize("theta,shape,R,steps,tol", [
+    (30.0, (160, 48), 24.0, 8000, 1.5), (60.0, (64, 36), 12.0, 6000, 1.5),
+    (90.0, (64, 36), 12.0, 6000, 1.5), (120.0, (64, 36), 12.0, 6000, 1.5),
+    (135.0, (64, 36), 12.0, 6000, 1.5), (150.0, (64, 36), 12.0, 18000, 3.0)])
+def test_young_lb(theta, shape, R, steps, tol):
+    """A drop started 5 degrees off relaxes on the flat diffuse wall to Young's
+    angle arccos((k3 - k2)/(k2 + k3)) (Supp. D: within 1.5 degrees for
+    15-165 degrees with drops of radius 40).  These drops are small (radius 12,
+    24 at 30 degrees, so that the flat cap rises above the fit's margin): at 150
+    degrees the diffuse interface (4.4 nodes) shifts the angle to 147.5 from
+    either side, so that case allows 3 degrees; the paper's own setup runs on
+    the GPU (tests/test_gpu_lb.py::test_young_lb_paper_setup)."""
+    nx, ny = shape
+    g = 0.03
     sd = S.slab_sd(shape, 1, 0, 6)
     a_s = S.width_to_alpha(4.0)
     c2 = S.cap_c2(shape, 5.5, R, theta + 5.0, 1.0, sd, a_s).ravel()
@@ -748,9 +758,34 @@ def test_young_lb(theta):
     p = O.make_params(O.D2Q9, shape, k, alpha_s=a_s)
     c1 = O.solid_profile(sd.ravel(), a_s)
     f, gg = O.lb_init(p, 2, c1, c2)
-    f, gg, F = O.lb_run(p, 2, c1, f, gg, 6000, want_fields=True)
+    f, gg, F = O.lb_run(p, 2, c1, f, gg, steps, want_fields=True)
     th = A.contact_angle_flat(F["C"].reshape(ny, nx), c1.reshape(ny, nx))
-    assert abs(th - theta) < 1.5, th
+    assert abs(th - theta) < tol, th
+
+
+@pytest.mark.slow
+def test_laplace_lb():
+    """Laplace's law from the lattice Boltzmann equilibrium of a free drop (no
+    solid, 2D): the chemical potential relaxes to one value mu0 inside and
+    outside (here the drop's bulk plateau, the outside within 20 % of it after
+    20k steps), and mu0 (C_in - C_out) = gamma_23 / R with R the radius of the
+    C = 1/2 circle (the drop's Laplace pressure in the potential form of the
+    force, reading R1), within 3 %."""
+    n, g, R0 = 64, 0.03, 15.0
+    shape = (n, n)
+    k, _ = O.kappa_from_angle(90.0, g, g)
+    p = O.make_params(O.D2Q9, shape, k)
+    c2 = S.drop_c2(shape, (n / 2 - 0.5, n / 2 - 0.5), R0, 1.0).ravel()
+    c1 = np.zeros(n * n)
+    f, gg = O.lb_init(p, 2, c1, c2)
+    f, gg, F = O.lb_run(p, 2, c1, f, gg, 20000, want_fields=True)
+    C, mu = F["C"].reshape(n, n), F["mu"].reshape(n, n)
+    mu_in, mu_out = mu[n // 2, n // 2], mu[0, 0]
+    assert abs(mu_in - mu_out) < 0.2 * abs(mu_in)       # one value, inside and out
+    _, R = A.kasa_fit(A.iso_points(C, 0.5))
+    dC = C[n // 2, n // 2] - C[0, 0]
+    # the drop's bulk plateau (the outside's mu approaches it by diffusion)
+    assert abs(mu_in * dC * R / g - 1.0) < 0.03
 
 
 @pytest.mark.slow
