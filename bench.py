@@ -921,13 +921,18 @@ def run_capillary(args, rank, world):
 
 
 def run_multi(args, rank, world):
-    """N fluid components (dsm_ml_*): three fluids on the D3Q19 FP32 pillar
-    slab 256x256x192, the liquid split into two fluids (x below and above the
-    middle).  tau_g = 1 and periodic faces, so g is held as g_eq.  Algorithmic
-    bytes per lattice update, g_eq form: read and write f (152), read C1, write
-    A_f of both fluids and u in the fused pass (176 B); read A_f, the previous
-    C_f and u and write C_f in the moments pass (36 B).  Population form:
-    460 B and 160 B."""
+    """N fluid components (dsm_ml_*): three (--nfluid 3) or four fluids on the
+    D3Q19 FP32 pillar slab 256x256x192, the liquid split into two fluids (x
+    below and above the middle; four fluids: the gas above z = 150 is fluid 4's).
+    tau_g = 1 and periodic faces, so g is held as g_eq, and the planes tile into
+    32 x 8 blocks, so each step is one pass (--step-form two_pass: the moments
+    passes and the fused pass).  Algorithmic bytes per lattice update with NF
+    free fluids: read and write f (152), read C1 (4), read and write A_f and C_f
+    of every free fluid (16 NF) and u (24): 212 B for three fluids, 228 B for
+    four; the two-pass form moves the same bytes (176 + 36 for three fluids).
+    Population form: f and every g_f in and out plus C1 in the fused pass, the
+    g_f in and C_f out in the moments passes, 2 * 76 (NF + 1) + 4 + 80 NF bytes
+    (620 for three fluids)."""
     import torch
     import paper_2504_19941_gb300 as P
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -937,12 +942,20 @@ def run_multi(args, rank, world):
     nx = shape[0]
     c2 = torch.as_tensor(case.c2, dtype=torch.float32, device=dev)
     xs = torch.arange(c2.numel(), device=dev) % nx
-    C = torch.stack([c2 * (xs < nx // 2), c2 * (xs >= nx // 2)]).contiguous()
+    nfl = args.nfluid
+    C = [c2 * (xs < nx // 2), c2 * (xs >= nx // 2)]
+    if nfl == 4:  # the upper gas becomes fluid 4
+        zs = torch.arange(c2.numel(), device=dev) // (shape[0] * shape[1])
+        c1 = torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev)
+        free = 1.0 - 0.5 * (1.0 + torch.tanh(c1 / (2.0 * case.alpha_s)))
+        C.append(((free - c2) * (zs >= int(0.78 * shape[2]))).clamp(min=0.0))
+    C = torch.stack(C).contiguous()
     p = P.make_params("D3Q19", shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
                       g23=case.g23, alpha_s=case.alpha_s)
     k = P._lib.dsm_kappa(p)
-    kappa = [k[0], k[1], k[1], k[2]]        # both liquids alike, the gas third
-    ml = P.MultiLattice(p, 3, kappa, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), device=dev)
+    kappa = [k[0]] + [k[1]] * (nfl - 1) + [k[2]]  # the liquids alike, the gases alike
+    ml = P.MultiLattice(p, nfl, kappa, (1.0,) * nfl, (1.0,) * nfl, device=dev)
+    ml.set_step_form(args.step_form, args.zrun)
     ml.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
     ml.set_fluids(C)
     for _ in range(args.warmup):
@@ -960,21 +973,28 @@ def run_multi(args, rank, world):
     ux = ml.field("ux")
     assert torch.isfinite(ux).all(), "non-finite velocity after the timed steps"
     peak, peak_kind = _peaks()
-    b = 176 + 36 if ml.g_implicit else 460 + 160
+    nf = nfl - 1
+    single = ml.single_pass
+    b = 180 + 16 * nf if ml.g_implicit else 2 * 19 * 4 * (nf + 1) + 4 + 80 * nf
+    launches = 1 if single else (nf + 1 if ml.g_implicit else 2)
+    names = {3: "three", 4: "four"}
     if rank == 0:
         print(json.dumps({
-            "metric": "D3Q19 three-fluid LB MLUPS (%dx%dx%d pillar slab)" % shape, "unit": "MLUPS",
+            "metric": "D3Q19 %s-fluid LB MLUPS (%dx%dx%d pillar slab)" % ((names[nfl],) + shape),
+            "unit": "MLUPS",
             "value": ml.n / t / 1e6, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "D3Q19 FP32 pillar slab %dx%dx%d, three fluids" % shape,
+            "config": {"workload": "D3Q19 FP32 pillar slab %dx%dx%d, %s fluids" % (shape + (names[nfl],)),
                        "nodes": ml.n,
                        "g_storage": "g_eq (A_f, u per node)" if ml.g_implicit else "populations",
+                       "step": "one pass (zrun %d)" % P._lib.dsm_ml_step_info(ml.h)[1]
+                       if single else "two passes",
                        "l2": "f alone 1.0 GB per buffer, larger than L2; no flush"},
             "roofline": {"bound": "hbm", "step_bytes_per_lu": b,
                          "achieved": b * ml.n / t / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": b * ml.n / t / 1e9 / peak, "peak_source": peak_kind},
-            "clocks": clk.summary(), "gpu_launches": 2 * args.steps}), flush=True)
+            "clocks": clk.summary(), "gpu_launches": launches * args.steps}), flush=True)
     return 0
 
 
@@ -1174,6 +1194,8 @@ def main():
                     help="six comma-separated faces x-,x+,y-,y+,z-,z+: periodic, mirror or wall")
     ap.add_argument("--step-form", default="auto", choices=["auto", "two_pass"],
                     help="auto: one pass per step where the lattice allows it")
+    ap.add_argument("--nfluid", type=int, default=3, choices=[3, 4],
+                    help="fluid components of --workload multi")
     ap.add_argument("--zrun", type=int, default=0,
                     help="z planes per block of the one-pass step (0: automatic)")
     ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],

@@ -494,8 +494,8 @@ dsm_status dsm_destroy(dsm_lattice *h);
  * dsm_ml_get_populations: f (Q planes) and g (N - 1 blocks of Q planes), dense
  * nx*ny*nz rows (held as g_eq: rebuilt from (A_f, C_f, u)).  The fused pass
  * latches a non-finite state in the workspace; dsm_ml_check synchronises the
- * stream and returns DSM_E_NONFINITE once it is latched (dsm_ml_set_fluids
- * clears it). */
+ * stream and returns DSM_E_NONFINITE once it is latched, DSM_E_TIMEOUT for a
+ * timed-out wait of the one-pass step (dsm_ml_set_fluids clears both). */
 typedef struct dsm_mlattice dsm_mlattice;
 dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes);
 dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa,
@@ -508,6 +508,29 @@ dsm_status dsm_ml_get_field(dsm_mlattice *h, int field, int index, void *d_dst);
 dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g);
 dsm_status dsm_ml_check(dsm_mlattice *h);
 dsm_status dsm_ml_destroy(dsm_mlattice *h);
+
+/* How dsm_ml_step advances an N-fluid lattice, as dsm_set_step_form does for
+ * two fluids.  For D3Q19 lattices that hold every g_f as g_eq (tau_g = 1,
+ * periodic faces) with nx a multiple of 32 and ny a multiple of 8,
+ * DSM_STEP_AUTO runs each step as ONE pass: blocks march 32 x 8 tiles up runs
+ * of z planes, stage the previous collision's (A_f, C_f) of every free fluid,
+ * u and C1 into shared memory by tensor-memory-accelerator copies, rebuild
+ * every C_f of the step on the tile and a one-node halo, and run the fused
+ * pass from there.  The same step up to FP contraction order; the state then
+ * lives in padded buffers of the workspace (per padded node, (nx + 8)(ny + 4)
+ * nz of them, two buffers of 5 + 2 (N - 2) reals, and C1; included in
+ * dsm_ml_workspace_bytes) and is converted back before dsm_ml_get_field or
+ * dsm_ml_get_populations reads it.  A staged plane that never arrives (a
+ * bounded wait of about two seconds) latches DSM_E_TIMEOUT, which
+ * dsm_ml_check returns.  DSM_STEP_TWO_PASS always runs the two passes.  zrun:
+ * z planes per block, 0 = chosen from the lattice and the GPU.  DSM_E_INVAL
+ * for an unknown form or zrun < 0. */
+dsm_status dsm_ml_set_step_form(dsm_mlattice *h, int form, int zrun);
+
+/* Whether dsm_ml_step runs the one-pass step (*single_pass = 1) and with how
+ * many z planes per block (*zrun; 0 for the two-pass step).  Either pointer
+ * may be NULL. */
+dsm_status dsm_ml_step_info(dsm_mlattice *h, int *single_pass, int *zrun);
 
 #ifdef __cplusplus
 }

@@ -232,6 +232,17 @@ class MultiLattice:
     def step(self, nsteps: int = 1):
         _lib.dsm_ml_step(self.h, int(nsteps))
 
+    def set_step_form(self, form: str, zrun: int = 0):
+        """'auto' (one pass per step where the lattice allows it) or 'two_pass';
+        zrun: z planes per block of the one-pass step (0: automatic)."""
+        _lib.dsm_ml_set_step_form(self.h, {"auto": _lib.DSM_STEP_AUTO,
+                                           "two_pass": _lib.DSM_STEP_TWO_PASS}[form], int(zrun))
+
+    @property
+    def single_pass(self) -> bool:
+        """True when dsm_ml_step runs the one-pass step on this lattice."""
+        return _lib.dsm_ml_step_info(self.h)[0]
+
     def field(self, name: str, index: int = 0, out=None):
         """name as for Lattice.field; "C" with index f is C_{2+f} (index N - 1:
         the dependent fluid), "mu" with index f is mu_{2+f}."""
@@ -244,7 +255,8 @@ class MultiLattice:
         return out
 
     def status(self) -> int:
-        """0, or the status latched by the fused pass (DSM_E_NONFINITE)."""
+        """0, or the status latched on the device (DSM_E_NONFINITE, or
+        DSM_E_TIMEOUT when a staged plane of the one-pass step never arrived)."""
         return _lib.dsm_ml_check(self.h, check=False)
 
     def populations(self):

@@ -37,7 +37,7 @@ EXPORTED = (
     "dsm_batch_scratch_bytes", "dsm_batch_step", "dsm_set_wait_limit",
     "dsm_destroy", "dsm_ml_workspace_bytes", "dsm_ml_create", "dsm_ml_set_solid",
     "dsm_ml_set_fluids", "dsm_ml_step", "dsm_ml_get_field", "dsm_ml_get_populations",
-    "dsm_ml_check", "dsm_ml_destroy",
+    "dsm_ml_check", "dsm_ml_destroy", "dsm_ml_set_step_form", "dsm_ml_step_info",
 )
 
 
@@ -149,6 +149,8 @@ def load():
         "dsm_ml_get_populations": (st, [vp, vp, vp]),
         "dsm_ml_check": (st, [vp]),
         "dsm_ml_destroy": (st, [vp]),
+        "dsm_ml_set_step_form": (st, [vp, C.c_int, C.c_int]),
+        "dsm_ml_step_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -558,6 +560,17 @@ def dsm_ml_check(h: int, check=True) -> int:
     if check:
         _check(s, "dsm_ml_check")
     return s
+
+
+def dsm_ml_set_step_form(h: int, form: int, zrun: int = 0):
+    _check(load().dsm_ml_set_step_form(h, form, zrun), "dsm_ml_set_step_form")
+
+
+def dsm_ml_step_info(h: int):
+    """(single_pass, zrun) of dsm_ml_step_info."""
+    sp, zr = C.c_int(0), C.c_int(0)
+    _check(load().dsm_ml_step_info(h, C.byref(sp), C.byref(zr)), "dsm_ml_step_info")
+    return bool(sp.value), zr.value
 
 
 def dsm_ml_destroy(h: int):

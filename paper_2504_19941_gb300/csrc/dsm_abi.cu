@@ -10,6 +10,7 @@
 
 #include "dsm_em.cuh"
 #include "dsm_lb_impl.cuh"
+#include "dsm_tmap.cuh"
 #include "dsm_trace.cuh"
 
 using namespace dsm;
@@ -209,41 +210,6 @@ LBRaw raw_of(const dsm_lattice *h, int src) {
 }
 
 // ---- single-pass step -------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = []() -> EncodeTiledFn {
-    void *f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return nullptr;
-    return (EncodeTiledFn)f;
-  }();
-  return fn;
-}
-
-// A 3-D tensor map over padded planes of `comp` interleaved reals per node
-// (dims comp * nxp, nyp, nz) whose box is comp * ZB_X wide and `rows` high.
-bool encode_plane_map(CUtensorMap *m, void *base, int real_bytes, int comp, int nxp, int nyp,
-                      int nz, int rows) {
-  EncodeTiledFn enc = encode_tiled();
-  if (!enc) return false;
-  const cuuint64_t dim[3] = {(cuuint64_t)comp * nxp, (cuuint64_t)nyp, (cuuint64_t)nz};
-  const cuuint64_t stride[2] = {(cuuint64_t)comp * nxp * real_bytes,
-                                (cuuint64_t)comp * nxp * nyp * real_bytes};
-  const cuuint32_t box[3] = {(cuuint32_t)(comp * ZB_X), (cuuint32_t)rows, 1};
-  const cuuint32_t estride[3] = {1, 1, 1};
-  return enc(m, real_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-             3, base, dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 bool z_maps(dsm_lattice *h) {
   if (h->zmaps_ok) return true;
   const int rb = h->tab.real_bytes, nz = h->prm.nz;

@@ -28,6 +28,7 @@
 #include <new>
 
 #include "dsm_lb_impl.cuh"
+#include "dsm_tmap.cuh"
 #include "dsm_trace.cuh"
 
 namespace dsm {
@@ -54,7 +55,10 @@ struct MLArgs {
   const T *C1;
   T *out;                // fields mode: one plane
   int field, index;
-  int *err;              // latched error word (bit ERR_NONFINITE)
+  int *err;              // latched error word (bits ERR_NONFINITE, ERR_TIMEOUT)
+  // single-pass step (dsm_mlz.cuh): the padded output buffers, their widths
+  T *Qz, *Uz, *Pz;
+  int nxp, nyp;
 };
 
 template <class T>
@@ -156,23 +160,50 @@ __device__ __forceinline__ T ml_rho(const MLArgs<T> &a, const T (&c)[NF], T c1) 
 
 enum { ML_STEP = 0, ML_FIELDS = 1 };
 
+// The fused pass's view of the neighbourhood in the two-pass step: C1 and the
+// free fluids' C from their global planes (the moments pass wrote this step's
+// C), the g_eq state (A_f, u) to its canonical planes.  The single-pass step
+// (dsm_mlz.cuh) reads C1 and C from shared memory instead.
+template <class T>
+struct MLGlobalIO {
+  static constexpr bool kSolidFirst = false;  // pull f at every node
+  static constexpr bool kZ = false;           // canonical layout, faces at run time
+  static constexpr bool kUnrollWall = false;  // wall links in a rolled loop
+  template <class L>
+  __device__ __forceinline__ T C1(const MLArgs<T> &a, const Hood &h, int n, int i) const {
+    return i == 0 ? a.C1[n] : __ldg(a.C1 + h.plus<L>(i));
+  }
+  template <class L>
+  __device__ __forceinline__ T C(const MLArgs<T> &a, const Hood &h, int n, int f, int i) const {
+    return i == 0 ? a.C[f * a.pitch + n] : __ldg(a.C + f * a.pitch + h.plus<L>(i));
+  }
+  template <class L, int NF>
+  __device__ __forceinline__ void put_eq(const MLArgs<T> &a, long long n, const T (&A)[NF],
+                                         const T (&)[NF], const T (&u)[3]) const {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.A[f * a.pitch + n] = A[f];
+    a.U[n] = u[0];
+    a.U[a.pitch + n] = u[1];
+    if (L::D == 3) a.U[2 * a.pitch + n] = u[2];
+  }
+};
+
 // FC: the lattice has a mirror or wall face (populations only); without one the
 // face code is compiled out, which keeps the periodic step's register count
-template <int K, class T, int NF, int MODE, bool EQ, bool FC>
-__device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
+template <int K, class T, int NF, int MODE, bool EQ, bool FC, class IO = MLGlobalIO<T>>
+__device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, int z,
+                                             const IO &io = IO()) {
   static_assert(!(EQ && FC), "the g_eq form is periodic only");
   using L = Lat<K>;
   constexpr int Q = L::Q;
   constexpr int NC = NF + 2;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z * blockDim.z + threadIdx.z;
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   // RTF: face offsets and the interpolated bounce-back's face check at run
-  // time.  The g_eq variant keeps them although its faces are periodic: with
-  // them compiled out its schedule changed and the step took 13 % longer.
-  constexpr bool RTF = FC || EQ;
+  // time.  The two-pass g_eq variant keeps them although its faces are
+  // periodic: with them compiled out its schedule changed and the step took
+  // 13 % longer.
+  constexpr bool RTF = FC || (EQ && !IO::kZ);
   if constexpr (RTF) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
   const int n = h.ox[1] + h.oy[1] + h.oz[1];
@@ -180,11 +211,11 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
   // ---- the neighbourhood: C1 and the free fluids, stencils of every component
   T cv[NC], lap[NC], gC[NF][3], gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
   unsigned nb_solid = 0;  // bit i: x + c_i is solid
-  cv[0] = a.C1[n];
+  cv[0] = io.template C1<L>(a, h, n, 0);
   T last = T(1) - cv[0];
 #pragma unroll
   for (int f = 0; f < NF; f++) {
-    cv[1 + f] = a.C[f * a.pitch + n];
+    cv[1 + f] = io.template C<L>(a, h, n, f, 0);
     last -= cv[1 + f];
   }
   cv[NC - 1] = last;
@@ -194,14 +225,13 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
   for (int f = 0; f < NF; f++) gC[f][0] = gC[f][1] = gC[f][2] = T(0);
 #pragma unroll
   for (int i = 1; i < Q; i++) {
-    const int m = h.plus<L>(i);
     const T w = T(L::w(i));
     const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
-    const T c1m = __ldg(a.C1 + m);
+    const T c1m = io.template C1<L>(a, h, n, i);
     T cm[NF], lastm = T(1) - c1m;
 #pragma unroll
     for (int f = 0; f < NF; f++) {
-      cm[f] = __ldg(a.C + f * a.pitch + m);
+      cm[f] = io.template C<L>(a, h, n, f, i);
       lastm -= cm[f];
       lap[1 + f] += w * (cm[f] - cv[1 + f]);
       gC[f][0] += w * cx * cm[f];
@@ -254,11 +284,13 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
 
   // ---- pull f and every g_f from x - c_j, all loads issued up front; the
   // rare links (a solid upstream node, a domain face) are corrected below
+  // (IO::kSolidFirst: a solid node, whose f is reset to w, pulls nothing)
   T fs[Q], gs[EQ ? 1 : NF][Q];
+  const bool pull = !IO::kSolidFirst || !solid_x;
 #pragma unroll
   for (int j = 0; j < Q; j++) {
     const int src = h.minus<L>(j);
-    fs[j] = __ldg(plane(a.f_in, a.pitch, j) + src);
+    fs[j] = pull ? __ldg(plane(a.f_in, a.pitch, j) + src) : T(L::w(j));
     if constexpr (!EQ) {
 #pragma unroll
       for (int f = 0; f < NF; f++)
@@ -271,26 +303,38 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
     const T cc = cv[0] < T(1e-9) ? T(1e-9) : (cv[0] > T(0.5) ? T(0.5) : cv[0]);
     const T xs = T(2) * a.alpha_s * atanh(T(2) * cc - T(1));
     const T gn = sqrt(gc1[0] * gc1[0] + gc1[1] * gc1[1] + gc1[2] * gc1[2]);
-    for (int j = 1; j < Q; j++) {
-      const int i = L::opp(j);
-      if (!((nb_solid >> i) & 1u)) continue;
-      const T q = link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i);
+    // IO::kUnrollWall: unrolled over the directions (a warp executes the body
+    // of a direction only when one of its nodes has that wall link, and each
+    // result lands in a fixed register); else a rolled loop whose result goes
+    // through a select over all directions (in the two-pass fused pass the
+    // unrolled form ran slower)
+    auto link = [&](int j, int i, T q) {
       const T fi_x = plane(a.f_in, a.pitch, i)[n];
       int ki = i;
       bool second = !((nb_solid >> j) & 1u);
       if (RTF && a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2)
         second = false;
-      T v;
-      if (q < T(0.5) && second) {
-        v = T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
-      } else if (q < T(0.5)) {
-        v = fi_x;
-      } else {
-        v = (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * plane(a.f_in, a.pitch, j)[n];
-      }
+      if (q < T(0.5) && second)
+        return T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
+      if (q < T(0.5)) return fi_x;
+      return (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * plane(a.f_in, a.pitch, j)[n];
+    };
+    if constexpr (IO::kUnrollWall) {
 #pragma unroll
-      for (int k = 1; k < Q; k++)
-        if (k == j) fs[k] = v;
+      for (int j = 1; j < Q; j++) {
+        const int i = L::opp(j);
+        if ((nb_solid >> i) & 1u)
+          fs[j] = link(j, i, link_fraction<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i));
+      }
+    } else {
+      for (int j = 1; j < Q; j++) {
+        const int i = L::opp(j);
+        if (!((nb_solid >> i) & 1u)) continue;
+        const T v = link(j, i, link_fraction_rt<L, T>(xs, gn, gc1[0], gc1[1], gc1[2], i));
+#pragma unroll
+        for (int k = 1; k < Q; k++)
+          if (k == j) fs[k] = v;
+      }
     }
   }
   // mirror and wall faces: specular reflection or halfway bounce-back for f
@@ -383,17 +427,21 @@ __device__ __forceinline__ void ml_node_body(MLArgs<T> a) {
   }
   if constexpr (EQ) {
     // g* = g_eq (tau_g = 1): store what fixes it
+    T Af[NF], Cf[NF];
 #pragma unroll
-    for (int f = 0; f < NF; f++) a.A[f * a.pitch + n] = mu[f] - T(1.5) * cv[1 + f] * uu;
-    a.U[n] = u[0];
-    a.U[a.pitch + n] = u[1];
-    if (L::D == 3) a.U[2 * a.pitch + n] = u[2];
+    for (int f = 0; f < NF; f++) {
+      Af[f] = mu[f] - T(1.5) * cv[1 + f] * uu;
+      Cf[f] = cv[1 + f];
+    }
+    io.template put_eq<L, NF>(a, n, Af, Cf, u);
   }
 }
 
 template <int K, class T, int NF, int MODE, bool EQ, bool FC>
 __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
-  ml_node_body<K, T, NF, MODE, EQ, FC>(a);
+  ml_node_body<K, T, NF, MODE, EQ, FC>(a, blockIdx.x * blockDim.x + threadIdx.x,
+                                       blockIdx.y * blockDim.y + threadIdx.y,
+                                       blockIdx.z * blockDim.z + threadIdx.z);
 }
 // D3Q19 FP32 with three free fluids and a mirror or wall face: the unrolled
 // face fix-ups raise the register count past one 256-thread block per SM, and
@@ -401,7 +449,9 @@ __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
 // fluids the cap was slower, so those keep the plain kernel.
 template <int K, class T, int NF, int MODE>
 __global__ void __launch_bounds__(256, 2) ml_node_faces_kernel(MLArgs<T> a) {
-  ml_node_body<K, T, NF, MODE, false, true>(a);
+  ml_node_body<K, T, NF, MODE, false, true>(a, blockIdx.x * blockDim.x + threadIdx.x,
+                                           blockIdx.y * blockDim.y + threadIdx.y,
+                                           blockIdx.z * blockDim.z + threadIdx.z);
 }
 template <int K, class T, int NF>
 constexpr bool ml_faces_capped() {
@@ -489,6 +539,8 @@ __global__ void __launch_bounds__(256) ml_g_of_eq_kernel(MLArgs<T> a, T *out) {
 
 }  // namespace dsm
 
+#include "dsm_mlz.cuh"
+
 using namespace dsm;
 
 struct dsm_mlattice {
@@ -502,18 +554,30 @@ struct dsm_mlattice {
   int cur;
   bool eq;  // g held as g_eq (tau_g = 1, periodic faces)
   bool has_solid, has_fluid;
+  // single-pass step (dsm_mlz.cuh): eligible lattice, state held in the padded
+  // buffers (zc: the current one), tensor maps per buffer (quads, u_z, pairs, C1)
+  bool zok, zpacked, zmaps_ok;
+  int zc, nxp, nyp, step_form, zrun, zrun_auto;
+  char *Qz[2], *Uz[2], *Pz[2], *C1z;
+  CUtensorMap maps[2][4];
 };
 
 namespace {
 
 struct MLLayout {
-  size_t f[2], g[2], C[2], C1, M, err, total;
+  size_t f[2], g[2], C[2], C1, M, err, Qz[2], Uz[2], Pz[2], C1z, total;
 };
 
 // g held as g_eq: tau_g = 1 and every face periodic
 bool ml_eq(const dsm_params *p) { return p->tau_g == 1.0 && !has_walls(p); }
 
-MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq) {
+// the single-pass step applies: D3Q19, g held as g_eq, whole 32 x 8 tiles
+bool ml_z_eligible(const dsm_params *p) {
+  return p->lattice == DSM_D3Q19 && ml_eq(p) && p->nx % ZT_X == 0 && p->ny % ZT_Y == 0;
+}
+
+MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq,
+                   const dsm_params *p = nullptr) {
   MLLayout L;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -527,6 +591,16 @@ MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq) {
   L.C1 = take((size_t)pitch * real_bytes);
   L.M = take(eq ? (size_t)(nf + 3) * pitch * real_bytes : 0);
   L.err = take(sizeof(int));
+  // padded buffers of the single-pass step: per padded node a quad, u_z and
+  // nf - 1 pairs (two buffers), and C1
+  const bool z = p && ml_z_eligible(p);
+  const size_t P = z ? (size_t)(p->nx + 2 * ZPAD_X) * (p->ny + 2 * ZPAD_Y) * p->nz : 0;
+  for (int b = 0; b < 2; b++) {
+    L.Qz[b] = take(4 * P * real_bytes);
+    L.Uz[b] = take(P * real_bytes);
+    L.Pz[b] = take(2 * (size_t)(nf - 1) * P * real_bytes);
+  }
+  L.C1z = take(P * real_bytes);
   L.total = o;
   return L;
 }
@@ -583,6 +657,13 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
   a.U = h->M ? (T *)h->M + (long long)h->nf * h->pitch : nullptr;
   a.C1 = (const T *)h->C1;
   a.err = h->err;
+  a.nxp = h->nxp;
+  a.nyp = h->nyp;
+  if (h->zok) {  // the single-pass step writes the other padded buffer
+    a.Qz = (T *)h->Qz[h->zc ^ 1];
+    a.Uz = (T *)h->Uz[h->zc ^ 1];
+    a.Pz = (T *)h->Pz[h->zc ^ 1];
+  }
   return a;
 }
 
@@ -692,10 +773,144 @@ struct GofEqL {
   }
 };
 
+// ---- single-pass step --------------------------------------------------------
+template <class T, int NF>
+struct MLZ {
+  static bool prepare() {  // opt in to the kernel's dynamic shared memory, once
+    static const bool ok =
+        cudaFuncSetAttribute(mlz_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MLZSmem<T, NF>::total) == cudaSuccess;
+    return ok;
+  }
+  static int resident() {
+    int b = 0;
+    if (!prepare() || cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &b, mlz_kernel<T, NF>, ZT_X * ZT_Y, MLZSmem<T, NF>::total) != cudaSuccess)
+      return 0;
+    return b;
+  }
+  static cudaError_t step(const MLArgs<T> &a, const CUtensorMap *m, int zrun, cudaStream_t s) {
+    if (!prepare()) return cudaErrorInvalidValue;
+    const dim3 grid(a.nx / ZT_X, a.ny / ZT_Y, (a.nz + zrun - 1) / zrun), blk(ZT_X, ZT_Y, 1);
+    mlz_kernel<T, NF><<<grid, blk, MLZSmem<T, NF>::total, s>>>(a, zrun, m[0], m[1], m[2], m[3]);
+    return cudaGetLastError();
+  }
+  static cudaError_t pack(const MLArgs<T> &a, dsm_mlattice *h, cudaStream_t s) {
+    mlz_pack_kernel<T, NF><<<152 * 8, 256, 0, s>>>(a, (T *)h->Qz[0], (T *)h->Qz[1], (T *)h->Uz[0],
+                                                   (T *)h->Uz[1], (T *)h->Pz[0], (T *)h->Pz[1],
+                                                   (T *)h->C1z);
+    return cudaGetLastError();
+  }
+  static cudaError_t unpack(const MLArgs<T> &a, dsm_mlattice *h, T *Cout, cudaStream_t s) {
+    mlz_unpack_kernel<T, NF><<<152 * 8, 256, 0, s>>>(a, (const T *)h->Qz[h->zc],
+                                                     (const T *)h->Uz[h->zc],
+                                                     (const T *)h->Pz[h->zc], Cout);
+    return cudaGetLastError();
+  }
+};
+
+// dispatch over the free fluids of a D3Q19 lattice
+template <class T, class Fn>
+cudaError_t mlz_dispatch(const dsm_mlattice *h, Fn fn) {
+  switch (h->nf) {
+    case 1: return fn(MLZ<T, 1>());
+    case 2: return fn(MLZ<T, 2>());
+    case 3: return fn(MLZ<T, 3>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool mlz_maps(dsm_mlattice *h) {
+  if (h->zmaps_ok) return true;
+  const int rb = h->real_bytes, nz = h->prm.nz;
+  for (int b = 0; b < 2; b++) {
+    CUtensorMap *m = h->maps[b];
+    if (!encode_plane_map(&m[0], h->Qz[b], rb, 4, h->nxp, h->nyp, nz, ZB_Y) ||
+        !encode_plane_map(&m[1], h->Uz[b], rb, 1, h->nxp, h->nyp, nz, ZB_Y) ||
+        !encode_plane_map(&m[3], h->C1z, rb, 1, h->nxp, h->nyp, nz, ZB1_Y))
+      return false;
+    if (h->nf > 1) {
+      if (!encode_plane_map(&m[2], h->Pz[b], rb, 2, h->nxp, h->nyp, (h->nf - 1) * nz, ZB_Y))
+        return false;
+    } else {
+      m[2] = m[0];  // no pairs: never loaded
+    }
+  }
+  h->zmaps_ok = true;
+  return true;
+}
+
+// planes per block: the same wave model as the two-fluid single-pass step
+// (runs of zr planes in waves of the resident blocks, each run paying about
+// 0.7 of a plane for its prologue)
+template <class T>
+int mlz_auto_run(dsm_mlattice *h) {
+  if (h->zrun_auto) return h->zrun_auto;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  mlz_dispatch<T>(h, [&](auto k) {
+    per_sm = k.resident();
+    return cudaSuccess;
+  });
+  const long long resident = (long long)(sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
+  const long long tiles = (long long)(h->prm.nx / ZT_X) * (h->prm.ny / ZT_Y);
+  const int nz = h->prm.nz;
+  double best = 1e300;
+  int run = nz;
+  for (int zr = 1; zr <= nz; zr++) {
+    const long long blocks = tiles * ((nz + zr - 1) / zr);
+    const double waves = (double)((blocks + resident - 1) / resident);
+    const double cost = waves * (zr + 0.7);
+    if (cost < best - 1e-9) {
+      best = cost;
+      run = zr;
+    }
+  }
+  h->zrun_auto = run;
+  return run;
+}
+
+bool mlz_active(const dsm_mlattice *h) { return h->zok && h->step_form == DSM_STEP_AUTO; }
+
+// padded state -> canonical state, before anything reads the canonical layout
+template <class T>
+cudaError_t mlz_unpack(dsm_mlattice *h) {
+  if (!h->zpacked) return cudaSuccess;
+  const MLArgs<T> a = ml_args<T>(h, h->cur);
+  T *Cout = (T *)h->C[h->cur];
+  const cudaError_t e = mlz_dispatch<T>(h, [&](auto k) { return k.unpack(a, h, Cout, h->stream); });
+  if (e == cudaSuccess) h->zpacked = false;
+  return e;
+}
+
 template <class T>
 cudaError_t ml_step(dsm_mlattice *h) {
+  if (mlz_active(h)) {
+    if (!h->zpacked) {
+      if (!mlz_maps(h)) return cudaErrorInvalidValue;
+      const MLArgs<T> a = ml_args<T>(h, h->cur);
+      const cudaError_t e = mlz_dispatch<T>(h, [&](auto k) { return k.pack(a, h, h->stream); });
+      if (e != cudaSuccess) return e;
+      h->zc = 0;
+      h->zpacked = true;
+    }
+    const MLArgs<T> a = ml_args<T>(h, h->cur);
+    const int zrun = h->zrun > 0 ? h->zrun : mlz_auto_run<T>(h);
+    const CUtensorMap *m = h->maps[h->zc];
+    const cudaError_t e =
+        mlz_dispatch<T>(h, [&](auto k) { return k.step(a, m, zrun, h->stream); });
+    if (e == cudaSuccess) {
+      h->zc ^= 1;
+      h->cur ^= 1;
+    }
+    return e;
+  }
+  cudaError_t e = mlz_unpack<T>(h);
+  if (e != cudaSuccess) return e;
   MLArgs<T> a = ml_args<T>(h, h->cur);
-  cudaError_t e = ml_dispatch<T, MomentsL>(h, a);
+  e = ml_dispatch<T, MomentsL>(h, a);
   if (e == cudaSuccess) e = ml_dispatch<T, StepL>(h, a);
   if (e == cudaSuccess) h->cur ^= 1;
   return e;
@@ -703,6 +918,8 @@ cudaError_t ml_step(dsm_mlattice *h) {
 
 template <class T>
 cudaError_t ml_fields(dsm_mlattice *h, int field, int index, void *dst) {
+  const cudaError_t eu = mlz_unpack<T>(h);
+  if (eu != cudaSuccess) return eu;
   MLArgs<T> a = ml_args<T>(h, h->cur);
   a.field = field;
   a.index = index;
@@ -726,7 +943,7 @@ dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes
   if (p->precision != DSM_F64 && p->precision != DSM_F32) return DSM_E_UNSUPPORTED;
   const long long N = (long long)p->nx * p->ny * p->nz;
   const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
-  *bytes = ml_layout(q, nfluid - 1, p->precision == DSM_F64 ? 8 : 4, round_up(N, 64), ml_eq(p))
+  *bytes = ml_layout(q, nfluid - 1, p->precision == DSM_F64 ? 8 : 4, round_up(N, 64), ml_eq(p), p)
                .total;
   return DSM_OK;
 }
@@ -742,7 +959,7 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   const long long pitch = round_up(N, 64);
   const int q = p->lattice == DSM_D2Q9 ? 9 : 19;
   const int rb = p->precision == DSM_F64 ? 8 : 4;
-  const MLLayout L = ml_layout(q, nfluid - 1, rb, pitch, ml_eq(p));
+  const MLLayout L = ml_layout(q, nfluid - 1, rb, pitch, ml_eq(p), p);
   if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255u)) return DSM_E_WORKSPACE;
   dsm_mlattice *h = new (std::nothrow) dsm_mlattice;
   if (!h) return DSM_E_INVAL;
@@ -769,6 +986,15 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   h->C1 = w + L.C1;
   h->M = h->eq ? w + L.M : nullptr;
   h->err = (int *)(w + L.err);
+  h->zok = ml_z_eligible(p);
+  h->nxp = p->nx + 2 * ZPAD_X;
+  h->nyp = p->ny + 2 * ZPAD_Y;
+  for (int b = 0; b < 2 && h->zok; b++) {
+    h->Qz[b] = w + L.Qz[b];
+    h->Uz[b] = w + L.Uz[b];
+    h->Pz[b] = w + L.Pz[b];
+  }
+  h->C1z = h->zok ? w + L.C1z : nullptr;
   // no solid until one is set: C1 = 0; no error latched
   if (cudaMemsetAsync(h->C1, 0, (size_t)pitch * rb, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) {
@@ -800,6 +1026,7 @@ dsm_status dsm_ml_set_solid(dsm_mlattice *h, const void *d_field, int kind) {
   if (e != cudaSuccess) return DSM_E_CUDA;
   h->has_solid = true;
   h->has_fluid = false;
+  h->zpacked = false;
   return DSM_OK;
 }
 
@@ -815,6 +1042,7 @@ dsm_status dsm_ml_set_fluids(dsm_mlattice *h, const void *d_c) {
     if (e != cudaSuccess) return DSM_E_CUDA;
   }
   h->cur = 0;
+  h->zpacked = false;
   if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return DSM_E_CUDA;
   cudaError_t e;
   if (h->real_bytes == 8) e = ml_dispatch<double, InitL>(h, ml_args<double>(h, 1));
@@ -854,6 +1082,8 @@ dsm_status dsm_ml_get_populations(dsm_mlattice *h, void *d_f, void *d_g) {
                         cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       return DSM_E_CUDA;
   if (d_g && h->eq) {  // rebuilt from (A_f, C_f, u)
+    const cudaError_t eu = h->real_bytes == 8 ? mlz_unpack<double>(h) : mlz_unpack<float>(h);
+    if (eu != cudaSuccess) return DSM_E_CUDA;
     const cudaError_t e = h->real_bytes == 8
                               ? ml_dispatch<double, GofEqL>(h, ml_args<double>(h, h->cur), d_g)
                               : ml_dispatch<float, GofEqL>(h, ml_args<float>(h, h->cur), d_g);
@@ -873,7 +1103,28 @@ dsm_status dsm_ml_check(dsm_mlattice *h) {
           cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return DSM_E_CUDA;
+  if (word & ERR_TIMEOUT) return DSM_E_TIMEOUT;
   return (word & ERR_NONFINITE) ? DSM_E_NONFINITE : DSM_OK;
+}
+
+dsm_status dsm_ml_set_step_form(dsm_mlattice *h, int form, int zrun) {
+  if (!h || (form != DSM_STEP_AUTO && form != DSM_STEP_TWO_PASS) || zrun < 0) return DSM_E_INVAL;
+  h->step_form = form;
+  h->zrun = zrun;
+  return DSM_OK;
+}
+
+dsm_status dsm_ml_step_info(dsm_mlattice *h, int *single_pass, int *zrun) {
+  if (!h) return DSM_E_INVAL;
+  const bool single = mlz_active(h);
+  if (single_pass) *single_pass = single ? 1 : 0;
+  if (zrun) {
+    *zrun = 0;
+    if (single) *zrun = h->zrun > 0 ? h->zrun
+                                    : (h->real_bytes == 8 ? mlz_auto_run<double>(h)
+                                                          : mlz_auto_run<float>(h));
+  }
+  return DSM_OK;
 }
 
 dsm_status dsm_ml_destroy(dsm_mlattice *h) {

@@ -110,9 +110,8 @@ def test_lbfgs_multi_lens_matches_oracle():
 
 
 # ---------------------------------------------------------------- LB, N fluids
-from oracle.multi_lb import MultiLB  # noqa: E402
 
-from dsm_helpers import direction_map  # noqa: E402
+from dsm_helpers import ml_compare, ml_run  # noqa: E402
 
 
 def _ml_case_2d(nf):
@@ -159,49 +158,11 @@ def _ml_case_3d(nf):
 
 
 def _ml_run(case, prec, steps, tau_g=0.9):
-    shape, c1, C, kappa, rho, tau, faces, body = case
-    nf = C.shape[0]
-    lat = "D2Q9" if len(shape) == 2 else "D3Q19"
-    kind = O.D2Q9 if lat == "D2Q9" else O.D3Q19
-    real = torch.float64 if prec == "f64" else torch.float32
-    p = P.make_params(lat, shape, prec, theta_deg=90.0, tau_g=tau_g, body=body, faces=faces,
-                      alpha_s=1.0)
-    ml = P.MultiLattice(p, nf + 1, kappa, rho, tau)
-    ml.set_solid_c1(_t(c1, real))
-    ml.set_fluids(_t(C, real))
-    ml.step(steps)
-    po = O.make_params(kind, shape, kappa[:3], tau_g=tau_g, body=body, faces=faces, alpha_s=1.0)
-    c1r = _t(c1, real).double().cpu().numpy()
-    m = MultiLB(po, kappa, rho, tau, c1r)
-    f, g = m.init(_t(C, real).double().cpu().numpy())
-    f, g = m.run(f, g, steps)
-    return ml, m, f, g, kind
+    return ml_run(case, prec, steps, tau_g)
 
 
 def _ml_compare(ml, m, f, g, kind):
-    perm = direction_map(kind)
-    inv = np.empty_like(perm)
-    inv[perm] = np.arange(len(perm))
-    fg_, gg_ = ml.populations()
-    q, n, nf = ml.q, ml.n, ml.nfluid - 1
-    gf = fg_.double().cpu().numpy().reshape(q, n)[inv]
-    gg = gg_.double().cpu().numpy().reshape(nf, q, n)[:, inv]
-    errs = {"f": rel_err(gf, f), "g": rel_err(gg, g)}
-    F = m.fields(f, g)
-    for k in range(nf):
-        errs[f"C{k}"] = rel_err(ml.field("C", k).double().cpu().numpy(), F["C"][k])
-        errs[f"mu{k}"] = rel_err(ml.field("mu", k).double().cpu().numpy(), F["mu"][k])
-    umax = np.abs(F["u"]).max()
-    for a, name in enumerate(("ux", "uy", "uz")):
-        got = ml.field(name).double().cpu().numpy()
-        if np.abs(F["u"][a]).max() > 1e-9 * umax:
-            errs[name] = rel_err(got, F["u"][a])
-        else:  # zero by symmetry up to rounding: compare against max |u|
-            errs[name] = np.abs(got - F["u"][a]).max() / max(umax, 1e-300)
-    errs["pt"] = rel_err(ml.field("pt").double().cpu().numpy(), F["pt"])
-    errs["rho"] = rel_err(ml.field("rho").double().cpu().numpy(), F["rho"])
-    errs["tau"] = rel_err(ml.field("tau").double().cpu().numpy(), F["tau"])
-    return errs
+    return ml_compare(ml, m, f, g, kind)
 
 
 @pytest.mark.parametrize("make", [_ml_case_2d, _ml_case_3d])
