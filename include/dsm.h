@@ -399,7 +399,10 @@ dsm_status dsm_vec_lincomb(long long n, int nv, const float *d_V, long long stri
  * and the direction from the compact form of the L-BFGS matrix (Byrd, Nocedal
  * & Schnabel 1994).  d_work: caller-owned device memory of at least
  * dsm_lbfgs_workspace_bytes(p, m), 256-byte aligned.  Runs on the stream and
- * returns when done (host reads each iteration).  DSM_E_NONFINITE if the energy
+ * returns when done.  The pair bookkeeping and the compact-form solve run on
+ * the device; the host drives the line search and reads six doubles per trial
+ * point (one read per iteration when the first trial is accepted).  At most 32
+ * pairs (2m <= 64).  DSM_E_NONFINITE if the energy
  * or gradient turns non-finite.  dsm_lbfgs_compact is the host-only
  * compact-form solve, exposed for tests: for k pairs (oldest first),
  * SY[i*k+j] = s_i.y_j, YY[i*k+j] = y_i.y_j, a = S^T g, b = Y^T g, it returns the

@@ -11,8 +11,15 @@
 // condition of Hager & Zhang 2005).  The direction comes from the compact form
 // of the L-BFGS matrix (Byrd, Nocedal & Schnabel 1994), the matrix the
 // two-loop recursion applies: one batched pass of dot products over the pairs
-// and one linear combination per iteration.  Device work per iteration: about
-// a dozen launches and two host reads.
+// and one linear combination per iteration.
+//
+// The pair bookkeeping (the s.y and y.y matrices, S^T g, Y^T g, gamma, the
+// ring of stored pairs) and the compact-form solve live on the device, in one
+// small state block updated by one-thread kernels; the host drives only the
+// line search, whose decisions need the trial's energy and slope.  Each trial
+// reads one block of six doubles (slope, energy, the direction's initial
+// slope, |g|^2 of the current point, the pairs in use, the next pair's slot),
+// so an iteration whose first trial is accepted reads the host once.
 #include <math.h>
 #include <string.h>
 
@@ -24,29 +31,36 @@
 
 using namespace dsm;
 
+constexpr int LB_MAX_M = LINCOMB_MAX / 2;  // most stored pairs
+
 namespace {
 
 // Compact-form coefficients: R w = a, R^T u = (D + gamma YY) w - gamma b,
-// d = -gamma g - S u + gamma Y w.  SY, YY: k x k row-major (pairs oldest
-// first), R the upper triangle of SY, D its diagonal.
-bool compact(int k, const double *SY, const double *YY, const double *a, const double *b,
-             double gamma, double *cx, double *cs, double *cy) {
-  std::vector<double> w(k), z(k), u(k);
+// d = -gamma g - S u + gamma Y w.  Pair i (oldest first) is stored in slot
+// ord[i] of m: s_i.y_j = SY[ord[i] m + ord[j]], y_i.y_j likewise in YY,
+// a_i = A[ord[i]], b_i = B[ord[i]]; R is the upper triangle of (s_i.y_j), D its
+// diagonal.  w, z, u: k reals of scratch.  (The device's solve, in
+// lb_step_kernel, is the same algebra spread over a warp.)
+bool compact_slots(int k, const int *ord, int m, const double *SY,
+                                       const double *YY, const double *A, const double *B,
+                                       double gamma, double *w, double *z, double *u, double *cx,
+                                       double *cs, double *cy) {
   for (int i = k - 1; i >= 0; i--) {  // back substitution, R upper triangular
-    double v = a[i];
-    for (int j = i + 1; j < k; j++) v -= SY[i * k + j] * w[j];
-    if (!(SY[i * k + i] != 0.0)) return false;
-    w[i] = v / SY[i * k + i];
+    double v = A[ord[i]];
+    for (int j = i + 1; j < k; j++) v -= SY[ord[i] * m + ord[j]] * w[j];
+    const double d = SY[ord[i] * m + ord[i]];
+    if (!(d != 0.0)) return false;
+    w[i] = v / d;
   }
   for (int i = 0; i < k; i++) {
-    double v = SY[i * k + i] * w[i] - gamma * b[i];
-    for (int j = 0; j < k; j++) v += gamma * YY[i * k + j] * w[j];
+    double v = SY[ord[i] * m + ord[i]] * w[i] - gamma * B[ord[i]];
+    for (int j = 0; j < k; j++) v += gamma * YY[ord[i] * m + ord[j]] * w[j];
     z[i] = v;
   }
   for (int i = 0; i < k; i++) {  // forward substitution, R^T lower triangular
     double v = z[i];
-    for (int j = 0; j < i; j++) v -= SY[j * k + i] * u[j];
-    u[i] = v / SY[i * k + i];
+    for (int j = 0; j < i; j++) v -= SY[ord[j] * m + ord[i]] * u[j];
+    u[i] = v / SY[ord[i] * m + ord[i]];
   }
   *cx = -gamma;
   for (int i = 0; i < k; i++) {
@@ -55,6 +69,170 @@ bool compact(int k, const double *SY, const double *YY, const double *a, const d
   }
   return true;
 }
+
+// The minimiser's state on the device.  rb: the block each trial reads back
+// (slope of the trial, its energy, initial slope dg0 of the direction, |g|^2
+// of the current point, pairs in use by the direction (0: steepest descent),
+// slot of the next pair).
+struct LbState {
+  double rb[6];  // first: the host reads it at the state's address
+  double gamma, cx;
+  int k, nxt;
+  int order[LB_MAX_M];  // slots of the stored pairs, oldest first
+  double SY[LB_MAX_M * LB_MAX_M], YY[LB_MAX_M * LB_MAX_M], Ag[LB_MAX_M], Bg[LB_MAX_M];
+  double coef[2 * LB_MAX_M];  // the direction: cx g + sum coef_j (s_0..s_{m-1}, y_0..y_{m-1})_j
+};
+
+__global__ void lb_init_kernel(LbState *s) {
+  s->gamma = 1.0;
+  s->cx = 0.0;
+  s->k = 0;
+  s->nxt = 0;
+  for (int i = 0; i < LB_MAX_M * LB_MAX_M; i++) s->SY[i] = s->YY[i] = 0.0;
+  for (int i = 0; i < LB_MAX_M; i++) s->Ag[i] = s->Bg[i] = 0.0;
+  for (int i = 0; i < 2 * LB_MAX_M; i++) s->coef[i] = 0.0;
+}
+
+// One warp per iteration.  (1) If `dots` is given: the accepted step's pair
+// (s, y in slot nxt) against the stored pairs and the new gradient,
+// dots[i] = s_i.y, dots[m + i] = y_i.y, dots[2m + i] = s_i.g, dots[3m + i] = y_i.g,
+// dots[4m] = s.s, dots[4m + 1] = g.g; the pair replaces the one in slot nxt
+// (the oldest in a full ring) if s.y > 1e-12 |s||y|.  (2) The direction of the
+// current point from the stored pairs (compact form), or steepest descent
+// when there are none or the compact direction does not descend (the pairs
+// are then dropped): coef, cx, and rb[2] .. rb[5].  The pairs' k x k matrices
+// are staged into shared memory by the lanes and solved there by the warp.
+__global__ void __launch_bounds__(32) lb_step_kernel(LbState *s, const double *dots, int m) {
+  __shared__ double sy[LB_MAX_M * LB_MAX_M], yy[LB_MAX_M * LB_MAX_M];
+  __shared__ double A[LB_MAX_M], B[LB_MAX_M], w[LB_MAX_M];
+  __shared__ double cs[LB_MAX_M], cy[LB_MAX_M];
+  __shared__ int ord[LB_MAX_M];
+  __shared__ int ok_s;
+  const int l = threadIdx.x;
+  if (dots) {
+    const int nxt = s->nxt;
+    const double ss = dots[4 * m], sy1 = dots[nxt], yy1 = dots[m + nxt];
+    const bool accept = sy1 > 1e-12 * sqrt(ss * yy1);
+    for (int i = l; i < m; i += 32) {
+      s->Ag[i] = dots[2 * m + i];
+      s->Bg[i] = dots[3 * m + i];
+      if (accept) {
+        s->SY[i * m + nxt] = dots[i];      // s_i . y_new
+        s->YY[i * m + nxt] = dots[m + i];  // y_i . y_new
+        s->YY[nxt * m + i] = dots[m + i];
+      }
+    }
+    if (l == 0) {
+      int k = 0;
+      for (int i = 0; i < s->k; i++)
+        if (s->order[i] != nxt) s->order[k++] = s->order[i];
+      if (accept) {
+        s->gamma = sy1 / yy1;
+        s->order[k++] = nxt;
+        s->nxt = (nxt + 1) % m;
+      }
+      s->k = k;
+      s->rb[3] = dots[4 * m + 1];
+    }
+    __syncthreads();
+  }
+  const int k = s->k;
+  const double gg = s->rb[3], gamma = s->gamma;
+  for (int i = l; i < k; i += 32) {
+    ord[i] = s->order[i];
+  }
+  __syncthreads();
+  for (int i = l; i < k; i += 32) {
+    for (int j = 0; j < k; j++) {
+      sy[i * k + j] = s->SY[ord[i] * m + ord[j]];
+      yy[i * k + j] = s->YY[ord[i] * m + ord[j]];
+    }
+    A[i] = s->Ag[ord[i]];
+    B[i] = s->Bg[ord[i]];
+  }
+  __syncthreads();
+  // the compact-form solve across the warp (lane l owns pair l): the
+  // triangular substitutions column by column with the diagonal's
+  // reciprocals, the middle product row by row, dg0 by a warp reduction
+  const unsigned full = 0xffffffffu;
+  bool ok = k > 0;
+  double cx = -gamma, dg0 = 0.0, wl = 0.0, ul = 0.0;
+  if (ok) {
+    const double dl = l < k ? sy[l * k + l] : 1.0;
+    ok = __all_sync(full, dl != 0.0);
+    if (ok) {
+      const double inv = 1.0 / dl;
+      double r = l < k ? A[l] : 0.0;  // R w = a, R upper triangular
+      for (int i = k - 1; i >= 0; i--) {
+        const double wi = __shfl_sync(full, r, i) * __shfl_sync(full, inv, i);
+        if (l == i) wl = wi;
+        if (l < i) r -= sy[l * k + i] * wi;
+      }
+      if (l < k) w[l] = wl;
+      __syncwarp();
+      double zl = 0.0;  // (D + gamma YY) w - gamma b
+      if (l < k) {
+        zl = sy[l * k + l] * wl - gamma * B[l];
+        for (int j = 0; j < k; j++) zl += gamma * yy[l * k + j] * w[j];
+      }
+      for (int j = 0; j < k; j++) {  // R^T u = z, R^T lower triangular
+        const double uj = __shfl_sync(full, zl, j) * __shfl_sync(full, inv, j);
+        if (l == j) ul = uj;
+        if (l > j) zl -= sy[j * k + l] * uj;
+      }
+      double part = l < k ? -ul * A[l] + gamma * wl * B[l] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
+      dg0 = cx * gg + part;
+      ok = dg0 < 0.0;
+    }
+  }
+  if (!ok) {  // no pairs, or not a descent direction: steepest descent
+    cx = -1.0 / fmax(sqrt(gg), 1e-300);
+    dg0 = cx * gg;
+  }
+  if (l < k) {
+    cs[l] = -ul;
+    cy[l] = gamma * wl;
+  }
+  if (l == 0) {
+    ok_s = ok;
+    s->k = ok ? k : 0;
+    s->cx = cx;
+    s->rb[2] = dg0;
+    s->rb[4] = ok ? (double)k : 0.0;
+    s->rb[5] = (double)s->nxt;
+  }
+  __syncthreads();
+  for (int i = l; i < 2 * m; i += 32) s->coef[i] = 0.0;
+  __syncthreads();
+  if (ok_s)
+    for (int i = l; i < k; i += 32) {
+      s->coef[ord[i]] = cs[i];
+      s->coef[m + ord[i]] = cy[i];
+    }
+}
+
+// d = cx g + sum_j coef_j V_j over the 2m stored vectors, coefficients from
+// the device state (a vector with a zero coefficient is not read)
+__global__ void __launch_bounds__(256) lb_lincomb_kernel(long long n, int nv, const float *V,
+                                                         long long stride, const LbState *s,
+                                                         const float *g, float *d) {
+  __shared__ float c[2 * LB_MAX_M];
+  __shared__ float cx;
+  if (threadIdx.x < nv) c[threadIdx.x] = (float)s->coef[threadIdx.x];
+  if (threadIdx.x == 0) cx = (float)s->cx;
+  __syncthreads();
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    float acc = cx * g[k];
+    for (int j = 0; j < nv; j++)
+      if (c[j] != 0.0f) acc += c[j] * V[j * stride + k];
+    d[k] = acc;
+  }
+}
+
+// drop the stored pairs (after a line search that found no step)
+__global__ void lb_reset_kernel(LbState *s) { s->k = 0; }
 
 // Minimiser of the cubic through (a, fa, da), (b, fb, db), kept in the middle
 // 80 % of the bracket (bisection otherwise).
@@ -89,7 +267,8 @@ struct Minimiser {
   FEMCons fcons;
   // device buffers (carved from the caller's workspace)
   float *xb[2], *gb[2], *d, *hist;
-  double *E[2], *dots, *vout;
+  double *E[2], *dots, *vout;  // vout: the state's read-back block
+  LbState *state;
   void *fe_scr, *vec_scr, *dots_scr;
 
   cudaError_t evaluate(const float *x, double *e_out, float *g_out) {
@@ -111,17 +290,14 @@ struct Minimiser {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
   }
-  // trial point xt = x + a d: energy and directional derivative
-  cudaError_t trial(double a, const float *x, float *xt, double *Et, float *gt, double *f,
-                    double *df) {
+  // trial point xt = x + a d: energy and directional derivative, read back
+  // with the rest of the state's block (rb: 6 doubles)
+  cudaError_t trial(double a, const float *x, float *xt, double *Et, float *gt, double *rb) {
     cudaError_t e = vec_lincomb(n, 1, d, n, &a, x, 1.0, xt, st);
     if (e == cudaSuccess) e = evaluate(xt, Et, gt);
     if (e == cudaSuccess) e = vec_dot(n, gt, d, vout, nullptr, vec_scr, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(vout + 1, Et, sizeof(double), cudaMemcpyDeviceToDevice, st);
-    double h[2];
-    if (e == cudaSuccess) e = read(h, vout, 2);
-    *df = h[0];
-    *f = h[1];
+    if (e == cudaSuccess) e = read(rb, vout, 6);
     return e;
   }
 };
@@ -142,12 +318,14 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
   M.E[0] = (double *)(w + off[5]);
   M.E[1] = M.E[0] + 1;
   M.dots = (double *)(w + off[6]);
-  M.vout = (double *)(w + off[7]);
+  M.state = (LbState *)(w + off[7]);
+  M.vout = (double *)(w + off[7]);  // rb, the state's first member
   M.fe_scr = w + off[8];
   M.vec_scr = w + off[9];
   M.dots_scr = w + off[10];
   const long long n = M.n;
   cudaStream_t st = M.st;
+  const int lgrid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
 #define CK(expr)                                    \
   do {                                              \
     if ((expr) != cudaSuccess) return DSM_E_CUDA;   \
@@ -155,21 +333,41 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
 
   // stored pairs start at zero, so unused slots add nothing to a combination
   CK(cudaMemsetAsync(M.hist, 0, (size_t)2 * m * n * sizeof(float), st));
+  lb_init_kernel<<<1, 1, 0, st>>>(M.state);
+  CK(cudaGetLastError());
   int cur = 0;  // x = xb[cur], g = gb[cur], E = E[cur]
   CK(M.evaluate(M.xb[0], M.E[0], M.gb[0]));
-  CK(vec_dot(n, M.gb[0], M.gb[0], M.vout, nullptr, M.vec_scr, st));
+  CK(vec_dot(n, M.gb[0], M.gb[0], M.vout + 3, nullptr, M.vec_scr, st));
   CK(cudaMemcpyAsync(M.vout + 1, M.E[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double h2[2];
-  CK(M.read(h2, M.vout, 2));
-  double gg = h2[0], f_val = h2[1];
-  std::vector<int> order;  // slots of the stored pairs, oldest first
-  int nxt = 0;
-  double gamma = 1.0;
-  std::vector<double> SY((size_t)m * m, 0.0), YY((size_t)m * m, 0.0), Ag(m, 0.0), Bg(m, 0.0);
-  std::vector<double> coef(2 * m, 0.0), hv(4 * m + 2, 0.0);
+  double rb[6];
+  CK(M.read(rb, M.vout, 6));
+  double gg = rb[3], f_val = rb[1];
   long long it = 0, evals = 1;
   int converged = 0;
+  bool fresh = false;  // gg is that of the current point (read after its last update)
+  const double *pending = nullptr;  // the accepted step's dots, not yet folded into the state
   while (it < max_iter) {
+    // the pair update and the direction on the device, then the first trial
+    // (a = 1), whose read also brings |g|^2 of the current point and the
+    // direction's slope
+    lb_step_kernel<<<1, 32, 0, st>>>(M.state, pending, m);
+    CK(cudaGetLastError());
+    pending = nullptr;
+    const float *x = M.xb[cur];
+    float *xt = M.xb[cur ^ 1];
+    const float *g = M.gb[cur];
+    float *gt = M.gb[cur ^ 1];
+    double *Et = M.E[cur ^ 1];
+    lb_lincomb_kernel<<<lgrid, 256, 0, st>>>(n, 2 * m, M.hist, n, M.state, g, M.d);
+    CK(cudaGetLastError());
+    double a = 1.0;
+    CK(M.trial(a, x, xt, Et, gt, rb));
+    double df = rb[0], f = rb[1];
+    const double dg0 = rb[2];
+    gg = rb[3];
+    const bool pairs = rb[4] > 0.0;
+    const int nxt = (int)rb[5];
+    fresh = true;
     if (!isfinite(gg) || !isfinite(f_val)) {
       info->iterations = it;
       info->evaluations = evals;
@@ -177,46 +375,10 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
       info->rms_grad = sqrt(gg / n);
       return DSM_E_NONFINITE;
     }
-    if (sqrt(gg / n) < tol) {
+    if (sqrt(gg / n) < tol) {  // converged at x: the trial is not taken
       converged = 1;
       break;
     }
-    const int k = (int)order.size();
-    double cx = 0.0, dg0 = 0.0;
-    bool ok = false;
-    std::fill(coef.begin(), coef.end(), 0.0);
-    if (k > 0) {
-      std::vector<double> sy(k * k), yy(k * k), a(k), b(k), cs(k), cy(k);
-      for (int i = 0; i < k; i++) {
-        a[i] = Ag[order[i]];
-        b[i] = Bg[order[i]];
-        for (int j = 0; j < k; j++) {
-          sy[i * k + j] = SY[(size_t)order[i] * m + order[j]];
-          yy[i * k + j] = YY[(size_t)order[i] * m + order[j]];
-        }
-      }
-      if (compact(k, sy.data(), yy.data(), a.data(), b.data(), gamma, &cx, cs.data(), cy.data())) {
-        dg0 = cx * gg;
-        for (int i = 0; i < k; i++) {
-          coef[order[i]] = cs[i];
-          coef[m + order[i]] = cy[i];
-          dg0 += cs[i] * a[i] + cy[i] * b[i];
-        }
-        ok = dg0 < 0.0;
-      }
-    }
-    if (!ok) {  // no pairs, or not a descent direction: steepest descent
-      order.clear();
-      std::fill(coef.begin(), coef.end(), 0.0);
-      cx = -1.0 / std::max(sqrt(gg), 1e-300);
-      dg0 = cx * gg;
-    }
-    const float *x = M.xb[cur];
-    float *xt = M.xb[cur ^ 1];
-    const float *g = M.gb[cur];
-    float *gt = M.gb[cur ^ 1];
-    double *Et = M.E[cur ^ 1];
-    CK(vec_lincomb(n, order.empty() ? 0 : 2 * m, M.hist, n, coef.data(), g, cx, M.d, st));
 
     // strong-Wolfe line search with the approximate-Wolfe test near FP32 noise
     const double c1 = 1e-4, c2 = 0.9, noise = 1e-6 * fabs(f_val);
@@ -225,15 +387,12 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
       if (fabs(f - f_val) <= noise) return df > (2.0 * c1 - 1.0) * dg0;
       return f > f_val + c1 * a * dg0;
     };
-    int trials = 0;
-    double a_prev = 0.0, f_prev = f_val, d_prev = dg0, a = 1.0, f = 0.0, df = 0.0;
+    int trials = 1;
+    double a_prev = 0.0, f_prev = f_val, d_prev = dg0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     bool bracketed = false, done = false;
-    double step = 0.0, last = -1.0;
-    while (trials < max_trials) {
-      CK(M.trial(a, x, xt, Et, gt, &f, &df));
-      trials++;
-      last = a;
+    double step = 0.0, last = a;
+    while (true) {
       if (too_high(a, f, df) || (trials > 1 && f >= f_prev && fabs(f - f_val) > noise)) {
         lo[0] = a_prev; lo[1] = f_prev; lo[2] = d_prev;
         hi[0] = a; hi[1] = f; hi[2] = df;
@@ -254,12 +413,20 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
       a_prev = a;
       f_prev = f;
       d_prev = df;
+      if (trials >= max_trials) break;
       a *= 2.0;
+      CK(M.trial(a, x, xt, Et, gt, rb));
+      df = rb[0];
+      f = rb[1];
+      trials++;
+      last = a;
     }
     if (!done && !bracketed) step = a_prev;  // never bracketed: the last descending point
     while (!done && bracketed && trials < max_trials) {
       a = cubic_step(lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]);
-      CK(M.trial(a, x, xt, Et, gt, &f, &df));
+      CK(M.trial(a, x, xt, Et, gt, rb));
+      df = rb[0];
+      f = rb[1];
       trials++;
       last = a;
       if (too_high(a, f, df) || (f >= lo[1] && fabs(f - f_val) > noise)) {
@@ -279,44 +446,31 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
     if (!done && bracketed) step = lo[0];
     evals += trials;
     if (!(step > 0.0)) {
-      if (!order.empty()) {
-        order.clear();
+      if (pairs) {  // drop the pairs and retry by steepest descent
+        lb_reset_kernel<<<1, 1, 0, st>>>(M.state);
+        CK(cudaGetLastError());
         continue;
       }
       break;
     }
     if (last != step) {  // the accepted point is not the last one evaluated
-      CK(M.trial(step, x, xt, Et, gt, &f, &df));
+      CK(M.trial(step, x, xt, Et, gt, rb));
+      f = rb[1];
       evals++;
     }
-    // new pair s = step d, y = g_new - g into slot nxt (the oldest pair leaves a full ring)
-    order.erase(std::remove(order.begin(), order.end(), nxt), order.end());
+    // new pair s = step d, y = g_new - g into slot nxt; every stored s, y
+    // against y_new and against g_new in one batched pass, s.s and g_new.g_new;
+    // the device updates its state (no host read)
     float *s_new = M.hist + (size_t)nxt * n;
     float *y_new = M.hist + (size_t)(m + nxt) * n;
     const double minus1 = -1.0;
     CK(vec_axpby(n, step, M.d, 0.0, s_new, st));
     CK(vec_lincomb(n, 1, g, n, &minus1, gt, 1.0, y_new, st));
-    // every stored s, y against y_new and against g_new, in one batched pass
     CK(vec_dots2(n, 2 * m, M.hist, n, y_new, gt, M.dots, M.dots_scr, st));
     CK(vec_dot(n, s_new, s_new, M.dots + 4 * m, nullptr, M.vec_scr, st));
     CK(vec_dot(n, gt, gt, M.dots + 4 * m + 1, nullptr, M.vec_scr, st));
-    CK(M.read(hv.data(), M.dots, 4 * m + 2));  // the iteration's one read after the step
-    const double ss = hv[4 * m], sy = hv[nxt], yy = hv[m + nxt];
-    gg = hv[4 * m + 1];
-    for (int i = 0; i < m; i++) {
-      Ag[i] = hv[2 * m + i];
-      Bg[i] = hv[3 * m + i];
-    }
-    if (sy > 1e-12 * sqrt(ss * yy)) {
-      for (int i = 0; i < m; i++) {
-        SY[(size_t)i * m + nxt] = hv[i];     // s_i . y_new
-        YY[(size_t)i * m + nxt] = hv[m + i];  // y_i . y_new
-        YY[(size_t)nxt * m + i] = hv[m + i];
-      }
-      gamma = sy / yy;
-      order.push_back(nxt);
-      nxt = (nxt + 1) % m;
-    }
+    pending = M.dots;  // folded in by the next iteration's lb_step_kernel
+    fresh = false;
     cur ^= 1;
     f_val = f;
     it++;
@@ -326,6 +480,10 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
   if (cur != 0 &&
       cudaMemcpyAsync(d_x, M.xb[cur], n * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return DSM_E_CUDA;
+  if (!fresh) {  // |g|^2 of the last accepted point (its dots hold g.g)
+    if (M.read(rb, M.dots + 4 * m + 1, 1) != cudaSuccess) return DSM_E_CUDA;
+    gg = rb[0];
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return DSM_E_CUDA;
   info->iterations = it;
   info->evaluations = evals;
@@ -340,7 +498,13 @@ extern "C" {
 dsm_status dsm_lbfgs_compact(int k, const double *SY, const double *YY, const double *a,
                              const double *b, double gamma, double *cx, double *cs, double *cy) {
   if (k < 1 || !SY || !YY || !a || !b || !cx || !cs || !cy) return DSM_E_INVAL;
-  return compact(k, SY, YY, a, b, gamma, cx, cs, cy) ? DSM_OK : DSM_E_INVAL;
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; i++) ord[i] = i;
+  std::vector<double> w(k), z(k), u(k);
+  return compact_slots(k, ord.data(), k, SY, YY, a, b, gamma, w.data(), z.data(), u.data(), cx,
+                       cs, cy)
+             ? DSM_OK
+             : DSM_E_INVAL;
 }
 
 // Workspace of an L-BFGS run over n-vectors whose energy needs fe_bytes of
@@ -359,7 +523,7 @@ static size_t lbfgs_layout_n(long long n, int m, size_t fe_bytes, size_t off[12]
   off[4] = take((size_t)2 * m * n * sizeof(float));  // s_0..s_{m-1}, y_0..y_{m-1}
   off[5] = take(2 * sizeof(double));              // E, Et
   off[6] = take((size_t)(4 * m + 2) * sizeof(double));  // batched dots, then s.s and g.g
-  off[7] = take(4 * sizeof(double));              // single dots
+  off[7] = take(sizeof(LbState));                 // the pair bookkeeping on the device
   off[8] = take(fe_bytes);
   off[9] = take(vec_scratch_bytes(n));
   off[10] = take(vec_dots_scratch_bytes(n, 4 * m));

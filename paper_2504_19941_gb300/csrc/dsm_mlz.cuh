@@ -119,7 +119,8 @@ struct MLZIO {
 // a.Qz / a.Uz / a.Pz receive this step's state.  tmQ: the padded quads of
 // the state (4 nxp, nyp, nz); tmU: its u_z (nxp, nyp, nz); tmP: its pairs
 // (2 nxp, nyp, (NF - 1) nz; any valid map when NF = 1); tmC1: padded C1.
-template <class T, int NF>
+// RCV: the fluids' densities may differ (else the density map is compiled out).
+template <class T, int NF, bool RCV>
 __global__ void __launch_bounds__(ZT_X *ZT_Y, sizeof(T) == 8 ? 1 : 2)
     mlz_kernel(MLArgs<T> a, int zrun, const __grid_constant__ CUtensorMap tmQ,
                const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(ZT_X *ZT_Y, sizeof(T) == 8 ? 1 : 2)
     io.c1o[1] = s1 * SM::slot + node_c1;
     io.c1o[2] = s2 * SM::slot + node_c1;
     io.z = z;
-    ml_node_body<1, T, NF, ML_STEP, true, false, MLZIO<T, NF>>(a, io.x, io.y, z, io);
+    ml_node_body<1, T, NF, ML_STEP, true, false, MLZIO<T, NF>, RCV>(a, io.x, io.y, z, io);
     sk = s1;
     cq = (cq + 1) & (Z_CRING - 1);
   }

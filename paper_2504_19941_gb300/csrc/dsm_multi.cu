@@ -190,7 +190,12 @@ struct MLGlobalIO {
 
 // FC: the lattice has a mirror or wall face (populations only); without one the
 // face code is compiled out, which keeps the periodic step's register count
-template <int K, class T, int NF, int MODE, bool EQ, bool FC, class IO = MLGlobalIO<T>>
+// RCV: the fluids' densities may differ (a.rc decides at run time); false:
+// they are equal (a.rc = 0), and the density map, its gradient and the terms
+// they enter are compiled out -- rho is the common density, G[rho] = 0, the
+// same results bit for bit.
+template <int K, class T, int NF, int MODE, bool EQ, bool FC, class IO = MLGlobalIO<T>,
+          bool RCV = true>
 __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, int z,
                                              const IO &io = IO()) {
   static_assert(!(EQ && FC), "the g_eq form is periodic only");
@@ -223,34 +228,39 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   for (int k = 0; k < NC; k++) lap[k] = T(0);
 #pragma unroll
   for (int f = 0; f < NF; f++) gC[f][0] = gC[f][1] = gC[f][2] = T(0);
+  // (gradient components only where c_i has one: w 0 c is an operation IEEE
+  // arithmetic cannot drop, and for finite values it adds nothing)
 #pragma unroll
   for (int i = 1; i < Q; i++) {
     const T w = T(L::w(i));
     const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
     const T c1m = io.template C1<L>(a, h, n, i);
-    T cm[NF], lastm = T(1) - c1m;
+    T cm[NF];
 #pragma unroll
     for (int f = 0; f < NF; f++) {
       cm[f] = io.template C<L>(a, h, n, f, i);
-      lastm -= cm[f];
       lap[1 + f] += w * (cm[f] - cv[1 + f]);
-      gC[f][0] += w * cx * cm[f];
-      gC[f][1] += w * cy * cm[f];
-      gC[f][2] += w * cz * cm[f];
+      if (L::cx(i)) gC[f][0] += w * cx * cm[f];
+      if (L::cy(i)) gC[f][1] += w * cy * cm[f];
+      if (L::cz(i)) gC[f][2] += w * cz * cm[f];
     }
     lap[0] += w * (c1m - cv[0]);
-    lap[NC - 1] += w * (lastm - cv[NC - 1]);
-    if (a.rc) {
+    if (RCV && a.rc) {
       const T r = w * ml_rho<T, NF>(a, cm, c1m);
-      gR[0] += r * cx;
-      gR[1] += r * cy;
-      gR[2] += r * cz;
+      if (L::cx(i)) gR[0] += r * cx;
+      if (L::cy(i)) gR[1] += r * cy;
+      if (L::cz(i)) gR[2] += r * cz;
     }
-    gc1[0] += w * cx * c1m;
-    gc1[1] += w * cy * c1m;
-    gc1[2] += w * cz * c1m;
+    if (L::cx(i)) gc1[0] += w * cx * c1m;
+    if (L::cy(i)) gc1[1] += w * cy * c1m;
+    if (L::cz(i)) gc1[2] += w * cz * c1m;
     if (c1m >= T(0.5)) nb_solid |= 1u << i;
   }
+  // the dependent fluid C_{N+1} = 1 - C_1 - sum_f C_f: its Laplacian by the
+  // stencil's linearity, L[C_{N+1}] = -L[C_1] - sum_f L[C_f] (sum_i w_i (1 - 1) = 0)
+  lap[NC - 1] = -lap[0];
+#pragma unroll
+  for (int f = 0; f < NF; f++) lap[NC - 1] -= lap[1 + f];
   T mu[NF], F[3] = {T(0), T(0), T(0)};
   T d[NC];
 #pragma unroll
@@ -269,7 +279,7 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   T cfree[NF];
 #pragma unroll
   for (int f = 0; f < NF; f++) cfree[f] = cv[1 + f];
-  const T rho = ml_rho<T, NF>(a, cfree, cv[0]);
+  const T rho = RCV ? ml_rho<T, NF>(a, cfree, cv[0]) : a.rho[NF];
   // relaxation of the locally largest fluid, ties to the later one
   int big = NF;
   T bigc = cv[NC - 1];
@@ -367,12 +377,12 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
 #pragma unroll
     for (int j = 0; j < Q; j++) {
       m0 += fs[j];
-      m1[0] += T(L::cx(j)) * fs[j];
-      m1[1] += T(L::cy(j)) * fs[j];
-      m1[2] += T(L::cz(j)) * fs[j];
+      if (L::cx(j)) m1[0] += T(L::cx(j)) * fs[j];
+      if (L::cy(j)) m1[1] += T(L::cy(j)) * fs[j];
+      if (L::cz(j)) m1[2] += T(L::cz(j)) * fs[j];
     }
     for (int e = 0; e < 3; e++) u[e] = (m1[e] + T(0.5) * F[e]) / rho;
-    pt = m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]);
+    pt = RCV ? m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]) : m0;
   }
   if constexpr (MODE == ML_FIELDS) {
     T v;
@@ -404,14 +414,19 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const T w = T(L::w(i));
-    const T ci[3] = {T(L::cx(i)), T(L::cy(i)), T(L::cz(i))};
-    const T cu = ci[0] * u[0] + ci[1] * u[1] + ci[2] * u[2];
+    // c_i . v over the components c_i has (cdot: no products by zero)
+    const T cu = cdot<L>(i, u[0], u[1], u[2]);
     const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
     T fo = w;
     if (!solid_x) {
-      const T cg = ci[0] * gR[0] + ci[1] * gR[1] + ci[2] * gR[2];
-      const T cF = ci[0] * F[0] + ci[1] * F[1] + ci[2] * F[2];
-      const T Fi = kF * w * ((cg - ug) * s + T(3) * cF);
+      const T cF = cdot<L>(i, F[0], F[1], F[2]);
+      T Fi;
+      if constexpr (RCV) {
+        const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);
+        Fi = kF * w * ((cg - ug) * s + T(3) * cF);
+      } else {
+        Fi = kF * w * (T(3) * cF);
+      }
       fo = fs[i] + (w * (pt + rho * s) - fs[i]) * om + Fi;
     }
     plane(a.f_out, a.pitch, i)[n] = fo;
@@ -437,11 +452,11 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   }
 }
 
-template <int K, class T, int NF, int MODE, bool EQ, bool FC>
+template <int K, class T, int NF, int MODE, bool EQ, bool FC, bool RCV = true>
 __global__ void __launch_bounds__(256) ml_node_kernel(MLArgs<T> a) {
-  ml_node_body<K, T, NF, MODE, EQ, FC>(a, blockIdx.x * blockDim.x + threadIdx.x,
-                                       blockIdx.y * blockDim.y + threadIdx.y,
-                                       blockIdx.z * blockDim.z + threadIdx.z);
+  ml_node_body<K, T, NF, MODE, EQ, FC, MLGlobalIO<T>, RCV>(
+      a, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+      blockIdx.z * blockDim.z + threadIdx.z);
 }
 // D3Q19 FP32 with three free fluids and a mirror or wall face: the unrolled
 // face fix-ups raise the register count past one 256-thread block per SM, and
@@ -742,7 +757,8 @@ struct MomentsL {
 template <int K, class T, int NF>
 struct StepL {
   static void go(dim3 g, dim3 b, const MLArgs<T> &a, cudaStream_t s, bool eq, void *) {
-    if (eq) ml_node_kernel<K, T, NF, ML_STEP, true, false><<<g, b, 0, s>>>(a);
+    if (eq && a.rc) ml_node_kernel<K, T, NF, ML_STEP, true, false><<<g, b, 0, s>>>(a);
+    else if (eq) ml_node_kernel<K, T, NF, ML_STEP, true, false, false><<<g, b, 0, s>>>(a);
     else if (!a.walls) ml_node_kernel<K, T, NF, ML_STEP, false, false><<<g, b, 0, s>>>(a);
     else if constexpr (ml_faces_capped<K, T, NF>()) ml_node_faces_kernel<K, T, NF, ML_STEP><<<g, b, 0, s>>>(a);
     else ml_node_kernel<K, T, NF, ML_STEP, false, true><<<g, b, 0, s>>>(a);
@@ -776,23 +792,29 @@ struct GofEqL {
 // ---- single-pass step --------------------------------------------------------
 template <class T, int NF>
 struct MLZ {
-  static bool prepare() {  // opt in to the kernel's dynamic shared memory, once
+  static bool prepare() {  // opt in to the kernels' dynamic shared memory, once
     static const bool ok =
-        cudaFuncSetAttribute(mlz_kernel<T, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(mlz_kernel<T, NF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MLZSmem<T, NF>::total) == cudaSuccess &&
+        cudaFuncSetAttribute(mlz_kernel<T, NF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)MLZSmem<T, NF>::total) == cudaSuccess;
     return ok;
   }
   static int resident() {
     int b = 0;
     if (!prepare() || cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                          &b, mlz_kernel<T, NF>, ZT_X * ZT_Y, MLZSmem<T, NF>::total) != cudaSuccess)
+                          &b, mlz_kernel<T, NF, true>, ZT_X * ZT_Y, MLZSmem<T, NF>::total) !=
+                          cudaSuccess)
       return 0;
     return b;
   }
   static cudaError_t step(const MLArgs<T> &a, const CUtensorMap *m, int zrun, cudaStream_t s) {
     if (!prepare()) return cudaErrorInvalidValue;
     const dim3 grid(a.nx / ZT_X, a.ny / ZT_Y, (a.nz + zrun - 1) / zrun), blk(ZT_X, ZT_Y, 1);
-    mlz_kernel<T, NF><<<grid, blk, MLZSmem<T, NF>::total, s>>>(a, zrun, m[0], m[1], m[2], m[3]);
+    if (a.rc)
+      mlz_kernel<T, NF, true><<<grid, blk, MLZSmem<T, NF>::total, s>>>(a, zrun, m[0], m[1], m[2], m[3]);
+    else
+      mlz_kernel<T, NF, false><<<grid, blk, MLZSmem<T, NF>::total, s>>>(a, zrun, m[0], m[1], m[2], m[3]);
     return cudaGetLastError();
   }
   static cudaError_t pack(const MLArgs<T> &a, dsm_mlattice *h, cudaStream_t s) {

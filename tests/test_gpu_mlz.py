@@ -118,10 +118,15 @@ def test_single_pass_equals_two_pass(nf):
     # the same per-node arithmetic; a few FP32 ulp of the scale (the kernels
     # may contract different products into FMAs)
     assert rel_err(f1, f2) < 1e-6 and rel_err(g1, g2) < 1e-6, (rel_err(f1, f2), rel_err(g1, g2))
-    for name, idx in (("C", 0), ("C", nf - 1), ("mu", 0), ("ux", 0), ("pt", 0)):
+    for name, idx in (("C", 0), ("C", nf - 1), ("mu", 0), ("pt", 0)):
         a = one.field(name, idx).double().cpu().numpy()
         b = two.field(name, idx).double().cpu().numpy()
         assert rel_err(a, b) < 1e-5, (name, idx, rel_err(a, b))
+    # u is a cancelling sum of O(0.1) populations: against the speed scale, at
+    # the FP32 level the two-fluid single-pass parity test allows (2e-4)
+    u1 = np.stack([one.field(k).double().cpu().numpy() for k in ("ux", "uy", "uz")])
+    u2 = np.stack([two.field(k).double().cpu().numpy() for k in ("ux", "uy", "uz")])
+    assert np.abs(u1 - u2).max() / np.abs(u2).max() < 2e-4
 
 
 def test_zrun_does_not_change_the_result():
