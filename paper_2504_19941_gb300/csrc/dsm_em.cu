@@ -141,9 +141,16 @@ __global__ void fe_finalize_kernel(const double *partials, long long nb, double 
 
 __global__ void add_dev_scalar_kernel(long long n, const double *c, float *g) {
   const float v = (float)c[0];
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    g[k] += v;
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {  // four loads in flight per thread
+    const float a0 = g[k], a1 = g[k + G], a2 = g[k + 2 * G], a3 = g[k + 3 * G];
+    g[k] = a0 + v;
+    g[k + G] = a1 + v;
+    g[k + 2 * G] = a2 + v;
+    g[k + 3 * G] = a3 + v;
+  }
+  for (; k < n; k += G) g[k] += v;
 }
 
 dsm_status fem_args_of(const dsm_params *p, int nfluid, const double *kappa, const double *dP,
@@ -223,7 +230,7 @@ size_t fe_scratch_bytes(int kind, int nx, int ny, int nz) {
 }
 
 cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, double *energy,
-                      double *terms, void *scratch, cudaStream_t st) {
+                      double *terms, void *scratch, cudaStream_t st, const double **defer) {
   const long long nb = fe_blocks(kind, a.nx, a.ny, a.nz);
   double *partials = (double *)scratch;
   double *dEcs = (double *)((char *)scratch + round_up(nb * FE_K * sizeof(double), 256));
@@ -234,6 +241,10 @@ cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, doub
   if (kind == 0) fe_kernel<0><<<(unsigned)nb, fe_block(0), 0, st>>>(a, g.x, g.y, nbricks);
   else fe_kernel<1><<<(unsigned)nb, fe_block(1), 0, st>>>(a, g.x, g.y, nbricks);
   fe_finalize_kernel<<<1, 256, 0, st>>>(partials, nb, dP, kcs, V0, energy, terms, dEcs);
+  if (defer) {  // the caller adds the constraint's constant (null: none)
+    *defer = (kcs != 0.0 && a.active == 2) ? dEcs : nullptr;
+    return cudaGetLastError();
+  }
   if (kcs != 0.0 && a.active == 2) {
     const long long N = (long long)a.nx * a.ny * a.nz;
     long long blocks = (N + 255) / 256;
@@ -417,16 +428,118 @@ cudaError_t fe_multi_launch(int kind, FEMArgs a, const FEMCons &cons, double *en
 // ---------------------------------------------------------------------------
 // K6: L-BFGS vector kernels.  Fixed grid (VEC_BLOCKS x 256), grid-stride in a
 // fixed order, FP64 accumulation, block partials summed in block order: the
-// result does not depend on timing.
+// result does not depend on timing.  Every grid-stride loop takes four
+// elements a grid apart per iteration, so that four loads per stream are in
+// flight (the order of the elements, and so of every sum, is unchanged).
 // ---------------------------------------------------------------------------
+
+static int vec_grid(long long n);
+
+// The exact product a b (TwoProd: p + e, e from one FMA) added to the pair s:
+// TwoSum into s.hi, both rounding errors into s.lo.  FP64 accuracy from FP32
+// instructions, without renormalising the pair at every element.
+__device__ __forceinline__ void acc_prod(FF &s, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  const FF t = two_sum(s.hi, p);
+  s.hi = t.hi;
+  s.lo += t.lo + pe;
+}
+
+// The last block of a grid sums the grid's partials in block order (as
+// dot_finalize_kernel does) into out[0] and rearms the counter: each block
+// publishes its partial, counts itself, and the block that counts last (every
+// other partial is then visible) finishes.  No block waits for another.
+__device__ __forceinline__ void last_block_sum(const double *partials, unsigned *counter,
+                                               double *out) {
+  __shared__ bool last;
+  __shared__ double sh[256];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    s += ((volatile const double *)partials)[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0];
+    *counter = 0u;
+  }
+}
+
+// A trial point's gradient completed and its slope: g += c[0] (the
+// constraint's constant, when c is given), out[0] = g.d, in one pass (the
+// sum as dot_kernel's); blockDim.x = 256.
+__global__ void __launch_bounds__(256) trial_slope_kernel(long long n, const double *c, float *g,
+                                                          const float *d, double *partials,
+                                                          unsigned *counter, double *out) {
+  const float cv = c ? (float)c[0] : 0.0f;
+  FF s[1] = {FF{0.0f, 0.0f}};
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    float gg[4], dd[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      gg[u] = g[k + u * G];
+      dd[u] = d[k + u * G];
+    }
+    if (c) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        gg[u] += cv;
+        g[k + u * G] = gg[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) acc_prod(s[0], gg[u], dd[u]);
+  }
+  for (; k < n; k += G) {
+    float gk = g[k];
+    if (c) {
+      gk += cv;
+      g[k] = gk;
+    }
+    acc_prod(s[0], gk, d[k]);
+  }
+  const int sums[1] = {0};
+  block_reduce_ff<1>(s, sums, partials + blockIdx.x);
+  last_block_sum(partials, counter, out);
+}
+
+cudaError_t vec_trial_slope(long long n, const double *c, float *g, const float *d, double *out,
+                            void *scratch, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  double *partials = (double *)scratch;
+  unsigned *counter = vec_scratch_counter(scratch);
+  trial_slope_kernel<<<vec_grid(n), 256, 0, st>>>(n, c, g, d, partials, counter, out);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) dot_kernel(long long n, const float *x, const float *y,
                                                   double *partials) {
-  // exact FP32 products (TwoProd) summed with carried errors: FP64 accuracy
-  // without FP64 instructions per element
   FF s[1] = {FF{0.0f, 0.0f}};
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    s[0] = ff_add(s[0], two_prod(x[k], y[k]));
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    const float x0 = x[k], x1 = x[k + G], x2 = x[k + 2 * G], x3 = x[k + 3 * G];
+    const float y0 = y[k], y1 = y[k + G], y2 = y[k + 2 * G], y3 = y[k + 3 * G];
+    acc_prod(s[0], x0, y0);
+    acc_prod(s[0], x1, y1);
+    acc_prod(s[0], x2, y2);
+    acc_prod(s[0], x3, y3);
+  }
+  for (; k < n; k += G) acc_prod(s[0], x[k], y[k]);
   const int sums[1] = {0};
   block_reduce_ff<1>(s, sums, partials + blockIdx.x);
 }
@@ -452,44 +565,65 @@ __global__ void __launch_bounds__(256) dots_kernel(long long n, const float *V, 
                                                    const float *x, double *partials) {
   const float *v = V + blockIdx.y * stride;
   FF s[1] = {FF{0.0f, 0.0f}};
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    s[0] = ff_add(s[0], two_prod(v[k], x[k]));
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    const float v0 = v[k], v1 = v[k + G], v2 = v[k + 2 * G], v3 = v[k + 3 * G];
+    const float x0 = x[k], x1 = x[k + G], x2 = x[k + 2 * G], x3 = x[k + 3 * G];
+    acc_prod(s[0], v0, x0);
+    acc_prod(s[0], v1, x1);
+    acc_prod(s[0], v2, x2);
+    acc_prod(s[0], v3, x3);
+  }
+  for (; k < n; k += G) acc_prod(s[0], v[k], x[k]);
   const int sums[1] = {0};
   block_reduce_ff<1>(s, sums, partials + (long long)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-// the dots of every V_k against two vectors in one pass over V: partials
-// (k, block) hold the two sums side by side
-__global__ void __launch_bounds__(256) dots2_kernel(long long n, const float *V, long long stride,
-                                                    const float *x, const float *y,
-                                                    double *partials) {
-  const float *v = V + blockIdx.y * stride;
-  FF s[2] = {FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const float vk = v[k];
-    s[0] = ff_add(s[0], two_prod(vk, x[k]));
-    s[1] = ff_add(s[1], two_prod(vk, y[k]));
+// a.a, b.b and c.c in one pass: partials (block) hold the three sums side by
+// side; each sum as dot_kernel's
+__global__ void __launch_bounds__(256) sumsq3_kernel(long long n, const float *a, const float *b,
+                                                     const float *c, double *partials) {
+  FF s[3] = {FF{0.0f, 0.0f}, FF{0.0f, 0.0f}, FF{0.0f, 0.0f}};
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    float aa[4], bb[4], cc[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      aa[u] = a[k + u * G];
+      bb[u] = b[k + u * G];
+      cc[u] = c[k + u * G];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      acc_prod(s[0], aa[u], aa[u]);
+      acc_prod(s[1], bb[u], bb[u]);
+      acc_prod(s[2], cc[u], cc[u]);
+    }
   }
-  const int sums[2] = {0, 0};
-  block_reduce_ff<2>(s, sums, partials + 2 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+  for (; k < n; k += G) {
+    const float ak = a[k], bk = b[k], ck = c[k];
+    acc_prod(s[0], ak, ak);
+    acc_prod(s[1], bk, bk);
+    acc_prod(s[2], ck, ck);
+  }
+  const int sums[3] = {0, 0, 0};
+  block_reduce_ff<3>(s, sums, partials + 3 * (long long)blockIdx.x);
 }
 
-// block (k, t): the partials of V_k against target t summed in block order,
-// as dots_finalize_kernel sums a single target's
-__global__ void dots2_finalize_kernel(const double *partials, int nb, int nv, double *out) {
+// block t: partial t of every block (partials[stride b + t]) summed in block order
+__global__ void strided_finalize_kernel(const double *partials, int nb, int stride, double *out) {
   __shared__ double sh[256];
-  const double *p = partials + 2 * (long long)blockIdx.x * nb + blockIdx.y;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[2 * b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[(long long)stride * b + blockIdx.x];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[blockIdx.y * nv + blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
 // one block per dot product: its block partials summed in block order
@@ -511,8 +645,24 @@ __global__ void dots_finalize_kernel(const double *partials, int nb, double *out
 __global__ void __launch_bounds__(256) lincomb_kernel(long long n, int nv, const float *V,
                                                       long long stride, LinCoef c,
                                                       const float *x, float *y) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    float acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) acc[u] = c.cx * x[k + u * G];
+    for (int j = 0; j < nv; j++) {
+      const float *vj = V + j * stride + k;
+      float vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) vv[u] = vj[u * G];
+#pragma unroll
+      for (int u = 0; u < 4; u++) acc[u] += c.c[j] * vv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) y[k + u * G] = acc[u];
+  }
+  for (; k < n; k += G) {
     float acc = c.cx * x[k];
     for (int j = 0; j < nv; j++) acc += c.c[j] * V[j * stride + k];
     y[k] = acc;
@@ -530,9 +680,20 @@ __global__ void __launch_bounds__(256) axpy_dev_kernel(long long n, double sign,
 
 __global__ void __launch_bounds__(256) axpby_kernel(long long n, float a, const float *x, float b,
                                                     float *y) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x)
-    y[k] = (b == 0.0f) ? a * x[k] : a * x[k] + b * y[k];
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b == 0.0f) {
+    for (; k + 3 * G < n; k += 4 * G) {
+      const float x0 = x[k], x1 = x[k + G], x2 = x[k + 2 * G], x3 = x[k + 3 * G];
+      y[k] = a * x0;
+      y[k + G] = a * x1;
+      y[k + 2 * G] = a * x2;
+      y[k + 3 * G] = a * x3;
+    }
+    for (; k < n; k += G) y[k] = a * x[k];
+  } else {
+    for (; k < n; k += G) y[k] = a * x[k] + b * y[k];
+  }
 }
 
 // y = s[0] * x
@@ -555,13 +716,13 @@ size_t vec_dots_scratch_bytes(long long n, int nv) {
   return (size_t)(nv > 0 ? nv : 1) * vec_grid(n) * sizeof(double) + 256;
 }
 
-cudaError_t vec_dots2(long long n, int nv, const float *V, long long stride, const float *x,
-                      const float *y, double *out, void *scratch, cudaStream_t st) {
-  if (nv <= 0 || n <= 0) return cudaSuccess;
+cudaError_t vec_sumsq3(long long n, const float *a, const float *b, const float *c, double *out,
+                       void *scratch, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   const int g = vec_grid(n);
   double *partials = (double *)scratch;
-  dots2_kernel<<<dim3(g, nv), 256, 0, st>>>(n, V, stride, x, y, partials);
-  dots2_finalize_kernel<<<dim3(nv, 2), 256, 0, st>>>(partials, g, nv, out);
+  sumsq3_kernel<<<g, 256, 0, st>>>(n, a, b, c, partials);
+  strided_finalize_kernel<<<3, 256, 0, st>>>(partials, g, 3, out);
   return cudaGetLastError();
 }
 

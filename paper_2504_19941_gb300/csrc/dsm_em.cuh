@@ -63,8 +63,11 @@ cudaError_t fe_multi_launch(int kind, FEMArgs a, const FEMCons &cons, double *en
 
 long long fe_blocks(int kind, int nx, int ny, int nz);
 size_t fe_scratch_bytes(int kind, int nx, int ny, int nz);
+// defer: when given, the constraint's constant is not added to the gradient;
+// *defer receives its device address (null when there is none).
 cudaError_t fe_launch(int kind, FEArgs a, double dP, double kcs, double V0, double *energy,
-                      double *terms, void *scratch, cudaStream_t st);
+                      double *terms, void *scratch, cudaStream_t st,
+                      const double **defer = nullptr);
 
 constexpr int LINCOMB_MAX = 64;  // most vectors one dsm_vec_lincomb combines
 struct LinCoef {
@@ -76,10 +79,19 @@ size_t vec_scratch_bytes(long long n);
 size_t vec_dots_scratch_bytes(long long n, int nv);
 cudaError_t vec_dots(long long n, int nv, const float *V, long long stride, const float *x,
                      double *out, void *scratch, cudaStream_t st);
-// out[0..nv) = V_k . x and out[nv..2nv) = V_k . y in one pass over V, each
-// bitwise equal to vec_dots' (scratch: vec_dots_scratch_bytes(n, 2 nv))
-cudaError_t vec_dots2(long long n, int nv, const float *V, long long stride, const float *x,
-                      const float *y, double *out, void *scratch, cudaStream_t st);
+// A trial point's gradient and slope: g += c[0] if c is given, out[0] = g.d,
+// one launch (scratch: vec_scratch_bytes(n), whose counter word starts and
+// ends at zero).
+cudaError_t vec_trial_slope(long long n, const double *c, float *g, const float *d, double *out,
+                            void *scratch, cudaStream_t st);
+// the counter word of a vec_scratch_bytes scratch (behind the block partials)
+inline unsigned *vec_scratch_counter(void *scratch) {
+  return (unsigned *)((char *)scratch + VEC_BLOCKS * sizeof(double));
+}
+// out[0] = a.a, out[1] = b.b, out[2] = c.c in one pass (scratch:
+// vec_dots_scratch_bytes(n, 3))
+cudaError_t vec_sumsq3(long long n, const float *a, const float *b, const float *c, double *out,
+                       void *scratch, cudaStream_t st);
 cudaError_t vec_lincomb(long long n, int nv, const float *V, long long stride, const double *coef,
                         const float *x, double cx, float *y, cudaStream_t st);
 cudaError_t vec_dot(long long n, const float *x, const float *y, double *out, const double *scale,

@@ -94,15 +94,20 @@ __global__ void lb_init_kernel(LbState *s) {
 }
 
 // One warp per iteration.  (1) If `dots` is given: the accepted step's pair
-// (s, y in slot nxt) against the stored pairs and the new gradient,
-// dots[i] = s_i.y, dots[m + i] = y_i.y, dots[2m + i] = s_i.g, dots[3m + i] = y_i.g,
-// dots[4m] = s.s, dots[4m + 1] = g.g; the pair replaces the one in slot nxt
-// (the oldest in a full ring) if s.y > 1e-12 |s||y|.  (2) The direction of the
+// (s, y already stored in slot nxt).  dots[i] = s_i.g and dots[m + i] = y_i.g
+// for every slot against the new gradient g (slot nxt holding the new pair),
+// dots[2m] = y.y, dots[2m + 1] = g.g, dots[2m + 2] = s.s; sy = s.y of the new
+// pair, from the line search's slopes.  The new column of the pair matrices
+// needs no pass of its own: s_i.y = s_i.g - s_i.g_old and y_i.y = y_i.g -
+// y_i.g_old, where s_i.g_old and y_i.g_old are the previous iteration's
+// S^T g and Y^T g (Ag, Bg).  The pair replaces the one in slot nxt (the oldest
+// in a full ring) if s.y > 1e-12 |s||y|.  (2) The direction of the
 // current point from the stored pairs (compact form), or steepest descent
 // when there are none or the compact direction does not descend (the pairs
 // are then dropped): coef, cx, and rb[2] .. rb[5].  The pairs' k x k matrices
 // are staged into shared memory by the lanes and solved there by the warp.
-__global__ void __launch_bounds__(32) lb_step_kernel(LbState *s, const double *dots, int m) {
+__global__ void __launch_bounds__(32) lb_step_kernel(LbState *s, const double *dots, int m,
+                                                     double sy1) {
   __shared__ double sy[LB_MAX_M * LB_MAX_M], yy[LB_MAX_M * LB_MAX_M];
   __shared__ double A[LB_MAX_M], B[LB_MAX_M], w[LB_MAX_M];
   __shared__ double cs[LB_MAX_M], cy[LB_MAX_M];
@@ -111,16 +116,23 @@ __global__ void __launch_bounds__(32) lb_step_kernel(LbState *s, const double *d
   const int l = threadIdx.x;
   if (dots) {
     const int nxt = s->nxt;
-    const double ss = dots[4 * m], sy1 = dots[nxt], yy1 = dots[m + nxt];
+    const double yy1 = dots[2 * m], ss = dots[2 * m + 2];
     const bool accept = sy1 > 1e-12 * sqrt(ss * yy1);
     for (int i = l; i < m; i += 32) {
-      s->Ag[i] = dots[2 * m + i];
-      s->Bg[i] = dots[3 * m + i];
+      const double agn = dots[i], bgn = dots[m + i];
       if (accept) {
-        s->SY[i * m + nxt] = dots[i];      // s_i . y_new
-        s->YY[i * m + nxt] = dots[m + i];  // y_i . y_new
-        s->YY[nxt * m + i] = dots[m + i];
+        if (i == nxt) {
+          s->SY[i * m + nxt] = sy1;
+          s->YY[i * m + nxt] = yy1;
+        } else {
+          const double yy_i = bgn - s->Bg[i];  // y_i . y_new
+          s->SY[i * m + nxt] = agn - s->Ag[i];  // s_i . y_new
+          s->YY[i * m + nxt] = yy_i;
+          s->YY[nxt * m + i] = yy_i;
+        }
       }
+      s->Ag[i] = agn;
+      s->Bg[i] = bgn;
     }
     if (l == 0) {
       int k = 0;
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(32) lb_step_kernel(LbState *s, const double *d
         s->nxt = (nxt + 1) % m;
       }
       s->k = k;
-      s->rb[3] = dots[4 * m + 1];
+      s->rb[3] = dots[2 * m + 1];
     }
     __syncthreads();
   }
@@ -222,8 +234,26 @@ __global__ void __launch_bounds__(256) lb_lincomb_kernel(long long n, int nv, co
   if (threadIdx.x < nv) c[threadIdx.x] = (float)s->coef[threadIdx.x];
   if (threadIdx.x == 0) cx = (float)s->cx;
   __syncthreads();
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
+  // four elements a grid apart per iteration: four loads per stream in flight
+  const long long G = (long long)gridDim.x * blockDim.x;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; k + 3 * G < n; k += 4 * G) {
+    float acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) acc[u] = cx * g[k + u * G];
+    for (int j = 0; j < nv; j++) {
+      if (c[j] == 0.0f) continue;
+      const float *vj = V + j * stride + k;
+      float vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) vv[u] = vj[u * G];
+#pragma unroll
+      for (int u = 0; u < 4; u++) acc[u] += c[j] * vv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) d[k + u * G] = acc[u];
+  }
+  for (; k < n; k += G) {
     float acc = cx * g[k];
     for (int j = 0; j < nv; j++)
       if (c[j] != 0.0f) acc += c[j] * V[j * stride + k];
@@ -291,12 +321,25 @@ struct Minimiser {
     return e;
   }
   // trial point xt = x + a d: energy and directional derivative, read back
-  // with the rest of the state's block (rb: 6 doubles)
+  // with the rest of the state's block (rb: 6 doubles).  Two fluids: the
+  // energy goes straight into the block, and the constraint's constant is
+  // added to the gradient in the same pass that takes the slope.
   cudaError_t trial(double a, const float *x, float *xt, double *Et, float *gt, double *rb) {
     cudaError_t e = vec_lincomb(n, 1, d, n, &a, x, 1.0, xt, st);
-    if (e == cudaSuccess) e = evaluate(xt, Et, gt);
-    if (e == cudaSuccess) e = vec_dot(n, gt, d, vout, nullptr, vec_scr, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(vout + 1, Et, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (multi) {
+      if (e == cudaSuccess) e = evaluate(xt, Et, gt);
+      if (e == cudaSuccess) e = vec_dot(n, gt, d, vout, nullptr, vec_scr, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(vout + 1, Et, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else {
+      FEArgs b = fa;
+      b.c1 = active == 2 ? fixed : xt;
+      b.c2 = active == 2 ? xt : fixed;
+      b.grad = gt;
+      const double *cst = nullptr;
+      if (e == cudaSuccess) e = fe_launch(kind, b, dP, kcs, V0, vout + 1, nullptr, fe_scr, st, &cst);
+      if (e == cudaSuccess) e = vec_trial_slope(n, cst, gt, d, vout, vec_scr, st);
+    }
     if (e == cudaSuccess) e = read(rb, vout, 6);
     return e;
   }
@@ -331,8 +374,10 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
     if ((expr) != cudaSuccess) return DSM_E_CUDA;   \
   } while (0)
 
-  // stored pairs start at zero, so unused slots add nothing to a combination
+  // stored pairs start at zero, so unused slots add nothing to a combination;
+  // the fused slope pass's block counter starts at zero
   CK(cudaMemsetAsync(M.hist, 0, (size_t)2 * m * n * sizeof(float), st));
+  CK(cudaMemsetAsync(vec_scratch_counter(M.vec_scr), 0, sizeof(unsigned), st));
   lb_init_kernel<<<1, 1, 0, st>>>(M.state);
   CK(cudaGetLastError());
   int cur = 0;  // x = xb[cur], g = gb[cur], E = E[cur]
@@ -346,11 +391,12 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
   int converged = 0;
   bool fresh = false;  // gg is that of the current point (read after its last update)
   const double *pending = nullptr;  // the accepted step's dots, not yet folded into the state
+  double pending_sy = 0.0;          // and its pair's s.y
   while (it < max_iter) {
     // the pair update and the direction on the device, then the first trial
     // (a = 1), whose read also brings |g|^2 of the current point and the
     // direction's slope
-    lb_step_kernel<<<1, 32, 0, st>>>(M.state, pending, m);
+    lb_step_kernel<<<1, 32, 0, st>>>(M.state, pending, m, pending_sy);
     CK(cudaGetLastError());
     pending = nullptr;
     const float *x = M.xb[cur];
@@ -455,21 +501,23 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
     }
     if (last != step) {  // the accepted point is not the last one evaluated
       CK(M.trial(step, x, xt, Et, gt, rb));
+      df = rb[0];
       f = rb[1];
       evals++;
     }
     // new pair s = step d, y = g_new - g into slot nxt; every stored s, y
-    // against y_new and against g_new in one batched pass, s.s and g_new.g_new;
-    // the device updates its state (no host read)
+    // against g_new in one batched pass (the new pair's included), then y.y,
+    // g_new.g_new and s.s; s.y = step (g_new.d - g.d) from the slopes.  The
+    // device folds them into its state (no host read).
     float *s_new = M.hist + (size_t)nxt * n;
     float *y_new = M.hist + (size_t)(m + nxt) * n;
     const double minus1 = -1.0;
     CK(vec_axpby(n, step, M.d, 0.0, s_new, st));
     CK(vec_lincomb(n, 1, g, n, &minus1, gt, 1.0, y_new, st));
-    CK(vec_dots2(n, 2 * m, M.hist, n, y_new, gt, M.dots, M.dots_scr, st));
-    CK(vec_dot(n, s_new, s_new, M.dots + 4 * m, nullptr, M.vec_scr, st));
-    CK(vec_dot(n, gt, gt, M.dots + 4 * m + 1, nullptr, M.vec_scr, st));
+    CK(vec_dots(n, 2 * m, M.hist, n, gt, M.dots, M.dots_scr, st));
+    CK(vec_sumsq3(n, y_new, gt, s_new, M.dots + 2 * m, M.dots_scr, st));
     pending = M.dots;  // folded in by the next iteration's lb_step_kernel
+    pending_sy = step * (df - dg0);
     fresh = false;
     cur ^= 1;
     f_val = f;
@@ -481,7 +529,7 @@ static dsm_status run_lbfgs(Minimiser &M, char *w, const size_t off[12], float *
       cudaMemcpyAsync(d_x, M.xb[cur], n * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return DSM_E_CUDA;
   if (!fresh) {  // |g|^2 of the last accepted point (its dots hold g.g)
-    if (M.read(rb, M.dots + 4 * m + 1, 1) != cudaSuccess) return DSM_E_CUDA;
+    if (M.read(rb, M.dots + 2 * m + 1, 1) != cudaSuccess) return DSM_E_CUDA;
     gg = rb[0];
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return DSM_E_CUDA;
@@ -522,7 +570,7 @@ static size_t lbfgs_layout_n(long long n, int m, size_t fe_bytes, size_t off[12]
   off[3] = take(n * sizeof(float));               // d
   off[4] = take((size_t)2 * m * n * sizeof(float));  // s_0..s_{m-1}, y_0..y_{m-1}
   off[5] = take(2 * sizeof(double));              // E, Et
-  off[6] = take((size_t)(4 * m + 2) * sizeof(double));  // batched dots, then s.s and g.g
+  off[6] = take((size_t)(2 * m + 3) * sizeof(double));  // S^T g, Y^T g, then y.y, g.g, s.s
   off[7] = take(sizeof(LbState));                 // the pair bookkeeping on the device
   off[8] = take(fe_bytes);
   off[9] = take(vec_scratch_bytes(n));
