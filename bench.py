@@ -998,6 +998,32 @@ def run_multi(args, rank, world):
     return 0
 
 
+def _em_iterations(args, case, p, dev):
+    """A fixed number of L-BFGS iterations (tol 0) on the 128^3 sphere case, for
+    profiling one iteration: prints the wall time per iteration."""
+    import torch
+    import paper_2504_19941_gb300 as P
+    from paper_2504_19941_gb300.energy import FreeEnergy, lbfgs
+    lat = P.Lattice(P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg,
+                                  g23=case.g23, g12=case.g12, alpha_s=1.0), device=dev)
+    lat.set_solid_distance(torch.as_tensor(case.solid_sd, dtype=torch.float32, device=dev))
+    c1 = lat.field("C1")
+    del lat
+    c2 = torch.as_tensor(case.c2, dtype=torch.float32, device=dev)
+    fe = FreeEnergy(p, device=dev)
+    V0 = float(c2.double().sum())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, E, info = lbfgs(fe, c2, c1, active=2, kcs=1e-2, V0=V0, tol=0.0, max_iter=args.lbfgs_iters)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    print(json.dumps({"metric": "L-BFGS wall time per iteration (128^3 sphere at the interface)",
+                      "value": wall / max(info["iterations"], 1) * 1e6, "unit": "us",
+                      "higher_is_better": False, "iterations": info["iterations"],
+                      "evaluations": info["evaluations"]}), flush=True)
+    return 0
+
+
 def run_critical(args, rank, world):
     """Critical pressure of the Cassie-Baxter to Wenzel transition on 2D pillars
     (Sec. III) by bisection over GPU energy minimisations, for a sweep of five
@@ -1065,6 +1091,8 @@ def run_em(args, rank, world):
     n = case.n
     p = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg, g23=case.g23,
                       g12=case.g12)
+    if args.lbfgs_iters > 0:
+        return _em_iterations(args, case, p, dev)
     # the solid's tanh profile of Sec. II.A, written by the library from the distance
     lat_p = P.make_params("D3Q19", case.shape, "f32", theta_deg=case.theta_deg, g23=case.g23,
                           g12=case.g12, alpha_s=1.0)
@@ -1194,6 +1222,8 @@ def main():
                     help="six comma-separated faces x-,x+,y-,y+,z-,z+: periodic, mirror or wall")
     ap.add_argument("--step-form", default="auto", choices=["auto", "two_pass"],
                     help="auto: one pass per step where the lattice allows it")
+    ap.add_argument("--lbfgs-iters", type=int, default=0,
+                    help="--workload em: only this many L-BFGS iterations (tol 0), for profiling")
     ap.add_argument("--nfluid", type=int, default=3, choices=[3, 4],
                     help="fluid components of --workload multi")
     ap.add_argument("--zrun", type=int, default=0,
