@@ -133,7 +133,8 @@ dsm_status dsm_kappa(const dsm_params *p, double kappa_out[3]);
  * buffers each; C1; C, two buffers; the four g_eq planes; solid mask;
  * reduction scratch; for lattices the one-pass step applies to (see
  * dsm_set_step_form), padded (A, u, C), two buffers, and padded C1:
- * 11 reals per padded node, (nx + 8)(ny + 4) nz nodes). */
+ * 11 reals per padded node, (nx + 8, rounded up to a multiple of 4)(ny + 4) nz
+ * nodes). */
 dsm_status dsm_workspace_bytes(const dsm_params *p, size_t *bytes);
 
 /* Create a handle over a caller-owned device workspace (>= the size above,
@@ -196,9 +197,10 @@ dsm_status dsm_set_body_force(dsm_lattice *h, const double *body);
 /* How dsm_step advances a lattice.  The step of Sec. II.B needs C = sum_i g_i
  * of the streamed populations on each node's neighbourhood before it can form
  * mu, so dsm_step normally runs it as the two passes above.  For D3Q19 lattices
- * with nx a multiple of 32, ny a multiple of 8, tau_g = 1 (g held as g_eq, see
+ * with nx >= 32, ny >= 8, tau_g = 1 (g held as g_eq, see
  * dsm_set_g_storage) and periodic faces, DSM_STEP_AUTO instead runs each step
- * as ONE pass: blocks march 32 x 8 tiles up runs of z planes, rebuild the C of
+ * as ONE pass: blocks march 32 x 8 tiles (the last ones ragged) up runs of z
+ * planes, rebuild the C of
  * the step on chip from the staged (A, u, C) of the previous collision and
  * collide.  The results are the same step (the same per-node arithmetic, so
  * equal to the two-pass step up to nothing but FP32 contraction order); the
@@ -514,13 +516,14 @@ dsm_status dsm_ml_destroy(dsm_mlattice *h);
 
 /* How dsm_ml_step advances an N-fluid lattice, as dsm_set_step_form does for
  * two fluids.  For D3Q19 lattices that hold every g_f as g_eq (tau_g = 1,
- * periodic faces) with nx a multiple of 32 and ny a multiple of 8,
+ * periodic faces) with nx >= 32 and ny >= 8,
  * DSM_STEP_AUTO runs each step as ONE pass: blocks march 32 x 8 tiles up runs
  * of z planes, stage the previous collision's (A_f, C_f) of every free fluid,
  * u and C1 into shared memory by tensor-memory-accelerator copies, rebuild
  * every C_f of the step on the tile and a one-node halo, and run the fused
  * pass from there.  The same step up to FP contraction order; the state then
- * lives in padded buffers of the workspace (per padded node, (nx + 8)(ny + 4)
+ * lives in padded buffers of the workspace (per padded node, (nx + 8 rounded
+ * up to a multiple of 4)(ny + 4)
  * nz of them, two buffers of 5 + 2 (N - 2) reals, and C1; included in
  * dsm_ml_workspace_bytes) and is converted back before dsm_ml_get_field or
  * dsm_ml_get_populations reads it.  A staged plane that never arrives (a

@@ -106,14 +106,15 @@ struct Layout {
   size_t f[2], g[2], g0[2], C[2], M, C1, mask, partials, obs, err, Qz[2], Uz[2], C1z, total;
 };
 
-// The single-pass step applies to D3Q19 lattices whose planes tile into 32 x 8
-// blocks, with tau_g = 1 (g held as g_eq) and periodic faces.
+// The single-pass step applies to D3Q19 lattices at least one 32 x 8 tile wide
+// (the last tiles may be ragged), with tau_g = 1 (g held as g_eq) and periodic
+// faces.
 bool z_eligible(const dsm_params *p) {
   if (p->lattice != DSM_D3Q19 || p->tau_g != 1.0 || has_walls(p)) return false;
-  return p->nx % ZT_X == 0 && p->ny % ZT_Y == 0;
+  return z_tiles(p->nx, p->ny);
 }
 long long z_padded_nodes(const dsm_params *p) {
-  return (long long)(p->nx + 2 * ZPAD_X) * (p->ny + 2 * ZPAD_Y) * p->nz;
+  return (long long)z_padded_x(p->nx) * z_padded_y(p->ny) * p->nz;
 }
 
 long long obs_blocks_of(int kind, int nx, int ny, int nz) {
@@ -233,7 +234,7 @@ int z_auto_run(dsm_lattice *h) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long resident = (long long)(sms > 0 ? sms : 152) * (h->tab.zresident() > 0 ? h->tab.zresident() : 1);
-  const long long tiles = (long long)(h->prm.nx / ZT_X) * (h->prm.ny / ZT_Y);
+  const long long tiles = (long long)z_tiles_x(h->prm.nx) * z_tiles_y(h->prm.ny);
   const int nz = h->prm.nz;
   double best = 1e300;
   int run = nz;
@@ -414,8 +415,8 @@ dsm_status dsm_create(const dsm_params *p, void *d_workspace, size_t bytes, void
   h->err = (int *)(h->ws + L.err);
   h->obs_blocks = obs_blocks_of(p->lattice, p->nx, p->ny, p->nz);
   h->zok = z_eligible(p);
-  h->nxp = p->nx + 2 * ZPAD_X;
-  h->nyp = p->ny + 2 * ZPAD_Y;
+  h->nxp = z_padded_x(p->nx);
+  h->nyp = z_padded_y(p->ny);
   for (int b = 0; b < 2; b++) {
     h->Qz[b] = h->zok ? h->ws + L.Qz[b] : nullptr;
     h->Uz[b] = h->zok ? h->ws + L.Uz[b] : nullptr;

@@ -1406,8 +1406,9 @@ struct LBOps {
       return cudaErrorNotSupported;
     } else {
       if (!zprepare()) return cudaErrorInvalidValue;
-      if (zrun < 1 || r.nx % ZT_X || r.ny % ZT_Y) return cudaErrorInvalidValue;
-      const dim3 grid(r.nx / ZT_X, r.ny / ZT_Y, (r.nz + zrun - 1) / zrun), blk(ZT_X, ZT_Y, 1);
+      if (zrun < 1 || !z_tiles(r.nx, r.ny)) return cudaErrorInvalidValue;
+      const dim3 grid(z_tiles_x(r.nx), z_tiles_y(r.ny), (r.nz + zrun - 1) / zrun),
+          blk(ZT_X, ZT_Y, 1);
       if (r.p.rho_contrast)
         zstep_kernel<T, S, true><<<grid, blk, ZSmem<T>::total, st>>>(typed<T, S>(r), zrun, m.Q, m.U, m.C1);
       else

@@ -115,7 +115,8 @@ struct MLZIO {
   }
 };
 
-// One N-fluid step.  Grid (nx / 32, ny / 8, ceil(nz / zrun)); block 32 x 8;
+// One N-fluid step.  Grid (ceil(nx / 32), ceil(ny / 8), ceil(nz / zrun)); block
+// 32 x 8 (threads of a ragged last tile beyond the lattice run no pass);
 // a.Qz / a.Uz / a.Pz receive this step's state.  tmQ: the padded quads of
 // the state (4 nxp, nyp, nz); tmU: its u_z (nxp, nyp, nz); tmP: its pairs
 // (2 nxp, nyp, (NF - 1) nz; any valid map when NF = 1); tmC1: padded C1.

@@ -586,9 +586,10 @@ struct MLLayout {
 // g held as g_eq: tau_g = 1 and every face periodic
 bool ml_eq(const dsm_params *p) { return p->tau_g == 1.0 && !has_walls(p); }
 
-// the single-pass step applies: D3Q19, g held as g_eq, whole 32 x 8 tiles
+// the single-pass step applies: D3Q19, g held as g_eq, at least one 32 x 8
+// tile (the last tiles may be ragged)
 bool ml_z_eligible(const dsm_params *p) {
-  return p->lattice == DSM_D3Q19 && ml_eq(p) && p->nx % ZT_X == 0 && p->ny % ZT_Y == 0;
+  return p->lattice == DSM_D3Q19 && ml_eq(p) && z_tiles(p->nx, p->ny);
 }
 
 MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq,
@@ -609,7 +610,7 @@ MLLayout ml_layout(int q, int nf, int real_bytes, long long pitch, bool eq,
   // padded buffers of the single-pass step: per padded node a quad, u_z and
   // nf - 1 pairs (two buffers), and C1
   const bool z = p && ml_z_eligible(p);
-  const size_t P = z ? (size_t)(p->nx + 2 * ZPAD_X) * (p->ny + 2 * ZPAD_Y) * p->nz : 0;
+  const size_t P = z ? (size_t)z_padded_x(p->nx) * z_padded_y(p->ny) * p->nz : 0;
   for (int b = 0; b < 2; b++) {
     L.Qz[b] = take(4 * P * real_bytes);
     L.Uz[b] = take(P * real_bytes);
@@ -810,7 +811,8 @@ struct MLZ {
   }
   static cudaError_t step(const MLArgs<T> &a, const CUtensorMap *m, int zrun, cudaStream_t s) {
     if (!prepare()) return cudaErrorInvalidValue;
-    const dim3 grid(a.nx / ZT_X, a.ny / ZT_Y, (a.nz + zrun - 1) / zrun), blk(ZT_X, ZT_Y, 1);
+    const dim3 grid(z_tiles_x(a.nx), z_tiles_y(a.ny), (a.nz + zrun - 1) / zrun),
+        blk(ZT_X, ZT_Y, 1);
     if (a.rc)
       mlz_kernel<T, NF, true><<<grid, blk, MLZSmem<T, NF>::total, s>>>(a, zrun, m[0], m[1], m[2], m[3]);
     else
@@ -877,7 +879,7 @@ int mlz_auto_run(dsm_mlattice *h) {
     return cudaSuccess;
   });
   const long long resident = (long long)(sms > 0 ? sms : 152) * (per_sm > 0 ? per_sm : 1);
-  const long long tiles = (long long)(h->prm.nx / ZT_X) * (h->prm.ny / ZT_Y);
+  const long long tiles = (long long)z_tiles_x(h->prm.nx) * z_tiles_y(h->prm.ny);
   const int nz = h->prm.nz;
   double best = 1e300;
   int run = nz;
@@ -1009,8 +1011,8 @@ dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa, c
   h->M = h->eq ? w + L.M : nullptr;
   h->err = (int *)(w + L.err);
   h->zok = ml_z_eligible(p);
-  h->nxp = p->nx + 2 * ZPAD_X;
-  h->nyp = p->ny + 2 * ZPAD_Y;
+  h->nxp = z_padded_x(p->nx);
+  h->nyp = z_padded_y(p->ny);
   for (int b = 0; b < 2 && h->zok; b++) {
     h->Qz[b] = w + L.Qz[b];
     h->Uz[b] = w + L.Uz[b];

@@ -67,6 +67,18 @@ struct ZSmem {
   static constexpr unsigned tx_bytes = sizeof(T) * (4 * ZB_X * ZB_Y + ZB_X * ZB_Y + ZB_X * ZB1_Y);
 };
 
+// Width and height of a padded plane: 4 ghost columns and 2 ghost rows on each
+// side, the width rounded up to a multiple of 4 reals so that every row starts
+// on a 16-byte boundary (the tensor maps' strides).  A lattice of any nx >= 32,
+// ny >= 8 tiles into 32 x 8 blocks, the last ones ragged: their threads beyond
+// the lattice take part in the rebuild and the barriers but run no pass, and
+// boxes reaching past the padded planes read zeros (never used).
+__host__ __device__ __forceinline__ int z_padded_x(int nx) { return (nx + 2 * ZPAD_X + 3) / 4 * 4; }
+__host__ __device__ __forceinline__ int z_padded_y(int ny) { return ny + 2 * ZPAD_Y; }
+__host__ __device__ __forceinline__ bool z_tiles(int nx, int ny) { return nx >= ZT_X && ny >= ZT_Y; }
+__host__ __device__ __forceinline__ int z_tiles_x(int nx) { return (nx + ZT_X - 1) / ZT_X; }
+__host__ __device__ __forceinline__ int z_tiles_y(int ny) { return (ny + ZT_Y - 1) / ZT_Y; }
+
 // Padded index of node (x, y, z), x in [-ZPAD_X, nx + ZPAD_X), y in [-ZPAD_Y, ny + ZPAD_Y).
 __host__ __device__ __forceinline__ long long zpidx(int x, int y, int z, int nxp, int nyp) {
   return ((long long)z * nyp + (y + ZPAD_Y)) * nxp + (x + ZPAD_X);
@@ -166,7 +178,7 @@ struct ZIO {
   }
 };
 
-// K2z: one step.  Grid (nx / 32, ny / 8, ceil(nz / zrun)); block 32 x 8;
+// K2z: one step.  Grid (ceil(nx / 32), ceil(ny / 8), ceil(nz / zrun)); block 32 x 8;
 // a.Qz / a.Uz receive this step's quads (A, C, u_x, u_y) and u_z.  tmQ: the
 // padded quads of the state, as a 3-D tensor (4 nxp, nyp, nz); tmU: its u_z
 // (nxp, nyp, nz); tmC1: padded C1 (nxp, nyp, nz).
@@ -258,6 +270,7 @@ __global__ void __launch_bounds__(ZT_X *ZT_Y, sizeof(T) == 8 ? 1 : 3)
   ZIO<T> io;
   io.x = x0 + tx;
   io.y = y0 + ty;
+  const bool inside = io.x < a.nx && io.y < a.ny;  // ragged last tiles
   // ring positions at plane z, advanced by one each plane: sk, the slot of
   // staged plane z - 1; cq, the C ring slot of plane z - 1
   auto next5 = [](int v) { return v + 1 == Z_RING ? 0 : v + 1; };
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(ZT_X *ZT_Y, sizeof(T) == 8 ? 1 : 3)
     io.c1o[1] = s1 * SM::slot + node_c1;
     io.c1o[2] = s2 * SM::slot + node_c1;
     io.z = z;
-    node_body<1, T, S, 2, MODE_STEP, RC, true, false, ZIO<T>>(a, io.x, io.y, z, true, 0, io);
+    node_body<1, T, S, 2, MODE_STEP, RC, true, false, ZIO<T>>(a, io.x, io.y, z, inside, 0, io);
     sk = s1;
     cq = (cq + 1) & (Z_CRING - 1);
   }

@@ -137,16 +137,22 @@ def test_invalid_faces_refused_by_energy_functions(lib):
 
 @pytest.mark.parametrize("prec,sb,extra", [("f64", 8, 0), ("f32", 4, 0), ("bf16", 2, 1),
                                            ("f16", 2, 1)])
-def test_workspace_size(lib, prec, sb, extra):
+@pytest.mark.parametrize("shape", [(37, 29, 23), (21, 29, 23)])
+def test_workspace_size(lib, prec, sb, extra, shape):
     import paper_2504_19941_gb300 as P
-    shape = (37, 29, 23)
-    n = 37 * 29 * 23
+    nx, ny, nz = shape
+    n = nx * ny * nz
     p = P.make_params("D3Q19", shape, prec, theta_deg=100.0)
     nbytes = lib.dsm_workspace_bytes(p)
     pops = 4 * 19 * n * sb + extra * 2 * 4 * n
     # plus seven real fields (C1, C in two buffers, the four g_eq planes A, u),
     # the mask bytes and small reduction scratch
-    reals = 7 * n * (8 if prec == "f64" else 4)
+    rb = 8 if prec == "f64" else 4
+    reals = 7 * n * rb
+    # nx >= 32, ny >= 8: the one-pass step's padded buffers, 11 reals per node
+    # of (nx + 8 rounded up to a multiple of 4) (ny + 4) nz
+    if nx >= 32 and ny >= 8:
+        reals += 11 * ((nx + 8 + 3) // 4 * 4) * (ny + 4) * nz * rb
     assert pops + reals + n <= nbytes <= pops + reals + n + 10 * 2 ** 16
 
 
