@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "dsm_common.cuh"
+#include "dsm_pair.cuh"
 #include "dsm_reduce.cuh"
 
 namespace dsm {
@@ -242,7 +243,10 @@ __device__ __forceinline__ T geq_core(T A, T C, T cu) {
 template <class L, class T>
 __device__ __forceinline__ T moments_eq_node(const T (&Ay)[L::Q], const T (&Cy)[L::Q],
                                              const T (&uy)[L::Q][3]) {
-  T sa = T(0), sd = T(0);  // axis and diagonal links (one weight each)
+  // axis and diagonal links (one weight each).  Link by link: pairing the
+  // opposite links as the N-fluid rebuild does cost registers here (the
+  // one-pass kernel spilled and ran 4 % slower).
+  T sa = T(0), sd = T(0);
 #pragma unroll
   for (int i = 1; i < L::Q; i++) {
     const T v = geq_core(Ay[i], Cy[i], cdot<L>(i, uy[i][0], uy[i][1], uy[i][2]));
@@ -497,14 +501,24 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     C = Cn[0];
     c1 = C1n[0];
     T lapC = T(0), lapS = T(0);
+    // the two Laplacian sums as one pair per neighbour (stage 2)
+    Pr<T> lap2 = pr(T(0), T(0));
+    const Pr<T> mc = pr(-C, -c1);
 #pragma unroll
     for (int i = 1; i < Q; i++) {
       const T w = T(L::w(i));
-      lapC += w * (Cn[i] - C);
-      if (STAGE == 2) lapS += w * (C1n[i] - c1);
+      if (STAGE == 2) {
+        lap2 = pr_fma(pr(w, w), pr_add(pr(Cn[i], C1n[i]), mc), lap2);
+      } else {
+        lapC += w * (Cn[i] - C);
+      }
       if (L::cx(i)) gC[0] += w * T(L::cx(i)) * Cn[i];
       if (L::cy(i)) gC[1] += w * T(L::cy(i)) * Cn[i];
       if (L::cz(i)) gC[2] += w * T(L::cz(i)) * Cn[i];
+    }
+    if (STAGE == 2) {
+      lapC = lap2.a;
+      lapS = lap2.b;
     }
     lapC *= T(6);  // 2 / c_s^2
     lapS = lapC + T(6) * lapS;  // L[C1 + C] = L[C] + L[C1]
@@ -824,26 +838,36 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     const T cu = cdot<L>(i, u[0], u[1], u[2]);
     const T even = T(4.5) * cu * cu - m15uu;
     const T odd = T(3) * cu;
-    const T sp = even + odd, sm = even - odd;
+    // the opposite pair (i, ib) as one pair of values: s = even +- odd, and
+    // every later operation once for both
+    const Pr<T> pm = pr(T(1), T(-1)), m1 = pr(T(-1), T(-1));
+    const Pr<T> s2 = pr_fma(pr(odd, odd), pm, pr(even, even));
     T fp = w, fm = w;
     if (!solid_x) {
       const T wpt = w * pt, wr = w * rho;
       const T cF = cdot<L>(i, Fv[0], Fv[1], Fv[2]);
-      T Fp = w * kF3 * cF, Fm = -Fp;
+      const T Fp = w * kF3 * cF;
+      Pr<T> F2 = pr(Fp, -Fp);
       if (RC) {
         const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);
-        Fp += kF * w * ((cg - ug) * sp);
-        Fm += kF * w * ((-cg - ug) * sm);
+        const T kw = kF * w;
+        F2 = pr_fma(pr(kw, kw), pr_mul(pr(cg - ug, -cg - ug), s2), F2);
       }
-      fp = f[i] + (wpt + wr * sp - f[i]) * omf + Fp;
-      fm = f[ib] + (wpt + wr * sm - f[ib]) * omf + Fm;
+      const Pr<T> f2 = pr(f[i], f[ib]);
+      const Pr<T> eq = pr_fma(pr(wr, wr), s2, pr(wpt, wpt));  // w (pt + rho s)
+      const Pr<T> o = pr_add(pr_fma(pr_fma(f2, m1, eq), pr(omf, omf), f2), F2);
+      fp = o.a;
+      fm = o.b;
     }
     put_f(i, fp);
     put_f(ib, fm);
     if constexpr (!EQ) {
       const T wmu = w * mu, wC = w * C;
-      put_g(i, g[i] + (wmu + wC * sp - g[i]) * omg);
-      put_g(ib, g[ib] + (wmu + wC * sm - g[ib]) * omg);
+      const Pr<T> g2 = pr(g[i], g[ib]);
+      const Pr<T> geq = pr_fma(pr(wC, wC), s2, pr(wmu, wmu));
+      const Pr<T> go = pr_fma(pr_fma(g2, m1, geq), pr(omg, omg), g2);
+      put_g(i, go.a);
+      put_g(ib, go.b);
     }
   }
   if constexpr (EQ) {

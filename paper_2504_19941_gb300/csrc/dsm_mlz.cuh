@@ -178,52 +178,56 @@ __global__ void __launch_bounds__(ZT_X *ZT_Y, sizeof(T) == 8 ? 1 : 2)
   // (moments_eq_node), with u read once for all fluids
   auto rebuild_c = [&](unsigned m0, unsigned m1, unsigned m2, unsigned cdst) {
     for (int r = 0; r < nc; r++) {
-      T sa[NF], sd[NF], A0[NF], C0[NF], u0[3];
-#pragma unroll
-      for (int f = 0; f < NF; f++) sa[f] = sd[f] = T(0);
-#pragma unroll
-      for (int i = 0; i < L::Q; i++) {
+      // the staged values of link i at x - c_i: A_f, C_f, u (u_z only where
+      // c_i has a z component, or at the node itself)
+      auto link = [&](int i, T (&Af)[NF], T (&Cf)[NF], T (&ul)[3]) {
         const unsigned sl = L::cz(i) > 0 ? m0 : (L::cz(i) < 0 ? m2 : m1);
         const int p = bo[r] - (L::cy(i) * ZB_X + L::cx(i));  // box index of x - c_i
         const Quad<T> m = *reinterpret_cast<const Quad<T> *>(zsm + sl + sizeof(Quad<T>) * p);
-        const T uz = (i == 0 || L::cz(i))
-                         ? *reinterpret_cast<const T *>(zsm + sl + SM::woff + sizeof(T) * p)
-                         : T(0);
-        T Af[NF], Cf[NF];
+        ul[0] = m.v[2];
+        ul[1] = m.v[3];
+        ul[2] = (i == 0 || L::cz(i))
+                    ? *reinterpret_cast<const T *>(zsm + sl + SM::woff + sizeof(T) * p)
+                    : T(0);
         Af[0] = m.v[0];
         Cf[0] = m.v[1];
 #pragma unroll
         for (int e = 1; e < NF; e++) {
-          const Pair<T> pr = *reinterpret_cast<const Pair<T> *>(
+          const Pair<T> q = *reinterpret_cast<const Pair<T> *>(
               zsm + sl + SM::poff + (e - 1) * SM::pbox + sizeof(Pair<T>) * p);
-          Af[e] = pr.v[0];
-          Cf[e] = pr.v[1];
+          Af[e] = q.v[0];
+          Cf[e] = q.v[1];
         }
-        if (i == 0) {
+      };
+      T A0[NF], C0[NF], u0[3];
+      link(0, A0, C0, u0);
+      // opposite links (i, i + 1) of one weight as one pair: c.u and
+      // cu (3 + 9/2 cu) once for every fluid, then A + C t per fluid
+      // (moments_eq_node's arithmetic, paired; dsm_pair.cuh)
+      Pr<T> sa[NF], sd[NF];
 #pragma unroll
-          for (int f = 0; f < NF; f++) {
-            A0[f] = Af[f];
-            C0[f] = Cf[f];
-          }
-          u0[0] = m.v[2];
-          u0[1] = m.v[3];
-          u0[2] = uz;
-        } else {
-          const T cu = cdot<L>(i, m.v[2], m.v[3], uz);
+      for (int f = 0; f < NF; f++) sa[f] = sd[f] = pr(T(0), T(0));
 #pragma unroll
-          for (int f = 0; f < NF; f++) {
-            const T v = geq_core(Af[f], Cf[f], cu);
-            if (L::w(i) == L::w(1)) sa[f] += v;
-            else sd[f] += v;
-          }
+      for (int i = 1; i < L::Q; i += 2) {
+        T Ai[NF], Ci[NF], ui[3], Ab[NF], Cb[NF], ub[3];
+        link(i, Ai, Ci, ui);
+        link(i + 1, Ab, Cb, ub);
+        const Pr<T> cu = pr(cdot<L>(i, ui[0], ui[1], ui[2]), cdot<L>(i + 1, ub[0], ub[1], ub[2]));
+        const Pr<T> t = pr_mul(cu, pr_fma(pr(T(4.5), T(4.5)), cu, pr(T(3), T(3))));
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+          const Pr<T> v = pr_fma(pr(Ci[f], Cb[f]), t, pr(Ai[f], Ab[f]));
+          if (L::w(i) == L::w(1)) sa[f] = pr_add(sa[f], v);
+          else sd[f] = pr_add(sd[f], v);
         }
       }
       const T uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
 #pragma unroll
       for (int f = 0; f < NF; f++) {
         const T out = T(1.0 - L::w(0)) * A0[f] + T(1.5) * C0[f] * uu0;
+        const T saf = sa[f].a + sa[f].b, sdf = sd[f].a + sd[f].b;
         reinterpret_cast<T *>(zsm + cdst + f * SM::cplane)[tid + r * ZT_X * ZT_Y] =
-            C0[f] + ((T(L::w(1)) * sa[f] + T(L::w(L::Q - 1)) * sd[f]) - out);
+            C0[f] + ((T(L::w(1)) * saf + T(L::w(L::Q - 1)) * sdf) - out);
       }
     }
   };

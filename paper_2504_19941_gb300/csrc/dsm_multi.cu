@@ -28,6 +28,7 @@
 #include <new>
 
 #include "dsm_lb_impl.cuh"
+#include "dsm_pair.cuh"
 #include "dsm_tmap.cuh"
 #include "dsm_trace.cuh"
 
@@ -44,10 +45,15 @@ struct MLArgs {
   T kappa[ML_MAX_NF + 2];            // kappa_1, the free fluids', the dependent fluid's
   T rho[ML_MAX_NF + 1], om[ML_MAX_NF + 1];  // per fluid: density, 1 / tau
   T omg, a2, alpha_s;
+  T irho;                // 1 / rho of the dependent fluid (every rho when they are equal)
   T body[3];
   int rc;                // the fluids' densities differ (else rho is constant)
   const T *f_in, *g_in;  // Q planes; NF x Q planes (fluid-major)
   T *f_out, *g_out;
+  // the f planes one by one (fin[j] = f_in + j pitch): a pull or a store
+  // addresses its plane from a kernel parameter, with no 64-bit multiply
+  const T *fin[19];
+  T *fout[19];
   T *C;                  // NF planes: the moments pass output
   const T *Cprev;        // g_eq form: NF planes, C of the state's last collision
   T *A;                  // g_eq form: NF planes of A_f = mu_f - 3/2 C_f u.u
@@ -216,6 +222,7 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   // ---- the neighbourhood: C1 and the free fluids, stencils of every component
   T cv[NC], lap[NC], gC[NF][3], gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
   unsigned nb_solid = 0;  // bit i: x + c_i is solid
+  T c1max = T(0);         // one-pass form: the largest C1 of the neighbours
   cv[0] = io.template C1<L>(a, h, n, 0);
   T last = T(1) - cv[0];
 #pragma unroll
@@ -229,32 +236,81 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
 #pragma unroll
   for (int f = 0; f < NF; f++) gC[f][0] = gC[f][1] = gC[f][2] = T(0);
   // (gradient components only where c_i has one: w 0 c is an operation IEEE
-  // arithmetic cannot drop, and for finite values it adds nothing)
+  // arithmetic cannot drop, and for finite values it adds nothing.)  The
+  // Laplacian sums of C1 and the free fluids go in pairs of components, the
+  // gradient of two free fluids as one pair per component (dsm_pair.cuh).
+  constexpr int NP = (NF + 1) / 2;  // pairs among components 0 .. NF
+  Pr<T> lapP[NP > 0 ? NP : 1], mctr[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    lapP[k] = pr(T(0), T(0));
+    mctr[k] = pr(-cv[2 * k], -cv[2 * k + 1]);
+  }
 #pragma unroll
   for (int i = 1; i < Q; i++) {
     const T w = T(L::w(i));
     const T cx = T(L::cx(i)), cy = T(L::cy(i)), cz = T(L::cz(i));
     const T c1m = io.template C1<L>(a, h, n, i);
-    T cm[NF];
+    T cm[NF], val[NF + 1];
+    val[0] = c1m;
 #pragma unroll
     for (int f = 0; f < NF; f++) {
       cm[f] = io.template C<L>(a, h, n, f, i);
-      lap[1 + f] += w * (cm[f] - cv[1 + f]);
-      if (L::cx(i)) gC[f][0] += w * cx * cm[f];
-      if (L::cy(i)) gC[f][1] += w * cy * cm[f];
-      if (L::cz(i)) gC[f][2] += w * cz * cm[f];
+      val[1 + f] = cm[f];
     }
-    lap[0] += w * (c1m - cv[0]);
+#pragma unroll
+    for (int k = 0; k < NP; k++)
+      lapP[k] = pr_fma(pr(w, w), pr_add(pr(val[2 * k], val[2 * k + 1]), mctr[k]), lapP[k]);
+    if constexpr ((NF + 1) % 2) lap[NF] += w * (val[NF] - cv[NF]);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const int cd = d == 0 ? L::cx(i) : (d == 1 ? L::cy(i) : L::cz(i));
+      if (cd) {
+        const T wc = w * T(cd);
+#pragma unroll
+        for (int f = 0; f + 1 < NF; f += 2) {
+          const Pr<T> gg = pr_fma(pr(wc, wc), pr(cm[f], cm[f + 1]), pr(gC[f][d], gC[f + 1][d]));
+          gC[f][d] = gg.a;
+          gC[f + 1][d] = gg.b;
+        }
+        if constexpr (NF % 2) gC[NF - 1][d] += wc * cm[NF - 1];
+      }
+    }
     if (RCV && a.rc) {
       const T r = w * ml_rho<T, NF>(a, cm, c1m);
       if (L::cx(i)) gR[0] += r * cx;
       if (L::cy(i)) gR[1] += r * cy;
       if (L::cz(i)) gR[2] += r * cz;
     }
-    if (L::cx(i)) gc1[0] += w * cx * c1m;
-    if (L::cy(i)) gc1[1] += w * cy * c1m;
-    if (L::cz(i)) gc1[2] += w * cz * c1m;
-    if (c1m >= T(0.5)) nb_solid |= 1u << i;
+    if constexpr (IO::kZ) {
+      c1max = c1max > c1m ? c1max : c1m;
+    } else {
+      if (L::cx(i)) gc1[0] += w * cx * c1m;
+      if (L::cy(i)) gc1[1] += w * cy * c1m;
+      if (L::cz(i)) gc1[2] += w * cz * c1m;
+      if (c1m >= T(0.5)) nb_solid |= 1u << i;
+    }
+  }
+  // one-pass form: the wall-link bits and G[C1] only at a fluid node with a
+  // solid neighbour, from C1 in shared memory again (the same sums, in the
+  // same order); elsewhere one running maximum of C1 settles it
+  if constexpr (IO::kZ) {
+    if (c1max >= T(0.5) && !(cv[0] >= T(0.5))) {
+#pragma unroll
+      for (int i = 1; i < Q; i++) {
+        const T w = T(L::w(i));
+        const T c1m = io.template C1<L>(a, h, n, i);
+        if (L::cx(i)) gc1[0] += w * T(L::cx(i)) * c1m;
+        if (L::cy(i)) gc1[1] += w * T(L::cy(i)) * c1m;
+        if (L::cz(i)) gc1[2] += w * T(L::cz(i)) * c1m;
+        if (c1m >= T(0.5)) nb_solid |= 1u << i;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    lap[2 * k] = lapP[k].a;
+    lap[2 * k + 1] = lapP[k].b;
   }
   // the dependent fluid C_{N+1} = 1 - C_1 - sum_f C_f: its Laplacian by the
   // stencil's linearity, L[C_{N+1}] = -L[C_1] - sum_f L[C_f] (sum_i w_i (1 - 1) = 0)
@@ -300,7 +356,7 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
 #pragma unroll
   for (int j = 0; j < Q; j++) {
     const int src = h.minus<L>(j);
-    fs[j] = pull ? __ldg(plane(a.f_in, a.pitch, j) + src) : T(L::w(j));
+    fs[j] = pull ? __ldg(a.fin[j] + src) : T(L::w(j));
     if constexpr (!EQ) {
 #pragma unroll
       for (int f = 0; f < NF; f++)
@@ -319,15 +375,15 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
     // through a select over all directions (in the two-pass fused pass the
     // unrolled form ran slower)
     auto link = [&](int j, int i, T q) {
-      const T fi_x = plane(a.f_in, a.pitch, i)[n];
+      const T fi_x = a.fin[i][n];
       int ki = i;
       bool second = !((nb_solid >> j) & 1u);
       if (RTF && a.walls && face_cross<L>(a.face, x, y, z, a.nx, a.ny, a.nz, i, &ki) == 2)
         second = false;
       if (q < T(0.5) && second)
-        return T(2) * q * fi_x + (T(1) - T(2) * q) * plane(a.f_in, a.pitch, ki)[h.plus_rt<L>(j)];
+        return T(2) * q * fi_x + (T(1) - T(2) * q) * a.fin[ki][h.plus_rt<L>(j)];
       if (q < T(0.5)) return fi_x;
-      return (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * plane(a.f_in, a.pitch, j)[n];
+      return (T(1) / (T(2) * q)) * fi_x + (T(1) - T(1) / (T(2) * q)) * a.fin[j][n];
     };
     if constexpr (IO::kUnrollWall) {
 #pragma unroll
@@ -361,7 +417,7 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
         if (cr != 0) {
           const int src = cr == 2 ? n : h.plus_rt<L>(L::opp(j));
           const bool interp = cr == 1 && !solid_x && ((nb_solid >> L::opp(j)) & 1u);
-          if (!interp) fs[j] = plane(a.f_in, a.pitch, k)[src];
+          if (!interp) fs[j] = a.fin[k][src];
 #pragma unroll
           for (int f = 0; f < NF; f++)
             gs[f][j] = plane(a.g_in + (long long)f * Q * a.pitch, a.pitch, k)[src];
@@ -373,15 +429,22 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   // ---- moments: rho u = sum c f + F/2, pt = sum f + u.G[rho]/2
   T u[3] = {T(0), T(0), T(0)}, pt = T(1);
   if (!solid_x) {
-    T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
+    // opposite directions (j, j + 1) as one pair: their sum and difference
+    // in one operation, the sum into the density, the difference into the
+    // momentum (c_{j+1} = -c_j)
+    T m0 = fs[0], m1[3] = {T(0), T(0), T(0)};
+    const Pr<T> pmj = pr(T(1), T(-1));
 #pragma unroll
-    for (int j = 0; j < Q; j++) {
-      m0 += fs[j];
-      if (L::cx(j)) m1[0] += T(L::cx(j)) * fs[j];
-      if (L::cy(j)) m1[1] += T(L::cy(j)) * fs[j];
-      if (L::cz(j)) m1[2] += T(L::cz(j)) * fs[j];
+    for (int j = 1; j < Q; j += 2) {
+      const Pr<T> sd = pr_fma(pr(fs[j + 1], fs[j + 1]), pmj, pr(fs[j], fs[j]));
+      m0 += sd.a;
+      if (L::cx(j)) m1[0] += T(L::cx(j)) * sd.b;
+      if (L::cy(j)) m1[1] += T(L::cy(j)) * sd.b;
+      if (L::cz(j)) m1[2] += T(L::cz(j)) * sd.b;
     }
-    for (int e = 0; e < 3; e++) u[e] = (m1[e] + T(0.5) * F[e]) / rho;
+    // one reciprocal per node (with equal densities, the host's)
+    const T ir = RCV ? T(1) / rho : a.irho;
+    for (int e = 0; e < 3; e++) u[e] = (m1[e] + T(0.5) * F[e]) * ir;
     pt = RCV ? m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]) : m0;
   }
   if constexpr (MODE == ML_FIELDS) {
@@ -411,32 +474,68 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T ug = u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2];
   const T kF = T(1) - T(0.5) * om;
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    const T w = T(L::w(i));
-    // c_i . v over the components c_i has (cdot: no products by zero)
-    const T cu = cdot<L>(i, u[0], u[1], u[2]);
-    const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+  {  // rest population
+    const T w = T(L::w(0));
+    const T s = -(T(1.5) * uu);
     T fo = w;
     if (!solid_x) {
-      const T cF = cdot<L>(i, F[0], F[1], F[2]);
-      T Fi;
-      if constexpr (RCV) {
-        const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);
-        Fi = kF * w * ((cg - ug) * s + T(3) * cF);
-      } else {
-        Fi = kF * w * (T(3) * cF);
-      }
-      fo = fs[i] + (w * (pt + rho * s) - fs[i]) * om + Fi;
+      T Fi = T(0);
+      if constexpr (RCV) Fi = kF * w * (-ug * s);
+      fo = fs[0] + (w * (pt + rho * s) - fs[0]) * om + Fi;
     }
-    plane(a.f_out, a.pitch, i)[n] = fo;
+    a.fout[0][n] = fo;
     if constexpr (!EQ) {
 #pragma unroll
       for (int f = 0; f < NF; f++) {
         const T Cf = cv[1 + f];
-        const T geq = i == 0 ? Cf - (T(1) - w) * mu[f] + w * Cf * s : w * (mu[f] + Cf * s);
+        const T geq = Cf - (T(1) - w) * mu[f] + w * Cf * s;
         T *go = a.g_out + (long long)f * Q * a.pitch;
-        plane(go, a.pitch, i)[n] = gs[f][i] + (geq - gs[f][i]) * a.omg;
+        plane(go, a.pitch, 0)[n] = gs[f][0] + (geq - gs[f][0]) * a.omg;
+      }
+    }
+  }
+  // opposite directions (i, i + 1) as pairs: s = even +- odd (c_{i+1} = -c_i),
+  // and every later operation once for both (dsm_pair.cuh)
+  const Pr<T> pm = pr(T(1), T(-1)), m1 = pr(T(-1), T(-1));
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int ib = i + 1;
+    const T w = T(L::w(i));
+    // c_i . v over the components c_i has (cdot: no products by zero)
+    const T cu = cdot<L>(i, u[0], u[1], u[2]);
+    const T even = T(4.5) * cu * cu - T(1.5) * uu;
+    const T odd = T(3) * cu;
+    const Pr<T> s2 = pr_fma(pr(odd, odd), pm, pr(even, even));
+    T fp = w, fm = w;
+    if (!solid_x) {
+      const T cF3 = T(3) * cdot<L>(i, F[0], F[1], F[2]);
+      const T kw = kF * w;
+      Pr<T> F2;
+      if constexpr (RCV) {
+        const T cg = cdot<L>(i, gR[0], gR[1], gR[2]);
+        F2 = pr_mul(pr(kw, kw), pr_fma(pr(cg - ug, -cg - ug), s2, pr(cF3, -cF3)));
+      } else {
+        const T Fp = kw * cF3;
+        F2 = pr(Fp, -Fp);
+      }
+      const Pr<T> f2 = pr(fs[i], fs[ib]);
+      const Pr<T> e = pr_mul(pr(w, w), pr_fma(pr(rho, rho), s2, pr(pt, pt)));
+      const Pr<T> o = pr_add(pr_fma(pr_fma(f2, m1, e), pr(om, om), f2), F2);
+      fp = o.a;
+      fm = o.b;
+    }
+    a.fout[i][n] = fp;
+    a.fout[ib][n] = fm;
+    if constexpr (!EQ) {
+#pragma unroll
+      for (int f = 0; f < NF; f++) {
+        const T Cf = cv[1 + f];
+        const Pr<T> geq = pr_mul(pr(w, w), pr_fma(pr(Cf, Cf), s2, pr(mu[f], mu[f])));
+        const Pr<T> g2 = pr(gs[f][i], gs[f][ib]);
+        const Pr<T> go = pr_fma(pr_fma(g2, m1, geq), pr(a.omg, a.omg), g2);
+        T *gb = a.g_out + (long long)f * Q * a.pitch;
+        plane(gb, a.pitch, i)[n] = go.a;
+        plane(gb, a.pitch, ib)[n] = go.b;
       }
     }
   }
@@ -658,6 +757,7 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
     a.om[f] = T(1.0 / h->tau[f]);
   }
   a.omg = T(1.0 / h->prm.tau_g);
+  a.irho = T(1.0 / h->rho[h->nf]);
   for (int f = 0; f < h->nf; f++) a.rc |= h->rho[f] != h->rho[h->nf];
   a.a2 = T(h->prm.alpha * h->prm.alpha);
   a.alpha_s = T(h->prm.alpha_s > 0.0 ? h->prm.alpha_s : h->prm.alpha);
@@ -666,6 +766,10 @@ MLArgs<T> ml_args(const dsm_mlattice *h, int src) {
   a.f_in = (const T *)h->f[src];
   a.g_in = (const T *)h->g[src];
   a.f_out = (T *)h->f[src ^ 1];
+  for (int j = 0; j < h->q; j++) {
+    a.fin[j] = a.f_in + (long long)j * a.pitch;
+    a.fout[j] = a.f_out + (long long)j * a.pitch;
+  }
   a.g_out = (T *)h->g[src ^ 1];
   a.C = (T *)h->C[src ^ 1];
   a.Cprev = (const T *)h->C[src];
