@@ -707,19 +707,25 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
     Fv[2] += C * K_.body[2];
   }
   if (!solid_x) {
-    T m0 = T(0), m1[3] = {T(0), T(0), T(0)};
+    // opposite directions (j, j + 1) as one pair: their sum and difference in
+    // one operation, the sum into the density, the difference into the
+    // momentum (c_{j+1} = -c_j)
+    T m0 = f[0], m1[3] = {T(0), T(0), T(0)};
+    const Pr<T> pmj = pr(T(1), T(-1));
 #pragma unroll
-    for (int j = 0; j < Q; j++) {
-      m0 += f[j];
-      if (L::cx(j)) m1[0] += T(L::cx(j)) * f[j];
-      if (L::cy(j)) m1[1] += T(L::cy(j)) * f[j];
-      if (L::cz(j)) m1[2] += T(L::cz(j)) * f[j];
+    for (int j = 1; j < Q; j += 2) {
+      const Pr<T> sd = pr_fma(pr(f[j + 1], f[j + 1]), pmj, pr(f[j], f[j]));
+      m0 += sd.a;
+      if (L::cx(j)) m1[0] += T(L::cx(j)) * sd.b;
+      if (L::cy(j)) m1[1] += T(L::cy(j)) * sd.b;
+      if (L::cz(j)) m1[2] += T(L::cz(j)) * sd.b;
     }
     const T ir = (STAGE == 1) ? T(1) : (RC ? T(1) / rho : K_.inv_rho3);
     u[0] = (m1[0] + T(0.5) * Fv[0]) * ir;
     u[1] = (m1[1] + T(0.5) * Fv[1]) * ir;
     u[2] = (m1[2] + T(0.5) * Fv[2]) * ir;
-    pt = m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]);
+    // (G[rho] = 0 without a density contrast)
+    pt = RC ? m0 + T(0.5) * (u[0] * gR[0] + u[1] * gR[1] + u[2] * gR[2]) : m0;
   }
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 
