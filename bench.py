@@ -312,7 +312,8 @@ def run_gpu(args, rank, world):
         shape = (4096, 4096)
     case = make_case(shape, lattice)
     faces = tuple(args.faces.split(",")) if args.faces else None
-    params = P.make_params(lattice, shape, "f32", theta_deg=case.theta_deg, g12=case.g12,
+    store = args.storage
+    params = P.make_params(lattice, shape, store, theta_deg=case.theta_deg, g12=case.g12,
                            g23=case.g23, alpha_s=case.alpha_s, rho3=args.rho3, tau3=args.tau3,
                            faces=faces)
     lat = P.Lattice(params, device=dev)
@@ -342,9 +343,9 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     g_eq = lat.g_implicit
     if single:
-        k2_b, k1_b = lu_bytes_single("f32"), 0
+        k2_b, k1_b = lu_bytes_single(store), 0
     else:
-        k2_b, k1_b = lu_bytes(lattice, "f32", g_eq)
+        k2_b, k1_b = lu_bytes(lattice, store, g_eq)
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -400,7 +401,7 @@ def run_gpu(args, rank, world):
     peak, peak_kind = _peaks()
     achieved = k2_b * n / t_k2 / 1e9
     default = (shape == SHAPE and lattice == "D3Q19" and args.rho3 == 1.0 and args.tau3 == 1.0
-               and not faces)
+               and not faces and store == "f32")
     if single:
         traffic = measured_traffic("zstep_kernel_d3q19_f32") if default else None
     else:
@@ -412,7 +413,8 @@ def run_gpu(args, rank, world):
         cb = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
         out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32" if store == "f32" else store + "-storage/f32",
                "data": "synthetic",
                "config": gpu_config(shape, world,
                                     "g_eq (tau_g = 1): A, u per node" if g_eq else "populations",
@@ -1228,6 +1230,8 @@ def main():
                     help="fluid components of --workload multi")
     ap.add_argument("--zrun", type=int, default=0,
                     help="z planes per block of the one-pass step (0: automatic)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="population storage of the default workload (arithmetic in FP32)")
     ap.add_argument("--g-storage", default="auto", choices=["auto", "populations"],
                     help="g held as g_eq when tau_g = 1 (auto) or as populations")
     ap.add_argument("--shape", default=",".join(map(str, SHAPE)),
