@@ -45,7 +45,8 @@ typedef enum {
   DSM_E_NONFINITE = 4,   /* a NaN/Inf appeared in the populations */
   DSM_E_TIMEOUT = 5,     /* a bounded device wait ran out */
   DSM_E_STATE = 6,       /* call out of order, or handle latched in error */
-  DSM_E_UNSUPPORTED = 7  /* a valid request the library does not implement */
+  DSM_E_UNSUPPORTED = 7, /* a valid request the library does not implement */
+  DSM_E_BOUNDS = 8       /* (checked build) a kernel index left its buffer */
 } dsm_status;
 
 typedef enum { DSM_D2Q9 = 0, DSM_D3Q19 = 1 } dsm_lattice_kind;
@@ -119,6 +120,16 @@ enum {
 
 /* Status text (static storage; never NULL). */
 const char *dsm_status_string(dsm_status s);
+
+/* 1 in the checked build (libdsm_checked.so, compiled with -DDSM_CHECKED), 0
+ * in the normal one.  In the checked build every neighbour, pull, store and
+ * padded-plane index that the lattice Boltzmann kernels form is tested against
+ * its buffer; one outside it latches DSM_E_BOUNDS in the lattice's error word
+ * and the access goes to element 0 instead, so the kernel never touches
+ * memory outside the buffer.  dsm_get_observables and dsm_ml_check then
+ * return DSM_E_BOUNDS, and the handle stays latched as for DSM_E_TIMEOUT.  The
+ * checked build runs the same arithmetic; it is slower and exists to test. */
+int dsm_checked_build(void);
 
 /* Velocity set and weights of a lattice as this library orders them:
  * c_out[3*i + a], w_out[i] for i < *q (q_out receives 9 or 19).  D2Q9 follows
@@ -219,7 +230,9 @@ dsm_status dsm_set_step_form(dsm_lattice *h, int form, int zrun);
 dsm_status dsm_step_info(dsm_lattice *h, int *single_pass, int *zrun);
 
 /* Observables of the current state; synchronises the stream.  Returns
- * DSM_E_NONFINITE (and sets out->nonfinite) when the state holds a NaN/Inf. */
+ * DSM_E_NONFINITE (and sets out->nonfinite) when the state holds a NaN/Inf,
+ * DSM_E_TIMEOUT after a timed-out device wait, DSM_E_BOUNDS after an index
+ * fault caught by the checked build (dsm_checked_build). */
 dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out);
 
 /* One macroscopic field (DSM_FIELD_*) into d_dst (nx*ny*nz reals). */
@@ -500,7 +513,8 @@ dsm_status dsm_destroy(dsm_lattice *h);
  * nx*ny*nz rows (held as g_eq: rebuilt from (A_f, C_f, u)).  The fused pass
  * latches a non-finite state in the workspace; dsm_ml_check synchronises the
  * stream and returns DSM_E_NONFINITE once it is latched, DSM_E_TIMEOUT for a
- * timed-out wait of the one-pass step (dsm_ml_set_fluids clears both). */
+ * timed-out wait of the one-pass step, DSM_E_BOUNDS for an index fault caught
+ * by the checked build (dsm_ml_set_fluids clears all three). */
 typedef struct dsm_mlattice dsm_mlattice;
 dsm_status dsm_ml_workspace_bytes(const dsm_params *p, int nfluid, size_t *bytes);
 dsm_status dsm_ml_create(const dsm_params *p, int nfluid, const double *kappa,

@@ -11,10 +11,12 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdsm.so")
+# DSM_LIB=checked loads the bounds-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(HERE, "libdsm_checked.so" if os.environ.get("DSM_LIB") == "checked"
+                        else "libdsm.so")
 
 DSM_OK, DSM_E_INVAL, DSM_E_WORKSPACE, DSM_E_CUDA, DSM_E_NONFINITE, DSM_E_TIMEOUT, \
-    DSM_E_STATE, DSM_E_UNSUPPORTED = range(8)
+    DSM_E_STATE, DSM_E_UNSUPPORTED, DSM_E_BOUNDS = range(9)
 DSM_D2Q9, DSM_D3Q19 = 0, 1
 DSM_FACE_PERIODIC, DSM_FACE_MIRROR, DSM_FACE_WALL = 0, 1, 2
 DSM_F64, DSM_F32, DSM_BF16_STORE, DSM_F16_STORE = 0, 1, 2, 3
@@ -24,7 +26,7 @@ DSM_STEP_AUTO, DSM_STEP_TWO_PASS = 0, 1
  DSM_FIELD_UZ, DSM_FIELD_PT, DSM_FIELD_RHO, DSM_FIELD_TAU) = range(10)
 
 EXPORTED = (
-    "dsm_status_string", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
+    "dsm_status_string", "dsm_checked_build", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
     "dsm_set_solid", "dsm_relax_solid", "dsm_solid_region", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
     "dsm_step_collide", "dsm_set_body_force", "dsm_set_step_form", "dsm_step_info", "dsm_get_observables",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
@@ -77,13 +79,15 @@ def load():
         return _lib
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
-                          "paper_2504_19941_gb300.build.build() (nvcc, sm_103a)")
+                          "paper_2504_19941_gb300.build.build() (nvcc, sm_103a; "
+                          "checked=True for the checked library)")
     lib = C.CDLL(LIB_PATH)
     vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.c_void_p
     P = C.POINTER(dsm_params)
     st = C.c_int
     sig = {
         "dsm_status_string": (C.c_char_p, [st]),
+        "dsm_checked_build": (C.c_int, []),
         "dsm_lattice_table": (st, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]),
         "dsm_kappa": (st, [P, dp]),
         "dsm_workspace_bytes": (st, [P, C.POINTER(C.c_size_t)]),
@@ -158,6 +162,11 @@ def load():
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().dsm_checked_build())
 
 
 def status_string(s: int) -> str:

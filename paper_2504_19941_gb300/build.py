@@ -3,6 +3,11 @@
 Each .cu translation unit compiles in parallel into csrc/_build/, then nvcc
 links them into paper_2504_19941_gb300/libdsm.so (static CUDA runtime, no
 torch dependency).  Rebuilds only what changed.
+
+``build(checked=True)`` makes the bounds-checked library instead
+(libdsm_checked.so from csrc/_build_checked/, compiled with -DDSM_CHECKED):
+the same kernels with every index they form tested against its buffer.  The
+loader takes it when the environment sets DSM_LIB=checked.
 """
 from __future__ import annotations
 
@@ -16,6 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libdsm.so")
+BUILD_CHECKED = os.path.join(CSRC, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libdsm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-O3"]
@@ -42,8 +49,8 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.exists(d) and os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, bdir: str, extra, verbose: bool) -> str:
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, _deps(src)):
         cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
         if verbose:
@@ -53,25 +60,30 @@ def _compile(src: str, extra, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=(), force: bool = False) -> str:
-    """Compile every CUDA source of the library and link libdsm.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), force: bool = False, checked: bool = False) -> str:
+    """Compile every CUDA source of the library and link libdsm.so
+    (libdsm_checked.so with ``checked``)."""
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = list(extra) + (["-DDSM_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if force:
-        for o in glob.glob(os.path.join(BUILD, "*.o")):
+        for o in glob.glob(os.path.join(bdir, "*.o")):
             os.remove(o)
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra), verbose), srcs))
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, bdir, extra, verbose), srcs))
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(verbose=True, extra=sys.argv[1:]))
+    args = sys.argv[1:]
+    chk = "--checked" in args
+    print(build(verbose=True, extra=[a for a in args if a != "--checked"], checked=chk))

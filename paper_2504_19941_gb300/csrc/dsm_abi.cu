@@ -321,6 +321,14 @@ __global__ void __launch_bounds__(256) solid_region_kernel(const T *c1, unsigned
 
 extern "C" {
 
+int dsm_checked_build(void) {
+#ifdef DSM_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 const char *dsm_status_string(dsm_status s) {
   switch (s) {
     case DSM_OK: return "ok";
@@ -331,6 +339,7 @@ const char *dsm_status_string(dsm_status s) {
     case DSM_E_TIMEOUT: return "device wait timed out";
     case DSM_E_STATE: return "call out of order or handle latched in error";
     case DSM_E_UNSUPPORTED: return "unsupported";
+    case DSM_E_BOUNDS: return "index out of bounds (checked build)";
   }
   return "unknown status";
 }
@@ -629,6 +638,10 @@ dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out) {
   if (word & ERR_TIMEOUT) {
     h->latched = true;
     return DSM_E_TIMEOUT;
+  }
+  if (word & ERR_BOUNDS) {
+    h->latched = true;
+    return DSM_E_BOUNDS;
   }
   if (out->nonfinite) {
     h->latched = true;

@@ -186,7 +186,32 @@ struct LBArgs {
 };
 
 // Error bits latched in the workspace error word.
-enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
+
+// Index guard of the DSM_CHECKED build (compiled with -DDSM_CHECKED, the
+// library libdsm_checked.so): every neighbour, pull, store and padded index
+// the LB kernels compute passes through chk().  One outside [0, n) latches
+// ERR_BOUNDS in the lattice's error word and is replaced by 0, so the access
+// stays inside its buffer: the kernel reports the fault instead of making it.
+// In the normal build chk() is the identity.  (Host-callable so that the
+// index arithmetic can be checked on the CPU.)
+template <class I>
+__host__ __device__ __forceinline__ I chk(int *err, I i, long long n) {
+#ifdef DSM_CHECKED
+  if (i < 0 || (long long)i >= n) {
+#ifdef __CUDA_ARCH__
+    if (err) atomicOr(err, ERR_BOUNDS);
+#else
+    if (err) *err |= ERR_BOUNDS;
+#endif
+    return I(0);
+  }
+#else
+  (void)err;
+  (void)n;
+#endif
+  return i;
+}
 
 // Type-erased launch arguments: the ABI layer fills these and calls through an
 // LBTable, so that each precision compiles in its own translation unit.

@@ -37,10 +37,25 @@ __device__ __forceinline__ T bwell(T c) {
   return c * (T(1) - c) * (T(1) - T(2) * c);
 }
 
-// Periodic neighbourhood of node (x, y, z): linear index of x + c.
+// Periodic neighbourhood of node (x, y, z): linear index of x + c.  (Host-
+// callable: the CPU tests check its indices against the wrapped coordinates.)
 struct Hood {
   int ox[3], oy[3], oz[3];
-  __device__ __forceinline__ void init(int x, int y, int z, int nx, int ny, int nz) {
+#ifdef DSM_CHECKED
+  // checked build: the neighbour indices are guarded against the lattice
+  // (chk, dsm_common.cuh); guard() names the error word to latch
+  int *err = nullptr;
+  long long lim = 0;
+  __host__ __device__ __forceinline__ void guard(int *e) { err = e; }
+  __host__ __device__ __forceinline__ int g(int v) const { return chk(err, v, lim); }
+#else
+  __host__ __device__ __forceinline__ void guard(int *) {}
+  __host__ __device__ __forceinline__ int g(int v) const { return v; }
+#endif
+  __host__ __device__ __forceinline__ void init(int x, int y, int z, int nx, int ny, int nz) {
+#ifdef DSM_CHECKED
+    lim = (long long)nx * ny * nz;
+#endif
     ox[0] = x == 0 ? nx - 1 : x - 1;
     ox[1] = x;
     ox[2] = x + 1 == nx ? 0 : x + 1;
@@ -57,8 +72,8 @@ struct Hood {
   // The same with the lattice's faces: beyond a mirror or wall face the
   // stencils see the edge node itself, the image of the node across the plane
   // half a node out (zero normal gradient).
-  __device__ __forceinline__ void init_faces(int x, int y, int z, int nx, int ny, int nz,
-                                             const int (&face)[6]) {
+  __host__ __device__ __forceinline__ void init_faces(int x, int y, int z, int nx, int ny,
+                                                      int nz, const int (&face)[6]) {
     init(x, y, z, nx, ny, nz);
     if (x == 0 && face[0]) ox[0] = 0;
     if (x + 1 == nx && face[1]) ox[2] = nx - 1;
@@ -68,20 +83,20 @@ struct Hood {
     if (z + 1 == nz && face[5]) oz[2] = (nz - 1) * nx * ny;
   }
   template <class L>
-  __device__ __forceinline__ int plus(int i) const {  // x + c_i
-    return ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1];
+  __host__ __device__ __forceinline__ int plus(int i) const {  // x + c_i
+    return g(ox[L::cx(i) + 1] + oy[L::cy(i) + 1] + oz[L::cz(i) + 1]);
   }
   template <class L>
-  __device__ __forceinline__ int minus(int i) const {  // x - c_i
-    return ox[1 - L::cx(i)] + oy[1 - L::cy(i)] + oz[1 - L::cz(i)];
+  __host__ __device__ __forceinline__ int minus(int i) const {  // x - c_i
+    return g(ox[1 - L::cx(i)] + oy[1 - L::cy(i)] + oz[1 - L::cz(i)]);
   }
   // x + c_i for a direction known only at run time (selects without indexing
   // the offset arrays dynamically, so they stay in registers)
   template <class L>
-  __device__ __forceinline__ int plus_rt(int i) const {
+  __host__ __device__ __forceinline__ int plus_rt(int i) const {
     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    return (cx < 0 ? ox[0] : cx > 0 ? ox[2] : ox[1]) + (cy < 0 ? oy[0] : cy > 0 ? oy[2] : oy[1]) +
-           (cz < 0 ? oz[0] : cz > 0 ? oz[2] : oz[1]);
+    return g((cx < 0 ? ox[0] : cx > 0 ? ox[2] : ox[1]) + (cy < 0 ? oy[0] : cy > 0 ? oy[2] : oy[1]) +
+             (cz < 0 ? oz[0] : cz > 0 ? oz[2] : oz[1]));
   }
 };
 
@@ -186,7 +201,8 @@ __device__ __forceinline__ void moments_body(const LBArgs<T, S> &a, int x, int y
   Hood h;
   if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   // the moving populations are small next to the rest one (g_0 ~ C): summing
   // them first and adding g_0 last rounds once at the scale of C instead of
   // Q - 1 times, which keeps FP32 from drifting the liquid mass
@@ -265,7 +281,8 @@ __device__ __forceinline__ void moments_eq_body(const LBArgs<T, S> &a, int x, in
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   const T *pA = a.Mp[0], *pux = a.Mp[1], *puy = a.Mp[2], *puz = a.Mp[3];
   T Ay[Q], Cy[Q], uy[Q][3];
 #pragma unroll
@@ -462,7 +479,8 @@ __device__ __forceinline__ void node_body(const LBArgs<T, S> &a, int x, int y, i
   Hood h;
   if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   const ConstT<T> &K_ = a.c;
 
   // ---- every load of the node, issued up front ------------------------------
@@ -1002,7 +1020,8 @@ __global__ void __launch_bounds__(256) init_kernel(LBArgs<T, S> a, const T *cfie
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.p.face);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   const ConstT<T> &K_ = a.c;
   const T C = cfield[n];
   const T c1 = (STAGE == 2) ? a.C1[n] : T(0);

@@ -102,6 +102,7 @@ struct MLZIO {
     const long long gx = x < 2 ? a.nx : (x >= a.nx - 2 ? -a.nx : 0);
     const long long gy = (long long)(y < 2 ? a.ny : (y >= a.ny - 2 ? -a.ny : 0)) * a.nxp;
     auto put1 = [&](long long p) {
+      p = chk(a.err, p, P);  // (checked build)
       *reinterpret_cast<Quad<T> *>(a.Qz + 4 * p) = m;
       a.Uz[p] = u[2];
 #pragma unroll

@@ -61,7 +61,7 @@ struct MLArgs {
   const T *C1;
   T *out;                // fields mode: one plane
   int field, index;
-  int *err;              // latched error word (bits ERR_NONFINITE, ERR_TIMEOUT)
+  int *err;              // latched error word (bits ERR_NONFINITE, ERR_TIMEOUT, ERR_BOUNDS)
   // single-pass step (dsm_mlz.cuh): the padded output buffers, their widths
   T *Qz, *Uz, *Pz;
   int nxp, nyp;
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) ml_moments_kernel(MLArgs<T> a) {
   Hood h;
   if constexpr (FC) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   const bool edge = FC && on_wall_face(a.face, x, y, z, a.nx, a.ny, a.nz);
 #pragma unroll
   for (int f = 0; f < NF; f++) {
@@ -122,7 +123,8 @@ __global__ void __launch_bounds__(256) ml_moments_eq_kernel(MLArgs<T> a) {
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   T uy[Q][3];
 #pragma unroll
   for (int i = 0; i < Q; i++) {
@@ -217,7 +219,8 @@ __device__ __forceinline__ void ml_node_body(const MLArgs<T> &a, int x, int y, i
   constexpr bool RTF = FC || (EQ && !IO::kZ);
   if constexpr (RTF) h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
   else h.init(x, y, z, a.nx, a.ny, a.nz);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
 
   // ---- the neighbourhood: C1 and the free fluids, stencils of every component
   T cv[NC], lap[NC], gC[NF][3], gR[3] = {T(0), T(0), T(0)}, gc1[3] = {T(0), T(0), T(0)};
@@ -585,7 +588,8 @@ __global__ void __launch_bounds__(256) ml_init_kernel(MLArgs<T> a) {
   if (x >= a.nx || y >= a.ny || z >= a.nz) return;
   Hood h;
   h.init_faces(x, y, z, a.nx, a.ny, a.nz, a.face);
-  const int n = h.ox[1] + h.oy[1] + h.oz[1];
+  h.guard(a.err);
+  const int n = h.g(h.ox[1] + h.oy[1] + h.oz[1]);
   T cv[NC], lap[NC];
   cv[0] = a.C1[n];
   T last = T(1) - cv[0];
@@ -1232,6 +1236,7 @@ dsm_status dsm_ml_check(dsm_mlattice *h) {
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return DSM_E_CUDA;
   if (word & ERR_TIMEOUT) return DSM_E_TIMEOUT;
+  if (word & ERR_BOUNDS) return DSM_E_BOUNDS;
   return (word & ERR_NONFINITE) ? DSM_E_NONFINITE : DSM_OK;
 }
 

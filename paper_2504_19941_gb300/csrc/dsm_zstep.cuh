@@ -167,7 +167,9 @@ struct ZIO {
     const long long q = zpidx(x, y, z, a.nxp, a.nyp);
     const long long gx = x < 2 ? a.nx : (x >= a.nx - 2 ? -a.nx : 0);
     const long long gy = (long long)(y < 2 ? a.ny : (y >= a.ny - 2 ? -a.ny : 0)) * a.nxp;
+    const long long P = (long long)a.nxp * a.nyp * a.nz;  // padded nodes (checked build)
     auto put1 = [&](long long p) {
+      p = chk(a.err, p, P);
       *reinterpret_cast<Quad<T> *>(a.Qz + 4 * p) = m;
       a.Uz[p] = uz;
     };
