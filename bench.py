@@ -408,6 +408,13 @@ def run_gpu(args, rank, world):
         traffic = (measured_traffic("node_kernel_d3q19_f32_geq" if g_eq else "node_kernel_d3q19_f32")
                    if default else None)
     step_achieved = (k2_b + k1_b) * n / (t_max / args.steps) / 1e9
+    # the two secondary fractions of the measurement definitions: DRAM bytes
+    # that ncu measured per lattice update, and B_min, one read and one write
+    # of f and g per node plus a read of C1 (a form that moves less, as the
+    # g_eq form does, is credited for the bytes it avoids)
+    q = 9 if lattice == "D2Q9" else 19
+    b_min = (q * 2 * 2 + ((q - 1) * 2 + 4) * 2 + 4) if store in ("bf16", "f16") else 4 * q * 4 + 4
+    lups_gpu = n * args.steps / t_max  # one GPU's lattice updates per second
 
     if rank == 0:
         cb = cpu_baseline() if world == 1 and not args.no_cpu_baseline else None
@@ -430,7 +437,10 @@ def run_gpu(args, rank, world):
                                        ",density contrast" if args.rho3 != 1.0 else ""),
                             "bytes_per_lu": k2_b, "peak_source": peak_kind,
                             "k2_ms": t_k2 * 1e3, "step_bytes_per_lu": k1_b + k2_b,
-                            "step_achieved": step_achieved, "step_frac": step_achieved / peak},
+                            "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+                            "measured_bytes_per_lu": traffic / n if traffic else None,
+                            "measured_frac": (traffic / n * lups_gpu / 1e9 / peak) if traffic else None,
+                            "b_min_per_lu": b_min, "useful_frac": b_min * lups_gpu / 1e9 / peak},
                "clocks": clk.summary(), "e2e": e2e,
                "gpu_launches": (1 if single else 2) * args.steps,
                "cpu_baseline": cb,
