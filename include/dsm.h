@@ -235,6 +235,28 @@ dsm_status dsm_step_info(dsm_lattice *h, int *single_pass, int *zrun);
  * fault caught by the checked build (dsm_checked_build). */
 dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out);
 
+/* Observables ring: a time series of the observables kept on the device, so
+ * that a long run can be watched without a host synchronisation per sample.
+ * d_ring (device, caller-owned, 8-byte aligned, capacity * DSM_OBS_RECORD
+ * doubles) receives one record after every step of dsm_step whose step count
+ * (dsm_observables.step) is a multiple of `every`.  A record is
+ *   { step, mass_c2, mass_c1, kinetic, max_u, nonfinite nodes }
+ * as dsm_get_observables computes them (the same kernels, bitwise the same
+ * values), written by kernels on the lattice's stream; record k (counted
+ * from this call) sits in slot k % capacity, so the ring keeps the last
+ * `capacity` records.  dsm_observables_ring_count gives the number of records
+ * written so far (host bookkeeping, no synchronisation); read the ring after
+ * synchronising the lattice's stream.  Recording does not change the
+ * trajectory.  A record does not latch errors: dsm_get_observables reports
+ * them.  d_ring NULL or every 0 turns recording off.  Only dsm_step
+ * records: the split step (dsm_step_moments / dsm_step_collide) and
+ * dsm_batch_step do not.  DSM_E_INVAL: capacity < 1, every < 0, d_ring
+ * misaligned. */
+#define DSM_OBS_RECORD 6
+dsm_status dsm_set_observables_ring(dsm_lattice *h, double *d_ring, int capacity,
+                                    long long every);
+dsm_status dsm_observables_ring_count(const dsm_lattice *h, long long *written);
+
 /* One macroscopic field (DSM_FIELD_*) into d_dst (nx*ny*nz reals). */
 dsm_status dsm_get_field(dsm_lattice *h, int field, void *d_dst);
 

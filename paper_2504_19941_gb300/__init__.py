@@ -74,6 +74,7 @@ class Lattice:
         self.nbytes = _lib.dsm_workspace_bytes(params)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         self.h = _lib.dsm_create(params, self.workspace, self.nbytes, self.stream)
+        self.ring = None
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -125,6 +126,39 @@ class Lattice:
 
     def observables(self, check=True) -> dict:
         return _lib.dsm_get_observables(self.h, check)
+
+    RING_FIELDS = ("step", "mass_c2", "mass_c1", "kinetic", "max_u", "nonfinite")
+
+    def set_observables_ring(self, capacity: int, every: int):
+        """Record the observables on the device after every `every`-th step
+        (dsm_set_observables_ring) into a ring of `capacity` records; every=0
+        turns recording off."""
+        import torch
+        if every == 0:
+            self.ring = None
+            _lib.dsm_set_observables_ring(self.h, None, 0, 0)
+            return
+        # written only by the library's kernels on the lattice's stream
+        self.ring = torch.empty((int(capacity), len(self.RING_FIELDS)), dtype=torch.float64,
+                                device=self.device)
+        _lib.dsm_set_observables_ring(self.h, self.ring, capacity, every)
+
+    def observables_ring(self) -> list:
+        """The records the ring still holds, oldest first, as dicts (waits for
+        the lattice's stream)."""
+        written = _lib.dsm_observables_ring_count(self.h)
+        if self.ring is None or written == 0:
+            return []
+        self.stream.synchronize()
+        cap = self.ring.shape[0]
+        rows = self.ring.cpu().numpy()
+        first = max(0, written - cap)
+        out = []
+        for k in range(first, written):
+            r = rows[k % cap]
+            out.append({name: (int(v) if name in ("step", "nonfinite") else float(v))
+                        for name, v in zip(self.RING_FIELDS, r)})
+        return out
 
     def field(self, name: str, out=None):
         import torch

@@ -29,6 +29,7 @@ EXPORTED = (
     "dsm_status_string", "dsm_checked_build", "dsm_lattice_table", "dsm_kappa", "dsm_workspace_bytes", "dsm_create",
     "dsm_set_solid", "dsm_relax_solid", "dsm_solid_region", "dsm_set_fluid", "dsm_step", "dsm_step_moments",
     "dsm_step_collide", "dsm_set_body_force", "dsm_set_step_form", "dsm_step_info", "dsm_get_observables",
+    "dsm_set_observables_ring", "dsm_observables_ring_count",
     "dsm_get_field", "dsm_get_populations", "dsm_set_populations", "dsm_set_g_storage",
     "dsm_get_g_storage", "dsm_state_bytes", "dsm_get_state", "dsm_set_state", "dsm_fe_scratch_bytes",
     "dsm_fe_energy_grad", "dsm_fe_energy_grad_noalloc", "dsm_vec_scratch_bytes", "dsm_vec_dot", "dsm_vec_axpy_dev",
@@ -103,6 +104,8 @@ def load():
         "dsm_set_step_form": (st, [vp, C.c_int, C.c_int]),
         "dsm_step_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "dsm_get_observables": (st, [vp, C.POINTER(dsm_observables)]),
+        "dsm_set_observables_ring": (st, [vp, vp, C.c_int, C.c_longlong]),
+        "dsm_observables_ring_count": (st, [vp, C.POINTER(C.c_longlong)]),
         "dsm_get_field": (st, [vp, C.c_int, vp]),
         "dsm_get_populations": (st, [vp, vp, vp]),
         "dsm_set_populations": (st, [vp, vp, vp]),
@@ -313,6 +316,17 @@ def dsm_get_observables(h: int, check: bool = True) -> dict:
         _check(s, "dsm_get_observables")
     return dict(mass_c2=o.mass_c2, mass_c1=o.mass_c1, kinetic=o.kinetic, max_u=o.max_u,
                 step=o.step, nonfinite=o.nonfinite, status=s)
+
+
+def dsm_set_observables_ring(h: int, ring, capacity: int, every: int):
+    _check(load().dsm_set_observables_ring(h, _ptr(ring), int(capacity), int(every)),
+           "dsm_set_observables_ring")
+
+
+def dsm_observables_ring_count(h: int) -> int:
+    n = C.c_longlong(0)
+    _check(load().dsm_observables_ring_count(h, C.byref(n)), "dsm_observables_ring_count")
+    return n.value
 
 
 def dsm_get_field(h: int, field: int, dst):

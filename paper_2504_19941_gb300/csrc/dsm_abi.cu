@@ -52,6 +52,11 @@ struct dsm_lattice {
   int step_form;   // DSM_STEP_AUTO or DSM_STEP_TWO_PASS
   int zrun;        // planes per block of the single-pass step (0: automatic)
   int zrun_auto;
+  // observables ring (dsm_set_observables_ring): caller-owned device records,
+  // one appended by dsm_step after each step that is a multiple of ring_every
+  double *ring = nullptr;
+  int ring_cap = 0;
+  long long ring_every = 0, ring_count = 0;
 };
 
 namespace {
@@ -310,6 +315,30 @@ __global__ void obs_finalize_kernel(const double *partials, long long nb, double
   if (threadIdx.x < OBS_K) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// One observables record (step, then the OBS_K values) into the ring.
+__global__ void obs_record_kernel(const double *obs, double *rec, long long step) {
+  if (threadIdx.x == 0) rec[0] = (double)step;
+  if (threadIdx.x < OBS_K) rec[1 + threadIdx.x] = obs[threadIdx.x];
+}
+
+namespace {
+
+// The observables of the current state into h->obs, on the lattice's stream,
+// without synchronising: the moments and observables passes over the
+// canonical state, then the deterministic final reduction.
+cudaError_t obs_launch(dsm_lattice *h) {
+  cudaError_t e = z_unpack(h);
+  if (e != cudaSuccess) return e;
+  LBRaw a = raw_of(h, h->cur);
+  e = h->tab.moments(a, h->stream);
+  if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_OBS, h->stream);
+  if (e != cudaSuccess) return e;
+  obs_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, h->obs_blocks, h->obs);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 // S = {C1 > 1/2} (dsm_solid_region)
 template <class T>
 __global__ void __launch_bounds__(256) solid_region_kernel(const T *c1, unsigned char *mask,
@@ -556,8 +585,40 @@ dsm_status dsm_step(dsm_lattice *h, long long nsteps) {
     h->cur ^= 1;
     h->step++;
     h->g_implicit = h->eq;
+    if (h->ring && h->step % h->ring_every == 0) {
+      // observables record into the ring: device work only, no synchronisation
+      if ((e = obs_launch(h)) != cudaSuccess) return DSM_E_CUDA;
+      double *rec = h->ring + (h->ring_count % h->ring_cap) * DSM_OBS_RECORD;
+      obs_record_kernel<<<1, 32, 0, h->stream>>>(h->obs, rec, h->step);
+      if ((e = cudaGetLastError()) != cudaSuccess) return DSM_E_CUDA;
+      h->ring_count++;
+    }
   }
   h->moments_ready = false;
+  return DSM_OK;
+}
+
+dsm_status dsm_set_observables_ring(dsm_lattice *h, double *d_ring, int capacity,
+                                    long long every) {
+  if (!h) return DSM_E_INVAL;
+  if (!d_ring || every == 0) {
+    h->ring = nullptr;
+    h->ring_cap = 0;
+    h->ring_every = 0;
+    h->ring_count = 0;
+    return DSM_OK;
+  }
+  if (capacity < 1 || every < 0 || ((uintptr_t)d_ring & 7u)) return DSM_E_INVAL;
+  h->ring = d_ring;
+  h->ring_cap = capacity;
+  h->ring_every = every;
+  h->ring_count = 0;
+  return DSM_OK;
+}
+
+dsm_status dsm_observables_ring_count(const dsm_lattice *h, long long *written) {
+  if (!h || !written) return DSM_E_INVAL;
+  *written = h->ring_count;
   return DSM_OK;
 }
 
@@ -616,13 +677,8 @@ dsm_status dsm_step_collide(dsm_lattice *h) {
 dsm_status dsm_get_observables(dsm_lattice *h, dsm_observables *out) {
   if (!h || !out) return DSM_E_INVAL;
   if (!h->has_fluid) return DSM_E_STATE;
-  if (z_unpack(h) != cudaSuccess) return DSM_E_CUDA;
-  LBRaw a = raw_of(h, h->cur);
-  cudaError_t e = h->tab.moments(a, h->stream);
-  if (e == cudaSuccess) e = h->tab.node(a, 2, MODE_OBS, h->stream);
+  cudaError_t e = obs_launch(h);
   if (e != cudaSuccess) return DSM_E_CUDA;
-  obs_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, h->obs_blocks, h->obs);
-  if ((e = cudaGetLastError()) != cudaSuccess) return DSM_E_CUDA;
   double v[OBS_K];
   e = cudaMemcpyAsync(v, h->obs, sizeof(v), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return DSM_E_CUDA;

@@ -183,6 +183,9 @@ def test_null_arguments_rejected(lib):
     assert L.dsm_get_observables(None, None) == lib.DSM_E_INVAL
     assert L.dsm_batch_step(None, 1, None, None, 0) == lib.DSM_E_INVAL
     assert L.dsm_batch_scratch_bytes(None, 1, None) == lib.DSM_E_INVAL
+    assert L.dsm_set_observables_ring(None, None, 0, 0) == lib.DSM_E_INVAL
+    assert L.dsm_observables_ring_count(None, None) == lib.DSM_E_INVAL
+    assert L.dsm_checked_build() == (1 if lib.LIB_PATH.endswith("_checked.so") else 0)
 
 
 def test_vector_and_minimiser_arguments_rejected(lib):
