@@ -57,6 +57,18 @@ def make_params(lattice: str, shape, precision: str = "f32", *, theta_deg=None, 
     return p
 
 
+def ring_records(rows, written: int, fields) -> list:
+    """The records a ring of len(rows) slots holds after `written` appends
+    (record k in slot k % len(rows)), oldest first, as dicts of `fields`."""
+    cap = len(rows)
+    out = []
+    for k in range(max(0, written - cap), written):
+        r = rows[k % cap]
+        out.append({name: (int(v) if name in ("step", "nonfinite") else float(v))
+                    for name, v in zip(fields, r)})
+    return out
+
+
 class Lattice:
     """One lattice on the device: a torch workspace tensor plus a libdsm handle.
 
@@ -150,15 +162,7 @@ class Lattice:
         if self.ring is None or written == 0:
             return []
         self.stream.synchronize()
-        cap = self.ring.shape[0]
-        rows = self.ring.cpu().numpy()
-        first = max(0, written - cap)
-        out = []
-        for k in range(first, written):
-            r = rows[k % cap]
-            out.append({name: (int(v) if name in ("step", "nonfinite") else float(v))
-                        for name, v in zip(self.RING_FIELDS, r)})
-        return out
+        return ring_records(self.ring.cpu().numpy(), written, self.RING_FIELDS)
 
     def field(self, name: str, out=None):
         import torch

@@ -308,3 +308,21 @@ def test_tensor_arguments_are_checked_before_any_launch():
     with pytest.raises(ValueError, match="CUDA device"):
         L.cuda_device("cpu")
     assert L.cuda_device("cuda:1") == torch.device("cuda", 1)
+
+
+def test_ring_records_order():
+    # host side of the observables ring: record k sits in slot k % capacity
+    import numpy as np
+    from paper_2504_19941_gb300 import ring_records
+    fields = ("step", "mass_c2", "mass_c1", "kinetic", "max_u", "nonfinite")
+    cap = 4
+    rows = np.zeros((cap, 6))
+    for k in range(7):  # steps 10 .. 70, the last four kept
+        rows[k % cap] = (10 * (k + 1), k + 0.5, 0, 0, 0, 0)
+    got = ring_records(rows, 7, fields)
+    assert [r["step"] for r in got] == [40, 50, 60, 70]
+    assert [r["mass_c2"] for r in got] == [3.5, 4.5, 5.5, 6.5]
+    fresh = np.zeros((cap, 6))
+    fresh[0, 0], fresh[1, 0] = 10, 20  # two appends: not yet wrapped
+    assert [r["step"] for r in ring_records(fresh, 2, fields)] == [10, 20]
+    assert ring_records(rows, 0, fields) == []
