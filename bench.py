@@ -412,8 +412,7 @@ def run_gpu(args, rank, world):
     # that ncu measured per lattice update, and B_min, one read and one write
     # of f and g per node plus a read of C1 (a form that moves less, as the
     # g_eq form does, is credited for the bytes it avoids)
-    q = 9 if lattice == "D2Q9" else 19
-    b_min = (q * 2 * 2 + ((q - 1) * 2 + 4) * 2 + 4) if store in ("bf16", "f16") else 4 * q * 4 + 4
+    b_min = lu_bytes(lattice, store, False)[0]  # the population form's fused-pass bytes
     lups_gpu = n * args.steps / t_max  # one GPU's lattice updates per second
 
     if rank == 0:
