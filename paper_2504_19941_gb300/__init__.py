@@ -293,8 +293,10 @@ class MultiLattice:
         return out
 
     def status(self) -> int:
-        """0, or the status latched on the device (DSM_E_NONFINITE, or
-        DSM_E_TIMEOUT when a staged plane of the one-pass step never arrived)."""
+        """0, or the status latched on the device (DSM_E_NONFINITE;
+        DSM_E_TIMEOUT when a staged plane of the one-pass step never arrived;
+        DSM_E_BOUNDS when the checked library caught an index outside its
+        buffer)."""
         return _lib.dsm_ml_check(self.h, check=False)
 
     def populations(self):
