@@ -326,3 +326,19 @@ def test_ring_records_order():
     fresh[0, 0], fresh[1, 0] = 10, 20  # two appends: not yet wrapped
     assert [r["step"] for r in ring_records(fresh, 2, fields)] == [10, 20]
     assert ring_records(rows, 0, fields) == []
+
+
+def test_status_codes_match_the_header(lib):
+    # the binding's status constants are the header's enum values
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "dsm.h")).read()
+    body = hdr[hdr.index("DSM_OK = 0"):]
+    body = body[:body.index("} dsm_status;")]
+    codes = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"(DSM_\w+)\s*=\s*(\d+)", body))
+    assert codes["DSM_OK"] == 0 and len(codes) == 9
+    for name, value in codes.items():
+        assert getattr(lib, name) == value, name
+        if name != "DSM_OK":
+            assert lib.status_string(value) not in ("unknown status", "libdsm not loaded"), name
